@@ -1,0 +1,188 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the benchmark.
+
+This module only draws numbers and lays out input fields.  It holds none of the
+stencil or codec arithmetic, so the CPU oracle and the CUDA path can both take
+their inputs from here without sharing any of the method.
+
+Random numbers come from a counter-based generator: SplitMix64 (Steele, Lea and
+Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014), applied
+to ``key(seed) + index``.  Uniform floats keep the top 24 bits of the 64-bit
+output, so every value is exactly representable in FP32 and the same field is
+obtained on any machine.
+
+Workloads stand in for the paper's acoustic dataset (Table 1: four datasets of
+(1152+2*4)^3 doubles), which is not available: a layered velocity model with
+noise and a Ricker point source for the 25-point wave stencil, and a noisy
+field with a discrete sine mode for the 7-point heat stencil.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function of a uint64 counter array (wrapping arithmetic)."""
+    with np.errstate(over="ignore"):
+        z = (x.astype(np.uint64) + _GOLDEN)
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def _key(seed: int, stream: int) -> np.uint64:
+    with np.errstate(over="ignore"):
+        k = splitmix64(np.array([np.uint64(seed) * np.uint64(1_000_003) + np.uint64(stream)],
+                                dtype=np.uint64))[0]
+    return k
+
+
+def uniform01(seed: int, n: int, stream: int = 0, offset: int = 0) -> np.ndarray:
+    """n floats in [0, 1), each the top 24 bits of SplitMix64(key + offset + i) over 2^24.
+
+    Counter-based: ``uniform01(s, n, offset=o)[i] == uniform01(s, o + n)[o + i]``.
+    """
+    key = _key(seed, stream)
+    with np.errstate(over="ignore"):
+        ctr = key + np.arange(offset, offset + n, dtype=np.uint64)
+    bits = splitmix64(ctr) >> np.uint64(40)
+    return (bits.astype(np.float64) * (1.0 / 16777216.0)).astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# 7-point heat workload (128^3, alpha = 0.1)
+# ----------------------------------------------------------------------------
+
+def sine_mode(n: int) -> np.ndarray:
+    """sin(pi i/(n-1)) sin(pi j/(n-1)) sin(pi k/(n-1)) on nodes 0..n-1, FP64, [z][y][x]."""
+    s = np.sin(np.pi * np.arange(n) / (n - 1))
+    s[0] = 0.0
+    s[-1] = 0.0
+    return s[:, None, None] * s[None, :, None] * s[None, None, :]
+
+
+def heat_initial(n: int = 128, seed: int = 1, noise: bool = True, mode: bool = True) -> np.ndarray:
+    """Initial FP32 field of the heat workload: seeded U[0,1) noise plus the sine mode.
+
+    The Dirichlet shell (any index 0 or n-1) is exactly zero; noise is added to
+    interior nodes only.  Layout [z][y][x], x fastest.
+    """
+    f = np.zeros((n, n, n), dtype=np.float64)
+    if mode:
+        f += sine_mode(n)
+    if noise:
+        f += uniform01(seed, n * n * n).astype(np.float64).reshape(n, n, n)
+    f[0, :, :] = f[-1, :, :] = 0.0
+    f[:, 0, :] = f[:, -1, :] = 0.0
+    f[:, :, 0] = f[:, :, -1] = 0.0
+    return f.astype(np.float32)
+
+
+def uniform_field(shape, seed: int) -> np.ndarray:
+    """FP32 U[0,1) field of the given (nz, ny, nx) shape, shell of width 1 zeroed."""
+    nz, ny, nx = shape
+    f = uniform01(seed, nz * ny * nx).reshape(nz, ny, nx)
+    f[0] = f[-1] = 0.0
+    f[:, 0] = f[:, -1] = 0.0
+    f[:, :, 0] = f[:, :, -1] = 0.0
+    return f
+
+
+# ----------------------------------------------------------------------------
+# 25-point acoustic wave workload (512^3, dx = 10 m, dt = 0.8 ms)
+# ----------------------------------------------------------------------------
+
+WAVE_DX = 10.0          # m
+WAVE_DT = 0.8e-3        # s; Courant 4725*0.8e-3/10 = 0.378
+WAVE_F0 = 15.0          # Hz, Ricker peak frequency
+WAVE_VMIN = 1500.0      # m/s
+WAVE_VMAX = 4500.0      # m/s
+WAVE_NOISE = 0.05       # +-5 % uniform multiplicative noise
+WAVE_LAYERS = 8
+
+
+def layered_velocity(shape, seed: int = 2, layers: int = WAVE_LAYERS,
+                     vmin: float = WAVE_VMIN, vmax: float = WAVE_VMAX,
+                     noise: float = WAVE_NOISE) -> np.ndarray:
+    """Layered velocity model v[z][y][x] in m/s (FP64).
+
+    ``layers`` layers stacked along z whose inner boundaries are seeded sorted
+    depths; layer velocities rise linearly from vmin to vmax; every voxel is then
+    scaled by (1 + U(-noise, noise)).
+    """
+    nz, ny, nx = shape
+    cuts = np.sort((uniform01(seed, layers - 1, stream=1).astype(np.float64) * nz).astype(np.int64))
+    layer_of_z = np.searchsorted(cuts, np.arange(nz), side="right")
+    vel_layer = vmin + (vmax - vmin) * np.arange(layers) / max(layers - 1, 1)
+    v = np.broadcast_to(vel_layer[layer_of_z][:, None, None], (nz, ny, nx)).astype(np.float64)
+    u = uniform01(seed, nz * ny * nx, stream=2).astype(np.float64).reshape(nz, ny, nx)
+    return v * (1.0 + noise * (2.0 * u - 1.0))
+
+
+def wave_model(shape, seed: int = 2, dt: float = WAVE_DT, dx: float = WAVE_DX) -> np.ndarray:
+    """FP32 model field m = (v dt / dx)^2 of the layered velocity model."""
+    v = layered_velocity(shape, seed)
+    return ((v * dt / dx) ** 2).astype(np.float32)
+
+
+def ricker(nsteps: int, dt: float = WAVE_DT, f0: float = WAVE_F0, t0: float | None = None) -> np.ndarray:
+    """Ricker wavelet samples w[n] = (1 - 2 (pi f0 (t-t0))^2) exp(-(pi f0 (t-t0))^2), t = n dt, FP32."""
+    if t0 is None:
+        t0 = 1.0 / f0
+    t = np.arange(nsteps, dtype=np.float64) * dt
+    a = (math.pi * f0 * (t - t0)) ** 2
+    return ((1.0 - 2.0 * a) * np.exp(-a)).astype(np.float32)
+
+
+def centre(shape):
+    """Grid centre (z, y, x) = (nz/2, ny/2, nx/2) used as the source voxel."""
+    nz, ny, nx = shape
+    return nz // 2, ny // 2, nx // 2
+
+
+# 8th-order central second-derivative weights (Fornberg), for offsets 0..4.
+WAVE_COEF_1D = (-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0)
+
+
+def wave_star_coef() -> np.ndarray:
+    """Coefficients [centre, c1..c4] of the 3D 25-point star: centre = 3 c0 (FP64)."""
+    c = np.array(WAVE_COEF_1D, dtype=np.float64)
+    c[0] *= 3.0
+    return c
+
+
+def heat_star_coef(alpha: float = 0.1) -> np.ndarray:
+    """Coefficients [centre, c1] of u' = u + alpha (sum6 - 6u): [1 - 6 alpha, alpha] (FP64)."""
+    return np.array([1.0 - 6.0 * alpha, alpha], dtype=np.float64)
+
+
+def blocks_field(shape, seed: int, kind: str) -> np.ndarray:
+    """FP32 test fields for the codec: 'noise', 'smooth', 'zero', 'const', 'mixed', 'tiny', 'huge'."""
+    nz, ny, nx = shape
+    n = nz * ny * nx
+    if kind == "zero":
+        return np.zeros(shape, np.float32)
+    if kind == "const":
+        return np.full(shape, 0.7314, np.float32)
+    u = uniform01(seed, n, stream=7).astype(np.float64).reshape(shape)
+    if kind == "noise":
+        return (2.0 * u - 1.0).astype(np.float32)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    smooth = np.sin(0.11 * x + 0.3) * np.cos(0.07 * y - 0.2) * np.sin(0.05 * z + 1.1) * 3.0
+    if kind == "smooth":
+        return smooth.astype(np.float32)
+    if kind == "mixed":
+        # magnitudes spanning many binades plus signs, noise and structure
+        e = np.floor(u * 40.0) - 20.0
+        s = np.where(uniform01(seed, n, stream=8).reshape(shape) < 0.5, -1.0, 1.0)
+        return (s * np.exp2(e) * (1.0 + 0.5 * smooth)).astype(np.float32)
+    if kind == "tiny":
+        return ((2.0 * u - 1.0) * 1e-30).astype(np.float32)
+    if kind == "huge":
+        return ((2.0 * u - 1.0) * 3e38).astype(np.float32)
+    raise ValueError(kind)

@@ -1,0 +1,228 @@
+"""Pins of the reference block codec (oracle/oracle.c, part 2).
+
+The paper integrates a fixed-rate transform codec (Sec. 4.2, Sec. 5: rate 32
+bits per double) without describing it; the oracle follows the published ZFP
+method.  These tests tie every stage to something other than itself:
+exact sizes from the rate, the published 4-point transform matrix, base -2
+digit expansions, lossless and embedded (prefix) bit-plane coding, and a
+per-block error bound derived from the stages.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic
+
+RATES = [1, 2, 4, 8, 12, 16, 20, 24, 32]
+INV_GAIN = 3.75          # L-inf norm of the inverse 4-point transform (published matrix)
+
+
+def test_exact_compressed_size(orc):
+    """Fixed rate: a field of N values at rate R takes exactly N*R/8 bytes."""
+    for shape in [(4, 4, 4), (8, 12, 16), (12, 8, 4)]:
+        f = synthetic.blocks_field(shape, 1, "noise")
+        for rate in RATES:
+            words = orc.encode_field(f, rate)
+            assert words.nbytes == f.size * rate // 8
+
+
+def test_negabinary_is_base_minus_two(orc):
+    rng = np.random.default_rng(0)
+    vals = [0, 1, -1, 2, -2, 3, 2 ** 29 - 1, -(2 ** 29) + 1, 2 ** 30, -(2 ** 30), 123456789, -987654321]
+    vals += [int(x) for x in rng.integers(-(2 ** 31), 2 ** 31, 2000)]
+    for x in vals:
+        u = orc.to_negabinary(x)
+        digits = sum(((u >> i) & 1) * (-2) ** i for i in range(32))
+        # the 32-digit base -2 expansion equals x modulo 2^32
+        assert (digits - x) % (1 << 32) == 0
+        assert orc.from_negabinary(u) == x
+    # injective on a random sample
+    us = {orc.to_negabinary(int(x)) for x in rng.integers(-(2 ** 31), 2 ** 31, 5000)}
+    assert len(us) > 4990
+    # small magnitudes have few significant digits (what makes bit planes compressible)
+    for x in range(-10, 11):
+        assert orc.to_negabinary(x) < 64
+
+
+def test_lift_matches_published_matrix(orc):
+    """Forward 4-point transform = (1/16) [[4,4,4,4],[5,1,-1,-5],[-4,4,4,-4],[-2,6,-6,2]]."""
+    F = np.array([[4, 4, 4, 4], [5, 1, -1, -5], [-4, 4, 4, -4], [-2, 6, -6, 2]]) / 16.0
+    s = 1 << 24
+    for j in range(4):
+        e = np.zeros(4, np.int64)
+        e[j] = s
+        assert np.allclose(orc.fwd_lift4(e) / s, F[:, j], atol=1e-6)
+    Finv = np.linalg.inv(F)
+    for j in range(4):
+        e = np.zeros(4, np.int64)
+        e[j] = s
+        assert np.allclose(orc.inv_lift4(e) / s, Finv[:, j], atol=1e-6)
+    assert abs(np.max(np.sum(np.abs(Finv), axis=1)) - INV_GAIN) < 1e-12
+    # linear data: only the first two coefficients survive (decorrelation)
+    c = orc.fwd_lift4([1000, 2000, 3000, 4000])
+    assert abs(c[2]) <= 1 and abs(c[3]) <= 1
+
+
+def test_xform_range_and_roundtrip(orc):
+    rng = np.random.default_rng(1)
+    worst = 0
+    lim = (1 << 29) - 1
+    for t in range(4000):
+        kind = t % 4
+        if kind == 0:
+            q = rng.integers(-lim, lim + 1, 64)
+        elif kind == 1:
+            q = rng.choice([-lim, lim], 64)
+        elif kind == 2:
+            q = rng.integers(-40, 41, 64)
+        else:
+            q = np.cumsum(rng.integers(-5000, 5000, 64)).clip(-lim, lim)
+        c = orc.fwd_xform(q)
+        assert np.max(np.abs(c.astype(np.int64))) < (1 << 30)
+        r = orc.inv_xform(c)
+        worst = max(worst, int(np.max(np.abs(r.astype(np.int64) - q))))
+    assert not orc.xform_overflowed()
+    assert worst <= 32
+    # the DC of a constant block is the constant, and nothing else survives
+    c = orc.fwd_xform(np.full(64, 777))
+    assert c[0] == 777 and np.all(c[1:] == 0)
+
+
+def test_sequency_order(orc):
+    perm = orc.sequency_order()
+    assert sorted(perm.tolist()) == list(range(64))
+    seq = [(p & 3) + ((p >> 2) & 3) + (p >> 4) for p in perm]
+    assert seq == sorted(seq)
+    assert perm[0] == 0 and perm[-1] == 63
+    assert set(perm[1:4].tolist()) == {1, 4, 16}
+
+
+def test_bitplane_coder_lossless_and_embedded(orc):
+    rng = np.random.default_rng(2)
+    full = 64 * 32 + 64 + 32  # enough for every plane of every coefficient
+    for t in range(300):
+        kind = t % 3
+        if kind == 0:
+            u = rng.integers(0, 2 ** 32, 64, dtype=np.uint64).astype(np.uint32)
+        elif kind == 1:   # decaying magnitudes, as after a decorrelating transform
+            u = (rng.integers(0, 2 ** 20, 64) >> np.minimum(np.arange(64) // 3, 19)).astype(np.uint32)
+        else:
+            u = np.zeros(64, np.uint32)
+            u[rng.integers(0, 64, 3)] = rng.integers(1, 2 ** 31, 3)
+        w = orc.encode_planes(u, full)
+        dec, low = orc.decode_planes(w, full)
+        assert np.array_equal(dec, u)
+        assert low == 0
+        # embedded: a shorter budget codes a prefix of the same bit string
+        b = int(rng.integers(1, 1500))
+        ws = orc.encode_planes(u, b)
+        bits_full = np.unpackbits(w.view(np.uint8), bitorder="little")[:b]
+        bits_short = np.unpackbits(ws.view(np.uint8), bitorder="little")
+        assert np.array_equal(bits_short[:b], bits_full)
+        assert not bits_short[b:].any()
+        # and the truncated decode agrees with the coefficients on every complete plane
+        dec_s, low_s = orc.decode_planes(ws, b)
+        mask = np.uint32(0xFFFFFFFF) << np.uint32(low_s) if low_s < 32 else np.uint32(0)
+        assert np.array_equal(dec_s & mask, u & mask)
+
+
+def test_zero_and_constant_blocks(orc):
+    z = np.zeros(64, np.float32)
+    z[5] = -0.0
+    for rate in RATES:
+        w = orc.encode_block(z, rate)
+        assert not w.any()
+        v, _ = orc.decode_block(w, rate)
+        assert np.all(v == 0.0)
+    for rate in [2, 4, 8, 16]:
+        c = np.full(64, -3.140625, np.float32)
+        v, _ = orc.decode_block(orc.encode_block(c, rate), rate)
+        assert np.array_equal(v, c)
+
+
+def test_block_floating_point(orc):
+    rng = np.random.default_rng(3)
+    for t in range(500):
+        scale = 2.0 ** rng.integers(-90, 100)
+        v = (rng.standard_normal(64) * scale).astype(np.float32)
+        h = orc.block_header(v)
+        emax = h - 127
+        m = np.max(np.abs(v.astype(np.float64)))
+        assert 2.0 ** (emax - 1) <= m < 2.0 ** emax or emax == -95
+        q = orc.quantize(v, emax)
+        assert np.max(np.abs(q.astype(np.int64))) < 2 ** 29
+        back = orc.dequantize(q, emax).astype(np.float64)
+        # truncation toward zero: never larger in magnitude, error below one step
+        assert np.all(np.abs(back) <= np.abs(v.astype(np.float64)))
+        assert np.max(np.abs(back - v)) < 2.0 ** (emax - 29)
+    # values on the quantisation grid are kept exactly
+    v = (np.arange(64) - 31.0).astype(np.float32) * np.float32(2.0 ** -3)
+    emax = orc.block_header(v) - 127
+    assert np.array_equal(orc.dequantize(orc.quantize(v, emax), emax), v)
+    # the exponent clamp: a block below 2^-124 quantises to zero
+    tiny = np.full(64, 2.0 ** -126, np.float32)
+    assert orc.block_header(tiny) - 127 == -95
+    assert not orc.quantize(tiny, -95).any()
+
+
+@pytest.mark.parametrize("kind", ["noise", "smooth", "mixed", "tiny", "huge", "const"])
+def test_error_bound_every_block(orc, kind):
+    """|v' - v| <= (G^3 2^p + 33) 2^(emax-29) + ulp(v')/2 for every value, where p is the
+    lowest completely decoded plane and G = 3.75 the inverse transform gain.
+
+    Coefficient planes >= p are exact, so each coefficient is off by < 2^p; the
+    inverse transform multiplies that by at most G per dimension; lifting
+    round-off adds at most 32 units (round trip, test above) and quantisation
+    truncation one more; the final FP32 rounding adds half an ulp.
+    """
+    shape = (8, 8, 12)
+    f = synthetic.blocks_field(shape, 11, kind)
+    for rate in RATES:
+        words = orc.encode_field(f, rate)
+        g, low = orc.decode_field(words, shape, rate, with_planes=True)
+        fb = f.reshape(2, 4, 2, 4, 3, 4).transpose(0, 2, 4, 1, 3, 5).reshape(-1, 64).astype(np.float64)
+        gb = g.reshape(2, 4, 2, 4, 3, 4).transpose(0, 2, 4, 1, 3, 5).reshape(-1, 64).astype(np.float64)
+        for b in range(fb.shape[0]):
+            h = orc.block_header(fb[b].astype(np.float32))
+            if h == 0:
+                assert np.all(gb[b] == 0)
+                continue
+            unit = 2.0 ** (h - 127 - 29)
+            p = int(low[b])
+            fin = np.isfinite(gb[b])
+            ulp_half = np.where(fin, np.spacing(np.where(fin, np.abs(gb[b]), 0).astype(np.float32)), 0).astype(np.float64) / 2
+            bound = (INV_GAIN ** 3 * 2.0 ** p + 33.0) * unit + ulp_half
+            assert np.all(np.abs(gb[b] - fb[b])[fin] <= bound[fin]), (kind, rate, b)
+            # a value may round past FLT_MAX only where the bound reaches beyond it
+            big = np.float64(np.finfo(np.float32).max)
+            assert np.all(np.abs(fb[b])[~fin] + bound[~fin] >= big), (kind, rate, b)
+
+
+def test_error_falls_with_rate(orc):
+    for kind in ["noise", "smooth"]:
+        f = synthetic.blocks_field((16, 16, 16), 4, kind)
+        errs = []
+        for rate in [4, 8, 12, 16, 24]:
+            g = orc.decode_field(orc.encode_field(f, rate), f.shape, rate)
+            errs.append(np.linalg.norm((g - f).ravel()) / np.linalg.norm(f.ravel()))
+        # strictly better with rate until the FP32 rounding floor is reached
+        assert all(errs[i + 1] < errs[i] or errs[i] < 2e-8 for i in range(len(errs) - 1)), errs
+        assert all(errs[i + 1] <= errs[i] for i in range(len(errs) - 1)), errs
+    # about one more bit of precision per extra bit of rate on noise
+    f = synthetic.blocks_field((16, 16, 16), 4, "noise")
+    e8 = np.linalg.norm(orc.decode_field(orc.encode_field(f, 8), f.shape, 8) - f)
+    e16 = np.linalg.norm(orc.decode_field(orc.encode_field(f, 16), f.shape, 16) - f)
+    assert 2 ** 6 < e8 / e16 < 2 ** 10
+
+
+def test_block_layout_in_field(orc):
+    """Block (bx, by, bz) is at word offset ((bz*(ny/4)+by)*(nx/4)+bx)*2*rate."""
+    shape = (8, 12, 16)
+    f = synthetic.blocks_field(shape, 2, "noise")
+    rate = 8
+    words = orc.encode_field(f, rate)
+    for (bz, by, bx) in [(0, 0, 0), (1, 2, 3), (1, 0, 2), (0, 2, 1)]:
+        blk = f[4 * bz:4 * bz + 4, 4 * by:4 * by + 4, 4 * bx:4 * bx + 4].reshape(64)
+        off = ((bz * 3 + by) * 4 + bx) * 2 * rate
+        assert np.array_equal(words[off:off + 2 * rate], orc.encode_block(blk, rate))
