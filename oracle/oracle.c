@@ -179,15 +179,21 @@ void oracle_dequantize(const int32_t *q, int emax, float *v)
 /* floor(a / 2) for any sign */
 static int64_t fl2(int64_t a) { return (a >= 0) ? a / 2 : -((-a + 1) / 2); }
 
-/* Set when a lifting result leaves int32 (never expected: with three guard
- * bits every result stays below 2^30 in magnitude; the range tests read it). */
+/* The transform is defined in 32-bit two's complement arithmetic: every
+ * intermediate result is reduced modulo 2^32 into [-2^31, 2^31).  Valid data
+ * never wraps (three guard bits keep every value below 2^30 in magnitude);
+ * the flag below records any wrap so the range tests can assert that, and the
+ * rule makes the decoding of arbitrary words well defined.               */
 int oracle_xform_overflow = 0;
 
-static int32_t chk32(int64_t a)
+static int64_t w32(int64_t a)
 {
-    if (a > INT32_MAX || a < INT32_MIN)
+    int64_t r = ((a % 4294967296LL) + 4294967296LL) % 4294967296LL; /* [0, 2^32) */
+    if (r >= 2147483648LL)
+        r -= 4294967296LL;
+    if (r != a)
         oracle_xform_overflow = 1;
-    return (int32_t)a;
+    return r;
 }
 
 /* (3) The method's forward 4-point lifting transform on (a, b, c, d).
@@ -198,24 +204,24 @@ static int32_t chk32(int64_t a)
 static void fwd_lift(int32_t *p, int stride)
 {
     int64_t a = p[0], b = p[stride], c = p[2 * stride], d = p[3 * stride];
-    a = fl2(a + d);     d = d - a;        /* pair (a, d): mean and half difference */
-    c = fl2(c + b);     b = b - c;        /* pair (b, c) */
-    a = fl2(a + c);     c = c - a;        /* means of the means */
-    d = fl2(d + b);     b = b - d;        /* half differences combined */
-    d = d + fl2(b);     b = b - fl2(d);   /* final rotation of the odd pair */
-    p[0] = chk32(a); p[stride] = chk32(b); p[2 * stride] = chk32(c); p[3 * stride] = chk32(d);
+    a = fl2(w32(a + d)); d = w32(d - a);        /* pair (a, d): mean and half difference */
+    c = fl2(w32(c + b)); b = w32(b - c);        /* pair (b, c) */
+    a = fl2(w32(a + c)); c = w32(c - a);        /* means of the means */
+    d = fl2(w32(d + b)); b = w32(b - d);        /* half differences combined */
+    d = w32(d + fl2(b)); b = w32(b - fl2(d));   /* final rotation of the odd pair */
+    p[0] = (int32_t)a; p[stride] = (int32_t)b; p[2 * stride] = (int32_t)c; p[3 * stride] = (int32_t)d;
 }
 
 /* inverse of fwd_lift: the same steps undone in reverse order */
 static void inv_lift(int32_t *p, int stride)
 {
     int64_t a = p[0], b = p[stride], c = p[2 * stride], d = p[3 * stride];
-    b = b + fl2(d);     d = d - fl2(b);
-    b = b + d;          d = 2 * d - b;
-    c = c + a;          a = 2 * a - c;
-    b = b + c;          c = 2 * c - b;
-    d = d + a;          a = 2 * a - d;
-    p[0] = chk32(a); p[stride] = chk32(b); p[2 * stride] = chk32(c); p[3 * stride] = chk32(d);
+    b = w32(b + fl2(d)); d = w32(d - fl2(b));
+    b = w32(b + d);      d = w32(2 * d - b);
+    c = w32(c + a);      a = w32(2 * a - c);
+    b = w32(b + c);      c = w32(2 * c - b);
+    d = w32(d + a);      a = w32(2 * a - d);
+    p[0] = (int32_t)a; p[stride] = (int32_t)b; p[2 * stride] = (int32_t)c; p[3 * stride] = (int32_t)d;
 }
 
 void oracle_fwd_lift4(int32_t *v4) { fwd_lift(v4, 1); }
