@@ -1,0 +1,199 @@
+/*
+ * oocs.h -- compressed out-of-core 3D stencil sweeps on one GPU (C ABI).
+ *
+ * Method: Shen et al., "Compression-Based Optimizations for Out-of-Core GPU
+ * Stencil Computation".  A grid larger than the device budget lives in host
+ * memory as a stack of z-slabs ("chunks", Sec. 3.1).  Each slab is copied to
+ * the GPU with a halo of h >= k*r planes (temporal blocking, Sec. 3.1), its
+ * overlap with the previous slab is reused on the device (region sharing,
+ * Sec. 3.1 and Sec. 4.1), it is decompressed, advanced k time steps,
+ * recompressed with a fixed-rate block codec (Sec. 4.2) and copied back.  All
+ * slabs share ONE device working buffer (single working buffer, Sec. 5), and
+ * three streams are ordered by events as in Algorithm 1 ("Conflict-free
+ * scheduling") so that no two slabs touch the working buffer at once.
+ *
+ * Conventions for every entry point:
+ *  - Fields are FP32, layout [z][y][x] with x fastest; nx, ny, nz are
+ *    multiples of 4.  Points within `radius` of a face are the Dirichlet
+ *    shell and never change.
+ *  - The caller owns all memory: the device workspace, the host stores and
+ *    any raw host arrays.  The library allocates only CUDA events and small
+ *    host metadata, and frees only what it allocated.
+ *  - Every call returns an oocs_status and never aborts, throws or traps.
+ *    OOCS_ERR_CUDA and OOCS_ERR_TIMEOUT are sticky on a context until
+ *    oocs_destroy; the text of the last error is in oocs_last_error().
+ *  - Calls that enqueue GPU work are asynchronous with respect to the host;
+ *    completion and device-side errors surface in oocs_synchronize().
+ *  - A context is used by one host thread at a time.
+ *  - Stream arguments are cudaStream_t values passed as void*.
+ */
+#ifndef OOCS_H
+#define OOCS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OOCS_OK = 0,
+    OOCS_ERR_INVALID_ARG = 1,  /* bad pointer, size, shape, rate or state of an argument */
+    OOCS_ERR_BUDGET = 2,       /* the plan does not fit the device budget / workspace    */
+    OOCS_ERR_HOST_ALLOC = 3,   /* host metadata allocation failed                         */
+    OOCS_ERR_CUDA = 4,         /* a CUDA call failed (sticky)                             */
+    OOCS_ERR_TIMEOUT = 5,      /* oocs_synchronize ran out of time (sticky)               */
+    OOCS_ERR_STATE = 6,        /* call not valid in the context's current state           */
+    OOCS_ERR_UNSUPPORTED = 7   /* valid request this build does not implement             */
+} oocs_status;
+
+/* Time schemes (Sec. 6 uses a 25-point acoustic wave code).
+ *  OOCS_HEAT: u' = c0 u + sum_{d=1..r} c_d s_d(u)                 (first order in time)
+ *  OOCS_WAVE: u' = 2u - up + m (c0 u + sum_d c_d s_d(u) + w[t] at the source)  (leapfrog)
+ * with s_d(u)(p) = (u[p-d ex] + u[p+d ex]) + (u[p-d ey] + u[p+d ey]) + (u[p-d ez] + u[p+d ez]). */
+enum { OOCS_HEAT = 0, OOCS_WAVE = 1 };
+
+/* Fields of a context.  HEAT streams U.  WAVE streams U (u^t), U_PREV (u^(t-1))
+ * and the read-only model M = (v dt/dx)^2 (the paper's read-only dataset,
+ * Sec. 6.2); the write-only dataset is device-only.                        */
+enum { OOCS_FIELD_U = 0, OOCS_FIELD_U_PREV = 1, OOCS_FIELD_M = 2 };
+
+/* Working-buffer schemes (Sec. 5): 1 = single working buffer shared by the
+ * three streams (the paper's method); 3 = classic, one per stream (Fig. 6a). */
+enum { OOCS_SWB = 1, OOCS_CLASSIC = 3 };
+
+#define OOCS_MAX_RADIUS 4
+
+typedef struct {
+    int64_t nx, ny, nz;          /* full grid incl. the Dirichlet shell; multiples of 4      */
+    int32_t scheme;              /* OOCS_HEAT or OOCS_WAVE                                    */
+    int32_t radius;              /* r: 1 or 4 (star stencils; WAVE requires 4)                */
+    float coef[OOCS_MAX_RADIUS + 1]; /* [centre, c1 .. cr]; copied at create               */
+    uint64_t device_budget;      /* bytes of device workspace the context may use            */
+    int32_t rate_bits;           /* 0 = uncompressed store; 1..32 = fixed rate, bits/value   */
+    int32_t temporal_depth;      /* k >= 1 steps per slab visit; 0 = 4                        */
+    int32_t slab_planes;         /* T, multiple of 4; 0 = largest T that fits device_budget  */
+    int32_t working_buffers;     /* OOCS_SWB (1) or OOCS_CLASSIC (3)                          */
+} oocs_desc;
+
+/* Resolved plan (Sec. 3.1 chunking and temporal blocking; Sec. 6.2 memory model). */
+typedef struct {
+    int32_t slab_planes;         /* T                                                        */
+    int32_t temporal_depth;      /* k                                                        */
+    int32_t halo_planes;         /* h = 4 * ceil(k r / 4)                                    */
+    int32_t num_slabs;           /* S = ceil(nz / T)                                         */
+    int32_t window_planes;       /* min(T + 2h, nz)                                          */
+    int32_t fields_in;           /* streamed host->device fields (HEAT 1, WAVE 3)            */
+    int32_t fields_out;          /* streamed device->host fields (HEAT 1, WAVE 2)            */
+    int32_t reserved;
+    uint64_t layer_bytes;        /* bytes of one 4-plane layer of one field in the store     */
+    uint64_t host_store_bytes;   /* bytes of one field's host store = nz/4 * layer_bytes     */
+    uint64_t workspace_bytes;    /* device workspace for this desc                           */
+    uint64_t workspace_swb_bytes;     /* same plan with one working buffer                  */
+    uint64_t workspace_classic_bytes; /* same plan with three working buffers               */
+} oocs_plan;
+
+typedef struct {
+    uint64_t h2d_bytes;          /* bytes copied host->device by oocs_step so far            */
+    uint64_t d2h_bytes;          /* bytes copied device->host by oocs_step so far            */
+    uint64_t kernel_launches;    /* kernels launched by oocs_step so far                     */
+    uint64_t steps_done;         /* time steps enqueued so far (the global time index t)     */
+    uint64_t passes_done;        /* slab sweeps enqueued so far                              */
+    uint64_t slabs_done;         /* slab visits enqueued so far                              */
+    uint64_t workspace_bytes;    /* device bytes the context uses                            */
+    float last_step_ms;          /* device time of the last completed oocs_step (events)    */
+    float reserved_f;
+} oocs_stats;
+
+typedef struct oocs_ctx oocs_ctx;
+
+/* Plan `desc` without touching the GPU.  Fills *plan.  OOCS_ERR_INVALID_ARG
+ * for a malformed desc; OOCS_ERR_BUDGET when no slab thickness T >= max(4, 2h)
+ * fits device_budget.  Thread-safe; no context needed.                      */
+oocs_status oocs_query(const oocs_desc *desc, oocs_plan *plan);
+
+/* Create a context on the current CUDA device.  `workspace` is a device
+ * allocation of `workspace_bytes` >= plan.workspace_bytes, 256-byte aligned,
+ * owned by the caller and kept alive until oocs_destroy.  streams[0..2] are
+ * the three cudaStream_t the method pipelines over (Algorithm 1); they must be
+ * distinct, non-null and stay valid for the context's life.                */
+oocs_status oocs_create(const oocs_desc *desc, void *workspace, uint64_t workspace_bytes,
+                        void *const streams[3], oocs_ctx **out);
+
+/* Bind the host store of `field` (OOCS_FIELD_*): `bytes` >= plan.host_store_bytes
+ * of host memory, page-locked (cudaHostAlloc / pinned torch tensor) for the
+ * copies to overlap.  Layout: nz/4 layers of plan.layer_bytes; with
+ * rate_bits > 0 a layer holds (nx/4)(ny/4) codec blocks of 8*rate_bits bytes,
+ * block (bx, by) at ((by * nx/4) + bx) * 8*rate_bits; with rate_bits = 0 it is
+ * the raw FP32 planes.  Updated in place by oocs_step.                      */
+oocs_status oocs_bind_field(oocs_ctx *ctx, int32_t field, void *host_store, uint64_t bytes);
+
+/* Set the point source of the WAVE scheme: voxel (x, y, z) receives w[t] at
+ * the step that advances from time t (0-based, counted over the context's
+ * life).  w (host, nw values) is copied.  Steps t >= nw add nothing.        */
+oocs_status oocs_set_source(oocs_ctx *ctx, int64_t x, int64_t y, int64_t z, const float *w,
+                            int32_t nw);
+
+/* Fill the bound store of `field` from a raw FP32 host array of nx*ny*nz
+ * values (initial compression of the chunks, Algorithm 1 input (1)): copies
+ * go through the workspace and the codec kernels, using streams[0..1].
+ * Asynchronous: `src` must stay valid until oocs_synchronize.              */
+oocs_status oocs_compress(oocs_ctx *ctx, int32_t field, const float *src);
+
+/* Inverse of oocs_compress: decode the bound store of `field` into the raw
+ * FP32 host array `dst` of nx*ny*nz values.  Asynchronous.                 */
+oocs_status oocs_decompress(oocs_ctx *ctx, int32_t field, float *dst);
+
+/* Advance the bound fields `nsteps` time steps: ceil(nsteps/k) sweeps over
+ * the S slabs (the last with the remainder), each slab streamed through the
+ * three-stream pipeline of Algorithm 1 with the single working buffer.
+ * Asynchronous; the host stores hold the new state after oocs_synchronize. */
+oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps);
+
+/* Wait for all work of the context, at most timeout_ns nanoseconds
+ * (0 = no limit).  OOCS_ERR_TIMEOUT if it is still running (sticky);
+ * OOCS_ERR_CUDA on a device error.                                         */
+oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns);
+
+oocs_status oocs_get_stats(const oocs_ctx *ctx, oocs_stats *out);
+
+/* Text of the last error of ctx, or of the last failed context-free call in
+ * this thread when ctx is NULL.  Never NULL; valid until the next call.    */
+const char *oocs_last_error(const oocs_ctx *ctx);
+
+/* Release events and metadata (waits for outstanding work first).  The
+ * caller's workspace, stores and streams are not touched.                  */
+oocs_status oocs_destroy(oocs_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Device-level entry points (no context).  All pointers are device pointers
+ * unless stated; all calls are asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+
+/* In-core reference run of `nsteps` steps of desc's scheme on device-resident
+ * fields (Sec. 3.1 stencil without chunking), with the same FP32 arithmetic
+ * as oocs_step.  HEAT: u (in/out), scratch = nx*ny*nz floats.  WAVE: u = u^t,
+ * u_prev = u^(t-1) (both in/out), m read-only, scratch = nx*ny*nz floats;
+ * t0 = time index of u on entry (for the source), src_xyz and w as in
+ * oocs_set_source (w is a HOST array; src_xyz may be NULL for no source).  */
+oocs_status oocs_incore_run(const oocs_desc *desc, float *u, float *u_prev, const float *m,
+                            float *scratch, int32_t nsteps, int64_t t0,
+                            const int64_t *src_xyz, const float *w, int32_t nw, void *stream);
+
+/* Fixed-rate block codec (Sec. 4.2) on device arrays.  encode: field
+ * [nz][ny][nx] FP32 -> (nx/4)(ny/4)(nz/4) blocks of 8*rate bytes in layer
+ * order (block (bx,by,bz) at ((bz*(ny/4)+by)*(nx/4)+bx)).  decode: inverse.
+ * rate in [1, 32]; dims multiples of 4; pointers 16-byte aligned.          */
+oocs_status oocs_encode_device(const float *field, int64_t nx, int64_t ny, int64_t nz,
+                               int32_t rate, void *blocks, void *stream);
+oocs_status oocs_decode_device(const void *blocks, int64_t nx, int64_t ny, int64_t nz,
+                               int32_t rate, float *field, void *stream);
+
+/* Library version string. */
+const char *oocs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OOCS_H */

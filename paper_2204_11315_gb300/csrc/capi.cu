@@ -1,0 +1,886 @@
+// capi.cu -- the C ABI of include/oocs.h: planner, context, and the slab
+// scheduler of the single-working-buffer pipeline.
+//
+// Scheduling (Sec. 5, Algorithm 1 "Conflict-free scheduling", Fig. 8).  Slab
+// visits are numbered g = 0, 1, 2, ... over all sweeps; visit g runs on
+// stream g % 3 and owns staging slot g % 3.  Its operations, in stream order:
+//
+//   wait  decoded[g-2]            staging slot g%3 is free (visit g-2 has read
+//                                 the overlap it borrowed from slot (g-3)%3)
+//   wait  d2h[s], d2h[s+1]        host layers it reads were written back by the
+//                                 previous sweep (cross-sweep read-after-write)
+//   H2D   new layers -> slot      region sharing: only layers not already on
+//                                 the device (Sec. 3.1, Fig. 2)
+//   record h2d[g]
+//   wait  wrel[g-1], h2d[g-1]     the working buffer is free (SWB, Sec. 5) and
+//                                 the borrowed overlap has landed
+//   load  slot g-1 (overlap) + slot g -> working buffer (decode, Sec. 4.2)
+//   record decoded[g]
+//   k steps on the shrinking trapezoid (temporal blocking, Sec. 3.1)
+//   store working buffer interior -> out slot (encode)
+//   record wrel[g]
+//   D2H   out slot -> host layers [z0, z1), in place
+//   record d2h[s]
+//
+// This is the DAG of Fig. 8(a) with each stream waiting on its cyclic
+// predecessor before touching the working buffer; it adds the two hazards the
+// paper's listing leaves implicit (the borrowed overlap and the in-place host
+// store across sweeps) and the missing epilogue (every visit enqueues its own
+// compress and copy-back).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/oocs.h"
+#include "kernels.h"
+#include "stencil.cuh"
+
+using namespace oocs;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+const char *kVersion = "oocs 0.1 (sm_103a)";
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    // byte offsets inside the workspace
+    uint64_t w_off[3][3];     // [working buffer][buffer]
+    uint64_t in_off[3][3];    // [slot][field_in]
+    uint64_t out_off[3][2];   // [slot][field_out]
+    uint64_t total;
+    int nwb;                  // working buffers (1 SWB, 3 classic)
+    int nbuf;                 // buffers per working set (heat 2, wave 3)
+    uint64_t buf_bytes;       // one window buffer
+    uint64_t in_slot_bytes;   // one staging slot of one field
+    uint64_t out_slot_bytes;
+};
+
+struct Derived {
+    int r, k, h, T, S, wp, fin, fout;
+    uint64_t layer_bytes;
+    int64_t slot_layers_in, slot_layers_out;
+};
+
+Derived derive(const oocs_desc &d, int T)
+{
+    Derived v;
+    v.r = d.radius;
+    v.k = d.temporal_depth > 0 ? d.temporal_depth : 4;
+    v.h = (int)(4 * ceil_div((int64_t)v.k * v.r, 4));
+    v.T = T;
+    v.S = (int)ceil_div(d.nz, T);
+    v.wp = (int)std::min<int64_t>(T + 2 * (int64_t)v.h, d.nz);
+    v.fin = d.scheme == OOCS_WAVE ? 3 : 1;
+    v.fout = d.scheme == OOCS_WAVE ? 2 : 1;
+    v.layer_bytes = d.rate_bits > 0 ? (uint64_t)(d.nx / 4) * (d.ny / 4) * 8ull * d.rate_bits
+                                    : (uint64_t)4 * d.nx * d.ny * 4;
+    v.slot_layers_in = std::min<int64_t>(ceil_div(T + v.h, 4), d.nz / 4);
+    v.slot_layers_out = std::min<int64_t>(T / 4, d.nz / 4);
+    return v;
+}
+
+Layout layout_for(const oocs_desc &d, const Derived &v, int nwb)
+{
+    Layout L;
+    memset(&L, 0, sizeof(L));
+    L.nwb = nwb;
+    L.nbuf = d.scheme == OOCS_WAVE ? 3 : 2;
+    L.buf_bytes = align_up((uint64_t)v.wp * d.nx * d.ny * 4, 256);
+    L.in_slot_bytes = align_up((uint64_t)v.slot_layers_in * v.layer_bytes, 256);
+    L.out_slot_bytes = align_up((uint64_t)v.slot_layers_out * v.layer_bytes, 256);
+    uint64_t off = 0;
+    for (int w = 0; w < nwb; ++w)
+        for (int b = 0; b < L.nbuf; ++b) {
+            L.w_off[w][b] = off;
+            off += L.buf_bytes;
+        }
+    for (int q = 0; q < 3; ++q)
+        for (int f = 0; f < v.fin; ++f) {
+            L.in_off[q][f] = off;
+            off += L.in_slot_bytes;
+        }
+    for (int q = 0; q < 3; ++q)
+        for (int f = 0; f < v.fout; ++f) {
+            L.out_off[q][f] = off;
+            off += L.out_slot_bytes;
+        }
+    L.total = off;
+    return L;
+}
+
+oocs_status validate_desc(const oocs_desc *d, std::string &err)
+{
+    if (!d) {
+        err = "desc is NULL";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->nx < 4 || d->ny < 4 || d->nz < 4 || d->nx % 4 || d->ny % 4 || d->nz % 4) {
+        err = "nx, ny, nz must be positive multiples of 4";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->nx > (1 << 30) || d->ny > (1 << 30) || d->nz > (1 << 30)) {
+        err = "grid dimension too large";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->scheme != OOCS_HEAT && d->scheme != OOCS_WAVE) {
+        err = "scheme must be OOCS_HEAT or OOCS_WAVE";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->radius != 1 && d->radius != 4) {
+        err = "radius must be 1 or 4";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->scheme == OOCS_WAVE && d->radius != 4) {
+        err = "the wave scheme uses the 25-point star (radius 4)";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->nx <= 2 * d->radius || d->ny <= 2 * d->radius || d->nz <= 2 * d->radius) {
+        err = "grid must be larger than the Dirichlet shell";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->rate_bits < 0 || d->rate_bits > 32) {
+        err = "rate_bits must be 0 (uncompressed) or 1..32";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->temporal_depth < 0 || d->temporal_depth > 64) {
+        err = "temporal_depth must be 0 (auto) or 1..64";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->slab_planes < 0 || d->slab_planes % 4) {
+        err = "slab_planes must be 0 (auto) or a positive multiple of 4";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->working_buffers != OOCS_SWB && d->working_buffers != OOCS_CLASSIC) {
+        err = "working_buffers must be 1 (SWB) or 3 (classic)";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    return OOCS_OK;
+}
+
+bool slab_ok(const oocs_desc &d, int T, int h)
+{
+    if (T < 4 || T % 4)
+        return false;
+    if (T >= d.nz)
+        return true;    // one slab
+    return T >= 2 * h;  // the overlap of slab s lies in slab s-1's staging slot
+}
+
+oocs_status plan_impl(const oocs_desc *d, oocs_plan *p, std::string &err)
+{
+    oocs_status st = validate_desc(d, err);
+    if (st != OOCS_OK)
+        return st;
+    if (!p) {
+        err = "plan is NULL";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    const int nwb = d->working_buffers;
+    int T = d->slab_planes;
+    Derived v0 = derive(*d, 4);
+    if (T > 0) {
+        if (T > d->nz)
+            T = (int)d->nz;
+        if (!slab_ok(*d, T, v0.h)) {
+            err = "slab_planes must be >= 2 * halo (" + std::to_string(2 * v0.h) + ") when nz > T";
+            return OOCS_ERR_INVALID_ARG;
+        }
+        Derived v = derive(*d, T);
+        if (layout_for(*d, v, nwb).total > d->device_budget) {
+            err = "slab of " + std::to_string(T) + " planes needs " +
+                  std::to_string(layout_for(*d, v, nwb).total) + " bytes > device_budget";
+            return OOCS_ERR_BUDGET;
+        }
+    } else {
+        int best = 0;
+        for (int64_t t = 4; t <= d->nz; t += 4) {
+            if (!slab_ok(*d, (int)t, v0.h))
+                continue;
+            Derived v = derive(*d, (int)t);
+            if (layout_for(*d, v, nwb).total <= d->device_budget)
+                best = (int)t;
+            else if (best)
+                break;
+        }
+        if (!best) {
+            err = "no slab thickness fits device_budget";
+            return OOCS_ERR_BUDGET;
+        }
+        T = best;
+    }
+    Derived v = derive(*d, T);
+    memset(p, 0, sizeof(*p));
+    p->slab_planes = T;
+    p->temporal_depth = v.k;
+    p->halo_planes = v.h;
+    p->num_slabs = v.S;
+    p->window_planes = v.wp;
+    p->fields_in = v.fin;
+    p->fields_out = v.fout;
+    p->layer_bytes = v.layer_bytes;
+    p->host_store_bytes = (uint64_t)(d->nz / 4) * v.layer_bytes;
+    p->workspace_bytes = layout_for(*d, v, nwb).total;
+    p->workspace_swb_bytes = layout_for(*d, v, 1).total;
+    p->workspace_classic_bytes = layout_for(*d, v, 3).total;
+    return OOCS_OK;
+}
+
+}  // namespace
+
+struct oocs_ctx {
+    oocs_desc d;
+    oocs_plan p;
+    Derived v;
+    Layout L;
+    char *ws = nullptr;
+    cudaStream_t st[3] = {};
+    char *store[3] = {};
+    uint64_t store_bytes[3] = {};
+
+    bool has_src = false;
+    int64_t src[3] = {0, 0, -1};
+    std::vector<float> w;
+
+    cudaEvent_t ev_decoded[3] = {}, ev_h2d[3] = {}, ev_wrel[3] = {}, ev_join[3] = {};
+    std::vector<cudaEvent_t> ev_d2h;
+    std::vector<char> d2h_recorded;
+    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
+    bool timing_pending = false;
+
+    uint64_t g = 0;  // slab visits enqueued
+    oocs_stats stats;
+    oocs_status sticky = OOCS_OK;
+    std::string err = "no error";
+
+    float *wbuf(int wb, int b) const { return reinterpret_cast<float *>(ws + L.w_off[wb][b]); }
+    char *in_slot(int q, int f) const { return ws + L.in_off[q][f]; }
+    char *out_slot(int q, int f) const { return ws + L.out_off[q][f]; }
+};
+
+namespace {
+
+oocs_status fail(oocs_ctx *c, oocs_status s, const std::string &msg)
+{
+    if (c) {
+        c->err = msg;
+        if (s == OOCS_ERR_CUDA || s == OOCS_ERR_TIMEOUT)
+            c->sticky = s;
+    } else {
+        g_last_error = msg;
+    }
+    return s;
+}
+
+#define CU(ctx, call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), OOCS_ERR_CUDA,                                                \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+// in-field index -> context field id
+int in_field_id(const oocs_ctx *c, int f)
+{
+    (void)c;
+    return f;  // heat: U; wave: U, U_PREV, M
+}
+
+// make every stream wait for the work enqueued so far on all three
+oocs_status join_streams(oocs_ctx *c)
+{
+    for (int i = 0; i < 3; ++i)
+        CU(c, cudaEventRecord(c->ev_join[i], c->st[i]));
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (i != j)
+                CU(c, cudaStreamWaitEvent(c->st[i], c->ev_join[j], 0));
+    return OOCS_OK;
+}
+
+oocs_status check_ready(oocs_ctx *c)
+{
+    if (!c)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->sticky != OOCS_OK)
+        return c->sticky;
+    return OOCS_OK;
+}
+
+// Copy (rate 0) or decode (rate > 0) layers [l0, l1) held in staging memory
+// `src` (whose first layer is src_l0) into window buffer `dst` (first plane w0).
+oocs_status load_layers(oocs_ctx *c, const char *src, int64_t src_l0, int64_t l0, int64_t l1,
+                        float *dst, int64_t w0, cudaStream_t s)
+{
+    if (l1 <= l0)
+        return OOCS_OK;
+    const char *from = src + (l0 - src_l0) * c->v.layer_bytes;
+    float *to = dst + (4 * l0 - w0) * c->d.nx * c->d.ny;
+    if (c->d.rate_bits == 0) {
+        CU(c, cudaMemcpyAsync(to, from, (l1 - l0) * c->v.layer_bytes, cudaMemcpyDeviceToDevice, s));
+    } else {
+        CU(c, launch_decode_layers(from, c->d.nx, c->d.ny, l1 - l0, c->d.rate_bits, to, s));
+        c->stats.kernel_launches++;
+    }
+    return OOCS_OK;
+}
+
+// Copy (rate 0) or encode (rate > 0) window planes of layers [l0, l1) into `dst`.
+oocs_status store_layers(oocs_ctx *c, const float *src, int64_t w0, int64_t l0, int64_t l1,
+                         char *dst, cudaStream_t s)
+{
+    if (l1 <= l0)
+        return OOCS_OK;
+    const float *from = src + (4 * l0 - w0) * c->d.nx * c->d.ny;
+    if (c->d.rate_bits == 0) {
+        CU(c, cudaMemcpyAsync(dst, from, (l1 - l0) * c->v.layer_bytes, cudaMemcpyDeviceToDevice, s));
+    } else {
+        CU(c, launch_encode_layers(from, c->d.nx, c->d.ny, l1 - l0, c->d.rate_bits, dst, s));
+        c->stats.kernel_launches++;
+    }
+    return OOCS_OK;
+}
+
+// Enqueue one slab visit (slab s, k_eff steps starting at global time t).
+oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
+{
+    const Derived &v = c->v;
+    const oocs_desc &d = c->d;
+    const uint64_t g = c->g;
+    const int q = (int)(g % 3);
+    const int qp = (int)((g + 2) % 3);  // slot of visit g-1
+    cudaStream_t st = c->st[q];
+    const int wb = (d.working_buffers == OOCS_SWB) ? 0 : q;
+
+    const int64_t z0 = (int64_t)s * v.T;
+    const int64_t z1 = std::min<int64_t>(z0 + v.T, d.nz);
+    const int64_t w0 = std::max<int64_t>(z0 - v.h, 0);
+    const int64_t w1 = std::min<int64_t>(z1 + v.h, d.nz);
+    // layers new to the device: all of the window for the first slab of a
+    // sweep, else only what lies above the overlap kept from slab s-1
+    const int64_t n0 = (s == 0) ? w0 : std::min<int64_t>(z0 + v.h, w1);
+    const int64_t n1 = w1;
+
+    // 1. staging slot q is free once visit g-2 has read its borrowed overlap
+    if (g >= 2)
+        CU(c, cudaStreamWaitEvent(st, c->ev_decoded[(g - 2) % 3], 0));
+    // 2. host layers [n0, n1) were last written by slabs s and s+1 of the previous sweep
+    for (int ss = s; ss <= s + 1 && ss < v.S; ++ss)
+        if (c->d2h_recorded[ss])
+            CU(c, cudaStreamWaitEvent(st, c->ev_d2h[ss], 0));
+    // 3. H2D of the new layers of every streamed field
+    for (int f = 0; f < v.fin; ++f) {
+        const int id = in_field_id(c, f);
+        const uint64_t bytes = (uint64_t)(n1 - n0) / 4 * v.layer_bytes;
+        if (bytes) {
+            CU(c, cudaMemcpyAsync(c->in_slot(q, f), c->store[id] + (uint64_t)(n0 / 4) * v.layer_bytes,
+                                  bytes, cudaMemcpyHostToDevice, st));
+            c->stats.h2d_bytes += bytes;
+        }
+    }
+    CU(c, cudaEventRecord(c->ev_h2d[q], st));
+    // 4. working buffer released by visit g-1 (single working buffer); the
+    //    overlap borrowed from visit g-1's slot has landed
+    if (g >= 1 && d.working_buffers == OOCS_SWB)
+        CU(c, cudaStreamWaitEvent(st, c->ev_wrel[(g - 1) % 3], 0));
+    if (s > 0)
+        CU(c, cudaStreamWaitEvent(st, c->ev_h2d[qp], 0));
+    // 5. load / decode the window at time t
+    for (int f = 0; f < v.fin; ++f) {
+        float *dst = c->wbuf(wb, f);  // heat: U -> buf 0; wave: U, U_PREV, M -> 0, 1, 2
+        if (s > 0) {
+            // slot of slab s-1 holds layers starting at its own n0
+            const int64_t pz0 = (int64_t)(s - 1) * v.T;
+            const int64_t pw0 = std::max<int64_t>(pz0 - v.h, 0);
+            const int64_t pn0 = (s - 1 == 0) ? pw0 : pz0 + v.h;
+            oocs_status r = load_layers(c, c->in_slot(qp, f), pn0 / 4, w0 / 4, n0 / 4, dst, w0, st);
+            if (r != OOCS_OK)
+                return r;
+        }
+        oocs_status r = load_layers(c, c->in_slot(q, f), n0 / 4, n0 / 4, n1 / 4, dst, w0, st);
+        if (r != OOCS_OK)
+            return r;
+    }
+    CU(c, cudaEventRecord(c->ev_decoded[q], st));
+
+    // 6. k_eff steps over the shrinking trapezoid
+    int cur = 0, oth = 1;
+    StepLaunch Ls;
+    memset(&Ls, 0, sizeof(Ls));
+    Ls.scheme = d.scheme == OOCS_WAVE ? kWave : kHeat;
+    Ls.radius = d.radius;
+    Ls.nx = d.nx;
+    Ls.ny = d.ny;
+    Ls.nz = d.nz;
+    Ls.gz0 = w0;
+    Ls.wp = w1 - w0;
+    for (int i = 0; i <= d.radius; ++i)
+        Ls.coef[i] = d.coef[i];
+    for (int j = 1; j <= k_eff; ++j) {
+        const int64_t lo = std::max<int64_t>(z0 - (int64_t)(k_eff - j) * v.r, 0);
+        const int64_t hi = std::min<int64_t>(z1 + (int64_t)(k_eff - j) * v.r, d.nz);
+        Ls.z_lo = lo - w0;
+        Ls.z_hi = hi - w0;
+        Ls.cur = c->wbuf(wb, cur);
+        Ls.prev = c->wbuf(wb, oth);
+        Ls.m = d.scheme == OOCS_WAVE ? c->wbuf(wb, 2) : nullptr;
+        Ls.out = c->wbuf(wb, oth);
+        const int64_t tstep = t + j - 1;
+        Ls.src_z = -1;
+        Ls.w = 0.0f;
+        if (c->has_src && tstep < (int64_t)c->w.size()) {
+            Ls.src_x = c->src[0];
+            Ls.src_y = c->src[1];
+            Ls.src_z = c->src[2];
+            Ls.w = c->w[tstep];
+        }
+        CU(c, launch_star_step(Ls, st));
+        c->stats.kernel_launches++;
+        std::swap(cur, oth);
+    }
+    // 7. interior [z0, z1) -> out slot(s): u^(t+k) and, for the wave, u^(t+k-1)
+    {
+        oocs_status r = store_layers(c, c->wbuf(wb, cur), w0, z0 / 4, z1 / 4, c->out_slot(q, 0), st);
+        if (r != OOCS_OK)
+            return r;
+        if (v.fout == 2) {
+            r = store_layers(c, c->wbuf(wb, oth), w0, z0 / 4, z1 / 4, c->out_slot(q, 1), st);
+            if (r != OOCS_OK)
+                return r;
+        }
+    }
+    CU(c, cudaEventRecord(c->ev_wrel[q], st));
+    // 8. D2H into the host store, in place
+    for (int f = 0; f < v.fout; ++f) {
+        const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
+        CU(c, cudaMemcpyAsync(c->store[f] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, f),
+                              bytes, cudaMemcpyDeviceToHost, st));
+        c->stats.d2h_bytes += bytes;
+    }
+    CU(c, cudaEventRecord(c->ev_d2h[s], st));
+    c->d2h_recorded[s] = 1;
+    c->g++;
+    c->stats.slabs_done++;
+    return OOCS_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI ======
+
+extern "C" {
+
+const char *oocs_version(void) { return kVersion; }
+
+oocs_status oocs_query(const oocs_desc *desc, oocs_plan *plan)
+{
+    std::string err;
+    oocs_status s = plan_impl(desc, plan, err);
+    if (s != OOCS_OK)
+        g_last_error = err;
+    return s;
+}
+
+oocs_status oocs_create(const oocs_desc *desc, void *workspace, uint64_t workspace_bytes,
+                        void *const streams[3], oocs_ctx **out)
+{
+    if (!out)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    oocs_plan p;
+    std::string err;
+    oocs_status s = plan_impl(desc, &p, err);
+    if (s != OOCS_OK)
+        return fail(nullptr, s, err);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
+    if (workspace_bytes < p.workspace_bytes)
+        return fail(nullptr, OOCS_ERR_BUDGET,
+                    "workspace of " + std::to_string(workspace_bytes) + " bytes < plan's " +
+                        std::to_string(p.workspace_bytes));
+    if (!streams || !streams[0] || !streams[1] || !streams[2] || streams[0] == streams[1] ||
+        streams[1] == streams[2] || streams[0] == streams[2])
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "three distinct non-null streams are required");
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, workspace) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "workspace is not device memory");
+    }
+    oocs_ctx *c = new (std::nothrow) oocs_ctx();
+    if (!c)
+        return fail(nullptr, OOCS_ERR_HOST_ALLOC, "cannot allocate the context");
+    c->d = *desc;
+    if (c->d.temporal_depth == 0)
+        c->d.temporal_depth = p.temporal_depth;
+    c->p = p;
+    c->v = derive(c->d, p.slab_planes);
+    c->L = layout_for(c->d, c->v, c->d.working_buffers);
+    c->ws = static_cast<char *>(workspace);
+    for (int i = 0; i < 3; ++i)
+        c->st[i] = static_cast<cudaStream_t>(streams[i]);
+    memset(&c->stats, 0, sizeof(c->stats));
+    c->stats.workspace_bytes = p.workspace_bytes;
+    c->ev_d2h.assign(c->v.S, nullptr);
+    c->d2h_recorded.assign(c->v.S, 0);
+    auto mk = [&](cudaEvent_t *e) {
+        return cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+    };
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+        e = mk(&c->ev_decoded[i]);
+        if (e == cudaSuccess) e = mk(&c->ev_h2d[i]);
+        if (e == cudaSuccess) e = mk(&c->ev_wrel[i]);
+        if (e == cudaSuccess) e = mk(&c->ev_join[i]);
+    }
+    for (int i = 0; i < c->v.S && e == cudaSuccess; ++i)
+        e = mk(&c->ev_d2h[i]);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&c->ev_t0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&c->ev_t1);
+    if (e != cudaSuccess) {
+        std::string msg = std::string("cudaEventCreate: ") + cudaGetErrorString(e);
+        oocs_destroy(c);
+        return fail(nullptr, OOCS_ERR_CUDA, msg);
+    }
+    *out = c;
+    return OOCS_OK;
+}
+
+oocs_status oocs_bind_field(oocs_ctx *ctx, int32_t field, void *host_store, uint64_t bytes)
+{
+    oocs_status s = check_ready(ctx);
+    if (s != OOCS_OK)
+        return s;
+    const int nf = ctx->d.scheme == OOCS_WAVE ? 3 : 1;
+    if (field < 0 || field >= nf)
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "field id not used by this scheme");
+    if (!host_store || bytes < ctx->p.host_store_bytes)
+        return fail(ctx, OOCS_ERR_INVALID_ARG,
+                    "host store needs " + std::to_string(ctx->p.host_store_bytes) + " bytes");
+    ctx->store[field] = static_cast<char *>(host_store);
+    ctx->store_bytes[field] = bytes;
+    return OOCS_OK;
+}
+
+oocs_status oocs_set_source(oocs_ctx *ctx, int64_t x, int64_t y, int64_t z, const float *w, int32_t nw)
+{
+    oocs_status s = check_ready(ctx);
+    if (s != OOCS_OK)
+        return s;
+    if (ctx->d.scheme != OOCS_WAVE)
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "a point source needs the wave scheme");
+    if (x < 0 || y < 0 || z < 0 || x >= ctx->d.nx || y >= ctx->d.ny || z >= ctx->d.nz || nw < 0 ||
+        (nw > 0 && !w))
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "source voxel outside the grid or bad wavelet");
+    ctx->has_src = nw > 0;
+    ctx->src[0] = x;
+    ctx->src[1] = y;
+    ctx->src[2] = z;
+    ctx->w.assign(w, w + nw);
+    return OOCS_OK;
+}
+
+static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, float *dst, bool enc)
+{
+    oocs_status s = check_ready(ctx);
+    if (s != OOCS_OK)
+        return s;
+    const int nf = ctx->d.scheme == OOCS_WAVE ? 3 : 1;
+    if (field < 0 || field >= nf || !ctx->store[field])
+        return fail(ctx, OOCS_ERR_STATE, "field is not bound");
+    if (enc ? !src : !dst)
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "raw host array is NULL");
+    const oocs_desc &d = ctx->d;
+    const uint64_t plane_bytes = (uint64_t)d.nx * d.ny * 4;
+    s = join_streams(ctx);
+    if (s != OOCS_OK)
+        return s;
+    if (d.rate_bits == 0) {
+        const uint64_t bytes = (uint64_t)d.nz * plane_bytes;
+        if (enc)
+            CU(ctx, cudaMemcpyAsync(ctx->store[field], src, bytes, cudaMemcpyHostToHost, ctx->st[0]));
+        else
+            CU(ctx, cudaMemcpyAsync(dst, ctx->store[field], bytes, cudaMemcpyHostToHost, ctx->st[0]));
+        return join_streams(ctx);
+    }
+    // chunks of T planes through working buffer 0's first two buffers and
+    // out slots 0 / 1 of field 0, alternating between streams 0 and 1
+    const int64_t T = ctx->v.T;
+    int64_t chunk = 0;
+    for (int64_t z0 = 0; z0 < d.nz; z0 += T, ++chunk) {
+        const int64_t z1 = std::min<int64_t>(z0 + T, d.nz);
+        const int i = (int)(chunk & 1);
+        cudaStream_t st = ctx->st[i];
+        float *raw = ctx->wbuf(0, i);
+        char *blk = ctx->out_slot(i, 0);
+        const uint64_t cbytes = (uint64_t)(z1 - z0) / 4 * ctx->v.layer_bytes;
+        char *host_blk = ctx->store[field] + (uint64_t)(z0 / 4) * ctx->v.layer_bytes;
+        if (enc) {
+            CU(ctx, cudaMemcpyAsync(raw, src + z0 * d.nx * d.ny, (z1 - z0) * plane_bytes,
+                                    cudaMemcpyHostToDevice, st));
+            CU(ctx, launch_encode_layers(raw, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, blk, st));
+            CU(ctx, cudaMemcpyAsync(host_blk, blk, cbytes, cudaMemcpyDeviceToHost, st));
+        } else {
+            CU(ctx, cudaMemcpyAsync(blk, host_blk, cbytes, cudaMemcpyHostToDevice, st));
+            CU(ctx, launch_decode_layers(blk, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, raw, st));
+            CU(ctx, cudaMemcpyAsync(dst + z0 * d.nx * d.ny, raw, (z1 - z0) * plane_bytes,
+                                    cudaMemcpyDeviceToHost, st));
+        }
+    }
+    return join_streams(ctx);
+}
+
+oocs_status oocs_compress(oocs_ctx *ctx, int32_t field, const float *src)
+{
+    return codec_field(ctx, field, src, nullptr, true);
+}
+
+oocs_status oocs_decompress(oocs_ctx *ctx, int32_t field, float *dst)
+{
+    return codec_field(ctx, field, nullptr, dst, false);
+}
+
+oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
+{
+    oocs_status s = check_ready(ctx);
+    if (s != OOCS_OK)
+        return s;
+    if (nsteps < 0)
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "nsteps must be >= 0");
+    const int nf = ctx->d.scheme == OOCS_WAVE ? 3 : 1;
+    for (int f = 0; f < nf; ++f)
+        if (!ctx->store[f])
+            return fail(ctx, OOCS_ERR_STATE, "all fields of the scheme must be bound before oocs_step");
+    if (nsteps == 0)
+        return OOCS_OK;
+    s = join_streams(ctx);
+    if (s != OOCS_OK)
+        return s;
+    CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->st[0]));
+    s = join_streams(ctx);
+    if (s != OOCS_OK)
+        return s;
+    int64_t t = (int64_t)ctx->stats.steps_done;
+    int left = nsteps;
+    while (left > 0) {
+        const int k_eff = std::min(left, ctx->v.k);
+        for (int sl = 0; sl < ctx->v.S; ++sl) {
+            s = enqueue_slab(ctx, sl, k_eff, t);
+            if (s != OOCS_OK)
+                return s;
+        }
+        t += k_eff;
+        left -= k_eff;
+        ctx->stats.passes_done++;
+    }
+    ctx->stats.steps_done = (uint64_t)t;
+    s = join_streams(ctx);
+    if (s != OOCS_OK)
+        return s;
+    CU(ctx, cudaEventRecord(ctx->ev_t1, ctx->st[0]));
+    ctx->timing_pending = true;
+    return OOCS_OK;
+}
+
+oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns)
+{
+    if (!ctx)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "ctx is NULL");
+    if (ctx->sticky != OOCS_OK)
+        return ctx->sticky;
+    // mark the end of everything enqueued so far on each stream, then poll
+    for (int i = 0; i < 3; ++i)
+        CU(ctx, cudaEventRecord(ctx->ev_join[i], ctx->st[i]));
+    const auto t_start = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+            e = cudaEventQuery(ctx->ev_join[i]);
+        if (e == cudaSuccess)
+            break;
+        if (e != cudaErrorNotReady)
+            return fail(ctx, OOCS_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+        if (timeout_ns) {
+            const auto el = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                std::chrono::steady_clock::now() - t_start)
+                                .count();
+            if ((uint64_t)el > timeout_ns)
+                return fail(ctx, OOCS_ERR_TIMEOUT, "oocs_synchronize: timed out");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    for (int i = 0; i < 3; ++i) {
+        cudaError_t e = cudaStreamQuery(ctx->st[i]);
+        if (e != cudaSuccess && e != cudaErrorNotReady)
+            return fail(ctx, OOCS_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+    }
+    if (ctx->timing_pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_t0, ctx->ev_t1) == cudaSuccess)
+            ctx->stats.last_step_ms = ms;
+        ctx->timing_pending = false;
+    }
+    return OOCS_OK;
+}
+
+oocs_status oocs_get_stats(const oocs_ctx *ctx, oocs_stats *out)
+{
+    if (!ctx || !out)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "ctx or out is NULL");
+    *out = ctx->stats;
+    return OOCS_OK;
+}
+
+const char *oocs_last_error(const oocs_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+oocs_status oocs_destroy(oocs_ctx *ctx)
+{
+    if (!ctx)
+        return OOCS_OK;
+    for (int i = 0; i < 3; ++i)
+        if (ctx->st[i])
+            cudaStreamSynchronize(ctx->st[i]);
+    auto kill = [](cudaEvent_t &e) {
+        if (e)
+            cudaEventDestroy(e);
+        e = nullptr;
+    };
+    for (int i = 0; i < 3; ++i) {
+        kill(ctx->ev_decoded[i]);
+        kill(ctx->ev_h2d[i]);
+        kill(ctx->ev_wrel[i]);
+        kill(ctx->ev_join[i]);
+    }
+    for (auto &e : ctx->ev_d2h)
+        kill(e);
+    kill(ctx->ev_t0);
+    kill(ctx->ev_t1);
+    delete ctx;
+    return OOCS_OK;
+}
+
+// ------------------------------------------------------- device-level API --
+
+oocs_status oocs_incore_run(const oocs_desc *desc, float *u, float *u_prev, const float *m,
+                            float *scratch, int32_t nsteps, int64_t t0, const int64_t *src_xyz,
+                            const float *w, int32_t nw, void *stream)
+{
+    std::string err;
+    oocs_status s = validate_desc(desc, err);
+    if (s != OOCS_OK)
+        return fail(nullptr, s, err);
+    const bool wave = desc->scheme == OOCS_WAVE;
+    if (!u || !scratch || (wave && (!u_prev || !m)) || nsteps < 0 || (nw > 0 && !w))
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "missing device array or bad nsteps/wavelet");
+    if (src_xyz && (src_xyz[0] < 0 || src_xyz[1] < 0 || src_xyz[2] < 0 || src_xyz[0] >= desc->nx ||
+                    src_xyz[1] >= desc->ny || src_xyz[2] >= desc->nz))
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "source voxel outside the grid");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint64_t bytes = (uint64_t)desc->nx * desc->ny * desc->nz * 4;
+    StepLaunch Ls;
+    memset(&Ls, 0, sizeof(Ls));
+    Ls.scheme = wave ? kWave : kHeat;
+    Ls.radius = desc->radius;
+    Ls.nx = desc->nx;
+    Ls.ny = desc->ny;
+    Ls.nz = desc->nz;
+    Ls.gz0 = 0;
+    Ls.wp = desc->nz;
+    Ls.z_lo = 0;
+    Ls.z_hi = desc->nz;
+    for (int i = 0; i <= desc->radius; ++i)
+        Ls.coef[i] = desc->coef[i];
+    float *bufs[3] = {u, wave ? u_prev : scratch, scratch};
+    int cur = 0, oth = 1;
+    for (int j = 0; j < nsteps; ++j) {
+        Ls.cur = bufs[cur];
+        Ls.prev = bufs[oth];
+        Ls.out = bufs[oth];
+        Ls.m = m;
+        Ls.src_z = -1;
+        Ls.w = 0.0f;
+        const int64_t tstep = t0 + j;
+        if (wave && src_xyz && tstep >= 0 && tstep < nw) {
+            Ls.src_x = src_xyz[0];
+            Ls.src_y = src_xyz[1];
+            Ls.src_z = src_xyz[2];
+            Ls.w = w[tstep];
+        }
+        cudaError_t e = launch_star_step(Ls, st);
+        if (e != cudaSuccess)
+            return fail(nullptr, OOCS_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+        std::swap(cur, oth);
+    }
+    // bring the result back into the caller's (u, u_prev)
+    cudaError_t e = cudaSuccess;
+    if (cur == 1) {
+        if (!wave) {
+            e = cudaMemcpyAsync(u, scratch, bytes, cudaMemcpyDeviceToDevice, st);
+        } else {
+            // cur = u_prev buffer, prev = u buffer: swap via scratch
+            e = cudaMemcpyAsync(scratch, u_prev, bytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(u_prev, u, bytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(u, scratch, bytes, cudaMemcpyDeviceToDevice, st);
+        }
+    }
+    if (e != cudaSuccess)
+        return fail(nullptr, OOCS_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    return OOCS_OK;
+}
+
+static oocs_status codec_args(int64_t nx, int64_t ny, int64_t nz, int32_t rate, const void *a,
+                              const void *b)
+{
+    if (nx < 4 || ny < 4 || nz < 4 || nx % 4 || ny % 4 || nz % 4)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "dims must be positive multiples of 4");
+    if (rate < 1 || rate > 32)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "rate must be in [1, 32]");
+    if (!a || !b || (reinterpret_cast<uintptr_t>(a) & 15) || (reinterpret_cast<uintptr_t>(b) & 15))
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "pointers must be non-null and 16-byte aligned");
+    return OOCS_OK;
+}
+
+oocs_status oocs_encode_device(const float *field, int64_t nx, int64_t ny, int64_t nz, int32_t rate,
+                               void *blocks, void *stream)
+{
+    oocs_status s = codec_args(nx, ny, nz, rate, field, blocks);
+    if (s != OOCS_OK)
+        return s;
+    cudaError_t e = launch_encode_layers(field, nx, ny, nz / 4, rate, blocks,
+                                         static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return fail(nullptr, OOCS_ERR_CUDA, std::string("encode: ") + cudaGetErrorString(e));
+    return OOCS_OK;
+}
+
+oocs_status oocs_decode_device(const void *blocks, int64_t nx, int64_t ny, int64_t nz, int32_t rate,
+                               float *field, void *stream)
+{
+    oocs_status s = codec_args(nx, ny, nz, rate, blocks, field);
+    if (s != OOCS_OK)
+        return s;
+    cudaError_t e = launch_decode_layers(blocks, nx, ny, nz / 4, rate, field,
+                                         static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return fail(nullptr, OOCS_ERR_CUDA, std::string("decode: ") + cudaGetErrorString(e));
+    return OOCS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,403 @@
+// codec.cuh -- fixed-rate block codec, device side.
+//
+// The paper streams chunks through a fixed-rate transform codec (cuZFP, Sec. 4.2,
+// "customized compression rate"; Sec. 5: 32 bits per double, ratio 1/2).  This
+// is this project's own implementation of that kind of codec, following the
+// published ZFP method (Lindstrom, IEEE TVCG 2014) with a bitstream of its own.
+// One 4x4x4 block of FP32 values (index i + 4j + 16k for (x,y,z) = (i,j,k)) is
+// coded into exactly 64*rate bits = 2*rate little-endian 32-bit words:
+//
+//   bits 0..7   header h: 0 = all-zero block, else emax + 127, where emax is
+//               the largest frexp exponent in the block clamped to >= -95
+//   bits 8..    embedded bit planes 31..0 of the 64 transform coefficients
+//               (negabinary, sequency order) with group testing, cut at the
+//               rate budget and zero padded.
+//
+// The stages are: quantise q = trunc(v * 2^(29-emax)); 4-point lifting along
+// x, y, z; order by (i+j+k, i^2+j^2+k^2, index); negabinary; plane coding.
+// Decoding inverts them and returns RN(q) * 2^(emax-29).
+//
+// GPU design: one thread codes one block entirely in registers.  Bit planes are
+// formed by two 32x32 bit-matrix transposes (no per-bit loop), and each plane
+// is emitted in closed form: the verbatim part is one masked word, and each
+// group-test hit is one "1, zeros, 1" code found with a count-trailing-zeros.
+// Inputs must be finite.
+#pragma once
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "devmath.cuh"
+
+namespace oocs {
+
+constexpr uint32_t kNegaMask = 0xAAAAAAAAu;
+
+// compile-time loop: f(integral_constant<int, I>) for I = B .. E-1
+template <int B, int E, class F>
+OOCS_FN void static_for(F &&f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// Sequency order, built at compile time by enumerating the keys in increasing
+// order (i+j+k from 0 to 9, then i^2+j^2+k^2 from 0 to 27, then the index).
+struct SeqTable {
+    int v[64];
+};
+
+constexpr SeqTable make_seq_table()
+{
+    SeqTable t{};
+    int n = 0;
+    for (int s = 0; s <= 9; ++s)
+        for (int q = 0; q <= 27; ++q)
+            for (int idx = 0; idx < 64; ++idx) {
+                int i = idx & 3, j = (idx >> 2) & 3, k = idx >> 4;
+                if (i + j + k == s && i * i + j * j + k * k == q)
+                    t.v[n++] = idx;
+            }
+    return t;
+}
+
+template <int I>
+constexpr int kSeq = make_seq_table().v[I];
+
+// ---------------------------------------------------------------- transform --
+
+// 32-bit two's complement arithmetic with defined wrap-around (valid data never
+// wraps: three guard bits keep every lifting value below 2^30 in magnitude).
+OOCS_FN int32_t wadd(int32_t a, int32_t b) { return (int32_t)((uint32_t)a + (uint32_t)b); }
+OOCS_FN int32_t wsub(int32_t a, int32_t b) { return (int32_t)((uint32_t)a - (uint32_t)b); }
+OOCS_FN int32_t wdbl(int32_t a) { return (int32_t)((uint32_t)a << 1); }
+
+// The method's forward 4-point decorrelating lift (exact rational form
+// (1/16)[4 4 4 4; 5 1 -1 -5; -4 4 4 -4; -2 6 -6 2]); >> is floor halving.
+OOCS_FN void lift_fwd(int32_t &a, int32_t &b, int32_t &c, int32_t &d)
+{
+    a = wadd(a, d) >> 1;
+    d = wsub(d, a);
+    c = wadd(c, b) >> 1;
+    b = wsub(b, c);
+    a = wadd(a, c) >> 1;
+    c = wsub(c, a);
+    d = wadd(d, b) >> 1;
+    b = wsub(b, d);
+    d = wadd(d, b >> 1);
+    b = wsub(b, d >> 1);
+}
+
+OOCS_FN void lift_inv(int32_t &a, int32_t &b, int32_t &c, int32_t &d)
+{
+    b = wadd(b, d >> 1);
+    d = wsub(d, b >> 1);
+    b = wadd(b, d);
+    d = wsub(wdbl(d), b);
+    c = wadd(c, a);
+    a = wsub(wdbl(a), c);
+    b = wadd(b, c);
+    c = wsub(wdbl(c), b);
+    d = wadd(d, a);
+    a = wsub(wdbl(a), d);
+}
+
+OOCS_FN void xform_fwd(int32_t (&q)[64])
+{
+#pragma unroll
+    for (int l = 0; l < 16; ++l)  // x lines: (j, k) = (l & 3, l >> 2)
+        lift_fwd(q[4 * l + 0], q[4 * l + 1], q[4 * l + 2], q[4 * l + 3]);
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {  // y lines: (i, k) = (l & 3, l >> 2)
+        const int o = (l & 3) + 16 * (l >> 2);
+        lift_fwd(q[o + 0], q[o + 4], q[o + 8], q[o + 12]);
+    }
+#pragma unroll
+    for (int l = 0; l < 16; ++l)  // z lines: (i, j) = (l & 3, l >> 2)
+        lift_fwd(q[l + 0], q[l + 16], q[l + 32], q[l + 48]);
+}
+
+OOCS_FN void xform_inv(int32_t (&q)[64])
+{
+#pragma unroll
+    for (int l = 0; l < 16; ++l)
+        lift_inv(q[l + 0], q[l + 16], q[l + 32], q[l + 48]);
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        const int o = (l & 3) + 16 * (l >> 2);
+        lift_inv(q[o + 0], q[o + 4], q[o + 8], q[o + 12]);
+    }
+#pragma unroll
+    for (int l = 0; l < 16; ++l)
+        lift_inv(q[4 * l + 0], q[4 * l + 1], q[4 * l + 2], q[4 * l + 3]);
+}
+
+// In-place 32x32 bit-matrix transpose: afterwards bit i of a[p] is what bit p
+// of a[i] was.  Five block-swap levels (16, 8, 4, 2, 1).
+OOCS_FN void transpose32(uint32_t (&a)[32])
+{
+    uint32_t m = 0x0000FFFFu;
+#pragma unroll
+    for (int j = 16; j != 0; j >>= 1, m ^= (m << j)) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            if ((k & j) == 0) {
+                uint32_t t = ((a[k] >> j) ^ a[k + j]) & m;
+                a[k] ^= t << j;
+                a[k + j] ^= t;
+            }
+        }
+    }
+}
+
+OOCS_FN uint64_t low_mask64(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
+
+// ----------------------------------------------------------------- bit I/O --
+
+template <class Sink>
+struct BitWriter {
+    Sink &sink;
+    int nwords;
+    uint64_t acc = 0;
+    int nacc = 0;
+    int widx = 0;
+
+    OOCS_FN BitWriter(Sink &s, int nw) : sink(s), nwords(nw) {}
+
+    // append the low n bits of `bits`, n in [0, 32]
+    OOCS_FN void put(uint32_t bits, int n)
+    {
+        if (n < 32)
+            bits &= (1u << n) - 1u;
+        acc |= (uint64_t)bits << nacc;
+        nacc += n;
+        if (nacc >= 32) {
+            sink(widx++, (uint32_t)acc);
+            acc >>= 32;
+            nacc -= 32;
+        }
+    }
+    OOCS_FN void put64(uint64_t bits, int n)  // n in [0, 64]
+    {
+        if (n > 32) {
+            put((uint32_t)bits, 32);
+            put((uint32_t)(bits >> 32), n - 32);
+        } else {
+            put((uint32_t)bits, n);
+        }
+    }
+    OOCS_FN void finish()
+    {
+        if (nacc > 0)
+            sink(widx++, (uint32_t)acc);
+        while (widx < nwords)
+            sink(widx++, 0u);
+    }
+};
+
+template <class Src>
+struct BitReader {
+    Src &src;
+    uint64_t win = 0;
+    int nwin = 0;
+    int ridx = 0;
+
+    OOCS_FN explicit BitReader(Src &s) : src(s) {}
+    OOCS_FN void fill()
+    {
+        if (nwin < 32) {
+            win |= (uint64_t)src(ridx++) << nwin;
+            nwin += 32;
+        }
+    }
+    OOCS_FN uint32_t peek(int n)  // n in [1, 32]
+    {
+        fill();
+        uint32_t v = (uint32_t)win;
+        return n < 32 ? (v & ((1u << n) - 1u)) : v;
+    }
+    OOCS_FN void skip(int n)  // n in [0, 32]
+    {
+        fill();
+        win >>= n;
+        nwin -= n;
+    }
+    OOCS_FN uint32_t get(int n)  // n in [0, 32]
+    {
+        if (n == 0)
+            return 0;
+        uint32_t v = peek(n);
+        skip(n);
+        return v;
+    }
+    OOCS_FN uint64_t get64(int n)  // n in [0, 64]
+    {
+        if (n > 32) {
+            uint64_t lo = get(32);
+            return lo | ((uint64_t)get(n - 32) << 32);
+        }
+        return get(n);
+    }
+};
+
+// ------------------------------------------------------------------- codec --
+
+// Encode one block.  sink(word_index, word) receives words 0 .. 2*rate-1 in order.
+template <class Sink>
+OOCS_FN void encode_block(const float (&v)[64], int rate, Sink &&sink)
+{
+    const int nwords = 2 * rate;
+    uint32_t mag = 0;
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+        mag = max(mag, f32_bits(v[i]) & 0x7FFFFFFFu);
+    BitWriter<Sink> bw(sink, nwords);
+    if (mag == 0) {
+        bw.finish();
+        return;
+    }
+    // emax = max(biased - 126, -95); header = emax + 127
+    const int hdr = max((int)(mag >> 23), 31) + 1;
+    const int emax = hdr - 127;
+    const float scale = bits_f32((uint32_t)(156 - emax) << 23);  // 2^(29 - emax)
+
+    int32_t q[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+        q[i] = f2i_rz(fmul_rn(v[i], scale));
+    xform_fwd(q);
+
+    uint32_t lo[32], hi[32];  // negabinary coefficients in sequency order
+    static_for<0, 64>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const uint32_t u = ((uint32_t)q[kSeq<i>] + kNegaMask) ^ kNegaMask;
+        if constexpr (i < 32)
+            lo[i] = u;
+        else
+            hi[i - 32] = u;
+    });
+    transpose32(lo);  // lo[p] / hi[p]: plane p of coefficients 0..31 / 32..63
+    transpose32(hi);
+
+    bw.put((uint32_t)hdr, 8);
+    int left = 64 * rate - 8;
+    int n = 0;  // leading coefficients already significant
+    for (int p = 31; p >= 0 && left > 0; --p) {
+        const uint64_t X = ((uint64_t)hi[p] << 32) | lo[p];
+        const int t = min(n, left);
+        bw.put64(X, t);  // verbatim bits of the significant coefficients
+        left -= t;
+        if (t < n)
+            break;
+        while (n < 64 && left > 0) {
+            const uint64_t rest = X >> n;
+            if (rest == 0) {  // group test: nothing new in this plane
+                bw.put(0u, 1);
+                --left;
+                break;
+            }
+            bw.put(1u, 1);
+            --left;
+            const int f = n + ctz64(rest);  // next significant coefficient
+            // zeros for n .. f-1 then a one; at f = 63 the one is implied
+            const int len = (f < 63) ? (f - n + 1) : (63 - n);
+            const uint64_t code = (f < 63) ? (1ull << (f - n)) : 0ull;
+            if (len > left) {
+                bw.put64(code, left);
+                left = 0;
+                break;
+            }
+            bw.put64(code, len);
+            left -= len;
+            n = f + 1;
+        }
+    }
+    bw.finish();
+}
+
+// Decode one block.  src(word_index) returns word i of the block (0 past the end).
+template <class Src>
+OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64])
+{
+    const uint32_t w0 = src(0);
+    const int hdr = (int)(w0 & 0xFFu);
+    if (hdr == 0) {
+#pragma unroll
+        for (int i = 0; i < 64; ++i)
+            v[i] = 0.0f;
+        return;
+    }
+    const int emax = hdr - 127;
+    BitReader<Src> br(src);
+    br.skip(8);
+
+    uint32_t lo[32], hi[32];
+#pragma unroll
+    for (int p = 0; p < 32; ++p) {
+        lo[p] = 0u;
+        hi[p] = 0u;
+    }
+    int left = 64 * rate - 8;
+    int n = 0;
+    for (int p = 31; p >= 0 && left > 0; --p) {
+        const int t = min(n, left);
+        uint64_t X = br.get64(t);
+        left -= t;
+        if (t == n) {
+            while (n < 64 && left > 0) {
+                const uint32_t g = br.get(1);
+                --left;
+                if (!g)
+                    break;
+                const int lim = 63 - n;  // zeros possible before the implied last one
+                const int avail = min(lim, left);
+                int z = 0;
+                bool found = false;
+                while (z < avail) {
+                    const int c = min(32, avail - z);
+                    const uint32_t w = br.peek(c);
+                    if (w) {
+                        const int o = ctz32(w);
+                        br.skip(o + 1);
+                        z += o;
+                        found = true;
+                        break;
+                    }
+                    br.skip(c);
+                    z += c;
+                }
+                if (found) {
+                    left -= z + 1;
+                    X |= 1ull << (n + z);
+                    n += z + 1;
+                } else {
+                    left -= z;
+                    if (z == lim) {
+                        X |= 1ull << 63;
+                        n = 64;
+                    }
+                }
+            }
+        }
+        lo[p] = (uint32_t)X;
+        hi[p] = (uint32_t)(X >> 32);
+    }
+    transpose32(lo);  // back to coefficient words
+    transpose32(hi);
+
+    int32_t q[64];
+    static_for<0, 64>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const uint32_t u = (i < 32) ? lo[i & 31] : hi[i & 31];
+        q[kSeq<i>] = (int32_t)((u ^ kNegaMask) - kNegaMask);
+    });
+    xform_inv(q);
+    const float scale = bits_f32((uint32_t)(98 + emax) << 23);  // 2^(emax - 29)
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+        v[i] = fmul_rn(i2f_rn(q[i]), scale);
+}
+
+}  // namespace oocs

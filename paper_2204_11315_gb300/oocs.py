@@ -1,0 +1,301 @@
+"""ctypes binding of include/oocs.h (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and does no
+arithmetic of its own: all work runs in liboocs.so's CUDA kernels.  There is no
+CPU fallback: if the library is missing, ``lib()`` raises.
+
+PyTorch is used only as plumbing by the ``OutOfCoreStencil`` helper: device
+workspace (``torch.empty(..., device='cuda')``), page-locked host stores
+(``pin_memory=True``) and the three CUDA streams the pipeline runs on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OOCS_OK = 0
+STATUS_NAMES = {0: "OOCS_OK", 1: "OOCS_ERR_INVALID_ARG", 2: "OOCS_ERR_BUDGET",
+                3: "OOCS_ERR_HOST_ALLOC", 4: "OOCS_ERR_CUDA", 5: "OOCS_ERR_TIMEOUT",
+                6: "OOCS_ERR_STATE", 7: "OOCS_ERR_UNSUPPORTED"}
+OOCS_HEAT, OOCS_WAVE = 0, 1
+OOCS_FIELD_U, OOCS_FIELD_U_PREV, OOCS_FIELD_M = 0, 1, 2
+OOCS_SWB, OOCS_CLASSIC = 1, 3
+MAX_RADIUS = 4
+
+
+class OOCSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class oocs_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("scheme", ctypes.c_int32), ("radius", ctypes.c_int32),
+                ("coef", ctypes.c_float * (MAX_RADIUS + 1)),
+                ("device_budget", ctypes.c_uint64), ("rate_bits", ctypes.c_int32),
+                ("temporal_depth", ctypes.c_int32), ("slab_planes", ctypes.c_int32),
+                ("working_buffers", ctypes.c_int32)]
+
+
+class oocs_plan(ctypes.Structure):
+    _fields_ = [("slab_planes", ctypes.c_int32), ("temporal_depth", ctypes.c_int32),
+                ("halo_planes", ctypes.c_int32), ("num_slabs", ctypes.c_int32),
+                ("window_planes", ctypes.c_int32), ("fields_in", ctypes.c_int32),
+                ("fields_out", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("layer_bytes", ctypes.c_uint64), ("host_store_bytes", ctypes.c_uint64),
+                ("workspace_bytes", ctypes.c_uint64), ("workspace_swb_bytes", ctypes.c_uint64),
+                ("workspace_classic_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class oocs_stats(ctypes.Structure):
+    _fields_ = [("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64), ("steps_done", ctypes.c_uint64),
+                ("passes_done", ctypes.c_uint64), ("slabs_done", ctypes.c_uint64),
+                ("workspace_bytes", ctypes.c_uint64), ("last_step_ms", ctypes.c_float),
+                ("reserved_f", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved_f"}
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+
+# name -> (restype, argtypes); the C-ABI of include/oocs.h
+SIGNATURES = {
+    "oocs_version": (ctypes.c_char_p, []),
+    "oocs_query": (_i32, [ctypes.POINTER(oocs_desc), ctypes.POINTER(oocs_plan)]),
+    "oocs_create": (_i32, [ctypes.POINTER(oocs_desc), _vp, _u64, ctypes.POINTER(_vp),
+                           ctypes.POINTER(_vp)]),
+    "oocs_bind_field": (_i32, [_vp, _i32, _vp, _u64]),
+    "oocs_set_source": (_i32, [_vp, _i64, _i64, _i64, _vp, _i32]),
+    "oocs_compress": (_i32, [_vp, _i32, _vp]),
+    "oocs_decompress": (_i32, [_vp, _i32, _vp]),
+    "oocs_step": (_i32, [_vp, _i32]),
+    "oocs_synchronize": (_i32, [_vp, _u64]),
+    "oocs_get_stats": (_i32, [_vp, ctypes.POINTER(oocs_stats)]),
+    "oocs_last_error": (ctypes.c_char_p, [_vp]),
+    "oocs_destroy": (_i32, [_vp]),
+    "oocs_incore_run": (_i32, [ctypes.POINTER(oocs_desc), _vp, _vp, _vp, _vp, _i32, _i64, _vp, _vp,
+                               _i32, _vp]),
+    "oocs_encode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
+    "oocs_decode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load liboocs.so (building it in-tree with nvcc if absent).  Raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path) or not _build.up_to_date():
+                if not build_if_missing:
+                    raise RuntimeError(f"CUDA library {path} is not built")
+                _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, ctx=None):
+    if status != OOCS_OK:
+        msg = lib().oocs_last_error(ctx)
+        raise OOCSError(status, msg.decode() if msg else "")
+
+
+def make_desc(nx, ny, nz, scheme, coef, device_budget, rate_bits=0, temporal_depth=0,
+              slab_planes=0, working_buffers=OOCS_SWB, radius=None) -> oocs_desc:
+    coef = [float(c) for c in coef]
+    d = oocs_desc()
+    d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
+    d.scheme = int(scheme)
+    d.radius = int(radius if radius is not None else len(coef) - 1)
+    for i, c in enumerate(coef):
+        d.coef[i] = c
+    d.device_budget = int(device_budget)
+    d.rate_bits = int(rate_bits)
+    d.temporal_depth = int(temporal_depth)
+    d.slab_planes = int(slab_planes)
+    d.working_buffers = int(working_buffers)
+    return d
+
+
+# ---------------------------------------------------------------- C ABI --
+
+def oocs_version() -> str:
+    return lib().oocs_version().decode()
+
+
+def oocs_query(desc: oocs_desc) -> oocs_plan:
+    p = oocs_plan()
+    _check(lib().oocs_query(ctypes.byref(desc), ctypes.byref(p)))
+    return p
+
+
+def oocs_create(desc: oocs_desc, workspace_ptr: int, workspace_bytes: int, streams) -> int:
+    arr = (_vp * 3)(*[int(s) for s in streams])
+    out = _vp()
+    _check(lib().oocs_create(ctypes.byref(desc), _vp(workspace_ptr), workspace_bytes, arr,
+                             ctypes.byref(out)))
+    return out.value
+
+
+def oocs_bind_field(ctx: int, field: int, host_ptr: int, nbytes: int):
+    _check(lib().oocs_bind_field(ctx, field, _vp(host_ptr), nbytes), ctx)
+
+
+def oocs_set_source(ctx: int, x: int, y: int, z: int, w: np.ndarray):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    _check(lib().oocs_set_source(ctx, x, y, z, w.ctypes.data_as(_vp), int(w.size)), ctx)
+
+
+def oocs_compress(ctx: int, field: int, src_ptr: int):
+    _check(lib().oocs_compress(ctx, field, _vp(src_ptr)), ctx)
+
+
+def oocs_decompress(ctx: int, field: int, dst_ptr: int):
+    _check(lib().oocs_decompress(ctx, field, _vp(dst_ptr)), ctx)
+
+
+def oocs_step(ctx: int, nsteps: int):
+    _check(lib().oocs_step(ctx, int(nsteps)), ctx)
+
+
+def oocs_synchronize(ctx: int, timeout_ns: int = 0):
+    _check(lib().oocs_synchronize(ctx, int(timeout_ns)), ctx)
+
+
+def oocs_get_stats(ctx: int) -> oocs_stats:
+    s = oocs_stats()
+    _check(lib().oocs_get_stats(ctx, ctypes.byref(s)), ctx)
+    return s
+
+
+def oocs_last_error(ctx=None) -> str:
+    return lib().oocs_last_error(ctx).decode()
+
+
+def oocs_destroy(ctx: int):
+    _check(lib().oocs_destroy(ctx))
+
+
+def oocs_incore_run(desc, u_ptr, up_ptr, m_ptr, scratch_ptr, nsteps, t0=0, src=None, w=None,
+                    stream=0):
+    srcarr = (_i64 * 3)(*src) if src is not None else None
+    wv = np.ascontiguousarray(w if w is not None else np.zeros(0), dtype=np.float32)
+    _check(lib().oocs_incore_run(ctypes.byref(desc), _vp(u_ptr), _vp(up_ptr), _vp(m_ptr),
+                                 _vp(scratch_ptr), int(nsteps), int(t0),
+                                 ctypes.cast(srcarr, _vp) if srcarr is not None else None,
+                                 wv.ctypes.data_as(_vp), int(wv.size), _vp(stream)))
+
+
+def oocs_encode_device(field_ptr, nx, ny, nz, rate, blocks_ptr, stream=0):
+    _check(lib().oocs_encode_device(_vp(field_ptr), nx, ny, nz, rate, _vp(blocks_ptr), _vp(stream)))
+
+
+def oocs_decode_device(blocks_ptr, nx, ny, nz, rate, field_ptr, stream=0):
+    _check(lib().oocs_decode_device(_vp(blocks_ptr), nx, ny, nz, rate, _vp(field_ptr), _vp(stream)))
+
+
+# ------------------------------------------------- torch-plumbed helper --
+
+class OutOfCoreStencil:
+    """A context plus the memory it needs, allocated through PyTorch.
+
+    Device workspace: one ``torch.uint8`` CUDA tensor of plan.workspace_bytes.
+    Host stores: one pinned ``torch.uint8`` tensor per streamed field.
+    Streams: three ``torch.cuda.Stream`` objects.
+    """
+
+    def __init__(self, desc: oocs_desc, device: int = 0):
+        import torch
+        self.torch = torch
+        self.desc = desc
+        self.plan = oocs_query(desc)
+        self.device = torch.device("cuda", device)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.plan.workspace_bytes + 256, dtype=torch.uint8,
+                                         device=self.device)
+            base = self.workspace.data_ptr()
+            self._ws_ptr = (base + 255) // 256 * 256
+            self.streams = [torch.cuda.Stream(device=self.device) for _ in range(3)]
+            self.ctx = oocs_create(desc, self._ws_ptr, self.plan.workspace_bytes,
+                                   [s.cuda_stream for s in self.streams])
+        nfields = 3 if desc.scheme == OOCS_WAVE else 1
+        self.stores = []
+        for f in range(nfields):
+            st = torch.zeros(self.plan.host_store_bytes, dtype=torch.uint8, pin_memory=True)
+            oocs_bind_field(self.ctx, f, st.data_ptr(), st.numel())
+            self.stores.append(st)
+        self._keep = []
+
+    @property
+    def shape(self):
+        return (self.desc.nz, self.desc.ny, self.desc.nx)
+
+    def pinned_field(self):
+        return self.torch.empty(self.shape, dtype=self.torch.float32, pin_memory=True)
+
+    def set_source(self, x, y, z, w):
+        oocs_set_source(self.ctx, x, y, z, w)
+
+    def compress(self, field: int, src):
+        """src: pinned FP32 torch tensor (or numpy array, copied into pinned memory)."""
+        t = src
+        if not hasattr(t, "data_ptr"):
+            t = self.pinned_field()
+            t.numpy()[...] = np.asarray(src, dtype=np.float32)
+        assert t.dtype == self.torch.float32 and t.is_contiguous() and t.numel() == np.prod(self.shape)
+        self._keep.append(t)
+        oocs_compress(self.ctx, field, t.data_ptr())
+
+    def decompress(self, field: int, dst=None):
+        if dst is None:
+            dst = self.pinned_field()
+        oocs_decompress(self.ctx, field, dst.data_ptr())
+        self._keep.append(dst)
+        return dst
+
+    def step(self, nsteps: int):
+        oocs_step(self.ctx, nsteps)
+
+    def synchronize(self, timeout_s: float = 0.0):
+        oocs_synchronize(self.ctx, int(timeout_s * 1e9))
+        self._keep.clear()
+
+    def stats(self) -> dict:
+        return oocs_get_stats(self.ctx).as_dict()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            oocs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -186,3 +186,13 @@ def blocks_field(shape, seed: int, kind: str) -> np.ndarray:
     if kind == "huge":
         return ((2.0 * u - 1.0) * 3e38).astype(np.float32)
     raise ValueError(kind)
+
+
+# ----------------------------------------------------------------------------
+# Accuracy bar of each workload (relative L2 error against the FP64 oracle),
+# fixed before any timed run.  Uncompressed FP32 runs: 1e-6 (heat), 1e-5
+# (wave).  Compressed: per codec rate in bits/value.
+# ----------------------------------------------------------------------------
+
+TOL_UNCOMPRESSED = {"heat": 1e-6, "wave": 1e-5}
+TOL_COMPRESSED = {16: 1e-4, 12: 2e-3, 8: 3e-2}

@@ -1,0 +1,151 @@
+"""Out-of-core slab streaming (oocs_step) on the GPU.
+
+Uncompressed: the slab-streamed run (z-slabs, temporal blocking with halo
+h = 4 ceil(k r / 4), region sharing, single working buffer; Sec. 3.1, Sec. 5,
+Algorithm 1) must be bit-exact against the in-core GPU run of the same FP32
+arithmetic.  Compressed (Sec. 4): within the per-rate bar of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from gpu_util import heat_desc, incore, rel_l2, streamed, wave_desc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2204_11315_gb300 as P
+    P.lib()
+    return P
+
+
+# ------------------------------------------------------------- heat ------
+
+@pytest.mark.parametrize("k", [1, 2, 5])
+@pytest.mark.parametrize("wb", [1, 3])
+def test_heat_streamed_bitexact_vs_incore(P, k, wb):
+    u0 = synthetic.heat_initial(128)
+    desc = heat_desc(P, u0.shape, rate=0, k=k, T=32, wb=wb)
+    ref = incore(P, desc, u0, 10)
+    got, _, _, stats, plan = streamed(P, desc, u0, 10)
+    assert plan.num_slabs == 4
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    # region sharing: every layer crosses the link once per sweep in each direction
+    passes = -(-10 // k)
+    assert stats["passes_done"] == passes
+    assert stats["h2d_bytes"] == passes * plan.host_store_bytes
+    assert stats["d2h_bytes"] == passes * plan.host_store_bytes
+
+
+@pytest.mark.parametrize("shape,T,k", [((120, 52, 44), 32, 3), ((64, 36, 100), 8, 2),
+                                       ((40, 16, 24), 64, 4)])
+def test_heat_ragged_slabs_bitexact(P, shape, T, k):
+    """Last slab thinner than T, x-y sizes off the tile grid, one-slab case."""
+    u0 = synthetic.uniform_field(shape, 5)
+    desc = heat_desc(P, shape, rate=0, k=k, T=T, alpha=0.12)
+    ref = incore(P, desc, u0, 7)
+    got, _, _, _, _ = streamed(P, desc, u0, 7, chunks=[3, 4])
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("rate", [16, 12, 8])
+def test_heat_compressed_within_tolerance(P, orc, rate):
+    u0 = synthetic.heat_initial(128)
+    desc = heat_desc(P, u0.shape, rate=rate, k=1, T=32)
+    got, _, stores, stats, plan = streamed(P, desc, u0, 10)
+    ref = orc.heat_run(u0, synthetic.heat_star_coef(0.1), 10)
+    assert rel_l2(got, ref) <= synthetic.TOL_COMPRESSED[rate]
+    # fixed rate: exactly rate bits per value in the store and over the link
+    assert plan.host_store_bytes == u0.size * rate // 8
+    assert stats["h2d_bytes"] == 10 * plan.host_store_bytes
+
+
+def test_compress_matches_reference_codec(P, orc):
+    """oocs_compress writes exactly the reference codec's bytes into the host store."""
+    u0 = synthetic.heat_initial(128)
+    desc = heat_desc(P, u0.shape, rate=16, k=1, T=32)
+    st = P.OutOfCoreStencil(desc)
+    try:
+        st.compress(P.OOCS_FIELD_U, u0)
+        st.synchronize(60.0)
+        got = st.stores[0].numpy().view(np.uint32).copy()
+        back = st.decompress(P.OOCS_FIELD_U)
+        st.synchronize(60.0)
+        back = back.numpy().copy()
+    finally:
+        st.close()
+    ref = orc.encode_field(u0, 16)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(back.view(np.uint32), orc.decode_field(ref, u0.shape, 16).view(np.uint32))
+
+
+# ------------------------------------------------------------- wave ------
+
+def _wave_inputs(shape, steps):
+    m = synthetic.wave_model(shape)
+    w = synthetic.ricker(steps)
+    cz, cy, cx = synthetic.centre(shape)
+    z = np.zeros(shape, np.float32)
+    return m, w, (cx, cy, cz), z
+
+
+@pytest.mark.parametrize("shape,T,k,wb", [((128, 72, 40), 32, 4, 1), ((128, 72, 40), 32, 4, 3),
+                                          ((96, 48, 64), 24, 3, 1), ((80, 40, 40), 16, 1, 1)])
+def test_wave_streamed_bitexact_vs_incore(P, shape, T, k, wb):
+    steps = 10
+    m, w, src, z = _wave_inputs(shape, steps)
+    desc = wave_desc(P, shape, rate=0, k=k, T=T, wb=wb)
+    ru, rup = incore(P, desc, z, steps, up0=z, m=m, src=src, w=w)
+    gu, gup, _, stats, plan = streamed(P, desc, z, steps, up0=z, m=m, src=src, w=w)
+    assert np.array_equal(gu.view(np.uint32), ru.view(np.uint32))
+    assert np.array_equal(gup.view(np.uint32), rup.view(np.uint32))
+    passes = -(-steps // k)
+    assert stats["h2d_bytes"] == 3 * passes * plan.host_store_bytes
+    assert stats["d2h_bytes"] == 2 * passes * plan.host_store_bytes
+
+
+def test_wave_split_calls_bitexact(P):
+    """Several oocs_step calls continue the source time index and the state."""
+    shape = (96, 40, 48)
+    steps = 11
+    m, w, src, z = _wave_inputs(shape, steps)
+    desc = wave_desc(P, shape, rate=0, k=4, T=32)
+    ru, rup = incore(P, desc, z, steps, up0=z, m=m, src=src, w=w)
+    gu, gup, _, _, _ = streamed(P, desc, z, steps, up0=z, m=m, src=src, w=w, chunks=[5, 2, 4])
+    assert np.array_equal(gu.view(np.uint32), ru.view(np.uint32))
+    assert np.array_equal(gup.view(np.uint32), rup.view(np.uint32))
+
+
+@pytest.mark.parametrize("rate", [16, 12, 8])
+def test_wave_compressed_within_tolerance(P, orc, rate):
+    shape = (128, 128, 128)
+    steps = 100
+    m, w, src, z = _wave_inputs(shape, steps)
+    desc = wave_desc(P, shape, rate=rate, k=4, T=32)
+    gu, gup, _, _, _ = streamed(P, desc, z, steps, up0=z, m=m, src=src, w=w)
+    ru, rup = orc.wave_run(z, z, m, synthetic.wave_star_coef(), steps,
+                           src=synthetic.centre(shape), w=w)
+    assert rel_l2(gu, ru) <= synthetic.TOL_COMPRESSED[rate]
+    assert rel_l2(gup, rup) <= synthetic.TOL_COMPRESSED[rate]
+
+
+def test_wave_full_size_uncompressed_bitexact(P):
+    """The benchmark workload's grid and plan (512^3, 8 slabs of 64, k = 4), uncompressed."""
+    shape = (512, 512, 512)
+    steps = 12
+    m, w, src, z = _wave_inputs(shape, steps)
+    desc = wave_desc(P, shape, rate=0, k=4, T=64, budget=4 << 30)
+    ru, rup = incore(P, desc, z, steps, up0=z, m=m, src=src, w=w)
+    gu, gup, _, _, plan = streamed(P, desc, z, steps, up0=z, m=m, src=src, w=w)
+    assert plan.num_slabs == 8 and plan.workspace_bytes <= 4 << 30
+    assert np.array_equal(gu.view(np.uint32), ru.view(np.uint32))
+    assert np.array_equal(gup.view(np.uint32), rup.view(np.uint32))
+
+
+def test_budget_too_small(P):
+    desc = wave_desc(P, (128, 128, 128), rate=16, k=4, T=0, budget=1 << 20)
+    with pytest.raises(P.OOCSError) as e:
+        P.oocs_query(desc)
+    assert e.value.status == 2
