@@ -436,7 +436,11 @@ int oracle_decode_block(const uint32_t *words, int rate, float *v)
             v[i] = 0.0f;
         return CODEC_PLANES;
     }
+    /* the encoder never writes headers 1..31 (emax is clamped to >= -95); a
+     * decoder given one applies the same clamp                               */
     int emax = hdr - 127;
+    if (emax < CODEC_EMIN)
+        emax = CODEC_EMIN;
     uint32_t u[64];
     int low = oracle_decode_planes(words, 8, 64 * rate - 8, u);
     int perm[64];
