@@ -329,7 +329,7 @@ OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64])
             v[i] = 0.0f;
         return;
     }
-    const int emax = hdr - 127;
+    const int emax = max(hdr, 32) - 127;  // headers 1..31 are never written: clamp as the encoder does
     BitReader<Src> br(src);
     br.skip(8);
 
