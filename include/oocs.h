@@ -93,6 +93,19 @@ typedef struct {
     uint64_t workspace_classic_bytes; /* same plan with three working buffers               */
 } oocs_plan;
 
+/* Per kernel class counters.  `units` are grid values processed: for LOAD the
+ * values decoded (or copied) into the working buffer, for STEP the points
+ * updated (including the redundant halo recomputation of temporal blocking),
+ * for STORE the values encoded (or copied) out of it.  `device_ms` is the sum
+ * of CUDA-event durations of those launches on their own streams, collected
+ * only while profiling is on (oocs_set_profiling) and read at
+ * oocs_synchronize.                                                        */
+typedef struct {
+    uint64_t launches;
+    uint64_t units;
+    double device_ms;
+} oocs_kernel_stats;
+
 typedef struct {
     uint64_t h2d_bytes;          /* bytes copied host->device by oocs_step so far            */
     uint64_t d2h_bytes;          /* bytes copied device->host by oocs_step so far            */
@@ -101,8 +114,10 @@ typedef struct {
     uint64_t passes_done;        /* slab sweeps enqueued so far                              */
     uint64_t slabs_done;         /* slab visits enqueued so far                              */
     uint64_t workspace_bytes;    /* device bytes the context uses                            */
-    float last_step_ms;          /* device time of the last completed oocs_step (events)    */
-    float reserved_f;
+    double last_step_ms;         /* device time of the last completed oocs_step (events)    */
+    oocs_kernel_stats load;      /* decode / copy of staged layers into the working buffer  */
+    oocs_kernel_stats step;      /* stencil time steps                                       */
+    oocs_kernel_stats store;     /* encode / copy of the slab interior out of it            */
 } oocs_stats;
 
 typedef struct oocs_ctx oocs_ctx;
@@ -156,6 +171,10 @@ oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps);
 oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns);
 
 oocs_status oocs_get_stats(const oocs_ctx *ctx, oocs_stats *out);
+
+/* Turn per-launch event timing of the kernels enqueued by oocs_step on (1) or
+ * off (0).  Adds two event records per kernel on its own stream.           */
+oocs_status oocs_set_profiling(oocs_ctx *ctx, int32_t enable);
 
 /* Text of the last error of ctx, or of the last failed context-free call in
  * this thread when ctx is NULL.  Never NULL; valid until the next call.    */

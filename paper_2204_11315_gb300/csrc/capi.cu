@@ -260,6 +260,16 @@ struct oocs_ctx {
 
     uint64_t g = 0;  // slab visits enqueued
     oocs_stats stats;
+
+    // per-launch event timing (oocs_set_profiling)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;  // created on demand, reused after collection
+    size_t ev_used = 0;
+    struct Pending {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
     oocs_status sticky = OOCS_OK;
     std::string err = "no error";
 
@@ -318,6 +328,71 @@ oocs_status check_ready(oocs_ctx *c)
     return OOCS_OK;
 }
 
+enum { kClsLoad = 0, kClsStep = 1, kClsStore = 2 };
+
+oocs_kernel_stats &cls_stats(oocs_ctx *c, int cls)
+{
+    return cls == kClsLoad ? c->stats.load : (cls == kClsStep ? c->stats.step : c->stats.store);
+}
+
+oocs_status take_event(oocs_ctx *c, cudaEvent_t *e)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t n = nullptr;
+        CU(c, cudaEventCreate(&n));
+        c->ev_pool.push_back(n);
+    }
+    *e = c->ev_pool[c->ev_used++];
+    return OOCS_OK;
+}
+
+// Bracket one kernel (or device copy) of class `cls` on stream s: counts it
+// and, while profiling, records events around it.
+struct KernelScope {
+    oocs_ctx *c;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    oocs_status begin(oocs_ctx *cc, cudaStream_t ss)
+    {
+        c = cc;
+        s = ss;
+        if (!c->prof)
+            return OOCS_OK;
+        oocs_status r = take_event(c, &a);
+        if (r != OOCS_OK)
+            return r;
+        CU(c, cudaEventRecord(a, s));
+        return OOCS_OK;
+    }
+    oocs_status end(int cls, uint64_t units)
+    {
+        oocs_kernel_stats &k = cls_stats(c, cls);
+        k.launches++;
+        k.units += units;
+        if (!a)
+            return OOCS_OK;
+        cudaEvent_t b;
+        oocs_status r = take_event(c, &b);
+        if (r != OOCS_OK)
+            return r;
+        CU(c, cudaEventRecord(b, s));
+        c->pending.push_back({cls, a, b});
+        return OOCS_OK;
+    }
+};
+
+// fold the durations of completed profiled launches into the stats
+void collect_profile(oocs_ctx *c)
+{
+    for (const auto &p : c->pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+            cls_stats(c, p.cls).device_ms += ms;
+    }
+    c->pending.clear();
+    c->ev_used = 0;
+}
+
 // Copy (rate 0) or decode (rate > 0) layers [l0, l1) held in staging memory
 // `src` (whose first layer is src_l0) into window buffer `dst` (first plane w0).
 oocs_status load_layers(oocs_ctx *c, const char *src, int64_t src_l0, int64_t l0, int64_t l1,
@@ -327,13 +402,17 @@ oocs_status load_layers(oocs_ctx *c, const char *src, int64_t src_l0, int64_t l0
         return OOCS_OK;
     const char *from = src + (l0 - src_l0) * c->v.layer_bytes;
     float *to = dst + (4 * l0 - w0) * c->d.nx * c->d.ny;
+    KernelScope ks;
+    oocs_status r = ks.begin(c, s);
+    if (r != OOCS_OK)
+        return r;
     if (c->d.rate_bits == 0) {
         CU(c, cudaMemcpyAsync(to, from, (l1 - l0) * c->v.layer_bytes, cudaMemcpyDeviceToDevice, s));
     } else {
         CU(c, launch_decode_layers(from, c->d.nx, c->d.ny, l1 - l0, c->d.rate_bits, to, s));
         c->stats.kernel_launches++;
     }
-    return OOCS_OK;
+    return ks.end(kClsLoad, (uint64_t)(l1 - l0) * 4 * c->d.nx * c->d.ny);
 }
 
 // Copy (rate 0) or encode (rate > 0) window planes of layers [l0, l1) into `dst`.
@@ -343,13 +422,17 @@ oocs_status store_layers(oocs_ctx *c, const float *src, int64_t w0, int64_t l0, 
     if (l1 <= l0)
         return OOCS_OK;
     const float *from = src + (4 * l0 - w0) * c->d.nx * c->d.ny;
+    KernelScope ks;
+    oocs_status r = ks.begin(c, s);
+    if (r != OOCS_OK)
+        return r;
     if (c->d.rate_bits == 0) {
         CU(c, cudaMemcpyAsync(dst, from, (l1 - l0) * c->v.layer_bytes, cudaMemcpyDeviceToDevice, s));
     } else {
         CU(c, launch_encode_layers(from, c->d.nx, c->d.ny, l1 - l0, c->d.rate_bits, dst, s));
         c->stats.kernel_launches++;
     }
-    return OOCS_OK;
+    return ks.end(kClsStore, (uint64_t)(l1 - l0) * 4 * c->d.nx * c->d.ny);
 }
 
 // Enqueue one slab visit (slab s, k_eff steps starting at global time t).
@@ -445,8 +528,15 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             Ls.src_z = c->src[2];
             Ls.w = c->w[tstep];
         }
+        KernelScope ks;
+        oocs_status r = ks.begin(c, st);
+        if (r != OOCS_OK)
+            return r;
         CU(c, launch_star_step(Ls, st));
         c->stats.kernel_launches++;
+        r = ks.end(kClsStep, (uint64_t)(hi - lo) * d.nx * d.ny);
+        if (r != OOCS_OK)
+            return r;
         std::swap(cur, oth);
     }
     // 7. interior [z0, z1) -> out slot(s): u^(t+k) and, for the wave, u^(t+k-1)
@@ -732,6 +822,7 @@ oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns)
             ctx->stats.last_step_ms = ms;
         ctx->timing_pending = false;
     }
+    collect_profile(ctx);
     return OOCS_OK;
 }
 
@@ -740,6 +831,15 @@ oocs_status oocs_get_stats(const oocs_ctx *ctx, oocs_stats *out)
     if (!ctx || !out)
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "ctx or out is NULL");
     *out = ctx->stats;
+    return OOCS_OK;
+}
+
+oocs_status oocs_set_profiling(oocs_ctx *ctx, int32_t enable)
+{
+    oocs_status s = check_ready(ctx);
+    if (s != OOCS_OK)
+        return s;
+    ctx->prof = enable != 0;
     return OOCS_OK;
 }
 
@@ -767,6 +867,8 @@ oocs_status oocs_destroy(oocs_ctx *ctx)
         kill(ctx->ev_join[i]);
     }
     for (auto &e : ctx->ev_d2h)
+        kill(e);
+    for (auto &e : ctx->ev_pool)
         kill(e);
     kill(ctx->ev_t0);
     kill(ctx->ev_t1);

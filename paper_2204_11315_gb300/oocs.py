@@ -56,15 +56,28 @@ class oocs_plan(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class oocs_kernel_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("units", ctypes.c_uint64),
+                ("device_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class oocs_stats(ctypes.Structure):
     _fields_ = [("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("steps_done", ctypes.c_uint64),
                 ("passes_done", ctypes.c_uint64), ("slabs_done", ctypes.c_uint64),
-                ("workspace_bytes", ctypes.c_uint64), ("last_step_ms", ctypes.c_float),
-                ("reserved_f", ctypes.c_float)]
+                ("workspace_bytes", ctypes.c_uint64), ("last_step_ms", ctypes.c_double),
+                ("load", oocs_kernel_stats), ("step", oocs_kernel_stats),
+                ("store", oocs_kernel_stats)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved_f"}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = v.as_dict() if isinstance(v, oocs_kernel_stats) else v
+        return d
 
 
 _vp = ctypes.c_void_p
@@ -85,6 +98,7 @@ SIGNATURES = {
     "oocs_step": (_i32, [_vp, _i32]),
     "oocs_synchronize": (_i32, [_vp, _u64]),
     "oocs_get_stats": (_i32, [_vp, ctypes.POINTER(oocs_stats)]),
+    "oocs_set_profiling": (_i32, [_vp, _i32]),
     "oocs_last_error": (ctypes.c_char_p, [_vp]),
     "oocs_destroy": (_i32, [_vp]),
     "oocs_incore_run": (_i32, [ctypes.POINTER(oocs_desc), _vp, _vp, _vp, _vp, _i32, _i64, _vp, _vp,
@@ -194,6 +208,10 @@ def oocs_get_stats(ctx: int) -> oocs_stats:
     return s
 
 
+def oocs_set_profiling(ctx: int, enable: bool):
+    _check(lib().oocs_set_profiling(ctx, 1 if enable else 0), ctx)
+
+
 def oocs_last_error(ctx=None) -> str:
     return lib().oocs_last_error(ctx).decode()
 
@@ -285,6 +303,9 @@ class OutOfCoreStencil:
     def synchronize(self, timeout_s: float = 0.0):
         oocs_synchronize(self.ctx, int(timeout_s * 1e9))
         self._keep.clear()
+
+    def set_profiling(self, enable: bool = True):
+        oocs_set_profiling(self.ctx, enable)
 
     def stats(self) -> dict:
         return oocs_get_stats(self.ctx).as_dict()
