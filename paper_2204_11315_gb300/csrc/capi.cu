@@ -816,6 +816,11 @@ oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns)
         if (e != cudaSuccess && e != cudaErrorNotReady)
             return fail(ctx, OOCS_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
     }
+    unsigned int code = 0;
+    CU(ctx, read_device_error(&code, true));
+    if (code)
+        return fail(ctx, OOCS_ERR_CUDA, "a kernel's bounded wait ran out (device error " +
+                                            std::to_string(code) + ")");
     if (ctx->timing_pending) {
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, ctx->ev_t0, ctx->ev_t1) == cudaSuccess)

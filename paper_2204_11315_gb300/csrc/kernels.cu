@@ -2,141 +2,309 @@
 //
 // Stencil step (Sec. 3.1, Sec. 6 25-point acoustic code): a 2.5D z-march.  A
 // CTA owns a 32 x 16 tile of the x-y plane and walks its share of the z range.
-// Each thread keeps the 2R+1 values u(z-R .. z+R) of its two columns in a
-// register queue (one coalesced load per plane), and the x-y neighbours of
-// plane z come from a (16+2R) x (32+2R) shared-memory tile.  Nothing here is a
-// dense contraction, so the kernel is HBM-bound and uses no tensor cores.
+// The u planes (with their x-y halo) arrive by TMA into a shared-memory ring
+// several planes ahead of use; each thread keeps u(z-R .. z+R) of its four
+// points in a register queue.  Nothing here is a dense contraction, so the
+// kernel is HBM-bound and uses no tensor cores.
 //
 // Codec (Sec. 4.2): one thread per 4x4x4 block; 16 float4 loads per block
 // (consecutive threads read consecutive blocks of a row: coalesced).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "codec.cuh"
 #include "kernels.h"
 #include "stencil.cuh"
+#include "tma.cuh"
 
 namespace oocs {
 
-constexpr int kTX = 32;
-constexpr int kTY = 16;
-constexpr int kRows = 2;  // rows per thread: ty and ty + kTY/kRows
-constexpr int kStepThreads = kTX * (kTY / kRows);
+constexpr int kTX = 32;                 // tile width (x)
+constexpr int kTY = 16;                 // tile height (y)
+constexpr int kRPT = 4;                 // consecutive rows per thread
+constexpr int kStepThreads = kTX * (kTY / kRPT);  // 128
+constexpr int kBoxW = kTX + 8;          // u tile loaded from x0-4 (16-byte aligned) to x0+36
+
+template <int R>
+struct StepCfg {
+    static constexpr int H = kTY + 2 * R;                       // u tile rows
+    static constexpr uint32_t kUBytes = H * kBoxW * 4;          // one TMA box of u
+    static constexpr int kUStage = ((kUBytes + 127) / 128 * 128) / 4;  // floats per ring stage
+    static constexpr int NSU = 2 * R + 4;                       // u ring stages
+    static constexpr int NSC = 6;                               // prev / m ring stages
+    static constexpr int kCStage = kTX * kTY;                   // floats per prev / m stage
+    static constexpr uint32_t kCBytes = kCStage * 4;
+    static constexpr size_t smem_bytes(bool wave)
+    {
+        return 128 + (size_t)NSU * kUStage * 4 + (wave ? 2ull * NSC * kCStage * 4 : 0) +
+               (NSU + NSC) * 8;
+    }
+};
 
 struct StepArgs {
-    const float *cur;
-    const float *prev;
-    const float *m;
     float *out;
     int nx, ny, nz;
     int64_t plane;
-    int gz0, wp;
+    int gz0;
     int z_lo, z_hi, zchunk;
     StarCoef c;
     int src_x, src_y, src_zw;
     float w;
 };
 
+// One time step over window planes [z_lo, z_hi).  CTA = 32 x 16 tile, walks a
+// z chunk.  u tiles (with a 4-column / R-row halo) stream through an NSU-deep
+// shared-memory ring filled by TMA; each thread keeps u(z-R .. z+R) of its 4
+// points in a register queue; prev and m (wave) stream through an NSC-deep
+// ring.  Planes outside the window or grid arrive zero-filled from TMA.
 template <int R, int SCHEME>
-__global__ void __launch_bounds__(kStepThreads) k_star_step(const StepArgs a)
+__global__ void __launch_bounds__(kStepThreads)
+    k_star_step(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
+                const __grid_constant__ CUtensorMap tm_m, const StepArgs a)
 {
-    constexpr int W = kTX + 2 * R;
-    constexpr int H = kTY + 2 * R;
-    constexpr int kHalo = 2 * R * W + 2 * R * kTY;
-    constexpr int kDy = kTY / kRows;
-    __shared__ float tile[H][W];
+    using C = StepCfg<R>;
+    constexpr bool kWaveS = SCHEME == kWave;
+    extern __shared__ unsigned char smem_raw[];
+    float *us = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float *ps = us + C::NSU * C::kUStage;
+    float *ms = ps + C::NSC * C::kCStage;
+    uint64_t *ubar = reinterpret_cast<uint64_t *>(kWaveS ? ms + C::NSC * C::kCStage : ps);
+    uint64_t *cbar = ubar + C::NSU;
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * kTX + tx;
-    const int x0 = blockIdx.x * kTX;
-    const int y0 = blockIdx.y * kTY;
-    const int x = x0 + tx;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int zs = a.z_lo + blockIdx.z * a.zchunk;
     const int ze = min(zs + a.zchunk, a.z_hi);
+    const int pu0 = zs - R;   // first u plane of the queue
+    const int pu_end = ze + R;
 
-    auto load_cur = [&](int z, int xx, int yy) -> float {
-        return (z >= 0 && z < a.wp && xx >= 0 && xx < a.nx && yy >= 0 && yy < a.ny)
-                   ? __ldg(a.cur + (int64_t)z * a.plane + (int64_t)yy * a.nx + xx)
-                   : 0.0f;
-    };
-
-    float q[kRows][2 * R + 1];
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-        q[r][0] = 0.0f;
-#pragma unroll
-        for (int i = 1; i <= 2 * R; ++i)
-            q[r][i] = load_cur(zs - R - 1 + i, x, y0 + ty + r * kDy);
+    if (tid == 0) {
+        for (int i = 0; i < C::NSU; ++i)
+            mbar_init(&ubar[i], 1);
+        for (int i = 0; i < C::NSC; ++i)
+            mbar_init(&cbar[i], 1);
+        fence_barrier_init();
     }
+    __syncthreads();
 
-    for (int z = zs; z < ze; ++z) {
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-#pragma unroll
-            for (int i = 0; i < 2 * R; ++i)
-                q[r][i] = q[r][i + 1];
-            q[r][2 * R] = load_cur(z + R, x, y0 + ty + r * kDy);
-            tile[ty + r * kDy + R][tx + R] = q[r][R];
+    int u_issued = pu0, c_issued = zs;  // next plane to request (thread 0)
+    auto issue_u = [&](int p) {
+        if (p < pu_end) {
+            const int st = (p - pu0) % C::NSU;
+            mbar_arrive_expect_tx(&ubar[st], C::kUBytes);
+            tma_load_3d(us + st * C::kUStage, &tm_cur, x0 - 4, y0 - R, p, &ubar[st]);
+            u_issued = p + 1;
         }
-        for (int i = tid; i < kHalo; i += kStepThreads) {
-            int hy, hx;
-            if (i < R * W) {
-                hy = i / W;
-                hx = i % W;
-            } else if (i < 2 * R * W) {
-                const int j = i - R * W;
-                hy = kTY + R + j / W;
-                hx = j % W;
-            } else {
-                const int j = i - 2 * R * W;
-                const int col = j % (2 * R);
-                hy = R + j / (2 * R);
-                hx = col < R ? col : kTX + col;
+    };
+    auto issue_c = [&](int z) {
+        if (kWaveS && z < ze) {
+            const int st = (z - zs) % C::NSC;
+            mbar_arrive_expect_tx(&cbar[st], 2 * C::kCBytes);
+            tma_load_3d(ps + st * C::kCStage, &tm_prev, x0, y0, z, &cbar[st]);
+            tma_load_3d(ms + st * C::kCStage, &tm_m, x0, y0, z, &cbar[st]);
+            c_issued = z + 1;
+        }
+    };
+    if (tid == 0) {
+        for (int i = 0; i < C::NSU; ++i)
+            issue_u(pu0 + i);
+        for (int i = 0; i < C::NSC; ++i)
+            issue_c(zs + i);
+    }
+    auto u_stage = [&](int p) { return (p - pu0) % C::NSU; };
+    auto u_phase = [&](int p) { return (uint32_t)(((p - pu0) / C::NSU) & 1); };
+
+    // register queue: q[r][i] = u(z - R + i) at row 4 ty + r
+    float q[kRPT][2 * R + 1];
+    bool good = true;
+#pragma unroll
+    for (int i = 1; i <= 2 * R; ++i) {
+        const int p = pu0 + i - 1;
+        if (good)
+            good = mbar_wait(&ubar[u_stage(p)], u_phase(p));
+        const float *P = us + u_stage(p) * C::kUStage;
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r)
+            q[r][i] = P[(R + kRPT * ty + r) * kBoxW + 4 + tx];
+    }
+    bool ok = __syncthreads_and(good);
+    if (ok && tid == 0)
+        for (int p = pu0; p < zs; ++p)  // their stages are free again
+            issue_u(p + C::NSU);
+
+    const int x = x0 + tx;
+    for (int z = zs; ok && z < ze; ++z) {
+        const int pn = z + R;
+        good = mbar_wait(&ubar[u_stage(pn)], u_phase(pn));
+        if (kWaveS && good)
+            good = mbar_wait(&cbar[(z - zs) % C::NSC], (uint32_t)(((z - zs) / C::NSC) & 1));
+        if (good) {
+            const float *Pn = us + u_stage(pn) * C::kUStage;
+            const float *P = us + u_stage(z) * C::kUStage;
+            const float *PS = ps + ((z - zs) % C::NSC) * C::kCStage;
+            const float *MS = ms + ((z - zs) % C::NSC) * C::kCStage;
+            const int gz = a.gz0 + z;
+            const bool zshell = gz < R || gz >= a.nz - R;
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) {
+#pragma unroll
+                for (int i = 0; i < 2 * R; ++i)
+                    q[r][i] = q[r][i + 1];
+                q[r][2 * R] = Pn[(R + kRPT * ty + r) * kBoxW + 4 + tx];
             }
-            tile[hy][hx] = load_cur(z, x0 + hx - R, y0 + hy - R);
-        }
-        __syncthreads();
-
-        const int gz = a.gz0 + z;
-        const bool zshell = gz < R || gz >= a.nz - R;
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            const int ly = ty + r * kDy;
-            const int y = y0 + ly;
-            if (x < a.nx && y < a.ny) {
-                const int64_t p = (int64_t)z * a.plane + (int64_t)y * a.nx + x;
-                const float u = q[r][R];
-                float res = u;  // Dirichlet shell keeps its value
-                if (!(zshell || x < R || x >= a.nx - R || y < R || y >= a.ny - R)) {
-                    float s[R + 1];
-                    s[0] = 0.0f;
+            for (int r = 0; r < kRPT; ++r) {
+                const int ly = kRPT * ty + r;
+                const int y = y0 + ly;
+                if (x < a.nx && y < a.ny) {
+                    const float u = q[r][R];
+                    float res = u;  // Dirichlet shell keeps its value
+                    if (!(zshell || x < R || x >= a.nx - R || y < R || y >= a.ny - R)) {
+                        const float *row = P + (R + ly) * kBoxW + 4 + tx;
+                        float s[R + 1];
+                        s[0] = 0.0f;
 #pragma unroll
-                    for (int d = 1; d <= R; ++d)
-                        s[d] = nbr_sum(tile[ly + R][tx + R - d], tile[ly + R][tx + R + d],
-                                       tile[ly + R - d][tx + R], tile[ly + R + d][tx + R],
-                                       q[r][R - d], q[r][R + d]);
-                    const float L = star_L<R>(a.c, u, s);
-                    if constexpr (SCHEME == kHeat) {
-                        res = L;
-                    } else {
-                        const bool at_src = (x == a.src_x && y == a.src_y && z == a.src_zw);
-                        res = wave_update(L, u, a.prev[p], a.m[p], at_src, a.w);
+                        for (int d = 1; d <= R; ++d)
+                            s[d] = nbr_sum(row[-d], row[d], row[-d * kBoxW], row[d * kBoxW], q[r][R - d],
+                                           q[r][R + d]);
+                        const float L = star_L<R>(a.c, u, s);
+                        if constexpr (SCHEME == kHeat) {
+                            res = L;
+                        } else {
+                            const bool at_src = (x == a.src_x && y == a.src_y && z == a.src_zw);
+                            res = wave_update(L, u, PS[ly * kTX + tx], MS[ly * kTX + tx], at_src, a.w);
+                        }
                     }
+                    a.out[(int64_t)z * a.plane + (int64_t)y * a.nx + x] = res;
                 }
-                a.out[p] = res;
             }
         }
-        __syncthreads();
+        ok = __syncthreads_and(good);
+        if (ok && tid == 0) {  // stage of plane z is free: refill
+            issue_u(z + C::NSU);
+            issue_c(z + C::NSC);
+        }
+    }
+    if (!ok && tid == 0) {
+        // a wait ran out: let the copies already requested land before leaving
+        for (int p = pu0; p < u_issued; ++p)
+            mbar_wait(&ubar[u_stage(p)], u_phase(p));
+        for (int z = zs; z < c_issued; ++z)
+            mbar_wait(&cbar[(z - zs) % C::NSC], (uint32_t)(((z - zs) / C::NSC) & 1));
     }
 }
 
-template <int R, int SCHEME>
-static cudaError_t launch_step_t(const StepArgs &a, int tiles_x, int tiles_y, int nchunks,
-                                 cudaStream_t s)
+// ---- host side: tensor maps and launch geometry
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// [planes][ny][nx] FP32 buffer, box (bw, bh, 1), zero fill out of bounds
+static cudaError_t make_plane_map(CUtensorMap *m, const float *base, int64_t nx, int64_t ny,
+                                  int64_t planes, uint32_t bw, uint32_t bh)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc)
+        return cudaErrorNotSupported;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (nx * 4) % 16)
+        return cudaErrorMisalignedAddress;
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)(nx * 4), (cuuint64_t)(nx * ny * 4)};
+    cuuint32_t box[3] = {bw, bh, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box,
+                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+struct DevInfo {
+    int sms = 0;
+};
+
+static const DevInfo &dev_info()
+{
+    static DevInfo info;
+    static int dev_cached = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != dev_cached) {
+        cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev);
+        dev_cached = dev;
+    }
+    return info;
+}
+
+template <int R, int SCHEME>
+static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s)
+{
+    using C = StepCfg<R>;
+    const size_t smem = C::smem_bytes(SCHEME == kWave);
+    auto kern = k_star_step<R, SCHEME>;
+    static int resident = 0;  // CTAs per SM (same on every GB300)
+    if (!resident) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, kStepThreads, smem);
+        if (e != cudaSuccess)
+            return e;
+        if (resident < 1)
+            return cudaErrorInvalidConfiguration;
+    }
+    CUtensorMap mc, mp, mm;
+    cudaError_t e = make_plane_map(&mc, L.cur, L.nx, L.ny, L.wp, kBoxW, C::H);
+    if (e == cudaSuccess)
+        e = make_plane_map(&mp, SCHEME == kWave ? L.prev : L.cur, L.nx, L.ny, L.wp, kTX, kTY);
+    if (e == cudaSuccess)
+        e = make_plane_map(&mm, SCHEME == kWave ? L.m : L.cur, L.nx, L.ny, L.wp, kTX, kTY);
+    if (e != cudaSuccess)
+        return e;
+
+    const int tiles_x = (int)((L.nx + kTX - 1) / kTX);
+    const int tiles_y = (int)((L.ny + kTY - 1) / kTY);
+    const int tiles = tiles_x * tiles_y;
+    const int nplanes = a.z_hi - a.z_lo;
+    // z chunks: keep >= 12 planes per CTA and choose the count whose last wave
+    // of CTAs (sms x resident per wave) is fullest
+    const int slots = dev_info().sms * resident;
+    int best = 1;
+    double best_eff = 0.0;
+    const int max_chunks = std::max(1, nplanes / 12);
+    for (int nc = 1; nc <= max_chunks && nc <= 64; ++nc) {
+        const int zc = (nplanes + nc - 1) / nc;
+        const int real = (nplanes + zc - 1) / zc;
+        const long total = (long)tiles * real;
+        const long waves = (total + slots - 1) / slots;
+        const double eff = (double)total / (double)(waves * slots);
+        if (eff > best_eff + 0.02) {
+            best_eff = eff;
+            best = nc;
+        }
+    }
+    a.zchunk = (nplanes + best - 1) / best;
+    const int nchunks = (nplanes + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles_x, tiles_y, nchunks);
-    dim3 block(kTX, kTY / kRows, 1);
-    k_star_step<R, SCHEME><<<grid, block, 0, s>>>(a);
+    dim3 block(kTX, kTY / kRPT, 1);
+    kern<<<grid, block, smem, s>>>(mc, mp, mm, a);
     return cudaGetLastError();
 }
 
@@ -145,50 +313,40 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
     if (L.z_hi <= L.z_lo)
         return cudaSuccess;
     StepArgs a;
-    a.cur = L.cur;
-    a.prev = L.prev;
-    a.m = L.m;
     a.out = L.out;
     a.nx = (int)L.nx;
     a.ny = (int)L.ny;
     a.nz = (int)L.nz;
     a.plane = L.nx * L.ny;
     a.gz0 = (int)L.gz0;
-    a.wp = (int)L.wp;
     a.z_lo = (int)L.z_lo;
     a.z_hi = (int)L.z_hi;
+    a.zchunk = 0;
     for (int i = 0; i < 5; ++i)
         a.c.c[i] = L.coef[i];
     a.src_x = (int)L.src_x;
     a.src_y = (int)L.src_y;
     a.src_zw = L.src_z >= 0 ? (int)(L.src_z - L.gz0) : -1;
     a.w = L.w;
-
-    const int tiles_x = (int)((L.nx + kTX - 1) / kTX);
-    const int tiles_y = (int)((L.ny + kTY - 1) / kTY);
-    const int nplanes = a.z_hi - a.z_lo;
-    // enough CTAs for ~2 waves at 8 CTAs/SM on 152 SMs, but at least 8R
-    // planes per CTA so the 2R-plane queue prologue stays a small overhead
-    const int target = 2 * 152 * 8;
-    const int min_planes = 8 * L.radius;
-    int nchunks = (target + tiles_x * tiles_y - 1) / (tiles_x * tiles_y);
-    const int max_chunks = (nplanes + min_planes - 1) / min_planes;
-    if (nchunks > max_chunks)
-        nchunks = max_chunks;
-    if (nchunks < 1)
-        nchunks = 1;
-    a.zchunk = (nplanes + nchunks - 1) / nchunks;
-    nchunks = (nplanes + a.zchunk - 1) / a.zchunk;
-
     if (L.radius == 1 && L.scheme == kHeat)
-        return launch_step_t<1, kHeat>(a, tiles_x, tiles_y, nchunks, s);
+        return launch_step_t<1, kHeat>(L, a, s);
     if (L.radius == 4 && L.scheme == kHeat)
-        return launch_step_t<4, kHeat>(a, tiles_x, tiles_y, nchunks, s);
+        return launch_step_t<4, kHeat>(L, a, s);
     if (L.radius == 1 && L.scheme == kWave)
-        return launch_step_t<1, kWave>(a, tiles_x, tiles_y, nchunks, s);
+        return launch_step_t<1, kWave>(L, a, s);
     if (L.radius == 4 && L.scheme == kWave)
-        return launch_step_t<4, kWave>(a, tiles_x, tiles_y, nchunks, s);
+        return launch_step_t<4, kWave>(L, a, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t read_device_error(unsigned int *code, bool clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(code, g_device_error, sizeof(unsigned int));
+    if (e == cudaSuccess && clear && *code) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_device_error, &zero, sizeof(unsigned int));
+    }
+    return e;
 }
 
 // ------------------------------------------------------------------ codec --

@@ -27,6 +27,10 @@ struct StepLaunch {
 
 cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s);
 
+// Read (and optionally clear) the device error word set by kernels whose
+// bounded waits ran out (0 = no error).
+cudaError_t read_device_error(unsigned int *code, bool clear);
+
 // Fixed-rate codec over whole 4-plane layers.  planes: first FP32 plane of the
 // first layer; blocks: first block of the first layer.
 cudaError_t launch_encode_layers(const float *planes, int64_t nx, int64_t ny, int64_t nlayers,
