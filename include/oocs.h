@@ -199,6 +199,28 @@ oocs_status oocs_incore_run(const oocs_desc *desc, float *u, float *u_prev, cons
                             float *scratch, int32_t nsteps, int64_t t0,
                             const int64_t *src_xyz, const float *w, int32_t nw, void *stream);
 
+/* oocs_incore_run for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this exists for callers such as a plugin inside a host
+ * application whose allocator owns the whole device memory pool, or a
+ * latency-critical loop where cudaMalloc / cudaFree would synchronise the
+ * device.  Same arguments and results as oocs_incore_run without `scratch`:
+ * the grid-sized scratch field comes from a library-owned static device array
+ * of OOCS_NOALLOC_MAX_VALUES floats (32 MiB), which every GPU that loads the
+ * library holds until the process exits.  Grids with nx*ny*nz above that
+ * maximum are rejected with OOCS_ERR_INVALID_ARG.  Allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library call.
+ *  - The first call made with a device current looks up the array's device
+ *    address (cudaGetSymbolAddress) and caches it; make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and it keeps the last call's contents;
+ *    nothing in it needs to start at zero (each step overwrites all of it
+ *    before reading it).  Calls that overlap on the GPU (other streams, other
+ *    host threads) race on the array: serialise them.                      */
+#define OOCS_NOALLOC_MAX_VALUES (8u << 20)
+oocs_status oocs_incore_run_noalloc(const oocs_desc *desc, float *u, float *u_prev, const float *m,
+                                    int32_t nsteps, int64_t t0, const int64_t *src_xyz,
+                                    const float *w, int32_t nw, void *stream);
+
 /* Fixed-rate block codec (Sec. 4.2) on device arrays.  encode: field
  * [nz][ny][nx] FP32 -> (nx/4)(ny/4)(nz/4) blocks of 8*rate bytes in layer
  * order (block (bx,by,bz) at ((bz*(ny/4)+by)*(nx/4)+bx)).  decode: inverse.

@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "../../include/oocs.h"
+#include "capi_internal.h"
 #include "kernels.h"
 #include "stencil.cuh"
 
@@ -237,6 +238,8 @@ oocs_status plan_impl(const oocs_desc *d, oocs_plan *p, std::string &err)
 }
 
 }  // namespace
+
+void oocs::set_last_error(const std::string &msg) { g_last_error = msg; }
 
 struct oocs_ctx {
     oocs_desc d;

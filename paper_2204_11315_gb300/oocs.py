@@ -103,6 +103,8 @@ SIGNATURES = {
     "oocs_destroy": (_i32, [_vp]),
     "oocs_incore_run": (_i32, [ctypes.POINTER(oocs_desc), _vp, _vp, _vp, _vp, _i32, _i64, _vp, _vp,
                                _i32, _vp]),
+    "oocs_incore_run_noalloc": (_i32, [ctypes.POINTER(oocs_desc), _vp, _vp, _vp, _i32, _i64, _vp,
+                                       _vp, _i32, _vp]),
     "oocs_encode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
     "oocs_decode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
 }
@@ -228,6 +230,16 @@ def oocs_incore_run(desc, u_ptr, up_ptr, m_ptr, scratch_ptr, nsteps, t0=0, src=N
                                  _vp(scratch_ptr), int(nsteps), int(t0),
                                  ctypes.cast(srcarr, _vp) if srcarr is not None else None,
                                  wv.ctypes.data_as(_vp), int(wv.size), _vp(stream)))
+
+
+def oocs_incore_run_noalloc(desc, u_ptr, up_ptr, m_ptr, nsteps, t0=0, src=None, w=None, stream=0):
+    """oocs_incore_run without a scratch argument (library-owned device scratch)."""
+    srcarr = (_i64 * 3)(*src) if src is not None else None
+    wv = np.ascontiguousarray(w if w is not None else np.zeros(0), dtype=np.float32)
+    _check(lib().oocs_incore_run_noalloc(ctypes.byref(desc), _vp(u_ptr), _vp(up_ptr), _vp(m_ptr),
+                                         int(nsteps), int(t0),
+                                         ctypes.cast(srcarr, _vp) if srcarr is not None else None,
+                                         wv.ctypes.data_as(_vp), int(wv.size), _vp(stream)))
 
 
 def oocs_encode_device(field_ptr, nx, ny, nz, rate, blocks_ptr, stream=0):
