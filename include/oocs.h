@@ -172,9 +172,11 @@ oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns);
 
 oocs_status oocs_get_stats(const oocs_ctx *ctx, oocs_stats *out);
 
-/* Turn per-launch event timing of the kernels enqueued by oocs_step on (1) or
- * off (0).  Adds two event records per kernel on its own stream.           */
-oocs_status oocs_set_profiling(oocs_ctx *ctx, int32_t enable);
+/* Per-launch event timing of the kernels enqueued by oocs_step.  `classes` is
+ * a bit mask: OOCS_PROF_LOAD | OOCS_PROF_STEP | OOCS_PROF_STORE; 0 = off.
+ * Adds two event records per timed kernel on its own stream.               */
+enum { OOCS_PROF_LOAD = 1, OOCS_PROF_STEP = 2, OOCS_PROF_STORE = 4 };
+oocs_status oocs_set_profiling(oocs_ctx *ctx, int32_t classes);
 
 /* Text of the last error of ctx, or of the last failed context-free call in
  * this thread when ctx is NULL.  Never NULL; valid until the next call.    */

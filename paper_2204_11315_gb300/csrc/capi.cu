@@ -264,8 +264,8 @@ struct oocs_ctx {
     uint64_t g = 0;  // slab visits enqueued
     oocs_stats stats;
 
-    // per-launch event timing (oocs_set_profiling)
-    bool prof = false;
+    // per-launch event timing (oocs_set_profiling): bit mask of kernel classes
+    int prof = 0;
     std::vector<cudaEvent_t> ev_pool;  // created on demand, reused after collection
     size_t ev_used = 0;
     struct Pending {
@@ -355,11 +355,11 @@ struct KernelScope {
     oocs_ctx *c;
     cudaStream_t s;
     cudaEvent_t a = nullptr;
-    oocs_status begin(oocs_ctx *cc, cudaStream_t ss)
+    oocs_status begin(oocs_ctx *cc, cudaStream_t ss, int cls)
     {
         c = cc;
         s = ss;
-        if (!c->prof)
+        if (!(c->prof & (1 << cls)))
             return OOCS_OK;
         oocs_status r = take_event(c, &a);
         if (r != OOCS_OK)
@@ -406,7 +406,7 @@ oocs_status load_layers(oocs_ctx *c, const char *src, int64_t src_l0, int64_t l0
     const char *from = src + (l0 - src_l0) * c->v.layer_bytes;
     float *to = dst + (4 * l0 - w0) * c->d.nx * c->d.ny;
     KernelScope ks;
-    oocs_status r = ks.begin(c, s);
+    oocs_status r = ks.begin(c, s, kClsLoad);
     if (r != OOCS_OK)
         return r;
     if (c->d.rate_bits == 0) {
@@ -426,7 +426,7 @@ oocs_status store_layers(oocs_ctx *c, const float *src, int64_t w0, int64_t l0, 
         return OOCS_OK;
     const float *from = src + (4 * l0 - w0) * c->d.nx * c->d.ny;
     KernelScope ks;
-    oocs_status r = ks.begin(c, s);
+    oocs_status r = ks.begin(c, s, kClsStore);
     if (r != OOCS_OK)
         return r;
     if (c->d.rate_bits == 0) {
@@ -532,7 +532,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             Ls.w = c->w[tstep];
         }
         KernelScope ks;
-        oocs_status r = ks.begin(c, st);
+        oocs_status r = ks.begin(c, st, kClsStep);
         if (r != OOCS_OK)
             return r;
         CU(c, launch_star_step(Ls, st));
@@ -842,12 +842,14 @@ oocs_status oocs_get_stats(const oocs_ctx *ctx, oocs_stats *out)
     return OOCS_OK;
 }
 
-oocs_status oocs_set_profiling(oocs_ctx *ctx, int32_t enable)
+oocs_status oocs_set_profiling(oocs_ctx *ctx, int32_t classes)
 {
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
-    ctx->prof = enable != 0;
+    if (classes < 0 || classes > 7)
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "profiling mask must be in [0, 7]");
+    ctx->prof = classes;
     return OOCS_OK;
 }
 

@@ -210,8 +210,12 @@ def oocs_get_stats(ctx: int) -> oocs_stats:
     return s
 
 
-def oocs_set_profiling(ctx: int, enable: bool):
-    _check(lib().oocs_set_profiling(ctx, 1 if enable else 0), ctx)
+OOCS_PROF_LOAD, OOCS_PROF_STEP, OOCS_PROF_STORE = 1, 2, 4
+
+
+def oocs_set_profiling(ctx: int, classes: int):
+    """classes: bit mask of OOCS_PROF_LOAD / _STEP / _STORE (0 = off)."""
+    _check(lib().oocs_set_profiling(ctx, int(classes)), ctx)
 
 
 def oocs_last_error(ctx=None) -> str:
@@ -316,8 +320,8 @@ class OutOfCoreStencil:
         oocs_synchronize(self.ctx, int(timeout_s * 1e9))
         self._keep.clear()
 
-    def set_profiling(self, enable: bool = True):
-        oocs_set_profiling(self.ctx, enable)
+    def set_profiling(self, classes: int = 7):
+        oocs_set_profiling(self.ctx, classes)
 
     def stats(self) -> dict:
         return oocs_get_stats(self.ctx).as_dict()
