@@ -159,6 +159,11 @@ oocs_status oocs_compress(oocs_ctx *ctx, int32_t field, const float *src);
  * FP32 host array `dst` of nx*ny*nz values.  Asynchronous.                 */
 oocs_status oocs_decompress(oocs_ctx *ctx, int32_t field, float *dst);
 
+/* Set the context's global time index t (the index of the source sample the
+ * next step adds; 0 after oocs_create).  For restarting from a stored state.
+ * Takes effect for work enqueued after the call.                           */
+oocs_status oocs_set_time(oocs_ctx *ctx, int64_t t);
+
 /* Advance the bound fields `nsteps` time steps: ceil(nsteps/k) sweeps over
  * the S slabs (the last with the remainder), each slab streamed through the
  * three-stream pipeline of Algorithm 1 with the single working buffer.

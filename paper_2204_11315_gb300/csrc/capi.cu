@@ -745,6 +745,17 @@ oocs_status oocs_decompress(oocs_ctx *ctx, int32_t field, float *dst)
     return codec_field(ctx, field, nullptr, dst, false);
 }
 
+oocs_status oocs_set_time(oocs_ctx *ctx, int64_t t)
+{
+    oocs_status s = check_ready(ctx);
+    if (s != OOCS_OK)
+        return s;
+    if (t < 0)
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "time index must be >= 0");
+    ctx->stats.steps_done = (uint64_t)t;
+    return OOCS_OK;
+}
+
 oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
 {
     oocs_status s = check_ready(ctx);

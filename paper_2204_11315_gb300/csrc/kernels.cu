@@ -23,21 +23,23 @@
 
 namespace oocs {
 
-constexpr int kTX = 32;                 // tile width (x)
-constexpr int kTY = 16;                 // tile height (y)
+constexpr int kVX = 2;                  // x-adjacent points per thread (float2)
+constexpr int kTX = 32 * kVX;           // tile width (x) = 64
 constexpr int kRPT = 4;                 // consecutive rows per thread
-constexpr int kStepThreads = kTX * (kTY / kRPT);  // 128
-constexpr int kBoxW = kTX + 8;          // u tile loaded from x0-4 (16-byte aligned) to x0+36
+constexpr int kTY = 4 * kRPT;           // tile height (y) = 16: 4 warps
+constexpr int kStepThreads = 128;
+constexpr int kBoxW = kTX + 8;          // u tile loaded from x0-4 (16-byte aligned) to x0+kTX+4
 
 template <int R>
 struct StepCfg {
     static constexpr int H = kTY + 2 * R;                       // u tile rows
     static constexpr uint32_t kUBytes = H * kBoxW * 4;          // one TMA box of u
     static constexpr int kUStage = ((kUBytes + 127) / 128 * 128) / 4;  // floats per ring stage
-    static constexpr int NSU = 2 * R + 4;                       // u ring stages
-    static constexpr int NSC = 6;                               // prev / m ring stages
+    static constexpr int NSU = (2 * R + 2) > 6 ? (2 * R + 2) : 6;  // u ring stages (>= R+1 ahead)
+    static constexpr int NSC = 4;                               // prev / m ring stages
     static constexpr int kCStage = kTX * kTY;                   // floats per prev / m stage
     static constexpr uint32_t kCBytes = kCStage * 4;
+    static constexpr int Q = 2 * R + 1;                         // register queue length
     static constexpr size_t smem_bytes(bool wave)
     {
         return 128 + (size_t)NSU * kUStage * 4 + (wave ? 2ull * NSC * kCStage * 4 : 0) +
@@ -56,11 +58,15 @@ struct StepArgs {
     float w;
 };
 
-// One time step over window planes [z_lo, z_hi).  CTA = 32 x 16 tile, walks a
-// z chunk.  u tiles (with a 4-column / R-row halo) stream through an NSU-deep
-// shared-memory ring filled by TMA; each thread keeps u(z-R .. z+R) of its 4
-// points in a register queue; prev and m (wave) stream through an NSC-deep
-// ring.  Planes outside the window or grid arrive zero-filled from TMA.
+// One time step over window planes [z_lo, z_hi).  CTA = 64 x 16 tile (128
+// threads), walks a z chunk.  Thread (tx, ty) owns the 2 x 4 points
+// x = x0 + 2 tx + {0, 1}, y = y0 + 4 ty + {0..3}.  u tiles (with a 4-column /
+// R-row halo) stream through an NSU-deep shared-memory ring filled by TMA;
+// each thread keeps u(z-R .. z+R) of its points in a circular register queue
+// (the z loop is unrolled by its length, so no values move); x neighbours come
+// from 64-bit shared loads, y neighbours inside the thread's 4 rows from the
+// queue; prev and m (wave) stream through an NSC-deep ring.  Planes outside the
+// window or grid arrive zero-filled from TMA.
 template <int R, int SCHEME>
 __global__ void __launch_bounds__(kStepThreads)
     k_star_step(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
@@ -68,6 +74,7 @@ __global__ void __launch_bounds__(kStepThreads)
 {
     using C = StepCfg<R>;
     constexpr bool kWaveS = SCHEME == kWave;
+    constexpr int Q = C::Q;
     extern __shared__ unsigned char smem_raw[];
     float *us = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *ps = us + C::NSU * C::kUStage;
@@ -76,7 +83,7 @@ __global__ void __launch_bounds__(kStepThreads)
     uint64_t *cbar = ubar + C::NSU;
 
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * kTX + tx;
+    const int tid = ty * 32 + tx;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int zs = a.z_lo + blockIdx.z * a.zchunk;
     const int ze = min(zs + a.zchunk, a.z_hi);
@@ -118,77 +125,132 @@ __global__ void __launch_bounds__(kStepThreads)
     }
     auto u_stage = [&](int p) { return (p - pu0) % C::NSU; };
     auto u_phase = [&](int p) { return (uint32_t)(((p - pu0) / C::NSU) & 1); };
+    // shared-memory float offset of (row r of this thread, column pair) in a u stage
+    const int ucol = 4 + kVX * tx;
+    auto urow = [&](int rel_row) { return (R + kRPT * ty + rel_row) * kBoxW + ucol; };
 
-    // register queue: q[r][i] = u(z - R + i) at row 4 ty + r
-    float q[kRPT][2 * R + 1];
+    // circular register queue: at sub-step J of a group of Q planes starting at
+    // z, slot (J + i) % Q holds u(z + J - R + i) for i = 0 .. 2R
+    float2 q[kRPT][Q];
     bool good = true;
 #pragma unroll
-    for (int i = 1; i <= 2 * R; ++i) {
-        const int p = pu0 + i - 1;
+    for (int i = 0; i < 2 * R; ++i) {
+        const int p = pu0 + i;
         if (good)
             good = mbar_wait(&ubar[u_stage(p)], u_phase(p));
         const float *P = us + u_stage(p) * C::kUStage;
 #pragma unroll
         for (int r = 0; r < kRPT; ++r)
-            q[r][i] = P[(R + kRPT * ty + r) * kBoxW + 4 + tx];
+            q[r][i] = *reinterpret_cast<const float2 *>(P + urow(r));
     }
+#pragma unroll
+    for (int r = 0; r < kRPT; ++r)
+        q[r][2 * R] = make_float2(0.0f, 0.0f);
     bool ok = __syncthreads_and(good);
     if (ok && tid == 0)
         for (int p = pu0; p < zs; ++p)  // their stages are free again
             issue_u(p + C::NSU);
 
-    const int x = x0 + tx;
-    for (int z = zs; ok && z < ze; ++z) {
-        const int pn = z + R;
-        good = mbar_wait(&ubar[u_stage(pn)], u_phase(pn));
-        if (kWaveS && good)
-            good = mbar_wait(&cbar[(z - zs) % C::NSC], (uint32_t)(((z - zs) / C::NSC) & 1));
-        if (good) {
-            const float *Pn = us + u_stage(pn) * C::kUStage;
-            const float *P = us + u_stage(z) * C::kUStage;
-            const float *PS = ps + ((z - zs) % C::NSC) * C::kCStage;
-            const float *MS = ms + ((z - zs) % C::NSC) * C::kCStage;
-            const int gz = a.gz0 + z;
-            const bool zshell = gz < R || gz >= a.nz - R;
+    const int x = x0 + kVX * tx;  // first of the thread's two columns
+    // x-y part of the Dirichlet-shell test per row and column
+    bool x_ok = x < a.nx;  // nx is a multiple of 4: both columns or neither
+    bool in_x[kVX];
 #pragma unroll
-            for (int r = 0; r < kRPT; ++r) {
+    for (int c = 0; c < kVX; ++c)
+        in_x[c] = (x + c) >= R && (x + c) < a.nx - R;
+    bool row_ok[kRPT], in_y[kRPT];
 #pragma unroll
-                for (int i = 0; i < 2 * R; ++i)
-                    q[r][i] = q[r][i + 1];
-                q[r][2 * R] = Pn[(R + kRPT * ty + r) * kBoxW + 4 + tx];
-            }
+    for (int r = 0; r < kRPT; ++r) {
+        const int y = y0 + kRPT * ty + r;
+        row_ok[r] = x_ok && y < a.ny;
+        in_y[r] = y >= R && y < a.ny - R;
+    }
+
+    for (int zb = zs; ok && zb < ze; zb += Q) {
+        static_for<0, Q>([&](auto JJ) {
+            constexpr int J = decltype(JJ)::value;
+            const int z = zb + J;
+            if (!ok || z >= ze)
+                return;
+            const int pn = z + R;
+            good = mbar_wait(&ubar[u_stage(pn)], u_phase(pn));
+            if (kWaveS && good)
+                good = mbar_wait(&cbar[(z - zs) % C::NSC], (uint32_t)(((z - zs) / C::NSC) & 1));
+            if (good) {
+                const float *Pn = us + u_stage(pn) * C::kUStage;
+                const float *P = us + u_stage(z) * C::kUStage;
+                [[maybe_unused]] const int cst = (z - zs) % C::NSC;
+                const int gz = a.gz0 + z;
+                const bool z_interior = gz >= R && gz < a.nz - R;
 #pragma unroll
-            for (int r = 0; r < kRPT; ++r) {
-                const int ly = kRPT * ty + r;
-                const int y = y0 + ly;
-                if (x < a.nx && y < a.ny) {
-                    const float u = q[r][R];
-                    float res = u;  // Dirichlet shell keeps its value
-                    if (!(zshell || x < R || x >= a.nx - R || y < R || y >= a.ny - R)) {
-                        const float *row = P + (R + ly) * kBoxW + 4 + tx;
-                        float s[R + 1];
-                        s[0] = 0.0f;
+                for (int r = 0; r < kRPT; ++r)
+                    q[r][(J + 2 * R) % Q] = *reinterpret_cast<const float2 *>(Pn + urow(r));
+                // y neighbours outside the thread's rows: R rows above, R below
+                float2 above[R], below[R];
 #pragma unroll
-                        for (int d = 1; d <= R; ++d)
-                            s[d] = nbr_sum(row[-d], row[d], row[-d * kBoxW], row[d * kBoxW], q[r][R - d],
-                                           q[r][R + d]);
-                        const float L = star_L<R>(a.c, u, s);
-                        if constexpr (SCHEME == kHeat) {
-                            res = L;
-                        } else {
-                            const bool at_src = (x == a.src_x && y == a.src_y && z == a.src_zw);
-                            res = wave_update(L, u, PS[ly * kTX + tx], MS[ly * kTX + tx], at_src, a.w);
+                for (int d = 1; d <= R; ++d) {
+                    above[d - 1] = *reinterpret_cast<const float2 *>(P + urow(-d));
+                    below[d - 1] = *reinterpret_cast<const float2 *>(P + urow(kRPT - 1 + d));
+                }
+#pragma unroll
+                for (int r = 0; r < kRPT; ++r) {
+                    if (!row_ok[r])
+                        continue;
+                    // x neighbours: columns x-4 .. x+5 of row r (five 64-bit loads)
+                    float xv[10];
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        const float2 v = *reinterpret_cast<const float2 *>(P + urow(r) - 4 + 2 * i);
+                        xv[2 * i] = v.x;
+                        xv[2 * i + 1] = v.y;
+                    }
+                    const float2 uc = q[r][(J + R) % Q];
+                    [[maybe_unused]] float2 pv, mv;
+                    if constexpr (kWaveS) {
+                        const int ci = cst * C::kCStage + (kRPT * ty + r) * kTX + kVX * tx;
+                        pv = *reinterpret_cast<const float2 *>(ps + ci);
+                        mv = *reinterpret_cast<const float2 *>(ms + ci);
+                    }
+                    float res[kVX];
+#pragma unroll
+                    for (int c = 0; c < kVX; ++c) {
+                        const float u = c ? uc.y : uc.x;
+                        res[c] = u;  // Dirichlet shell keeps its value
+                        if (z_interior && in_y[r] && in_x[c]) {
+                            float s[R + 1];
+                            s[0] = 0.0f;
+#pragma unroll
+                            for (int d = 1; d <= R; ++d) {
+                                const float2 ym = (r - d >= 0) ? q[(r - d) >= 0 ? r - d : 0][(J + R) % Q]
+                                                               : above[(d - r - 1) >= 0 ? d - r - 1 : 0];
+                                const float2 yp = (r + d < kRPT) ? q[(r + d) < kRPT ? r + d : 0][(J + R) % Q]
+                                                                 : below[(r + d - kRPT) >= 0 ? r + d - kRPT : 0];
+                                const float2 zm = q[r][(J + R - d) % Q];
+                                const float2 zp = q[r][(J + R + d) % Q];
+                                s[d] = nbr_sum(xv[4 + c - d], xv[4 + c + d], c ? ym.y : ym.x,
+                                               c ? yp.y : yp.x, c ? zm.y : zm.x, c ? zp.y : zp.x);
+                            }
+                            const float L = star_L<R>(a.c, u, s);
+                            if constexpr (SCHEME == kHeat) {
+                                res[c] = L;
+                            } else {
+                                const int y = y0 + kRPT * ty + r;
+                                const bool at_src = (x + c == a.src_x && y == a.src_y && z == a.src_zw);
+                                res[c] = wave_update(L, u, c ? pv.y : pv.x, c ? mv.y : mv.x, at_src, a.w);
+                            }
                         }
                     }
-                    a.out[(int64_t)z * a.plane + (int64_t)y * a.nx + x] = res;
+                    *reinterpret_cast<float2 *>(a.out + (int64_t)z * a.plane +
+                                                (int64_t)(y0 + kRPT * ty + r) * a.nx + x) =
+                        make_float2(res[0], res[1]);
                 }
             }
-        }
-        ok = __syncthreads_and(good);
-        if (ok && tid == 0) {  // stage of plane z is free: refill
-            issue_u(z + C::NSU);
-            issue_c(z + C::NSC);
-        }
+            ok = __syncthreads_and(good);
+            if (ok && tid == 0) {  // stage of plane z is free: refill
+                issue_u(z + C::NSU);
+                issue_c(z + C::NSC);
+            }
+        });
     }
     if (!ok && tid == 0) {
         // a wait ran out: let the copies already requested land before leaving
@@ -303,7 +365,7 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
     a.zchunk = (nplanes + best - 1) / best;
     const int nchunks = (nplanes + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles_x, tiles_y, nchunks);
-    dim3 block(kTX, kTY / kRPT, 1);
+    dim3 block(32, kTY / kRPT, 1);
     kern<<<grid, block, smem, s>>>(mc, mp, mm, a);
     return cudaGetLastError();
 }

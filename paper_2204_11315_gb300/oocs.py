@@ -95,6 +95,7 @@ SIGNATURES = {
     "oocs_set_source": (_i32, [_vp, _i64, _i64, _i64, _vp, _i32]),
     "oocs_compress": (_i32, [_vp, _i32, _vp]),
     "oocs_decompress": (_i32, [_vp, _i32, _vp]),
+    "oocs_set_time": (_i32, [_vp, _i64]),
     "oocs_step": (_i32, [_vp, _i32]),
     "oocs_synchronize": (_i32, [_vp, _u64]),
     "oocs_get_stats": (_i32, [_vp, ctypes.POINTER(oocs_stats)]),
@@ -194,6 +195,10 @@ def oocs_compress(ctx: int, field: int, src_ptr: int):
 
 def oocs_decompress(ctx: int, field: int, dst_ptr: int):
     _check(lib().oocs_decompress(ctx, field, _vp(dst_ptr)), ctx)
+
+
+def oocs_set_time(ctx: int, t: int):
+    _check(lib().oocs_set_time(ctx, int(t)), ctx)
 
 
 def oocs_step(ctx: int, nsteps: int):
@@ -315,6 +320,19 @@ class OutOfCoreStencil:
 
     def step(self, nsteps: int):
         oocs_step(self.ctx, nsteps)
+
+    def set_time(self, t: int):
+        oocs_set_time(self.ctx, t)
+
+    def snapshot_stores(self):
+        """Pinned host copies of the current stores (call after synchronize)."""
+        return [s.clone().pin_memory() for s in self.stores]
+
+    def restore_stores(self, snap, t: int = 0):
+        """Put the stores back to a snapshot and the time index to t (after synchronize)."""
+        for s, c in zip(self.stores, snap):
+            s.copy_(c)
+        self.set_time(t)
 
     def synchronize(self, timeout_s: float = 0.0):
         oocs_synchronize(self.ctx, int(timeout_s * 1e9))

@@ -149,3 +149,31 @@ def test_budget_too_small(P):
     with pytest.raises(P.OOCSError) as e:
         P.oocs_query(desc)
     assert e.value.status == 2
+
+
+def test_restore_and_set_time_repeat_the_run(P):
+    """Resetting the host stores and the time index repeats the same run bit for bit."""
+    shape = (64, 40, 48)
+    steps = 9
+    m, w, src, z = _wave_inputs(shape, steps)
+    desc = wave_desc(P, shape, rate=12, k=4, T=32)
+    st = P.OutOfCoreStencil(desc)
+    try:
+        st.compress(P.OOCS_FIELD_U, z)
+        st.compress(P.OOCS_FIELD_U_PREV, z)
+        st.compress(P.OOCS_FIELD_M, m)
+        st.set_source(src[0], src[1], src[2], w)
+        st.synchronize(60.0)
+        snap = st.snapshot_stores()
+        outs = []
+        for _ in range(2):
+            st.restore_stores(snap, 0)
+            st.step(steps)
+            st.synchronize(60.0)
+            outs.append([s.numpy().copy() for s in st.stores])
+        assert st.stats()["steps_done"] == steps
+    finally:
+        st.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    assert not np.array_equal(outs[0][0], snap[0].numpy())
