@@ -26,8 +26,9 @@ namespace oocs {
 constexpr int kVX = 2;                  // x-adjacent points per thread (float2)
 constexpr int kTX = 32 * kVX;           // tile width (x) = 64
 constexpr int kRPT = 4;                 // consecutive rows per thread
-constexpr int kTY = 4 * kRPT;           // tile height (y) = 16: 4 warps
-constexpr int kStepThreads = 128;
+constexpr int kConsumerWarps = 4;
+constexpr int kTY = kConsumerWarps * kRPT;         // tile height (y) = 16
+constexpr int kStepThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
 constexpr int kBoxW = kTX + 8;          // u tile loaded from x0-4 (16-byte aligned) to x0+kTX+4
 
 template <int R>
@@ -43,7 +44,7 @@ struct StepCfg {
     static constexpr size_t smem_bytes(bool wave)
     {
         return 128 + (size_t)NSU * kUStage * 4 + (wave ? 2ull * NSC * kCStage * 4 : 0) +
-               (NSU + NSC) * 8;
+               2 * (NSU + NSC) * 8;
     }
 };
 
@@ -58,17 +59,19 @@ struct StepArgs {
     float w;
 };
 
-// One time step over window planes [z_lo, z_hi).  CTA = 64 x 16 tile (128
-// threads), walks a z chunk.  Thread (tx, ty) owns the 2 x 4 points
-// x = x0 + 2 tx + {0, 1}, y = y0 + 4 ty + {0..3}.  u tiles (with a 4-column /
-// R-row halo) stream through an NSU-deep shared-memory ring filled by TMA;
-// each thread keeps u(z-R .. z+R) of its points in a circular register queue
-// (the z loop is unrolled by its length, so no values move); x neighbours come
-// from 64-bit shared loads, y neighbours inside the thread's 4 rows from the
-// queue; prev and m (wave) stream through an NSC-deep ring.  Planes outside the
-// window or grid arrive zero-filled from TMA.
+// One time step over window planes [z_lo, z_hi).  CTA = 64 x 16 tile walking
+// a z chunk, warp-specialised: warp 4 is the producer, which streams u tiles
+// (with a 4-column / R-row halo) into an NSU-deep shared-memory ring and the
+// prev / m tiles (wave) into an NSC-deep ring by TMA, each stage guarded by a
+// "full" mbarrier (TMA bytes landed) and an "empty" mbarrier (all four
+// consumer warps done with it).  Consumer warps run decoupled, with no
+// CTA-wide barrier per plane.  Consumer thread (tx, w) owns the 2 x 4 points
+// x = x0 + 2 tx + {0, 1}, y = y0 + 4 w + {0..3}; it keeps u(z-R .. z+R) of
+// them in a register queue, takes x neighbours from 64-bit shared loads and y
+// neighbours inside its four rows from the queue.  Planes outside the window
+// or grid arrive zero-filled from TMA.
 template <int R, int SCHEME>
-__global__ void __launch_bounds__(kStepThreads)
+__global__ void __launch_bounds__(kStepThreads, 2)
     k_star_step(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
                 const __grid_constant__ CUtensorMap tm_m, const StepArgs a)
 {
@@ -79,81 +82,108 @@ __global__ void __launch_bounds__(kStepThreads)
     float *us = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *ps = us + C::NSU * C::kUStage;
     float *ms = ps + C::NSC * C::kCStage;
-    uint64_t *ubar = reinterpret_cast<uint64_t *>(kWaveS ? ms + C::NSC * C::kCStage : ps);
-    uint64_t *cbar = ubar + C::NSU;
+    uint64_t *ufull = reinterpret_cast<uint64_t *>(kWaveS ? ms + C::NSC * C::kCStage : ps);
+    uint64_t *uempty = ufull + C::NSU;
+    uint64_t *cfull = uempty + C::NSU;
+    uint64_t *cempty = cfull + C::NSC;
 
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * 32 + tx;
+    const int tx = threadIdx.x, wid = threadIdx.y;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int zs = a.z_lo + blockIdx.z * a.zchunk;
     const int ze = min(zs + a.zchunk, a.z_hi);
     const int pu0 = zs - R;   // first u plane of the queue
     const int pu_end = ze + R;
 
-    if (tid == 0) {
-        for (int i = 0; i < C::NSU; ++i)
-            mbar_init(&ubar[i], 1);
-        for (int i = 0; i < C::NSC; ++i)
-            mbar_init(&cbar[i], 1);
+    if (wid == 0 && tx == 0) {
+        for (int i = 0; i < C::NSU; ++i) {
+            mbar_init(&ufull[i], 1);
+            mbar_init(&uempty[i], kConsumerWarps);
+        }
+        for (int i = 0; i < C::NSC; ++i) {
+            mbar_init(&cfull[i], 1);
+            mbar_init(&cempty[i], kConsumerWarps);
+        }
         fence_barrier_init();
     }
-    __syncthreads();
+    __syncthreads();  // the only CTA-wide barrier
 
-    int u_issued = pu0, c_issued = zs;  // next plane to request (thread 0)
-    auto issue_u = [&](int p) {
-        if (p < pu_end) {
-            const int st = (p - pu0) % C::NSU;
-            mbar_arrive_expect_tx(&ubar[st], C::kUBytes);
-            tma_load_3d(us + st * C::kUStage, &tm_cur, x0 - 4, y0 - R, p, &ubar[st]);
-            u_issued = p + 1;
+    if (wid == kConsumerWarps) {
+        // ------------------------------------------------ producer warp --
+        if (tx != 0)
+            return;
+        bool good = true;
+        int u_next = pu0, c_next = zs;
+        auto put_u = [&](int p) {
+            const int st = (p - pu0) % C::NSU, n = (p - pu0) / C::NSU;
+            if (n > 0 && !mbar_wait(&uempty[st], (uint32_t)((n - 1) & 1)))
+                return false;
+            mbar_arrive_expect_tx(&ufull[st], C::kUBytes);
+            tma_load_3d(us + st * C::kUStage, &tm_cur, x0 - 4, y0 - R, p, &ufull[st]);
+            u_next = p + 1;
+            return true;
+        };
+        auto put_c = [&](int z) {
+            const int st = (z - zs) % C::NSC, n = (z - zs) / C::NSC;
+            if (n > 0 && !mbar_wait(&cempty[st], (uint32_t)((n - 1) & 1)))
+                return false;
+            mbar_arrive_expect_tx(&cfull[st], 2 * C::kCBytes);
+            tma_load_3d(ps + st * C::kCStage, &tm_prev, x0, y0, z, &cfull[st]);
+            tma_load_3d(ms + st * C::kCStage, &tm_m, x0, y0, z, &cfull[st]);
+            c_next = z + 1;
+            return true;
+        };
+        // u planes are needed in order (queue prologue first), the c planes
+        // alongside the u plane R ahead of them
+        for (int p = pu0; good && p < pu_end; ++p) {
+            good = put_u(p);
+            const int z = p - R;
+            if (kWaveS && good && z >= zs && z < ze)
+                good = put_c(z);
         }
-    };
-    auto issue_c = [&](int z) {
-        if (kWaveS && z < ze) {
-            const int st = (z - zs) % C::NSC;
-            mbar_arrive_expect_tx(&cbar[st], 2 * C::kCBytes);
-            tma_load_3d(ps + st * C::kCStage, &tm_prev, x0, y0, z, &cbar[st]);
-            tma_load_3d(ms + st * C::kCStage, &tm_m, x0, y0, z, &cbar[st]);
-            c_issued = z + 1;
-        }
-    };
-    if (tid == 0) {
-        for (int i = 0; i < C::NSU; ++i)
-            issue_u(pu0 + i);
-        for (int i = 0; i < C::NSC; ++i)
-            issue_c(zs + i);
+        // drain: everything requested lands before the CTA may retire
+        for (int p = max(pu0, u_next - C::NSU); p < u_next; ++p)
+            mbar_wait(&ufull[(p - pu0) % C::NSU], (uint32_t)(((p - pu0) / C::NSU) & 1));
+        for (int z = max(zs, c_next - C::NSC); z < c_next; ++z)
+            mbar_wait(&cfull[(z - zs) % C::NSC], (uint32_t)(((z - zs) / C::NSC) & 1));
+        return;
     }
+
+    // --------------------------------------------------- consumer warps --
     auto u_stage = [&](int p) { return (p - pu0) % C::NSU; };
     auto u_phase = [&](int p) { return (uint32_t)(((p - pu0) / C::NSU) & 1); };
-    // shared-memory float offset of (row r of this thread, column pair) in a u stage
+    auto release_u = [&](int p) {
+        __syncwarp();
+        if (tx == 0)
+            mbar_arrive(&uempty[u_stage(p)]);
+    };
     const int ucol = 4 + kVX * tx;
-    auto urow = [&](int rel_row) { return (R + kRPT * ty + rel_row) * kBoxW + ucol; };
+    auto urow = [&](int rel_row) { return (R + kRPT * wid + rel_row) * kBoxW + ucol; };
 
-    // circular register queue: at sub-step J of a group of Q planes starting at
-    // z, slot (J + i) % Q holds u(z + J - R + i) for i = 0 .. 2R
+    // register queue: in iteration z, q[r][i] = u(z - R + i) at row 4 wid + r
     float2 q[kRPT][Q];
-    bool good = true;
-#pragma unroll
-    for (int i = 0; i < 2 * R; ++i) {
-        const int p = pu0 + i;
-        if (good)
-            good = mbar_wait(&ubar[u_stage(p)], u_phase(p));
-        const float *P = us + u_stage(p) * C::kUStage;
-#pragma unroll
-        for (int r = 0; r < kRPT; ++r)
-            q[r][i] = *reinterpret_cast<const float2 *>(P + urow(r));
-    }
 #pragma unroll
     for (int r = 0; r < kRPT; ++r)
         q[r][2 * R] = make_float2(0.0f, 0.0f);
-    bool ok = __syncthreads_and(good);
-    if (ok && tid == 0)
-        for (int p = pu0; p < zs; ++p)  // their stages are free again
-            issue_u(p + C::NSU);
+    bool good = true;
+    for (int i = 0; i < 2 * R && good; ++i) {
+        const int p = pu0 + i;
+        good = mbar_wait(&ufull[u_stage(p)], u_phase(p));
+        if (!good)
+            break;
+        const float *P = us + u_stage(p) * C::kUStage;
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r) {
+#pragma unroll
+            for (int j = 0; j < 2 * R; ++j)  // shift towards 0, newest at 2R:
+                q[r][j] = q[r][j + 1];       // ends with q[1 .. 2R] = u(zs-R .. zs+R-1)
+            q[r][2 * R] = *reinterpret_cast<const float2 *>(P + urow(r));
+        }
+        if (p < zs)  // planes before the chunk are only queue inputs
+            release_u(p);
+    }
 
     const int x = x0 + kVX * tx;  // first of the thread's two columns
-    // x-y part of the Dirichlet-shell test per row and column
-    bool x_ok = x < a.nx;  // nx is a multiple of 4: both columns or neither
+    const bool x_ok = x < a.nx;   // nx is a multiple of 4: both columns or neither
     bool in_x[kVX];
 #pragma unroll
     for (int c = 0; c < kVX; ++c)
@@ -161,103 +191,95 @@ __global__ void __launch_bounds__(kStepThreads)
     bool row_ok[kRPT], in_y[kRPT];
 #pragma unroll
     for (int r = 0; r < kRPT; ++r) {
-        const int y = y0 + kRPT * ty + r;
+        const int y = y0 + kRPT * wid + r;
         row_ok[r] = x_ok && y < a.ny;
         in_y[r] = y >= R && y < a.ny - R;
     }
 
-    for (int zb = zs; ok && zb < ze; zb += Q) {
-        static_for<0, Q>([&](auto JJ) {
-            constexpr int J = decltype(JJ)::value;
-            const int z = zb + J;
-            if (!ok || z >= ze)
-                return;
-            const int pn = z + R;
-            good = mbar_wait(&ubar[u_stage(pn)], u_phase(pn));
-            if (kWaveS && good)
-                good = mbar_wait(&cbar[(z - zs) % C::NSC], (uint32_t)(((z - zs) / C::NSC) & 1));
-            if (good) {
-                const float *Pn = us + u_stage(pn) * C::kUStage;
-                const float *P = us + u_stage(z) * C::kUStage;
-                [[maybe_unused]] const int cst = (z - zs) % C::NSC;
-                const int gz = a.gz0 + z;
-                const bool z_interior = gz >= R && gz < a.nz - R;
+    for (int z = zs; good && z < ze; ++z) {
+        const int pn = z + R;
+        good = mbar_wait(&ufull[u_stage(pn)], u_phase(pn));
+        const int cst = (z - zs) % C::NSC;
+        if (kWaveS && good)
+            good = mbar_wait(&cfull[cst], (uint32_t)(((z - zs) / C::NSC) & 1));
+        if (!good)
+            break;
+        const float *Pn = us + u_stage(pn) * C::kUStage;
+        const float *P = us + u_stage(z) * C::kUStage;
+        const int gz = a.gz0 + z;
+        const bool z_interior = gz >= R && gz < a.nz - R;
 #pragma unroll
-                for (int r = 0; r < kRPT; ++r)
-                    q[r][(J + 2 * R) % Q] = *reinterpret_cast<const float2 *>(Pn + urow(r));
-                // y neighbours outside the thread's rows: R rows above, R below
-                float2 above[R], below[R];
+        for (int r = 0; r < kRPT; ++r) {
 #pragma unroll
-                for (int d = 1; d <= R; ++d) {
-                    above[d - 1] = *reinterpret_cast<const float2 *>(P + urow(-d));
-                    below[d - 1] = *reinterpret_cast<const float2 *>(P + urow(kRPT - 1 + d));
-                }
+            for (int j = 0; j < 2 * R; ++j)
+                q[r][j] = q[r][j + 1];
+            q[r][2 * R] = *reinterpret_cast<const float2 *>(Pn + urow(r));
+        }
+        // y neighbours outside the thread's rows: R rows above, R below
+        float2 above[R], below[R];
 #pragma unroll
-                for (int r = 0; r < kRPT; ++r) {
-                    if (!row_ok[r])
-                        continue;
-                    // x neighbours: columns x-4 .. x+5 of row r (five 64-bit loads)
-                    float xv[10];
+        for (int d = 1; d <= R; ++d) {
+            above[d - 1] = *reinterpret_cast<const float2 *>(P + urow(-d));
+            below[d - 1] = *reinterpret_cast<const float2 *>(P + urow(kRPT - 1 + d));
+        }
 #pragma unroll
-                    for (int i = 0; i < 5; ++i) {
-                        const float2 v = *reinterpret_cast<const float2 *>(P + urow(r) - 4 + 2 * i);
-                        xv[2 * i] = v.x;
-                        xv[2 * i + 1] = v.y;
+        for (int r = 0; r < kRPT; ++r) {
+            if (!row_ok[r])
+                continue;
+            float xv[10];  // columns x-4 .. x+5 of row r (five 64-bit loads)
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const float2 v = *reinterpret_cast<const float2 *>(P + urow(r) - 4 + 2 * i);
+                xv[2 * i] = v.x;
+                xv[2 * i + 1] = v.y;
+            }
+            const float2 uc = q[r][R];
+            [[maybe_unused]] float2 pv, mv;
+            if constexpr (kWaveS) {
+                const int ci = cst * C::kCStage + (kRPT * wid + r) * kTX + kVX * tx;
+                pv = *reinterpret_cast<const float2 *>(ps + ci);
+                mv = *reinterpret_cast<const float2 *>(ms + ci);
+            }
+            float res[kVX];
+#pragma unroll
+            for (int c = 0; c < kVX; ++c) {
+                const float u = c ? uc.y : uc.x;
+                res[c] = u;  // Dirichlet shell keeps its value
+                if (z_interior && in_y[r] && in_x[c]) {
+                    float s[R + 1];
+                    s[0] = 0.0f;
+#pragma unroll
+                    for (int d = 1; d <= R; ++d) {
+                        const float2 ym = (r - d >= 0) ? q[(r - d) >= 0 ? r - d : 0][R]
+                                                       : above[(d - r - 1) >= 0 ? d - r - 1 : 0];
+                        const float2 yp = (r + d < kRPT) ? q[(r + d) < kRPT ? r + d : 0][R]
+                                                         : below[(r + d - kRPT) >= 0 ? r + d - kRPT : 0];
+                        const float2 zm = q[r][R - d];
+                        const float2 zp = q[r][R + d];
+                        s[d] = nbr_sum(xv[4 + c - d], xv[4 + c + d], c ? ym.y : ym.x, c ? yp.y : yp.x,
+                                       c ? zm.y : zm.x, c ? zp.y : zp.x);
                     }
-                    const float2 uc = q[r][(J + R) % Q];
-                    [[maybe_unused]] float2 pv, mv;
-                    if constexpr (kWaveS) {
-                        const int ci = cst * C::kCStage + (kRPT * ty + r) * kTX + kVX * tx;
-                        pv = *reinterpret_cast<const float2 *>(ps + ci);
-                        mv = *reinterpret_cast<const float2 *>(ms + ci);
+                    const float L = star_L<R>(a.c, u, s);
+                    if constexpr (SCHEME == kHeat) {
+                        res[c] = L;
+                    } else {
+                        const int y = y0 + kRPT * wid + r;
+                        const bool at_src = (x + c == a.src_x && y == a.src_y && z == a.src_zw);
+                        res[c] = wave_update(L, u, c ? pv.y : pv.x, c ? mv.y : mv.x, at_src, a.w);
                     }
-                    float res[kVX];
-#pragma unroll
-                    for (int c = 0; c < kVX; ++c) {
-                        const float u = c ? uc.y : uc.x;
-                        res[c] = u;  // Dirichlet shell keeps its value
-                        if (z_interior && in_y[r] && in_x[c]) {
-                            float s[R + 1];
-                            s[0] = 0.0f;
-#pragma unroll
-                            for (int d = 1; d <= R; ++d) {
-                                const float2 ym = (r - d >= 0) ? q[(r - d) >= 0 ? r - d : 0][(J + R) % Q]
-                                                               : above[(d - r - 1) >= 0 ? d - r - 1 : 0];
-                                const float2 yp = (r + d < kRPT) ? q[(r + d) < kRPT ? r + d : 0][(J + R) % Q]
-                                                                 : below[(r + d - kRPT) >= 0 ? r + d - kRPT : 0];
-                                const float2 zm = q[r][(J + R - d) % Q];
-                                const float2 zp = q[r][(J + R + d) % Q];
-                                s[d] = nbr_sum(xv[4 + c - d], xv[4 + c + d], c ? ym.y : ym.x,
-                                               c ? yp.y : yp.x, c ? zm.y : zm.x, c ? zp.y : zp.x);
-                            }
-                            const float L = star_L<R>(a.c, u, s);
-                            if constexpr (SCHEME == kHeat) {
-                                res[c] = L;
-                            } else {
-                                const int y = y0 + kRPT * ty + r;
-                                const bool at_src = (x + c == a.src_x && y == a.src_y && z == a.src_zw);
-                                res[c] = wave_update(L, u, c ? pv.y : pv.x, c ? mv.y : mv.x, at_src, a.w);
-                            }
-                        }
-                    }
-                    *reinterpret_cast<float2 *>(a.out + (int64_t)z * a.plane +
-                                                (int64_t)(y0 + kRPT * ty + r) * a.nx + x) =
-                        make_float2(res[0], res[1]);
                 }
             }
-            ok = __syncthreads_and(good);
-            if (ok && tid == 0) {  // stage of plane z is free: refill
-                issue_u(z + C::NSU);
-                issue_c(z + C::NSC);
-            }
-        });
-    }
-    if (!ok && tid == 0) {
-        // a wait ran out: let the copies already requested land before leaving
-        for (int p = pu0; p < u_issued; ++p)
-            mbar_wait(&ubar[u_stage(p)], u_phase(p));
-        for (int z = zs; z < c_issued; ++z)
-            mbar_wait(&cbar[(z - zs) % C::NSC], (uint32_t)(((z - zs) / C::NSC) & 1));
+            *reinterpret_cast<float2 *>(a.out + (int64_t)z * a.plane +
+                                        (int64_t)(y0 + kRPT * wid + r) * a.nx + x) =
+                make_float2(res[0], res[1]);
+        }
+        // plane z (xy neighbours) and its prev / m stage are done
+        __syncwarp();
+        if (tx == 0) {
+            mbar_arrive(&uempty[u_stage(z)]);
+            if (kWaveS)
+                mbar_arrive(&cempty[cst]);
+        }
     }
 }
 
@@ -365,7 +387,7 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
     a.zchunk = (nplanes + best - 1) / best;
     const int nchunks = (nplanes + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles_x, tiles_y, nchunks);
-    dim3 block(32, kTY / kRPT, 1);
+    dim3 block(32, kConsumerWarps + 1, 1);
     kern<<<grid, block, smem, s>>>(mc, mp, mm, a);
     return cudaGetLastError();
 }
