@@ -43,6 +43,10 @@ BUDGET = 4 << 30
 RATE = 16
 WAVE_BYTES_PER_POINT = 16  # read u, u_prev, m; write u_next (FP32)
 WORKLOAD = "wave25_512cubed_100steps_8slabs_k4_rate16_swb"
+# DRAM bytes (read + write) per updated point of the wave step kernel from one ncu
+# capture of a 512x512x192 case (profiles/k_star_step_and_codec_512x512x192.md);
+# scaled to a launch by its points.  Set to None whenever the kernel changes.
+STEP_TRAFFIC_B_PER_POINT = 15.53
 
 
 def parse():
@@ -323,7 +327,10 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": "k_star_step<4,wave>",
                 "achieved": step_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (step_gbs / hbm_peak) if step_gbs else None,
-                "traffic": None,
+                "traffic": (STEP_TRAFFIC_B_PER_POINT * cls["step"]["units"] / max(cls["step"]["launches"], 1)
+                            if STEP_TRAFFIC_B_PER_POINT else None),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 512x512x192 "
+                                  "launch, scaled by points per launch",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": step_bytes / max(cls["step"]["launches"], 1),
                 "avg_launch_ms": cls["step"]["device_ms"] / max(cls["step"]["launches"], 1)}
