@@ -483,20 +483,48 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     if (s > 0)
         CU(c, cudaStreamWaitEvent(st, c->ev_h2d[qp], 0));
     // 5. load / decode the window at time t
-    for (int f = 0; f < v.fin; ++f) {
-        float *dst = c->wbuf(wb, f);  // heat: U -> buf 0; wave: U, U_PREV, M -> 0, 1, 2
-        if (s > 0) {
-            // slot of slab s-1 holds layers starting at its own n0
-            const int64_t pz0 = (int64_t)(s - 1) * v.T;
-            const int64_t pw0 = std::max<int64_t>(pz0 - v.h, 0);
-            const int64_t pn0 = (s - 1 == 0) ? pw0 : pz0 + v.h;
-            oocs_status r = load_layers(c, c->in_slot(qp, f), pn0 / 4, w0 / 4, n0 / 4, dst, w0, st);
+    // slot of slab s-1 holds layers starting at its own n0
+    const int64_t pz0 = (int64_t)(s - 1) * v.T;
+    const int64_t pn0 = (s <= 1) ? 0 : pz0 + v.h;
+    const int64_t plane_f = d.nx * d.ny;
+    if (d.rate_bits > 0) {
+        // one decode launch for every field and both source slots
+        CodecSegments sg;
+        int64_t nl[kMaxCodecSegments];
+        for (int f = 0; f < v.fin; ++f) {
+            float *dst = c->wbuf(wb, f);  // heat: U -> buf 0; wave: U, U_PREV, M -> 0, 1, 2
+            if (s > 0 && n0 > w0) {
+                sg.blocks[sg.nseg] = c->in_slot(qp, f) + (w0 / 4 - pn0 / 4) * v.layer_bytes;
+                sg.planes[sg.nseg] = dst;
+                nl[sg.nseg++] = (n0 - w0) / 4;
+            }
+            if (n1 > n0) {
+                sg.blocks[sg.nseg] = c->in_slot(q, f);
+                sg.planes[sg.nseg] = dst + (n0 - w0) * plane_f;
+                nl[sg.nseg++] = (n1 - n0) / 4;
+            }
+        }
+        KernelScope ks;
+        oocs_status r = ks.begin(c, st, kClsLoad);
+        if (r != OOCS_OK)
+            return r;
+        CU(c, launch_decode_segments(sg, nl, d.nx, d.ny, d.rate_bits, st));
+        c->stats.kernel_launches++;
+        r = ks.end(kClsLoad, (uint64_t)v.fin * (w1 - w0) * plane_f);
+        if (r != OOCS_OK)
+            return r;
+    } else {
+        for (int f = 0; f < v.fin; ++f) {
+            float *dst = c->wbuf(wb, f);
+            if (s > 0) {
+                oocs_status r = load_layers(c, c->in_slot(qp, f), pn0 / 4, w0 / 4, n0 / 4, dst, w0, st);
+                if (r != OOCS_OK)
+                    return r;
+            }
+            oocs_status r = load_layers(c, c->in_slot(q, f), n0 / 4, n0 / 4, n1 / 4, dst, w0, st);
             if (r != OOCS_OK)
                 return r;
         }
-        oocs_status r = load_layers(c, c->in_slot(q, f), n0 / 4, n0 / 4, n1 / 4, dst, w0, st);
-        if (r != OOCS_OK)
-            return r;
     }
     CU(c, cudaEventRecord(c->ev_decoded[q], st));
 
@@ -543,7 +571,26 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         std::swap(cur, oth);
     }
     // 7. interior [z0, z1) -> out slot(s): u^(t+k) and, for the wave, u^(t+k-1)
-    {
+    if (d.rate_bits > 0) {
+        // one encode launch for both output fields
+        CodecSegments sg;
+        int64_t nl[kMaxCodecSegments];
+        const int src_buf[2] = {cur, oth};
+        for (int f = 0; f < v.fout; ++f) {
+            sg.blocks[sg.nseg] = c->out_slot(q, f);
+            sg.planes[sg.nseg] = c->wbuf(wb, src_buf[f]) + (z0 - w0) * plane_f;
+            nl[sg.nseg++] = (z1 - z0) / 4;
+        }
+        KernelScope ks;
+        oocs_status r = ks.begin(c, st, kClsStore);
+        if (r != OOCS_OK)
+            return r;
+        CU(c, launch_encode_segments(sg, nl, d.nx, d.ny, d.rate_bits, st));
+        c->stats.kernel_launches++;
+        r = ks.end(kClsStore, (uint64_t)v.fout * (z1 - z0) * plane_f);
+        if (r != OOCS_OK)
+            return r;
+    } else {
         oocs_status r = store_layers(c, c->wbuf(wb, cur), w0, z0 / 4, z1 / 4, c->out_slot(q, 0), st);
         if (r != OOCS_OK)
             return r;

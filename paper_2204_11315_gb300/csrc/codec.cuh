@@ -135,12 +135,30 @@ OOCS_FN void xform_inv(int32_t (&q)[64])
 }
 
 // In-place 32x32 bit-matrix transpose: afterwards bit i of a[p] is what bit p
-// of a[i] was.  Five block-swap levels (16, 8, 4, 2, 1).
+// of a[i] was.  Five block-swap levels; the 16- and 8-bit levels move whole
+// bytes (one byte permute per word), the 4-, 2- and 1-bit levels use masked
+// xor swaps.
 OOCS_FN void transpose32(uint32_t (&a)[32])
 {
-    uint32_t m = 0x0000FFFFu;
 #pragma unroll
-    for (int j = 16; j != 0; j >>= 1, m ^= (m << j)) {
+    for (int k = 0; k < 16; ++k) {  // swap 16-bit halves of rows k and k+16
+        const uint32_t lo = prmt(a[k], a[k + 16], 0x5410);
+        const uint32_t hi = prmt(a[k], a[k + 16], 0x7632);
+        a[k] = lo;
+        a[k + 16] = hi;
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {  // swap bytes of rows k and k+8
+        if ((k & 8) == 0 && k < 24) {
+            const uint32_t lo = prmt(a[k], a[k + 8], 0x6240);
+            const uint32_t hi = prmt(a[k], a[k + 8], 0x7351);
+            a[k] = lo;
+            a[k + 8] = hi;
+        }
+    }
+    uint32_t m = 0x0F0F0F0Fu;
+#pragma unroll
+    for (int j = 4; j != 0; j >>= 1, m ^= (m << j)) {
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
             if ((k & j) == 0) {
@@ -200,16 +218,18 @@ struct BitWriter {
 template <class Src>
 struct BitReader {
     Src &src;
-    uint64_t win = 0;
-    int nwin = 0;
-    int ridx = 0;
+    uint64_t win = 0;   // unread bits, least significant first
+    int nwin = 0;       // valid bits in win
+    int ridx = 0;       // index of `next`
+    uint32_t next;      // the following word, loaded one refill ahead
 
-    OOCS_FN explicit BitReader(Src &s) : src(s) {}
+    OOCS_FN explicit BitReader(Src &s) : src(s) { next = src(0); }
     OOCS_FN void fill()
     {
         if (nwin < 32) {
-            win |= (uint64_t)src(ridx++) << nwin;
+            win |= (uint64_t)next << nwin;
             nwin += 32;
+            next = src(++ridx);
         }
     }
     OOCS_FN uint32_t peek(int n)  // n in [1, 32]
@@ -298,12 +318,10 @@ OOCS_FN void encode_block(const float (&v)[64], int rate, Sink &&sink)
                 --left;
                 break;
             }
-            bw.put(1u, 1);
-            --left;
             const int f = n + ctz64(rest);  // next significant coefficient
-            // zeros for n .. f-1 then a one; at f = 63 the one is implied
-            const int len = (f < 63) ? (f - n + 1) : (63 - n);
-            const uint64_t code = (f < 63) ? (1ull << (f - n)) : 0ull;
+            // group-test 1, zeros for n .. f-1, then a one (implied at f = 63)
+            const int len = (f < 63) ? (f - n + 2) : (64 - n);
+            const uint64_t code = (f < 63) ? ((1ull << (f - n + 1)) | 1ull) : 1ull;
             if (len > left) {
                 bw.put64(code, left);
                 left = 0;
@@ -347,10 +365,39 @@ OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64])
         left -= t;
         if (t == n) {
             while (n < 64 && left > 0) {
-                const uint32_t g = br.get(1);
-                --left;
-                if (!g)
+                br.fill();  // >= 32 valid bits
+                const uint32_t w = (uint32_t)br.win;
+                if (!(w & 1u)) {  // group test 0: plane done
+                    br.win >>= 1;
+                    br.nwin -= 1;
+                    --left;
                     break;
+                }
+                {
+                    // fast path: the whole token lies in the 31 bits after the
+                    // group-test bit and inside the budget
+                    const int lim0 = 63 - n;
+                    const uint32_t after = w >> 1;
+                    const int z0 = after ? ctz32(after) : 32;
+                    if (z0 < lim0 && z0 < 31 && z0 + 2 <= left) {
+                        br.win >>= z0 + 2;
+                        br.nwin -= z0 + 2;
+                        left -= z0 + 2;
+                        X |= 1ull << (n + z0);
+                        n += z0 + 1;
+                        continue;
+                    }
+                    if (z0 >= lim0 && lim0 < 31 && lim0 + 1 <= left) {  // the implied last one
+                        br.win >>= lim0 + 1;
+                        br.nwin -= lim0 + 1;
+                        left -= lim0 + 1;
+                        X |= 1ull << 63;
+                        n = 64;
+                        continue;
+                    }
+                }
+                br.skip(1);  // general path: consume the group-test 1
+                --left;
                 const int lim = 63 - n;  // zeros possible before the implied last one
                 const int avail = min(lim, left);
                 int z = 0;

@@ -437,20 +437,34 @@ cudaError_t read_device_error(unsigned int *code, bool clear)
 
 constexpr int kCodecThreads = 128;
 
+// Locate global block b in a segment list; returns the segment and the block's
+// (bx, by, layer) inside it.
+OOCS_FN int find_segment(const CodecSegments &sg, int64_t b, int bnx, int bny, int &bx, int &by,
+                         int64_t &bl)
+{
+    int g = 0;
+#pragma unroll 1
+    while (g + 1 < sg.nseg && b >= sg.first[g + 1])
+        ++g;
+    const int64_t lb = b - sg.first[g];
+    bx = (int)(lb % bnx);
+    const int64_t t = lb / bnx;
+    by = (int)(t % bny);
+    bl = t / bny;
+    return g;
+}
+
 __global__ void __launch_bounds__(kCodecThreads)
-    k_encode_layers(const float *__restrict__ planes, int nx, int ny, int64_t nblocks, int rate,
-                    uint32_t *__restrict__ out)
+    k_encode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
     const int64_t b = (int64_t)blockIdx.x * kCodecThreads + threadIdx.x;
-    if (b >= nblocks)
+    if (b >= sg.first[sg.nseg])
         return;
-    const int bnx = nx >> 2, bny = ny >> 2;
-    const int bx = (int)(b % bnx);
-    const int64_t t = b / bnx;
-    const int by = (int)(t % bny);
-    const int64_t bl = t / bny;
+    int bx, by;
+    int64_t bl;
+    const int g = find_segment(sg, b, nx >> 2, ny >> 2, bx, by, bl);
     const int64_t plane = (int64_t)nx * ny;
-    const float *base = planes + 4 * bl * plane + (int64_t)(4 * by) * nx + 4 * bx;
+    const float *base = sg.planes[g] + 4 * bl * plane + (int64_t)(4 * by) * nx + 4 * bx;
     float v[64];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -462,28 +476,26 @@ __global__ void __launch_bounds__(kCodecThreads)
             v[16 * k + 4 * j + 2] = f.z;
             v[16 * k + 4 * j + 3] = f.w;
         }
-    uint32_t *o = out + b * (int64_t)(2 * rate);
+    uint32_t *o = static_cast<uint32_t *>(sg.blocks[g]) + (b - sg.first[g]) * (int64_t)(2 * rate);
     encode_block(v, rate, [&](int i, uint32_t w) { o[i] = w; });
 }
 
 __global__ void __launch_bounds__(kCodecThreads)
-    k_decode_layers(const uint32_t *__restrict__ in, int nx, int ny, int64_t nblocks, int rate,
-                    float *__restrict__ planes)
+    k_decode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
     const int64_t b = (int64_t)blockIdx.x * kCodecThreads + threadIdx.x;
-    if (b >= nblocks)
+    if (b >= sg.first[sg.nseg])
         return;
-    const int bnx = nx >> 2, bny = ny >> 2;
-    const int bx = (int)(b % bnx);
-    const int64_t t = b / bnx;
-    const int by = (int)(t % bny);
-    const int64_t bl = t / bny;
+    int bx, by;
+    int64_t bl;
+    const int g = find_segment(sg, b, nx >> 2, ny >> 2, bx, by, bl);
     const int64_t plane = (int64_t)nx * ny;
-    const uint32_t *src = in + b * (int64_t)(2 * rate);
+    const uint32_t *src =
+        static_cast<const uint32_t *>(sg.blocks[g]) + (b - sg.first[g]) * (int64_t)(2 * rate);
     const int nw = 2 * rate;
     float v[64];
     decode_block(rate, [&](int i) -> uint32_t { return i < nw ? __ldg(src + i) : 0u; }, v);
-    float *base = planes + 4 * bl * plane + (int64_t)(4 * by) * nx + 4 * bx;
+    float *base = sg.planes[g] + 4 * bl * plane + (int64_t)(4 * by) * nx + 4 * bx;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
@@ -493,28 +505,62 @@ __global__ void __launch_bounds__(kCodecThreads)
                             v[16 * k + 4 * j + 3]);
 }
 
+static cudaError_t seal_segments(CodecSegments &sg, int64_t nx, int64_t ny, const int64_t *nlayers)
+{
+    if (sg.nseg < 0 || sg.nseg > kMaxCodecSegments)
+        return cudaErrorInvalidValue;
+    sg.first[0] = 0;
+    for (int g = 0; g < sg.nseg; ++g)
+        sg.first[g + 1] = sg.first[g] + (nx / 4) * (ny / 4) * nlayers[g];
+    return cudaSuccess;
+}
+
+cudaError_t launch_encode_segments(CodecSegments sg, const int64_t *nlayers, int64_t nx, int64_t ny,
+                                   int rate, cudaStream_t s)
+{
+    cudaError_t e = seal_segments(sg, nx, ny, nlayers);
+    if (e != cudaSuccess)
+        return e;
+    const int64_t nb = sg.first[sg.nseg];
+    if (nb == 0)
+        return cudaSuccess;
+    k_encode_layers<<<(unsigned)((nb + kCodecThreads - 1) / kCodecThreads), kCodecThreads, 0, s>>>(
+        sg, (int)nx, (int)ny, rate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_segments(CodecSegments sg, const int64_t *nlayers, int64_t nx, int64_t ny,
+                                   int rate, cudaStream_t s)
+{
+    cudaError_t e = seal_segments(sg, nx, ny, nlayers);
+    if (e != cudaSuccess)
+        return e;
+    const int64_t nb = sg.first[sg.nseg];
+    if (nb == 0)
+        return cudaSuccess;
+    k_decode_layers<<<(unsigned)((nb + kCodecThreads - 1) / kCodecThreads), kCodecThreads, 0, s>>>(
+        sg, (int)nx, (int)ny, rate);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_encode_layers(const float *planes, int64_t nx, int64_t ny, int64_t nlayers,
                                  int rate, void *blocks, cudaStream_t s)
 {
-    const int64_t nb = (nx / 4) * (ny / 4) * nlayers;
-    if (nb == 0)
-        return cudaSuccess;
-    const int64_t grid = (nb + kCodecThreads - 1) / kCodecThreads;
-    k_encode_layers<<<(unsigned)grid, kCodecThreads, 0, s>>>(planes, (int)nx, (int)ny, nb, rate,
-                                                             static_cast<uint32_t *>(blocks));
-    return cudaGetLastError();
+    CodecSegments sg;
+    sg.nseg = 1;
+    sg.planes[0] = const_cast<float *>(planes);
+    sg.blocks[0] = blocks;
+    return launch_encode_segments(sg, &nlayers, nx, ny, rate, s);
 }
 
 cudaError_t launch_decode_layers(const void *blocks, int64_t nx, int64_t ny, int64_t nlayers,
                                  int rate, float *planes, cudaStream_t s)
 {
-    const int64_t nb = (nx / 4) * (ny / 4) * nlayers;
-    if (nb == 0)
-        return cudaSuccess;
-    const int64_t grid = (nb + kCodecThreads - 1) / kCodecThreads;
-    k_decode_layers<<<(unsigned)grid, kCodecThreads, 0, s>>>(
-        static_cast<const uint32_t *>(blocks), (int)nx, (int)ny, nb, rate, planes);
-    return cudaGetLastError();
+    CodecSegments sg;
+    sg.nseg = 1;
+    sg.planes[0] = planes;
+    sg.blocks[0] = const_cast<void *>(blocks);
+    return launch_decode_segments(sg, &nlayers, nx, ny, rate, s);
 }
 
 }  // namespace oocs

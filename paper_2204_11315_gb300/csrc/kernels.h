@@ -31,6 +31,22 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s);
 // bounded waits ran out (0 = no error).
 cudaError_t read_device_error(unsigned int *code, bool clear);
 
+// Up to kMaxCodecSegments runs of whole 4-plane layers coded by one launch:
+// segment g maps nlayers[g] layers of FP32 planes at planes[g] to / from the
+// codec blocks at blocks[g] (first[] is filled by the launcher).
+constexpr int kMaxCodecSegments = 8;
+struct CodecSegments {
+    float *planes[kMaxCodecSegments];
+    void *blocks[kMaxCodecSegments];
+    int64_t first[kMaxCodecSegments + 1];
+    int nseg = 0;
+};
+
+cudaError_t launch_encode_segments(CodecSegments sg, const int64_t *nlayers, int64_t nx, int64_t ny,
+                                   int rate, cudaStream_t s);
+cudaError_t launch_decode_segments(CodecSegments sg, const int64_t *nlayers, int64_t nx, int64_t ny,
+                                   int rate, cudaStream_t s);
+
 // Fixed-rate codec over whole 4-plane layers.  planes: first FP32 plane of the
 // first layer; blocks: first block of the first layer.
 cudaError_t launch_encode_layers(const float *planes, int64_t nx, int64_t ny, int64_t nlayers,
