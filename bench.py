@@ -405,7 +405,9 @@ def run_ours(args):
     compare = None
     if not args.no_compare:
         compare = {}
-        for name, rate, wb in (("uncompressed_swb", 0, 1), ("uncompressed_classic", 0, 3)):
+        for name, rate, wb in (("uncompressed_swb", 0, 1), ("uncompressed_classic", 0, 3),
+                               (f"rate{args.rate}_classic", args.rate, 3),
+                               ("rate8_swb", 8, 1), ("rate12_swb", 12, 1)):
             st, pin = open_ctx(P, torch, rate, wb, inputs)
             snap_u = st.snapshot_stores()
             timed_calls(torch, st, 1, snap_u)

@@ -99,7 +99,8 @@ typedef struct {
  * for STORE the values encoded (or copied) out of it.  `device_ms` is the sum
  * of CUDA-event durations of those launches on their own streams, collected
  * only while profiling is on (oocs_set_profiling) and read at
- * oocs_synchronize.                                                        */
+ * oocs_synchronize; the k STEP launches of one slab visit are timed as one
+ * interval (gaps between them included).                                   */
 typedef struct {
     uint64_t launches;
     uint64_t units;

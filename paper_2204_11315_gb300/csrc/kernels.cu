@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "codec.cuh"
 #include "kernels.h"
@@ -22,6 +23,26 @@
 #include "tma.cuh"
 
 namespace oocs {
+
+// Launch with programmatic stream serialization: the kernel may begin while its
+// predecessor in the stream drains (every kernel here waits in
+// pdl_wait_prior_grid before touching global memory).
+template <class... KArgs, class... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 constexpr int kVX = 2;                  // x-adjacent points per thread (float2)
 constexpr int kTX = 32 * kVX;           // tile width (x) = 64
@@ -106,6 +127,10 @@ __global__ void __launch_bounds__(kStepThreads, 2)
         fence_barrier_init();
     }
     __syncthreads();  // the only CTA-wide barrier
+    // everything above overlaps the previous kernel's tail; global memory is
+    // touched only after it has completed
+    pdl_launch_dependents();
+    pdl_wait_prior_grid();
 
     if (wid == kConsumerWarps) {
         // ------------------------------------------------ producer warp --
@@ -388,8 +413,7 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
     const int nchunks = (nplanes + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles_x, tiles_y, nchunks);
     dim3 block(32, kConsumerWarps + 1, 1);
-    kern<<<grid, block, smem, s>>>(mc, mp, mm, a);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, block, smem, s, mc, mp, mm, a);
 }
 
 cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
@@ -457,6 +481,8 @@ OOCS_FN int find_segment(const CodecSegments &sg, int64_t b, int bnx, int bny, i
 __global__ void __launch_bounds__(kCodecThreads)
     k_encode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
+    pdl_launch_dependents();
+    pdl_wait_prior_grid();
     const int64_t b = (int64_t)blockIdx.x * kCodecThreads + threadIdx.x;
     if (b >= sg.first[sg.nseg])
         return;
@@ -483,6 +509,8 @@ __global__ void __launch_bounds__(kCodecThreads)
 __global__ void __launch_bounds__(kCodecThreads)
     k_decode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
+    pdl_launch_dependents();
+    pdl_wait_prior_grid();
     const int64_t b = (int64_t)blockIdx.x * kCodecThreads + threadIdx.x;
     if (b >= sg.first[sg.nseg])
         return;
@@ -524,9 +552,8 @@ cudaError_t launch_encode_segments(CodecSegments sg, const int64_t *nlayers, int
     const int64_t nb = sg.first[sg.nseg];
     if (nb == 0)
         return cudaSuccess;
-    k_encode_layers<<<(unsigned)((nb + kCodecThreads - 1) / kCodecThreads), kCodecThreads, 0, s>>>(
-        sg, (int)nx, (int)ny, rate);
-    return cudaGetLastError();
+    return launch_pdl(k_encode_layers, dim3((unsigned)((nb + kCodecThreads - 1) / kCodecThreads)),
+                      dim3(kCodecThreads), 0, s, sg, (int)nx, (int)ny, rate);
 }
 
 cudaError_t launch_decode_segments(CodecSegments sg, const int64_t *nlayers, int64_t nx, int64_t ny,
@@ -538,9 +565,8 @@ cudaError_t launch_decode_segments(CodecSegments sg, const int64_t *nlayers, int
     const int64_t nb = sg.first[sg.nseg];
     if (nb == 0)
         return cudaSuccess;
-    k_decode_layers<<<(unsigned)((nb + kCodecThreads - 1) / kCodecThreads), kCodecThreads, 0, s>>>(
-        sg, (int)nx, (int)ny, rate);
-    return cudaGetLastError();
+    return launch_pdl(k_decode_layers, dim3((unsigned)((nb + kCodecThreads - 1) / kCodecThreads)),
+                      dim3(kCodecThreads), 0, s, sg, (int)nx, (int)ny, rate);
 }
 
 cudaError_t launch_encode_layers(const float *planes, int64_t nx, int64_t ny, int64_t nlayers,
