@@ -238,6 +238,40 @@ oocs_status oocs_encode_device(const float *field, int64_t nx, int64_t ny, int64
 oocs_status oocs_decode_device(const void *blocks, int64_t nx, int64_t ny, int64_t nz,
                                int32_t rate, float *field, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Schedule trace (no GPU needed): the operations oocs_step would enqueue, in
+ * enqueue order, for a fresh context, so their ordering can be checked on the
+ * host.  This is the DAG of Fig. 8(a) as built by Algorithm 1's scheduling.
+ * ------------------------------------------------------------------------- */
+enum { OOCS_OP_WAIT = 1, OOCS_OP_RECORD = 2, OOCS_OP_H2D = 3, OOCS_OP_D2H = 4, OOCS_OP_LOAD = 5,
+       OOCS_OP_STEP = 6, OOCS_OP_STORE = 7 };
+/* resources: the working buffer set, staging slots in / out, a host store */
+enum { OOCS_RES_WORK = 1, OOCS_RES_IN_SLOT = 2, OOCS_RES_OUT_SLOT = 3, OOCS_RES_HOST = 4 };
+
+typedef struct {
+    int32_t kind;     /* OOCS_RES_*                                                 */
+    int32_t index;    /* working-buffer set, slot number, or host field id          */
+    int64_t lo, hi;   /* 4-plane layers [lo, hi) in global z                        */
+    int32_t write;    /* 1 = written, 0 = read                                      */
+    int32_t reserved;
+} oocs_trace_access;
+
+typedef struct {
+    int32_t op;       /* OOCS_OP_*                                                  */
+    int32_t stream;   /* 0..2                                                       */
+    int32_t event;    /* WAIT / RECORD: event id (same id = same CUDA event); else -1 */
+    int32_t naccess;
+    int64_t visit;    /* slab visit number g of the op (-1 for events)              */
+    oocs_trace_access access[4];
+} oocs_trace_op;
+
+/* Trace ncalls successive oocs_step(nsteps[i]) calls for `desc`.  Writes up to
+ * `capacity` ops and the total needed to *count; OOCS_ERR_INVALID_ARG (with
+ * *count set) when capacity is too small.  Allocates and frees host memory
+ * only; touches no GPU.                                                    */
+oocs_status oocs_trace_schedule(const oocs_desc *desc, const int32_t *nsteps, int32_t ncalls,
+                                oocs_trace_op *ops, int64_t capacity, int64_t *count);
+
 /* Library version string. */
 const char *oocs_version(void);
 

@@ -33,6 +33,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <initializer_list>
 #include <new>
 #include <string>
 #include <thread>
@@ -264,6 +265,10 @@ struct oocs_ctx {
     uint64_t g = 0;  // slab visits enqueued
     oocs_stats stats;
 
+    // trace mode (oocs_trace_schedule): scheduling operations are recorded
+    // here instead of being issued to CUDA
+    std::vector<oocs_trace_op> *trace = nullptr;
+
     // per-launch event timing (oocs_set_profiling): bit mask of kernel classes
     int prof = 0;
     std::vector<cudaEvent_t> ev_pool;  // created on demand, reused after collection
@@ -311,14 +316,23 @@ int in_field_id(const oocs_ctx *c, int f)
 }
 
 // make every stream wait for the work enqueued so far on all three
+oocs_status sched_record(oocs_ctx *c, int si, int ev);
+oocs_status sched_wait(oocs_ctx *c, int si, int ev);
+
 oocs_status join_streams(oocs_ctx *c)
 {
-    for (int i = 0; i < 3; ++i)
-        CU(c, cudaEventRecord(c->ev_join[i], c->st[i]));
+    for (int i = 0; i < 3; ++i) {
+        oocs_status r = sched_record(c, i, 400 + i);
+        if (r != OOCS_OK)
+            return r;
+    }
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
-            if (i != j)
-                CU(c, cudaStreamWaitEvent(c->st[i], c->ev_join[j], 0));
+            if (i != j) {
+                oocs_status r = sched_wait(c, i, 400 + j);
+                if (r != OOCS_OK)
+                    return r;
+            }
     return OOCS_OK;
 }
 
@@ -330,6 +344,81 @@ oocs_status check_ready(oocs_ctx *c)
         return c->sticky;
     return OOCS_OK;
 }
+
+// ---- scheduling primitives: issued to CUDA, or recorded in trace mode
+
+enum : int { kEvDecoded = 100, kEvH2D = 200, kEvWrel = 300, kEvJoin = 400, kEvT0 = 500, kEvT1 = 501,
+             kEvD2H = 1000 };
+
+cudaEvent_t event_of(oocs_ctx *c, int id)
+{
+    if (id >= kEvD2H)
+        return c->ev_d2h[id - kEvD2H];
+    if (id == kEvT0)
+        return c->ev_t0;
+    if (id == kEvT1)
+        return c->ev_t1;
+    switch (id / 100) {
+    case 1: return c->ev_decoded[id % 100];
+    case 2: return c->ev_h2d[id % 100];
+    case 3: return c->ev_wrel[id % 100];
+    default: return c->ev_join[id % 100];
+    }
+}
+
+void trace_push(oocs_ctx *c, int op, int si, int ev, int64_t visit,
+                std::initializer_list<oocs_trace_access> acc)
+{
+    oocs_trace_op t;
+    memset(&t, 0, sizeof(t));
+    t.op = op;
+    t.stream = si;
+    t.event = ev;
+    t.visit = visit;
+    for (const auto &a : acc)
+        if (t.naccess < 4)
+            t.access[t.naccess++] = a;
+    c->trace->push_back(t);
+}
+
+oocs_trace_access acc(int kind, int index, int64_t lo, int64_t hi, bool write)
+{
+    oocs_trace_access a;
+    memset(&a, 0, sizeof(a));
+    a.kind = kind;
+    a.index = index;
+    a.lo = lo;
+    a.hi = hi;
+    a.write = write ? 1 : 0;
+    return a;
+}
+
+oocs_status sched_wait(oocs_ctx *c, int si, int ev)
+{
+    if (c->trace) {
+        trace_push(c, OOCS_OP_WAIT, si, ev, -1, {});
+        return OOCS_OK;
+    }
+    CU(c, cudaStreamWaitEvent(c->st[si], event_of(c, ev), 0));
+    return OOCS_OK;
+}
+
+oocs_status sched_record(oocs_ctx *c, int si, int ev)
+{
+    if (c->trace) {
+        trace_push(c, OOCS_OP_RECORD, si, ev, -1, {});
+        return OOCS_OK;
+    }
+    CU(c, cudaEventRecord(event_of(c, ev), c->st[si]));
+    return OOCS_OK;
+}
+
+#define SCHED(call)                  \
+    do {                             \
+        oocs_status r_ = (call);     \
+        if (r_ != OOCS_OK)           \
+            return r_;               \
+    } while (0)
 
 enum { kClsLoad = 0, kClsStep = 1, kClsStore = 2 };
 
@@ -460,34 +549,55 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
 
     // 1. staging slot q is free once visit g-2 has read its borrowed overlap
     if (g >= 2)
-        CU(c, cudaStreamWaitEvent(st, c->ev_decoded[(g - 2) % 3], 0));
+        SCHED(sched_wait(c, q, kEvDecoded + (int)((g - 2) % 3)));
     // 2. host layers [n0, n1) were last written by slabs s and s+1 of the previous sweep
     for (int ss = s; ss <= s + 1 && ss < v.S; ++ss)
         if (c->d2h_recorded[ss])
-            CU(c, cudaStreamWaitEvent(st, c->ev_d2h[ss], 0));
+            SCHED(sched_wait(c, q, kEvD2H + ss));
     // 3. H2D of the new layers of every streamed field
-    for (int f = 0; f < v.fin; ++f) {
-        const int id = in_field_id(c, f);
-        const uint64_t bytes = (uint64_t)(n1 - n0) / 4 * v.layer_bytes;
-        if (bytes) {
-            CU(c, cudaMemcpyAsync(c->in_slot(q, f), c->store[id] + (uint64_t)(n0 / 4) * v.layer_bytes,
-                                  bytes, cudaMemcpyHostToDevice, st));
-            c->stats.h2d_bytes += bytes;
+    if (c->trace) {
+        if (n1 > n0) {
+            oocs_trace_access a[4] = {acc(OOCS_RES_IN_SLOT, q, n0 / 4, n1 / 4, true)};
+            for (int f = 0; f < v.fin; ++f)
+                a[1 + f] = acc(OOCS_RES_HOST, in_field_id(c, f), n0 / 4, n1 / 4, false);
+            trace_push(c, OOCS_OP_H2D, q, -1, (int64_t)g, {a[0], a[1]});
+            for (int f = 1; f < v.fin; ++f)
+                c->trace->back().access[c->trace->back().naccess++] = a[1 + f];
+        }
+    } else {
+        for (int f = 0; f < v.fin; ++f) {
+            const int id = in_field_id(c, f);
+            const uint64_t bytes = (uint64_t)(n1 - n0) / 4 * v.layer_bytes;
+            if (bytes) {
+                CU(c, cudaMemcpyAsync(c->in_slot(q, f), c->store[id] + (uint64_t)(n0 / 4) * v.layer_bytes,
+                                      bytes, cudaMemcpyHostToDevice, st));
+            }
         }
     }
-    CU(c, cudaEventRecord(c->ev_h2d[q], st));
+    c->stats.h2d_bytes += (uint64_t)v.fin * (uint64_t)(n1 - n0) / 4 * v.layer_bytes;
+    SCHED(sched_record(c, q, kEvH2D + q));
     // 4. working buffer released by visit g-1 (single working buffer); the
     //    overlap borrowed from visit g-1's slot has landed
     if (g >= 1 && d.working_buffers == OOCS_SWB)
-        CU(c, cudaStreamWaitEvent(st, c->ev_wrel[(g - 1) % 3], 0));
+        SCHED(sched_wait(c, q, kEvWrel + (int)((g - 1) % 3)));
     if (s > 0)
-        CU(c, cudaStreamWaitEvent(st, c->ev_h2d[qp], 0));
+        SCHED(sched_wait(c, q, kEvH2D + qp));
     // 5. load / decode the window at time t
     // slot of slab s-1 holds layers starting at its own n0
     const int64_t pz0 = (int64_t)(s - 1) * v.T;
     const int64_t pn0 = (s <= 1) ? 0 : pz0 + v.h;
     const int64_t plane_f = d.nx * d.ny;
-    if (d.rate_bits > 0) {
+    if (c->trace) {
+        if (s > 0)
+            trace_push(c, OOCS_OP_LOAD, q, -1, (int64_t)g,
+                       {acc(OOCS_RES_IN_SLOT, qp, w0 / 4, n0 / 4, false),
+                        acc(OOCS_RES_IN_SLOT, q, n0 / 4, n1 / 4, false),
+                        acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
+        else
+            trace_push(c, OOCS_OP_LOAD, q, -1, (int64_t)g,
+                       {acc(OOCS_RES_IN_SLOT, q, n0 / 4, n1 / 4, false),
+                        acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
+    } else if (d.rate_bits > 0) {
         // one decode launch for every field and both source slots
         CodecSegments sg;
         int64_t nl[kMaxCodecSegments];
@@ -526,7 +636,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
                 return r;
         }
     }
-    CU(c, cudaEventRecord(c->ev_decoded[q], st));
+    SCHED(sched_record(c, q, kEvDecoded + q));
 
     // 6. k_eff steps over the shrinking trapezoid
     int cur = 0, oth = 1;
@@ -568,7 +678,10 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             Ls.src_z = c->src[2];
             Ls.w = c->w[tstep];
         }
-        CU(c, launch_star_step(Ls, st));
+        if (c->trace)
+            trace_push(c, OOCS_OP_STEP, q, -1, (int64_t)g, {acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
+        else
+            CU(c, launch_star_step(Ls, st));
         c->stats.kernel_launches++;
         step_units += (uint64_t)(hi - lo) * d.nx * d.ny;
         std::swap(cur, oth);
@@ -579,7 +692,10 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             return r;
     }
     // 7. interior [z0, z1) -> out slot(s): u^(t+k) and, for the wave, u^(t+k-1)
-    if (d.rate_bits > 0) {
+    if (c->trace) {
+        trace_push(c, OOCS_OP_STORE, q, -1, (int64_t)g,
+                   {acc(OOCS_RES_WORK, wb, z0 / 4, z1 / 4, false), acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, true)});
+    } else if (d.rate_bits > 0) {
         // one encode launch for both output fields
         CodecSegments sg;
         int64_t nl[kMaxCodecSegments];
@@ -608,15 +724,22 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
                 return r;
         }
     }
-    CU(c, cudaEventRecord(c->ev_wrel[q], st));
+    SCHED(sched_record(c, q, kEvWrel + q));
     // 8. D2H into the host store, in place
+    if (c->trace) {
+        trace_push(c, OOCS_OP_D2H, q, -1, (int64_t)g,
+                   {acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, false), acc(OOCS_RES_HOST, 0, z0 / 4, z1 / 4, true)});
+        if (v.fout == 2)
+            c->trace->back().access[c->trace->back().naccess++] = acc(OOCS_RES_HOST, 1, z0 / 4, z1 / 4, true);
+    }
     for (int f = 0; f < v.fout; ++f) {
         const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
-        CU(c, cudaMemcpyAsync(c->store[f] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, f),
-                              bytes, cudaMemcpyDeviceToHost, st));
+        if (!c->trace)
+            CU(c, cudaMemcpyAsync(c->store[f] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, f),
+                                  bytes, cudaMemcpyDeviceToHost, st));
         c->stats.d2h_bytes += bytes;
     }
-    CU(c, cudaEventRecord(c->ev_d2h[s], st));
+    SCHED(sched_record(c, q, kEvD2H + s));
     c->d2h_recorded[s] = 1;
     c->g++;
     c->stats.slabs_done++;
@@ -827,7 +950,9 @@ oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
     s = join_streams(ctx);
     if (s != OOCS_OK)
         return s;
-    CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->st[0]));
+    s = sched_record(ctx, 0, kEvT0);
+    if (s != OOCS_OK)
+        return s;
     s = join_streams(ctx);
     if (s != OOCS_OK)
         return s;
@@ -848,8 +973,10 @@ oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
     s = join_streams(ctx);
     if (s != OOCS_OK)
         return s;
-    CU(ctx, cudaEventRecord(ctx->ev_t1, ctx->st[0]));
-    ctx->timing_pending = true;
+    s = sched_record(ctx, 0, kEvT1);
+    if (s != OOCS_OK)
+        return s;
+    ctx->timing_pending = !ctx->trace;
     return OOCS_OK;
 }
 
@@ -916,6 +1043,51 @@ oocs_status oocs_set_profiling(oocs_ctx *ctx, int32_t classes)
     if (classes < 0 || classes > 7)
         return fail(ctx, OOCS_ERR_INVALID_ARG, "profiling mask must be in [0, 7]");
     ctx->prof = classes;
+    return OOCS_OK;
+}
+
+oocs_status oocs_trace_schedule(const oocs_desc *desc, const int32_t *nsteps, int32_t ncalls,
+                                oocs_trace_op *ops, int64_t capacity, int64_t *count)
+{
+    if (!count || (ncalls > 0 && !nsteps) || ncalls < 0 || capacity < 0 || (capacity > 0 && !ops))
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "bad trace arguments");
+    *count = 0;
+    oocs_plan p;
+    std::string err;
+    oocs_status s = plan_impl(desc, &p, err);
+    if (s != OOCS_OK)
+        return fail(nullptr, s, err);
+    oocs_ctx *c = new (std::nothrow) oocs_ctx();
+    if (!c)
+        return fail(nullptr, OOCS_ERR_HOST_ALLOC, "cannot allocate the context");
+    std::vector<oocs_trace_op> trace;
+    c->trace = &trace;
+    c->d = *desc;
+    if (c->d.temporal_depth == 0)
+        c->d.temporal_depth = p.temporal_depth;
+    c->p = p;
+    c->v = derive(c->d, p.slab_planes);
+    c->L = layout_for(c->d, c->v, c->d.working_buffers);
+    memset(&c->stats, 0, sizeof(c->stats));
+    c->ev_d2h.assign(c->v.S, nullptr);
+    c->d2h_recorded.assign(c->v.S, 0);
+    static char dummy;
+    for (int f = 0; f < 3; ++f)
+        c->store[f] = &dummy;  // never dereferenced in trace mode
+    for (int i = 0; i < ncalls && s == OOCS_OK; ++i)
+        s = oocs_step(c, nsteps[i]);
+    if (s != OOCS_OK) {
+        std::string msg = c->err;
+        delete c;
+        return fail(nullptr, s, msg);
+    }
+    *count = (int64_t)trace.size();
+    delete c;
+    if ((int64_t)trace.size() > capacity)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG,
+                    "trace needs " + std::to_string(trace.size()) + " entries");
+    for (size_t i = 0; i < trace.size(); ++i)
+        ops[i] = trace[i];
     return OOCS_OK;
 }
 

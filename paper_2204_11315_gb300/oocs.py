@@ -80,6 +80,21 @@ class oocs_stats(ctypes.Structure):
         return d
 
 
+class oocs_trace_access(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("index", ctypes.c_int32), ("lo", ctypes.c_int64),
+                ("hi", ctypes.c_int64), ("write", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class oocs_trace_op(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("stream", ctypes.c_int32), ("event", ctypes.c_int32),
+                ("naccess", ctypes.c_int32), ("visit", ctypes.c_int64),
+                ("access", oocs_trace_access * 4)]
+
+
+OOCS_OP_NAMES = {1: "WAIT", 2: "RECORD", 3: "H2D", 4: "D2H", 5: "LOAD", 6: "STEP", 7: "STORE"}
+OOCS_RES_NAMES = {1: "WORK", 2: "IN_SLOT", 3: "OUT_SLOT", 4: "HOST"}
+
+
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _i64 = ctypes.c_int64
@@ -106,6 +121,8 @@ SIGNATURES = {
                                _i32, _vp]),
     "oocs_incore_run_noalloc": (_i32, [ctypes.POINTER(oocs_desc), _vp, _vp, _vp, _i32, _i64, _vp,
                                        _vp, _i32, _vp]),
+    "oocs_trace_schedule": (_i32, [ctypes.POINTER(oocs_desc), ctypes.POINTER(_i32), _i32,
+                                   ctypes.POINTER(oocs_trace_op), _i64, ctypes.POINTER(_i64)]),
     "oocs_encode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
     "oocs_decode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
 }
@@ -249,6 +266,25 @@ def oocs_incore_run_noalloc(desc, u_ptr, up_ptr, m_ptr, nsteps, t0=0, src=None, 
                                          int(nsteps), int(t0),
                                          ctypes.cast(srcarr, _vp) if srcarr is not None else None,
                                          wv.ctypes.data_as(_vp), int(wv.size), _vp(stream)))
+
+
+def oocs_trace_schedule(desc, nsteps_calls):
+    """Operations oocs_step(n) would enqueue for each n in nsteps_calls, as dicts:
+    {op, stream, event, visit, access: [(kind, index, lo, hi, write), ...]}."""
+    calls = (_i32 * len(nsteps_calls))(*[int(n) for n in nsteps_calls])
+    count = _i64(0)
+    lib().oocs_trace_schedule(ctypes.byref(desc), calls, len(nsteps_calls), None, 0, ctypes.byref(count))
+    buf = (oocs_trace_op * max(count.value, 1))()
+    _check(lib().oocs_trace_schedule(ctypes.byref(desc), calls, len(nsteps_calls), buf, count.value,
+                                     ctypes.byref(count)))
+    out = []
+    for i in range(count.value):
+        o = buf[i]
+        out.append({"op": OOCS_OP_NAMES[o.op], "stream": o.stream, "event": o.event,
+                    "visit": o.visit,
+                    "access": [(OOCS_RES_NAMES[a.kind], a.index, a.lo, a.hi, bool(a.write))
+                               for a in o.access[:o.naccess]]})
+    return out
 
 
 def oocs_encode_device(field_ptr, nx, ny, nz, rate, blocks_ptr, stream=0):

@@ -1,0 +1,190 @@
+"""Hazard check of the slab scheduler on the host (no GPU).
+
+oocs_trace_schedule returns, in enqueue order, the operations oocs_step would
+issue on its three streams (Algorithm 1's copies, kernels and event
+records/waits; Fig. 8).  From them this test builds the happens-before
+relation of CUDA streams and events (stream order; a wait depends on the most
+recent record of its event enqueued before it) and checks:
+
+* no race: every pair of operations that touch the same physical buffer (the
+  working buffer set, a staging slot) or the same host-store layer, one of them
+  writing, is ordered;
+* single working buffer (Sec. 5): all kernels of different slab visits are
+  ordered, i.e. they never overlap;
+* region sharing (Sec. 3.1): the overlap a visit borrows from the previous
+  visit's staging slot is exactly what that slot last received;
+* the in-place host store: in sweep p+1 every layer read was last written by
+  sweep p.
+
+Deleting any one kind of cross-stream wait from a trace must make the check
+fail, which shows the check can see the hazards the waits prevent.
+"""
+import itertools
+
+import pytest
+
+import synthetic
+
+SHARED = {"WORK", "IN_SLOT", "OUT_SLOT"}  # physical buffers: any two accesses overlap
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2204_11315_gb300 as P
+    P.lib()
+    return P
+
+
+def happens_before(trace):
+    """preds[i] = bit set of ops that happen before op i."""
+    n = len(trace)
+    preds = [0] * n
+    last_in_stream = {}
+    last_record = {}
+    for i, o in enumerate(trace):
+        p = 0
+        s = o["stream"]
+        if s in last_in_stream:
+            j = last_in_stream[s]
+            p |= preds[j] | (1 << j)
+        if o["op"] == "WAIT" and o["event"] in last_record:
+            j = last_record[o["event"]]
+            p |= preds[j] | (1 << j)
+        preds[i] = p
+        last_in_stream[s] = i
+        if o["op"] == "RECORD":
+            last_record[o["event"]] = i
+    return preds
+
+
+def conflicts(a, b):
+    for (ka, ia, la, ha, wa) in a["access"]:
+        for (kb, ib, lb, hb, wb) in b["access"]:
+            if ka != kb or ia != ib or not (wa or wb):
+                continue
+            if ka in SHARED or (la < hb and lb < ha):
+                return True
+    return False
+
+
+def check(trace, swb=True):
+    preds = happens_before(trace)
+    data_ops = [i for i, o in enumerate(trace) if o["access"]]
+    for i, j in itertools.combinations(data_ops, 2):
+        if conflicts(trace[i], trace[j]) and not (preds[j] >> i) & 1:
+            return f"race between {trace[i]} and {trace[j]}"
+    kernels = [i for i in data_ops if trace[i]["op"] in ("LOAD", "STEP", "STORE")]
+    if swb:
+        for i, j in itertools.combinations(kernels, 2):
+            if trace[i]["visit"] != trace[j]["visit"] and not (preds[j] >> i) & 1:
+                return f"kernels of visits {trace[i]['visit']} and {trace[j]['visit']} may overlap"
+    # borrowed overlap: each staging-slot read lies inside the slot's last write
+    last_slot_write = {}
+    for o in trace:
+        for (k, idx, lo, hi, w) in o["access"]:
+            if k == "IN_SLOT" and not w:
+                wl = last_slot_write.get(idx)
+                if wl is None or not (wl[0] <= lo and hi <= wl[1]):
+                    return f"visit {o['visit']} reads slot {idx} layers [{lo},{hi}) not staged there"
+        for (k, idx, lo, hi, w) in o["access"]:
+            if k == "IN_SLOT" and w:
+                last_slot_write[idx] = (lo, hi)
+    return None
+
+
+def host_dataflow(trace, nlayers, nfields_out):
+    """Sweep index of the last writer of each host layer read by each H2D."""
+    writer = {}
+    reads = []
+    sweep_of_visit = {}
+    for o in trace:
+        if o["op"] == "H2D":
+            for (k, f, lo, hi, w) in o["access"]:
+                if k == "HOST" and f < nfields_out:
+                    reads.append((o["visit"], [writer.get((f, l)) for l in range(lo, hi)]))
+        if o["op"] == "D2H":
+            for (k, f, lo, hi, w) in o["access"]:
+                if k == "HOST" and w:
+                    for l in range(lo, hi):
+                        writer[(f, l)] = o["visit"]
+    return reads
+
+
+CASES = [
+    # (scheme, shape, rate, k, T, wb, calls)
+    ("heat", (128, 128, 128), 16, 1, 32, 1, [10]),
+    ("heat", (128, 128, 128), 0, 2, 32, 3, [10]),
+    ("heat", (120, 52, 44), 16, 3, 32, 1, [3, 4]),
+    ("heat", (64, 36, 100), 8, 2, 8, 1, [7]),
+    ("heat", (40, 16, 24), 16, 4, 64, 1, [9]),
+    ("wave", (128, 72, 40), 16, 4, 32, 1, [10]),
+    ("wave", (96, 48, 64), 12, 3, 24, 3, [10]),
+    ("wave", (512, 512, 512), 16, 4, 64, 1, [12]),
+    ("wave", (96, 40, 48), 0, 4, 32, 1, [5, 2, 4]),
+    ("wave", (160, 40, 40), 16, 4, 32, 1, [16]),
+]
+
+
+def _desc(P, scheme, shape, rate, k, T, wb):
+    nz, ny, nx = shape
+    if scheme == "heat":
+        return P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), 8 << 30,
+                           rate_bits=rate, temporal_depth=k, slab_planes=T, working_buffers=wb)
+    return P.make_desc(nx, ny, nz, P.OOCS_WAVE, synthetic.wave_star_coef(), 8 << 30,
+                       rate_bits=rate, temporal_depth=k, slab_planes=T, working_buffers=wb)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_schedule_is_race_free(P, case):
+    scheme, shape, rate, k, T, wb, calls = case
+    desc = _desc(P, scheme, shape, rate, k, T, wb)
+    trace = P.oocs_trace_schedule(desc, calls)
+    assert check(trace, swb=(wb == 1)) is None
+    plan = P.oocs_query(desc)
+    visits = {o["visit"] for o in trace if o["visit"] >= 0}
+    sweeps = sum(-(-c // k) for c in calls)
+    assert len(visits) == sweeps * plan.num_slabs
+    # every layer of every streamed field crosses the link once per sweep
+    h2d_layers = sum(o["access"][0][3] - o["access"][0][2] for o in trace if o["op"] == "H2D")
+    assert h2d_layers == sweeps * (shape[0] // 4)
+    # in sweep p+1 every host layer read was written back in sweep p
+    fout = 2 if scheme == "wave" else 1
+    for visit, writers in host_dataflow(trace, shape[0] // 4, fout):
+        sweep = visit // plan.num_slabs
+        expect = None if sweep == 0 else sweep - 1
+        got = {None if w is None else w // plan.num_slabs for w in writers}
+        assert got == {expect}, (visit, got)
+
+
+@pytest.mark.parametrize("drop", ["d2h", "decoded", "wrel", "h2d"])
+def test_check_detects_missing_waits(P, drop):
+    """Removing one kind of cross-stream wait leaves a hazard the check reports."""
+    base = {"d2h": range(1000, 2000), "decoded": range(100, 103), "wrel": range(300, 303),
+            "h2d": range(200, 203)}[drop]
+    # with one working buffer the borrowed-overlap wait is implied by the
+    # working-buffer chain; with three (classic) it is the only guard
+    wb = 3 if drop == "h2d" else 1
+    desc = _desc(P, "wave", (128, 72, 40), 16, 4, 32, wb)
+    trace = P.oocs_trace_schedule(desc, [12])
+    assert check(trace, swb=(wb == 1)) is None
+    cut = [o for o in trace if not (o["op"] == "WAIT" and o["event"] in base)]
+    assert len(cut) < len(trace)
+    assert check(cut, swb=(wb == 1)) is not None
+
+
+def test_classic_mode_lets_visits_overlap(P):
+    """With three working buffers (Fig. 6a) kernels of consecutive visits are not ordered."""
+    desc = _desc(P, "heat", (128, 128, 128), 0, 1, 32, 3)
+    trace = P.oocs_trace_schedule(desc, [4])
+    assert check(trace, swb=False) is None
+    assert check(trace, swb=True) is not None
+
+
+def test_trace_capacity_error(P):
+    import ctypes
+    desc = _desc(P, "heat", (128, 128, 128), 16, 1, 32, 1)
+    calls = (ctypes.c_int32 * 1)(3)
+    count = ctypes.c_int64(0)
+    buf = (P.oocs.oocs_trace_op * 2)()
+    st = P.lib().oocs_trace_schedule(ctypes.byref(desc), calls, 1, buf, 2, ctypes.byref(count))
+    assert st == 1 and count.value > 2
