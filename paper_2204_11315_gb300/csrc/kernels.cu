@@ -478,32 +478,59 @@ OOCS_FN int find_segment(const CodecSegments &sg, int64_t b, int bnx, int bny, i
     return g;
 }
 
+// The encoder's compressed words pass through shared memory, one row of
+// 2 rate + 1 words per thread, so that global memory sees contiguous, coalesced
+// runs of words instead of 32 lanes each writing a word of a different
+// 8 rate-byte block.
+OOCS_FN uint32_t *segment_word(const CodecSegments &sg, int64_t blk, int rate, int wi)
+{
+    int g = 0;
+#pragma unroll 1
+    while (g + 1 < sg.nseg && blk >= sg.first[g + 1])
+        ++g;
+    return static_cast<uint32_t *>(sg.blocks[g]) + (blk - sg.first[g]) * (int64_t)(2 * rate) + wi;
+}
+
 __global__ void __launch_bounds__(kCodecThreads)
     k_encode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
+    extern __shared__ uint32_t sw[];
     pdl_launch_dependents();
     pdl_wait_prior_grid();
-    const int64_t b = (int64_t)blockIdx.x * kCodecThreads + threadIdx.x;
-    if (b >= sg.first[sg.nseg])
-        return;
-    int bx, by;
-    int64_t bl;
-    const int g = find_segment(sg, b, nx >> 2, ny >> 2, bx, by, bl);
-    const int64_t plane = (int64_t)nx * ny;
-    const float *base = sg.planes[g] + 4 * bl * plane + (int64_t)(4 * by) * nx + 4 * bx;
-    float v[64];
+    const int nw = 2 * rate, stride = 2 * rate + 1;
+    const int64_t total = sg.first[sg.nseg];
+    const int64_t b0 = (int64_t)blockIdx.x * kCodecThreads;
+    const int64_t b = b0 + threadIdx.x;
+    if (b < total) {
+        int bx, by;
+        int64_t bl;
+        const int g = find_segment(sg, b, nx >> 2, ny >> 2, bx, by, bl);
+        const int64_t plane = (int64_t)nx * ny;
+        const float *base = sg.planes[g] + 4 * bl * plane + (int64_t)(4 * by) * nx + 4 * bx;
+        float v[64];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float4 f = __ldg(reinterpret_cast<const float4 *>(base + k * plane + (int64_t)j * nx));
-            v[16 * k + 4 * j + 0] = f.x;
-            v[16 * k + 4 * j + 1] = f.y;
-            v[16 * k + 4 * j + 2] = f.z;
-            v[16 * k + 4 * j + 3] = f.w;
-        }
-    uint32_t *o = static_cast<uint32_t *>(sg.blocks[g]) + (b - sg.first[g]) * (int64_t)(2 * rate);
-    encode_block(v, rate, [&](int i, uint32_t w) { o[i] = w; });
+            for (int j = 0; j < 4; ++j) {
+                const float4 f =
+                    __ldg(reinterpret_cast<const float4 *>(base + k * plane + (int64_t)j * nx));
+                v[16 * k + 4 * j + 0] = f.x;
+                v[16 * k + 4 * j + 1] = f.y;
+                v[16 * k + 4 * j + 2] = f.z;
+                v[16 * k + 4 * j + 3] = f.w;
+            }
+        uint32_t *row = sw + threadIdx.x * stride;
+        encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
+    }
+    __syncthreads();
+    // each warp copies whole blocks out, its lanes over the block's words
+    const int nblk = (int)(total - b0 < kCodecThreads ? total - b0 : kCodecThreads);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int blk = warp; blk < nblk; blk += kCodecThreads / 32) {
+        uint32_t *dst = segment_word(sg, b0 + blk, rate, 0);
+        for (int wi = lane; wi < nw; wi += 32)
+            dst[wi] = sw[blk * stride + wi];
+    }
 }
 
 __global__ void __launch_bounds__(kCodecThreads)
@@ -518,6 +545,8 @@ __global__ void __launch_bounds__(kCodecThreads)
     int64_t bl;
     const int g = find_segment(sg, b, nx >> 2, ny >> 2, bx, by, bl);
     const int64_t plane = (int64_t)nx * ny;
+    // a thread's words share its block's cache lines: the first load of each
+    // line brings the rest into L1
     const uint32_t *src =
         static_cast<const uint32_t *>(sg.blocks[g]) + (b - sg.first[g]) * (int64_t)(2 * rate);
     const int nw = 2 * rate;
@@ -553,7 +582,8 @@ cudaError_t launch_encode_segments(CodecSegments sg, const int64_t *nlayers, int
     if (nb == 0)
         return cudaSuccess;
     return launch_pdl(k_encode_layers, dim3((unsigned)((nb + kCodecThreads - 1) / kCodecThreads)),
-                      dim3(kCodecThreads), 0, s, sg, (int)nx, (int)ny, rate);
+                      dim3(kCodecThreads), (size_t)kCodecThreads * (2 * rate + 1) * 4, s, sg, (int)nx,
+                      (int)ny, rate);
 }
 
 cudaError_t launch_decode_segments(CodecSegments sg, const int64_t *nlayers, int64_t nx, int64_t ny,
