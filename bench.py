@@ -46,7 +46,7 @@ WORKLOAD = "wave25_512cubed_100steps_8slabs_k4_rate16_swb"
 # DRAM bytes (read + write) per updated point of the wave step kernel from one ncu
 # capture of a 512x512x192 case (profiles/k_star_step_and_codec_512x512x192.md);
 # scaled to a launch by its points.  Set to None whenever the kernel changes.
-STEP_TRAFFIC_B_PER_POINT = None  # recapture pending: the kernel changed
+STEP_TRAFFIC_B_PER_POINT = 15.53
 
 
 def parse():
