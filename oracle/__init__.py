@@ -68,6 +68,11 @@ def _declare(L):
                                    ctypes.c_double]
     L.oracle_heat_run.argtypes = [_i64, _i64, _i64, _i32, _dp, _i32, _dp, _dp]
     L.oracle_wave_run.argtypes = [_i64, _i64, _i64, _dp, _dp, _i32, _dp, _dp, _dp, _i64, _dp]
+    L.oracle_star_apply.argtypes = [_i64, _i64, _i64, _i32, _dp, _dp, _dp]
+    L.oracle_wave_adjoint_step.argtypes = [_i64, _i64, _i64, _dp, _dp, _dp, _dp, _dp, _dp, _i64, _dp]
+    L.oracle_wave_misfit_gradient.argtypes = [_i64, _i64, _i64, _dp, _dp, _i32, _i64, _dp, _i64,
+                                              _dp, _dp]
+    L.oracle_wave_misfit_gradient.restype = ctypes.c_double
     L.oracle_block_header.argtypes = [_fp]
     L.oracle_block_header.restype = _i32
     L.oracle_quantize.argtypes = [_fp, _i32, _i32p]
@@ -153,6 +158,61 @@ def wave_run(u0, up0, m, coef, nsteps, src=None, w=None):
                           _p(up, _dp), _p(scratch, _dp), s,
                           _p(ww, _dp) if ww is not None else None)
     return u, up
+
+
+def star_apply(u, coef):
+    """L u on the interior (0 on the shell of width r = len(coef) - 1), FP64."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    nz, ny, nx = u.shape
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    out = np.empty_like(u)
+    lib().oracle_star_apply(nx, ny, nz, len(c) - 1, _p(c, _dp), _p(u, _dp), _p(out, _dp))
+    return out
+
+
+def wave_adjoint_step(lam, lam_prev, m, coef, res=None, zr=-1):
+    """lam_new = 2 lam - lam_prev + L(m lam) + res at plane zr (shell 0), FP64."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    lp = np.ascontiguousarray(lam_prev, dtype=np.float64)
+    mm = np.ascontiguousarray(m, dtype=np.float64)
+    nz, ny, nx = lam.shape
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    out = np.empty_like(lam)
+    scratch = np.empty(2 * lam.size)
+    rr = np.ascontiguousarray(res, dtype=np.float64) if res is not None else None
+    lib().oracle_wave_adjoint_step(nx, ny, nz, _p(c, _dp), _p(mm, _dp), _p(lam, _dp), _p(lp, _dp),
+                                   _p(out, _dp), _p(rr, _dp) if rr is not None else None, int(zr),
+                                   _p(scratch, _dp))
+    return out
+
+
+def wave_misfit_gradient(m, coef, nsteps, src, w, zr, d):
+    """(J, dJ/dm) of the wave workload: forward + discrete adjoint, FP64.
+
+    d[n-1] (ny x nx) is the observed plane zr at time n, n = 1..nsteps."""
+    mm = np.ascontiguousarray(m, dtype=np.float64)
+    nz, ny, nx = mm.shape
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    ww = np.ascontiguousarray(np.asarray(w, dtype=np.float64)[:nsteps])
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    assert dd.shape == (nsteps, ny, nx)
+    g = np.empty_like(mm)
+    s = -1 if src is None else int((src[0] * ny + src[1]) * nx + src[2])
+    J = lib().oracle_wave_misfit_gradient(nx, ny, nz, _p(c, _dp), _p(mm, _dp), int(nsteps), s,
+                                          _p(ww, _dp), int(zr), _p(dd, _dp), _p(g, _dp))
+    return float(J), g
+
+
+def wave_receiver_data(m, coef, nsteps, src, w, zr):
+    """Plane zr of u^1 .. u^nsteps of the forward run from rest, FP64, [n][ny][nx]."""
+    mm = np.ascontiguousarray(m, dtype=np.float64)
+    u = np.zeros_like(mm)
+    up = np.zeros_like(mm)
+    out = []
+    for k in range(nsteps):
+        u, up = wave_run(u, up, mm, coef, 1, src=src, w=np.asarray(w)[k:k + 1])
+        out.append(u[zr].copy())
+    return np.array(out)
 
 
 # ---------------------------------------------------------------------------

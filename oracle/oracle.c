@@ -503,3 +503,126 @@ void oracle_decode_field(const uint32_t *in, int64_t nx, int64_t ny, int64_t nz,
         scatter(f, nx, ny, bx, by, bz, v);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* 3. adjoint of the leapfrog wave steps, FP64                              */
+/* ------------------------------------------------------------------------ */
+/*
+ * Forward (interior points; the Dirichlet shell stays 0 when it starts at 0):
+ *   u^(n+1) = 2 u^n - u^(n-1) + m (L u^n + w_n e_src),   u^0 = u^(-1) = 0,
+ *   J = 1/2 sum_{n=1..N} sum_{x,y} (u^n(x, y, z_r) - d^n(x, y))^2.
+ * Its discrete adjoint (Lagrange multipliers of the step equations):
+ *   lam^n = 2 lam^(n+1) - lam^(n+2) + L (m lam^(n+1)) + r^n e_(z_r),
+ *   lam^(N+1) = lam^(N+2) = 0,  r^n = u^n(z_r) - d^n,
+ *   dJ/dm = sum_{n=0..N-1} lam^(n+1) (L u^n + w_n e_src).
+ * L is the symmetric star operator on the interior with zero shell values, so
+ * its transpose applied to (m lam) is L applied to the product.            */
+
+/* L u at interior points (0 on the shell) */
+static void star_apply(int64_t nx, int64_t ny, int64_t nz, int r, const double *coef,
+                       const double *u, double *out)
+{
+    const int64_t sx = 1, sy = nx, sz = nx * ny;
+    int64_t z;
+#pragma omp parallel for schedule(static)
+    for (z = 0; z < nz; z++)
+        for (int64_t y = 0; y < ny; y++)
+            for (int64_t x = 0; x < nx; x++) {
+                int64_t p = IDX(x, y, z);
+                if (x < r || y < r || z < r || x >= nx - r || y >= ny - r || z >= nz - r) {
+                    out[p] = 0.0;
+                    continue;
+                }
+                double L = coef[0] * u[p];
+                for (int d = 1; d <= r; d++)
+                    L += coef[d] * ((u[p - d * sx] + u[p + d * sx]) + (u[p - d * sy] + u[p + d * sy]) +
+                                    (u[p - d * sz] + u[p + d * sz]));
+                out[p] = L;
+            }
+}
+
+void oracle_star_apply(int64_t nx, int64_t ny, int64_t nz, int r, const double *coef, const double *u,
+                       double *out)
+{
+    star_apply(nx, ny, nz, r, coef, u, out);
+}
+
+/* One adjoint step: lam_new = 2 lam - lam_prev + L(m lam) + (res at plane z_r).
+ * res (nx*ny, may be NULL) is added at plane zr of the interior.  Shell
+ * points of lam_new are 0.                                                 */
+void oracle_wave_adjoint_step(int64_t nx, int64_t ny, int64_t nz, const double *coef,
+                              const double *m, const double *lam, const double *lam_prev,
+                              double *lam_new, const double *res, int64_t zr, double *scratch)
+{
+    int64_t n = nx * ny * nz, i;
+    for (i = 0; i < n; i++)
+        scratch[n + i] = m[i] * lam[i];  /* second half of scratch: m lam */
+    star_apply(nx, ny, nz, 4, coef, scratch + n, scratch);
+    for (int64_t z = 0; z < nz; z++)
+        for (int64_t y = 0; y < ny; y++)
+            for (int64_t x = 0; x < nx; x++) {
+                int64_t p = IDX(x, y, z);
+                if (x < 4 || y < 4 || z < 4 || x >= nx - 4 || y >= ny - 4 || z >= nz - 4) {
+                    lam_new[p] = 0.0;
+                    continue;
+                }
+                double v = 2.0 * lam[p] - lam_prev[p] + scratch[p];
+                if (res && z == zr)
+                    v += res[y * nx + x];
+                lam_new[p] = v;
+            }
+}
+
+/* Misfit and gradient of the wave workload by forward run + adjoint run.
+ * Inputs: m (n), wavelet w[0..N), source index src (or -1), receiver plane zr,
+ * observed data d[N][ny][nx] (d[n-1] is compared with u^n).  Outputs: J and
+ * grad_m (n).  Keeps all N+1 states (small grids only).                    */
+double oracle_wave_misfit_gradient(int64_t nx, int64_t ny, int64_t nz, const double *coef,
+                                   const double *m, int nsteps, int64_t src, const double *w,
+                                   int64_t zr, const double *d, double *grad_m)
+{
+    int64_t n = nx * ny * nz, plane = nx * ny;
+    double *U = (double *)calloc((size_t)(nsteps + 2) * n, sizeof(double)); /* U[k] = u^(k-1) */
+    double *lam = (double *)calloc((size_t)3 * n, sizeof(double));
+    double *scratch = (double *)calloc((size_t)2 * n, sizeof(double));
+    double *res = (double *)calloc((size_t)plane, sizeof(double));
+    double J = 0.0;
+    /* forward: U[0] = u^-1 = 0, U[1] = u^0 = 0 */
+    for (int k = 0; k < nsteps; k++) {
+        oracle_star_step(nx, ny, nz, 4, coef, 1, m, U + (int64_t)(k + 1) * n, U + (int64_t)k * n,
+                         U + (int64_t)(k + 2) * n, src, w ? w[k] : 0.0);
+    }
+    for (int k = 1; k <= nsteps; k++)
+        for (int64_t q = 0; q < plane; q++) {
+            double r = U[(int64_t)(k + 1) * n + zr * plane + q] - d[(int64_t)(k - 1) * plane + q];
+            J += 0.5 * r * r;
+        }
+    /* adjoint: lam[0] = lam^(n+2), lam[1] = lam^(n+1); gradient uses u^n = U[n+1] */
+    for (int64_t q = 0; q < n; q++)
+        grad_m[q] = 0.0;
+    double *lpp = lam, *lp = lam + n, *lc = lam + 2 * n;
+    double *Lu = scratch; /* reused below after the adjoint step */
+    for (int k = nsteps; k >= 1; k--) {
+        /* lam^k from lam^(k+1) = lp, lam^(k+2) = lpp, residual of u^k */
+        for (int64_t q = 0; q < plane; q++)
+            res[q] = U[(int64_t)(k + 1) * n + zr * plane + q] - d[(int64_t)(k - 1) * plane + q];
+        oracle_wave_adjoint_step(nx, ny, nz, coef, m, lp, lpp, lc, res, zr, scratch);
+        /* gradient term n = k-1: lam^k (L u^(k-1) + w_(k-1) e_src) */
+        star_apply(nx, ny, nz, 4, coef, U + (int64_t)k * n, Lu);
+        for (int64_t q = 0; q < n; q++) {
+            double t = Lu[q];
+            if (q == src && w)
+                t += w[k - 1];
+            grad_m[q] += lc[q] * t;
+        }
+        double *t = lpp;
+        lpp = lp;
+        lp = lc;
+        lc = t;
+    }
+    free(U);
+    free(lam);
+    free(scratch);
+    free(res);
+    return J;
+}
