@@ -229,6 +229,37 @@ oocs_status oocs_incore_run_noalloc(const oocs_desc *desc, float *u, float *u_pr
                                     int32_t nsteps, int64_t t0, const int64_t *src_xyz,
                                     const float *w, int32_t nw, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Gradient of the receiver misfit of the WAVE scheme (device arrays, in-core).
+ * Forward: u^(n+1) = 2u^n - u^(n-1) + m (L u^n + w_n e_src), u^0 = u^(-1) = 0,
+ * J = 1/2 sum_{n=1..N} sum_xy (u^n(x, y, z_r) - d^n(x, y))^2.  Discrete adjoint,
+ * backwards in time: lam^n = 2 lam^(n+1) - lam^(n+2) + L(m lam^(n+1)) + r^n at z_r,
+ * lam^(N+1) = lam^(N+2) = 0, r^n = u^n(z_r) - d^n, and
+ * dJ/dm = sum_{n=0..N-1} lam^(n+1) (L u^n + w_n e_src).  desc must describe the
+ * WAVE scheme; only nx, ny, nz and coef are used.  Fields are nx*ny*nz FP32,
+ * zero on the shell.  Asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+
+/* One adjoint step.  In: lam = lam^(n+1), lam_prev = lam^(n+2), mu = m lam^(n+1).
+ * Out: lam_prev <- lam^n (in place), mu_out <- m lam^n (mu_out != mu).
+ * res: the residual plane r^n (nx*ny, device) added at plane zr, or NULL.   */
+oocs_status oocs_adjoint_step(const oocs_desc *desc, const float *lam, float *lam_prev, const float *mu,
+                              float *mu_out, const float *m, const float *res, int64_t zr, void *stream);
+
+/* grad_m += lam (L u + w at src_xyz) on the interior (src_xyz may be NULL). */
+oocs_status oocs_gradient_accumulate(const oocs_desc *desc, float *grad_m, const float *lam, const float *u,
+                                     float w, const int64_t *src_xyz, void *stream);
+
+/* res = u_plane - d_plane (n values) and *misfit += 1/2 sum res^2 (misfit is a
+ * device double, may be NULL).                                              */
+oocs_status oocs_receiver_residual(const float *u_plane, const float *d_plane, int64_t n, float *res,
+                                   double *misfit, void *stream);
+
+/* m = (v dt/dx)^2 and its chain rule grad_v = grad_m 2 v (dt/dx)^2 (n values). */
+oocs_status oocs_model_from_velocity(const float *v, float *m, int64_t n, float dt_over_dx, void *stream);
+oocs_status oocs_velocity_gradient(const float *grad_m, const float *v, float *grad_v, int64_t n,
+                                   float dt_over_dx, void *stream);
+
 /* Fixed-rate block codec (Sec. 4.2) on device arrays.  encode: field
  * [nz][ny][nx] FP32 -> (nx/4)(ny/4)(nz/4) blocks of 8*rate bytes in layer
  * order (block (bx,by,bz) at ((bz*(ny/4)+by)*(nx/4)+bx)).  decode: inverse.

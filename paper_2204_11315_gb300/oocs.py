@@ -123,6 +123,12 @@ SIGNATURES = {
                                        _vp, _i32, _vp]),
     "oocs_trace_schedule": (_i32, [ctypes.POINTER(oocs_desc), ctypes.POINTER(_i32), _i32,
                                    ctypes.POINTER(oocs_trace_op), _i64, ctypes.POINTER(_i64)]),
+    "oocs_adjoint_step": (_i32, [ctypes.POINTER(oocs_desc), _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "oocs_gradient_accumulate": (_i32, [ctypes.POINTER(oocs_desc), _vp, _vp, _vp, ctypes.c_float, _vp,
+                                        _vp]),
+    "oocs_receiver_residual": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "oocs_model_from_velocity": (_i32, [_vp, _vp, _i64, ctypes.c_float, _vp]),
+    "oocs_velocity_gradient": (_i32, [_vp, _vp, _vp, _i64, ctypes.c_float, _vp]),
     "oocs_encode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
     "oocs_decode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
 }
@@ -285,6 +291,35 @@ def oocs_trace_schedule(desc, nsteps_calls):
                     "access": [(OOCS_RES_NAMES[a.kind], a.index, a.lo, a.hi, bool(a.write))
                                for a in o.access[:o.naccess]]})
     return out
+
+
+def oocs_adjoint_step(desc, lam_ptr, lam_prev_ptr, mu_ptr, mu_out_ptr, m_ptr, res_ptr=0, zr=-1,
+                      stream=0):
+    _check(lib().oocs_adjoint_step(ctypes.byref(desc), _vp(lam_ptr), _vp(lam_prev_ptr), _vp(mu_ptr),
+                                   _vp(mu_out_ptr), _vp(m_ptr), _vp(res_ptr) if res_ptr else None,
+                                   int(zr), _vp(stream)))
+
+
+def oocs_gradient_accumulate(desc, grad_ptr, lam_ptr, u_ptr, w=0.0, src=None, stream=0):
+    srcarr = (_i64 * 3)(*src) if src is not None else None
+    _check(lib().oocs_gradient_accumulate(ctypes.byref(desc), _vp(grad_ptr), _vp(lam_ptr), _vp(u_ptr),
+                                          float(w),
+                                          ctypes.cast(srcarr, _vp) if srcarr is not None else None,
+                                          _vp(stream)))
+
+
+def oocs_receiver_residual(u_plane_ptr, d_plane_ptr, n, res_ptr, misfit_ptr=0, stream=0):
+    _check(lib().oocs_receiver_residual(_vp(u_plane_ptr), _vp(d_plane_ptr), int(n), _vp(res_ptr),
+                                        _vp(misfit_ptr) if misfit_ptr else None, _vp(stream)))
+
+
+def oocs_model_from_velocity(v_ptr, m_ptr, n, dt_over_dx, stream=0):
+    _check(lib().oocs_model_from_velocity(_vp(v_ptr), _vp(m_ptr), int(n), float(dt_over_dx), _vp(stream)))
+
+
+def oocs_velocity_gradient(gm_ptr, v_ptr, gv_ptr, n, dt_over_dx, stream=0):
+    _check(lib().oocs_velocity_gradient(_vp(gm_ptr), _vp(v_ptr), _vp(gv_ptr), int(n), float(dt_over_dx),
+                                        _vp(stream)))
 
 
 def oocs_encode_device(field_ptr, nx, ny, nz, rate, blocks_ptr, stream=0):

@@ -1,0 +1,211 @@
+"""GPU adjoint of the leapfrog wave scheme and the autograd gradient of the receiver misfit.
+
+Checked against the FP64 oracle (tests/test_oracle_adjoint.py pins it): the
+adjoint step and gradient kernels elementwise, the dot-product test
+<F x, y> = <x, F^T y> in FP32 for one and for ten steps, the autograd gradient
+against the oracle's gradient and against oracle central differences of the
+misfit in the velocity (h = 1e-3 relative) at 16 random voxels, and the
+workload size (256^3, 400 steps, checkpoints every 10 steps at 16 bits/value).
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from gpu_util import rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2204_11315_gb300 as P
+    P.lib()
+    return P
+
+
+def _desc(P, shape):
+    nz, ny, nx = shape
+    return P.make_desc(nx, ny, nz, P.OOCS_WAVE, synthetic.wave_star_coef(), 1 << 40, temporal_depth=1,
+                       slab_planes=nz)
+
+
+def _interior(shape, rng, r=4):
+    a = np.zeros(shape, np.float32)
+    nz, ny, nx = shape
+    a[r:nz - r, r:ny - r, r:nx - r] = rng.standard_normal((nz - 2 * r, ny - 2 * r, nx - 2 * r))
+    return a
+
+
+def _gpu_adjoint(P, torch, desc, lam, lam_prev, m, res=None, zr=-1):
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    L, LP, M = t(lam), t(lam_prev), t(m)
+    MU = t(m * lam)
+    MO = torch.empty_like(L)
+    R = t(res) if res is not None else None
+    P.oocs_adjoint_step(desc, L.data_ptr(), LP.data_ptr(), MU.data_ptr(), MO.data_ptr(), M.data_ptr(),
+                        R.data_ptr() if R is not None else 0, zr, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return LP.cpu().numpy(), MO.cpu().numpy()
+
+
+def test_adjoint_step_vs_oracle(P, orc):
+    torch = torch_cuda()
+    shape = (40, 36, 44)
+    rng = np.random.default_rng(0)
+    m = synthetic.wave_model(shape)
+    lam, lp = _interior(shape, rng), _interior(shape, rng)
+    res = rng.standard_normal((36, 44)).astype(np.float32)
+    got, mu = _gpu_adjoint(P, torch, _desc(P, shape), lam, lp, m, res, 7)
+    ref = orc.wave_adjoint_step(lam, lp, m, synthetic.wave_star_coef(), res, 7)
+    assert rel_l2(got, ref) <= 1e-6
+    assert rel_l2(mu, m.astype(np.float64) * ref) <= 1e-6
+    assert np.all(got[:4] == 0) and np.all(mu[:, :, -4:] == 0)
+
+
+def test_gradient_accumulate_vs_oracle(P, orc):
+    torch = torch_cuda()
+    shape = (32, 28, 36)
+    rng = np.random.default_rng(1)
+    u, lam = _interior(shape, rng), _interior(shape, rng)
+    g0 = rng.standard_normal(shape).astype(np.float32)
+    src = (18, 14, 16)  # x, y, z
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    G, L, U = T(g0), T(lam), T(u)
+    P.oocs_gradient_accumulate(_desc(P, shape), G.data_ptr(), L.data_ptr(), U.data_ptr(), 0.75, src,
+                               torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    t = orc.star_apply(u, synthetic.wave_star_coef())
+    t[src[2], src[1], src[0]] += 0.75
+    ref = g0.astype(np.float64) + lam.astype(np.float64) * t
+    ref[:4] = g0[:4]
+    assert rel_l2(G.cpu().numpy(), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("nsteps", [1, 10])
+def test_dot_product_fp32(P, orc, nsteps):
+    """<F^N x, y> = <x, (F^T)^N y> with the GPU forward step and the GPU adjoint step."""
+    torch = torch_cuda()
+    shape = (40, 40, 40)
+    rng = np.random.default_rng(2)
+    desc = _desc(P, shape)
+    m = synthetic.wave_model(shape)
+    u0, up0 = _interior(shape, rng), _interior(shape, rng)
+    y1, y2 = _interior(shape, rng), _interior(shape, rng)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    s = torch.cuda.current_stream().cuda_stream
+    U, UP, M, SC = T(u0), T(up0), T(m), torch.empty(shape, device="cuda")
+    P.oocs_incore_run(desc, U.data_ptr(), UP.data_ptr(), M.data_ptr(), SC.data_ptr(), nsteps, 0, None,
+                      None, s)
+    # transpose steps in the (lam, -lam_prev) form: lam_new = 2 lam - lam_prev + L(m lam)
+    LAM, LP = T(y1), T(-y2)
+    MU, MO = T(m * y1), torch.empty(shape, device="cuda")
+    for _ in range(nsteps):
+        P.oocs_adjoint_step(desc, LAM.data_ptr(), LP.data_ptr(), MU.data_ptr(), MO.data_ptr(),
+                            M.data_ptr(), 0, -1, s)
+        LAM, LP = LP, LAM
+        MU, MO = MO, MU
+    torch.cuda.synchronize()
+    f1, f2 = U.cpu().numpy().astype(np.float64), UP.cpu().numpy().astype(np.float64)
+    a1, a2 = LAM.cpu().numpy().astype(np.float64), LP.cpu().numpy().astype(np.float64)
+    lhs = np.vdot(f1, y1) + np.vdot(f2, y2)
+    rhs = np.vdot(u0, a1) + np.vdot(up0, -a2)
+    assert abs(lhs - rhs) <= 1e-5 * (np.linalg.norm(f1) * np.linalg.norm(y1) + np.linalg.norm(f2) * np.linalg.norm(y2))
+
+
+def _small_problem(P, rate, shape=(40, 36, 44), nsteps=80):
+    """Layered model at dx = 10 m, dt = 0.8 ms (stable), 40 Hz Ricker 8 planes
+    below the receiver plane z = 6, so the recorded wave is well inside the run."""
+    import paper_2204_11315_gb300.adjoint as A
+    dt, dx = synthetic.WAVE_DT, synthetic.WAVE_DX
+    w = synthetic.ricker(nsteps, dt=dt, f0=40.0)
+    v = synthetic.layered_velocity(shape).astype(np.float32)
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    bump = np.exp(-((x - 24) ** 2 + (y - 18) ** 2 + (z - 10) ** 2) / 20.0)
+    v_true = (v * (1.0 + 0.05 * bump)).astype(np.float32)
+    prob = A.WaveProblem(shape=shape, dt=dt, dx=dx, coef=synthetic.wave_star_coef(),
+                         src_xyz=(nx // 2, ny // 2, 14), wavelet=w, zr=6, nsteps=nsteps,
+                         checkpoint_every=10, rate=rate)
+    return A, prob, v, v_true, w
+
+
+@pytest.mark.parametrize("rate,tol", [(0, 1e-4), (16, 1e-3)])
+def test_autograd_gradient_vs_oracle(P, orc, rate, tol):
+    torch = torch_cuda()
+    A, prob, v, v_true, w = _small_problem(P, rate)
+    s = prob.dt / prob.dx
+    m64 = (v.astype(np.float64) * s) ** 2
+    mt64 = (v_true.astype(np.float64) * s) ** 2
+    src_zyx = prob.src_xyz[::-1]
+    d = orc.wave_receiver_data(mt64, prob.coef, prob.nsteps, src_zyx, w, prob.zr)
+    J_ref, gm_ref = orc.wave_misfit_gradient(m64, prob.coef, prob.nsteps, src_zyx, w, prob.zr, d)
+    gv_ref = gm_ref * 2.0 * v.astype(np.float64) * s * s
+    vt = torch.from_numpy(v).cuda().requires_grad_(True)
+    J = A.wave_misfit(vt, torch.from_numpy(d.astype(np.float32)).cuda(), prob)
+    J.backward()
+    assert J_ref > 0 and np.abs(gv_ref).max() > 0
+    assert abs(float(J.detach()) - J_ref) <= 1e-4 * J_ref
+    assert rel_l2(vt.grad.cpu().numpy(), gv_ref) <= tol
+
+
+def test_autograd_gradient_vs_oracle_finite_differences(P, orc):
+    """Central differences of the FP64 oracle misfit in v (h = 1e-3 relative) at 16 voxels."""
+    torch = torch_cuda()
+    A, prob, v, v_true, w = _small_problem(P, 16, shape=(32, 32, 36), nsteps=70)
+    s = prob.dt / prob.dx
+    src_zyx = prob.src_xyz[::-1]
+    mt64 = (v_true.astype(np.float64) * s) ** 2
+    d = orc.wave_receiver_data(mt64, prob.coef, prob.nsteps, src_zyx, w, prob.zr)
+    vt = torch.from_numpy(v).cuda().requires_grad_(True)
+    A.wave_misfit(vt, torch.from_numpy(d.astype(np.float32)).cuda(), prob).backward()
+    g = vt.grad.cpu().numpy().astype(np.float64)
+    assert np.abs(g).max() > 0
+    rng = np.random.default_rng(5)
+    nz, ny, nx = v.shape
+    # voxels where the gradient is not negligible (inside the illuminated region)
+    cand = np.argwhere(np.abs(g) > 0.05 * np.abs(g).max())
+    pick = cand[rng.choice(len(cand), 16, replace=False)]
+    for (z, y, x) in pick:
+        h = 1e-3 * float(v[z, y, x])
+        vals = []
+        for sgn in (1, -1):
+            vv = v.astype(np.float64).copy()
+            vv[z, y, x] += sgn * h
+            J, _ = orc.wave_misfit_gradient((vv * s) ** 2, prob.coef, prob.nsteps, src_zyx, w, prob.zr, d)
+            vals.append(J)
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - g[z, y, x]) <= 2e-2 * abs(fd) + 1e-3 * np.abs(g).max(), (z, y, x, fd, g[z, y, x])
+
+
+def test_workload_gradient_256cubed(P):
+    """256^3, 400 steps, checkpoints every 10 steps at rate 16 (the adjoint workload).
+
+    The 15 Hz source sits at depth z = 32 under the receiver plane z = 8 (a
+    source at the centre, z = 128, would not reach the receivers within 400
+    steps at these velocities, leaving a zero misfit)."""
+    torch = torch_cuda()
+    import paper_2204_11315_gb300.adjoint as A
+    shape = (256, 256, 256)
+    nsteps = 400
+    w = synthetic.ricker(nsteps)
+    v = synthetic.layered_velocity(shape, seed=4).astype(np.float32)
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    v_true = (v * (1.0 + 0.05 * np.exp(-((x - 140) ** 2 + (y - 120) ** 2 + (z - 40) ** 2) / 400.0))).astype(np.float32)
+    del x, y, z
+    kw = dict(shape=shape, dt=synthetic.WAVE_DT, dx=synthetic.WAVE_DX, coef=synthetic.wave_star_coef(),
+              src_xyz=(128, 128, 32), wavelet=w, zr=8, nsteps=nsteps, checkpoint_every=10)
+    prob16 = A.WaveProblem(rate=16, **kw)
+    d = A.receiver_data(torch.from_numpy(v_true).cuda(), prob16)
+    grads = {}
+    for rate in (16, 0):
+        prob = A.WaveProblem(rate=rate, **kw)
+        vt = torch.from_numpy(v).cuda().requires_grad_(True)
+        J = A.wave_misfit(vt, d, prob)
+        J.backward()
+        assert float(J.detach()) > 0
+        grads[rate] = vt.grad.cpu().numpy()
+        assert np.all(np.isfinite(grads[rate]))
+    assert np.abs(grads[0]).max() > 0
+    # compressing the checkpoints at rate 16 changes the gradient very little
+    assert rel_l2(grads[16], grads[0]) <= 1e-3
