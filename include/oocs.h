@@ -260,6 +260,32 @@ oocs_status oocs_model_from_velocity(const float *v, float *m, int64_t n, float 
 oocs_status oocs_velocity_gradient(const float *grad_m, const float *v, float *grad_v, int64_t n,
                                    float dt_over_dx, void *stream);
 
+/* Forward / backward driver of the misfit gradient with checkpoints.  The
+ * forward run from rest keeps, every `checkpoint_every` steps (K), the pair
+ * (u^s, u^(s-1)) in `workspace`, compressed by the fixed-rate block codec at
+ * `rate_bits` (Sec. 4.2; 0 = raw FP32 copies); the backward run walks the
+ * segments in reverse, decodes each checkpoint, recomputes the segment's states
+ * and applies the adjoint and gradient steps above, so the device holds the
+ * checkpoints plus K + 5 fields instead of all nsteps states.
+ *   workspace: device, 16-byte aligned, at least oocs_misfit_workspace_bytes()
+ *     bytes, owned by the caller; the backward call reads the checkpoints the
+ *     forward call with the same arguments left there.
+ *   src_xyz, w (nw values; w_n = 0 for n >= nw): host arrays.
+ *   d_obs, res: device [nsteps][ny][nx]; res[n] = u^(n+1)(z_r) - d_obs[n].
+ *   misfit: device double, set to J.  grad_m: device field, set to dJ/dm.
+ * Errors: OOCS_ERR_INVALID_ARG for a non-WAVE desc, bad sizes, pointers or a
+ * short workspace (nothing is launched); OOCS_ERR_CUDA for launch failures. */
+int64_t oocs_misfit_workspace_bytes(const oocs_desc *desc, int32_t nsteps, int32_t checkpoint_every,
+                                    int32_t rate_bits);
+oocs_status oocs_misfit_forward(const oocs_desc *desc, const float *m, const int64_t *src_xyz, const float *w,
+                                int32_t nw, int64_t zr, const float *d_obs, int32_t nsteps,
+                                int32_t checkpoint_every, int32_t rate_bits, void *workspace,
+                                int64_t workspace_bytes, float *res, double *misfit, void *stream);
+oocs_status oocs_misfit_backward(const oocs_desc *desc, const float *m, const int64_t *src_xyz, const float *w,
+                                 int32_t nw, int64_t zr, const float *res, int32_t nsteps,
+                                 int32_t checkpoint_every, int32_t rate_bits, void *workspace,
+                                 int64_t workspace_bytes, float *grad_m, void *stream);
+
 /* Fixed-rate block codec (Sec. 4.2) on device arrays.  encode: field
  * [nz][ny][nx] FP32 -> (nx/4)(ny/4)(nz/4) blocks of 8*rate bytes in layer
  * order (block (bx,by,bz) at ((bz*(ny/4)+by)*(nx/4)+bx)).  decode: inverse.

@@ -52,25 +52,32 @@ constexpr int kTY = kConsumerWarps * kRPT;         // tile height (y) = 16
 constexpr int kStepThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
 constexpr int kBoxW = kTX + 8;          // u tile loaded from x0-4 (16-byte aligned) to x0+kTX+4
 
-template <int R>
+// centre fields streamed beside the stencil field: wave (prev, m), adjoint
+// (lam^(n+2), m, lam^(n+1)), gradient (dJ/dm, lam^(n+1))
+template <int SCHEME>
+constexpr int centre_fields() { return SCHEME == kHeat ? 0 : SCHEME == kAdjoint ? 3 : 2; }
+
+template <int R, int NCF>
 struct StepCfg {
     static constexpr int H = kTY + 2 * R;                       // u tile rows
     static constexpr uint32_t kUBytes = H * kBoxW * 4;          // one TMA box of u
     static constexpr int kUStage = ((kUBytes + 127) / 128 * 128) / 4;  // floats per ring stage
     static constexpr int NSU = (2 * R + 2) > 6 ? (2 * R + 2) : 6;  // u ring stages (>= R+1 ahead)
-    static constexpr int NSC = 4;                               // prev / m ring stages
-    static constexpr int kCStage = kTX * kTY;                   // floats per prev / m stage
+    static constexpr int NSC = NCF == 3 ? 3 : 4;                // centre-field ring stages
+    static constexpr int kCStage = kTX * kTY;                   // floats per centre field and stage
     static constexpr uint32_t kCBytes = kCStage * 4;
     static constexpr int Q = 2 * R + 1;                         // register queue length
-    static constexpr size_t smem_bytes(bool wave)
+    static constexpr size_t smem_bytes()
     {
-        return 128 + (size_t)NSU * kUStage * 4 + (wave ? 2ull * NSC * kCStage * 4 : 0) +
-               2 * (NSU + NSC) * 8;
+        return 128 + (size_t)NSU * kUStage * 4 + (size_t)NCF * NSC * kCStage * 4 + 2 * (NSU + NSC) * 8;
     }
 };
 
 struct StepArgs {
     float *out;
+    float *out2;       // kAdjoint: m * out
+    const float *res;  // kAdjoint: residual plane or null
+    int zr;            // kAdjoint: global plane of res
     int nx, ny, nz;
     int64_t plane;
     int gz0;
@@ -91,19 +98,22 @@ struct StepArgs {
 // them in a register queue, takes x neighbours from 64-bit shared loads and y
 // neighbours inside its four rows from the queue.  Planes outside the window
 // or grid arrive zero-filled from TMA.
+//
+// kAdjoint and kGradient (the wave misfit's adjoint, see kernels.h) use the
+// same pipeline with three and two centre fields.
 template <int R, int SCHEME>
 __global__ void __launch_bounds__(kStepThreads, 2)
     k_star_step(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
-                const __grid_constant__ CUtensorMap tm_m, const StepArgs a)
+                const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_c2,
+                const StepArgs a)
 {
-    using C = StepCfg<R>;
-    constexpr bool kWaveS = SCHEME == kWave;
+    constexpr int NCF = centre_fields<SCHEME>();
+    using C = StepCfg<R, NCF>;
     constexpr int Q = C::Q;
     extern __shared__ unsigned char smem_raw[];
     float *us = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float *ps = us + C::NSU * C::kUStage;
-    float *ms = ps + C::NSC * C::kCStage;
-    uint64_t *ufull = reinterpret_cast<uint64_t *>(kWaveS ? ms + C::NSC * C::kCStage : ps);
+    float *cs = us + C::NSU * C::kUStage;  // centre field f, stage st at cs + (f NSC + st) kCStage
+    uint64_t *ufull = reinterpret_cast<uint64_t *>(cs + NCF * C::NSC * C::kCStage);
     uint64_t *uempty = ufull + C::NSU;
     uint64_t *cfull = uempty + C::NSU;
     uint64_t *cempty = cfull + C::NSC;
@@ -151,9 +161,11 @@ __global__ void __launch_bounds__(kStepThreads, 2)
             const int st = (z - zs) % C::NSC, n = (z - zs) / C::NSC;
             if (n > 0 && !mbar_wait(&cempty[st], (uint32_t)((n - 1) & 1)))
                 return false;
-            mbar_arrive_expect_tx(&cfull[st], 2 * C::kCBytes);
-            tma_load_3d(ps + st * C::kCStage, &tm_prev, x0, y0, z, &cfull[st]);
-            tma_load_3d(ms + st * C::kCStage, &tm_m, x0, y0, z, &cfull[st]);
+            mbar_arrive_expect_tx(&cfull[st], NCF * C::kCBytes);
+            tma_load_3d(cs + st * C::kCStage, &tm_prev, x0, y0, z, &cfull[st]);
+            tma_load_3d(cs + (C::NSC + st) * C::kCStage, &tm_m, x0, y0, z, &cfull[st]);
+            if constexpr (NCF == 3)
+                tma_load_3d(cs + (2 * C::NSC + st) * C::kCStage, &tm_c2, x0, y0, z, &cfull[st]);
             c_next = z + 1;
             return true;
         };
@@ -162,7 +174,7 @@ __global__ void __launch_bounds__(kStepThreads, 2)
         for (int p = pu0; good && p < pu_end; ++p) {
             good = put_u(p);
             const int z = p - R;
-            if (kWaveS && good && z >= zs && z < ze)
+            if (NCF > 0 && good && z >= zs && z < ze)
                 good = put_c(z);
         }
         // drain: everything requested lands before the CTA may retire
@@ -225,7 +237,7 @@ __global__ void __launch_bounds__(kStepThreads, 2)
         const int pn = z + R;
         good = mbar_wait(&ufull[u_stage(pn)], u_phase(pn));
         const int cst = (z - zs) % C::NSC;
-        if (kWaveS && good)
+        if (NCF > 0 && good)
             good = mbar_wait(&cfull[cst], (uint32_t)(((z - zs) / C::NSC) & 1));
         if (!good)
             break;
@@ -259,17 +271,36 @@ __global__ void __launch_bounds__(kStepThreads, 2)
                 xv[2 * i + 1] = v.y;
             }
             const float2 uc = q[r][R];
-            [[maybe_unused]] float2 pv, mv;
-            if constexpr (kWaveS) {
+            const int y = y0 + kRPT * wid + r;
+            float2 cv[NCF > 0 ? NCF : 1];
+            if constexpr (NCF > 0) {
                 const int ci = cst * C::kCStage + (kRPT * wid + r) * kTX + kVX * tx;
-                pv = *reinterpret_cast<const float2 *>(ps + ci);
-                mv = *reinterpret_cast<const float2 *>(ms + ci);
+#pragma unroll
+                for (int f = 0; f < NCF; ++f)
+                    cv[f] = *reinterpret_cast<const float2 *>(cs + f * C::NSC * C::kCStage + ci);
+            }
+            [[maybe_unused]] float2 rv = make_float2(0.0f, 0.0f);
+            [[maybe_unused]] bool at_rcv = false;
+            if constexpr (SCHEME == kAdjoint) {
+                at_rcv = a.res != nullptr && gz == a.zr;
+                if (at_rcv)
+                    rv = __ldg(reinterpret_cast<const float2 *>(a.res + (int64_t)y * a.nx + x));
             }
             float res[kVX];
+            [[maybe_unused]] float res2[kVX];
 #pragma unroll
             for (int c = 0; c < kVX; ++c) {
                 const float u = c ? uc.y : uc.x;
-                res[c] = u;  // Dirichlet shell keeps its value
+                // shell: heat / wave keep u (Dirichlet), the adjoint is zero
+                // there, the gradient keeps its value
+                if constexpr (SCHEME == kAdjoint) {
+                    res[c] = 0.0f;
+                    res2[c] = 0.0f;
+                } else if constexpr (SCHEME == kGradient) {
+                    res[c] = c ? cv[0].y : cv[0].x;
+                } else {
+                    res[c] = u;
+                }
                 if (z_interior && in_y[r] && in_x[c]) {
                     float s[R + 1];
                     s[0] = 0.0f;
@@ -285,24 +316,30 @@ __global__ void __launch_bounds__(kStepThreads, 2)
                                        c ? zm.y : zm.x, c ? zp.y : zp.x);
                     }
                     const float L = star_L<R>(a.c, u, s);
+                    [[maybe_unused]] const bool at_src = (x + c == a.src_x && y == a.src_y && z == a.src_zw);
                     if constexpr (SCHEME == kHeat) {
                         res[c] = L;
+                    } else if constexpr (SCHEME == kWave) {
+                        res[c] = wave_update(L, u, c ? cv[0].y : cv[0].x, c ? cv[1].y : cv[1].x, at_src, a.w);
+                    } else if constexpr (SCHEME == kAdjoint) {
+                        res[c] = adjoint_update(L, c ? cv[2].y : cv[2].x, c ? cv[0].y : cv[0].x, at_rcv,
+                                                c ? rv.y : rv.x);
+                        res2[c] = fmul_rn(c ? cv[1].y : cv[1].x, res[c]);
                     } else {
-                        const int y = y0 + kRPT * wid + r;
-                        const bool at_src = (x + c == a.src_x && y == a.src_y && z == a.src_zw);
-                        res[c] = wave_update(L, u, c ? pv.y : pv.x, c ? mv.y : mv.x, at_src, a.w);
+                        res[c] = gradient_update(L, c ? cv[1].y : cv[1].x, c ? cv[0].y : cv[0].x, at_src, a.w);
                     }
                 }
             }
-            *reinterpret_cast<float2 *>(a.out + (int64_t)z * a.plane +
-                                        (int64_t)(y0 + kRPT * wid + r) * a.nx + x) =
-                make_float2(res[0], res[1]);
+            const int64_t o = (int64_t)z * a.plane + (int64_t)y * a.nx + x;
+            *reinterpret_cast<float2 *>(a.out + o) = make_float2(res[0], res[1]);
+            if constexpr (SCHEME == kAdjoint)
+                *reinterpret_cast<float2 *>(a.out2 + o) = make_float2(res2[0], res2[1]);
         }
         // plane z (xy neighbours) and its prev / m stage are done
         __syncwarp();
         if (tx == 0) {
             mbar_arrive(&uempty[u_stage(z)]);
-            if (kWaveS)
+            if (NCF > 0)
                 mbar_arrive(&cempty[cst]);
         }
     }
@@ -365,8 +402,8 @@ static const DevInfo &dev_info()
 template <int R, int SCHEME>
 static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s)
 {
-    using C = StepCfg<R>;
-    const size_t smem = C::smem_bytes(SCHEME == kWave);
+    using C = StepCfg<R, centre_fields<SCHEME>()>;
+    const size_t smem = C::smem_bytes();
     auto kern = k_star_step<R, SCHEME>;
     static int resident = 0;  // CTAs per SM (same on every GB300)
     if (!resident) {
@@ -379,12 +416,15 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
         if (resident < 1)
             return cudaErrorInvalidConfiguration;
     }
-    CUtensorMap mc, mp, mm;
+    constexpr int NCF = centre_fields<SCHEME>();
+    CUtensorMap mc, mp, mm, m2;
     cudaError_t e = make_plane_map(&mc, L.cur, L.nx, L.ny, L.wp, kBoxW, C::H);
     if (e == cudaSuccess)
-        e = make_plane_map(&mp, SCHEME == kWave ? L.prev : L.cur, L.nx, L.ny, L.wp, kTX, kTY);
+        e = make_plane_map(&mp, NCF >= 1 ? L.prev : L.cur, L.nx, L.ny, L.wp, kTX, kTY);
     if (e == cudaSuccess)
-        e = make_plane_map(&mm, SCHEME == kWave ? L.m : L.cur, L.nx, L.ny, L.wp, kTX, kTY);
+        e = make_plane_map(&mm, NCF >= 2 ? L.m : L.cur, L.nx, L.ny, L.wp, kTX, kTY);
+    if (e == cudaSuccess)
+        e = make_plane_map(&m2, NCF >= 3 ? L.c2 : L.cur, L.nx, L.ny, L.wp, kTX, kTY);
     if (e != cudaSuccess)
         return e;
 
@@ -413,7 +453,7 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
     const int nchunks = (nplanes + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles_x, tiles_y, nchunks);
     dim3 block(32, kConsumerWarps + 1, 1);
-    return launch_pdl(kern, grid, block, smem, s, mc, mp, mm, a);
+    return launch_pdl(kern, grid, block, smem, s, mc, mp, mm, m2, a);
 }
 
 cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
@@ -422,6 +462,9 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
         return cudaSuccess;
     StepArgs a;
     a.out = L.out;
+    a.out2 = L.out2;
+    a.res = L.res;
+    a.zr = (int)L.zr;
     a.nx = (int)L.nx;
     a.ny = (int)L.ny;
     a.nz = (int)L.nz;
@@ -444,6 +487,10 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
         return launch_step_t<1, kWave>(L, a, s);
     if (L.radius == 4 && L.scheme == kWave)
         return launch_step_t<4, kWave>(L, a, s);
+    if (L.radius == 4 && L.scheme == kAdjoint && L.c2 && L.out2)
+        return launch_step_t<4, kAdjoint>(L, a, s);
+    if (L.radius == 4 && L.scheme == kGradient)
+        return launch_step_t<4, kGradient>(L, a, s);
     return cudaErrorInvalidValue;
 }
 

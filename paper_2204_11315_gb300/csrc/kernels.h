@@ -9,13 +9,27 @@ namespace oocs {
 // One time step of the star stencil over window-relative planes [z_lo, z_hi)
 // of a window buffer whose plane 0 is global plane gz0 (Sec. 3.1 temporal
 // blocking computes a shrinking trapezoid of planes per step).
+//
+// The same kernel runs the two steps of the wave misfit's discrete adjoint
+// (kAdjoint, kGradient); the fields then play these roles:
+//   scheme     cur (stencil)   prev          m       c2     out           out2
+//   kHeat      u^n             -             -       -      u^(n+1)       -
+//   kWave      u^n             u^(n-1)       m       -      u^(n+1)       -
+//   kAdjoint   m lam^(n+1)     lam^(n+2)     m       lam^(n+1)  lam^n     m lam^n
+//   kGradient  u^n             dJ/dm         lam^(n+1)  -   dJ/dm         -
+// (out may alias prev; kAdjoint adds res at global plane zr, kGradient adds w
+// at the source voxel.)
 struct StepLaunch {
-    int scheme;          // kHeat / kWave
-    int radius;          // 1 or 4
-    const float *cur;    // u at the previous time level, window buffer
-    const float *prev;   // wave: u two levels back (may alias out)
-    const float *m;      // wave: model field
+    int scheme;          // kHeat / kWave / kAdjoint / kGradient
+    int radius;          // 1 or 4 (4 for kAdjoint / kGradient)
+    const float *cur;    // stencil input, window buffer
+    const float *prev;   // first centre field (see the table)
+    const float *m;      // second centre field
+    const float *c2;     // kAdjoint: third centre field
     float *out;          // result, window buffer
+    float *out2;         // kAdjoint: m * result
+    const float *res;    // kAdjoint: residual plane (nx * ny) or null
+    int64_t zr;          // kAdjoint: global plane of res
     int64_t nx, ny, nz;  // grid (nz = global planes)
     int64_t gz0;         // global z of window plane 0
     int64_t wp;          // planes in the window buffers

@@ -9,12 +9,16 @@
 //   L     = fma(c_r, s_r, ... fma(c_1, s_1, c_0 * u))
 //   heat: u' = L
 //   wave: u' = fma(m, L (+ w at the source), (u + u) - up)
+//   adjoint of the wave step (stencil applied to mu = m lam):
+//         lam' = ((lam + lam) - lam_pp) + L (+ r at the receiver plane)
+//   gradient of the wave misfit (stencil applied to u):
+//         g' = fma(lam, L (+ w at the source), g)
 #pragma once
 #include "devmath.cuh"
 
 namespace oocs {
 
-enum { kHeat = 0, kWave = 1 };
+enum { kHeat = 0, kWave = 1, kAdjoint = 2, kGradient = 3 };
 
 struct StarCoef {
     float c[5];
@@ -41,6 +45,17 @@ OOCS_FN float wave_update(float L, float u, float up, float m, bool at_src, floa
     if (at_src)
         L = fadd_rn(L, w);
     return fma_rn(m, L, fsub_rn(fadd_rn(u, u), up));
+}
+
+OOCS_FN float adjoint_update(float L, float lam, float lam_pp, bool at_rcv, float r)
+{
+    const float v = fadd_rn(fsub_rn(fadd_rn(lam, lam), lam_pp), L);
+    return at_rcv ? fadd_rn(v, r) : v;
+}
+
+OOCS_FN float gradient_update(float L, float lam, float g, bool at_src, float w)
+{
+    return fma_rn(lam, at_src ? fadd_rn(L, w) : L, g);
 }
 
 }  // namespace oocs

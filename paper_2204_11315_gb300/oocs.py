@@ -129,6 +129,11 @@ SIGNATURES = {
     "oocs_receiver_residual": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "oocs_model_from_velocity": (_i32, [_vp, _vp, _i64, ctypes.c_float, _vp]),
     "oocs_velocity_gradient": (_i32, [_vp, _vp, _vp, _i64, ctypes.c_float, _vp]),
+    "oocs_misfit_workspace_bytes": (_i64, [ctypes.POINTER(oocs_desc), _i32, _i32, _i32]),
+    "oocs_misfit_forward": (_i32, [ctypes.POINTER(oocs_desc), _vp, _vp, _vp, _i32, _i64, _vp, _i32, _i32,
+                                   _i32, _vp, _i64, _vp, _vp, _vp]),
+    "oocs_misfit_backward": (_i32, [ctypes.POINTER(oocs_desc), _vp, _vp, _vp, _i32, _i64, _vp, _i32, _i32,
+                                    _i32, _vp, _i64, _vp, _vp]),
     "oocs_encode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
     "oocs_decode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
 }
@@ -320,6 +325,38 @@ def oocs_model_from_velocity(v_ptr, m_ptr, n, dt_over_dx, stream=0):
 def oocs_velocity_gradient(gm_ptr, v_ptr, gv_ptr, n, dt_over_dx, stream=0):
     _check(lib().oocs_velocity_gradient(_vp(gm_ptr), _vp(v_ptr), _vp(gv_ptr), int(n), float(dt_over_dx),
                                         _vp(stream)))
+
+
+def oocs_misfit_workspace_bytes(desc, nsteps, checkpoint_every, rate_bits):
+    n = lib().oocs_misfit_workspace_bytes(ctypes.byref(desc), int(nsteps), int(checkpoint_every),
+                                          int(rate_bits))
+    if n < 0:
+        raise OOCSError(1, "bad misfit workspace arguments")
+    return n
+
+
+def _src_w(src, w):
+    srcarr = (_i64 * 3)(*[int(v) for v in src])
+    wv = np.ascontiguousarray(w if w is not None else np.zeros(0), dtype=np.float32)
+    return srcarr, wv
+
+
+def oocs_misfit_forward(desc, m_ptr, src, w, zr, d_obs_ptr, nsteps, checkpoint_every, rate_bits, ws_ptr,
+                        ws_bytes, res_ptr, misfit_ptr, stream=0):
+    srcarr, wv = _src_w(src, w)
+    _check(lib().oocs_misfit_forward(ctypes.byref(desc), _vp(m_ptr), ctypes.cast(srcarr, _vp),
+                                     wv.ctypes.data_as(_vp), int(wv.size), int(zr), _vp(d_obs_ptr),
+                                     int(nsteps), int(checkpoint_every), int(rate_bits), _vp(ws_ptr),
+                                     int(ws_bytes), _vp(res_ptr), _vp(misfit_ptr), _vp(stream)))
+
+
+def oocs_misfit_backward(desc, m_ptr, src, w, zr, res_ptr, nsteps, checkpoint_every, rate_bits, ws_ptr,
+                         ws_bytes, grad_ptr, stream=0):
+    srcarr, wv = _src_w(src, w)
+    _check(lib().oocs_misfit_backward(ctypes.byref(desc), _vp(m_ptr), ctypes.cast(srcarr, _vp),
+                                      wv.ctypes.data_as(_vp), int(wv.size), int(zr), _vp(res_ptr),
+                                      int(nsteps), int(checkpoint_every), int(rate_bits), _vp(ws_ptr),
+                                      int(ws_bytes), _vp(grad_ptr), _vp(stream)))
 
 
 def oocs_encode_device(field_ptr, nx, ny, nz, rate, blocks_ptr, stream=0):

@@ -209,3 +209,70 @@ def test_workload_gradient_256cubed(P):
     assert np.abs(grads[0]).max() > 0
     # compressing the checkpoints at rate 16 changes the gradient very little
     assert rel_l2(grads[16], grads[0]) <= 1e-3
+
+
+def _granular_gradient(P, torch, prob, v, d):
+    """The backward pass written out with the per-step entry points (no driver):
+    raw states of every step, adjoint step, gradient accumulation."""
+    nz, ny, nx = prob.shape
+    n = nz * ny * nx
+    desc = prob.desc()
+    s = torch.cuda.current_stream().cuda_stream
+    m = torch.empty_like(v)
+    P.oocs_model_from_velocity(v.data_ptr(), m.data_ptr(), n, prob.dt / prob.dx, s)
+    w = np.asarray(prob.wavelet, np.float32)
+    N = prob.nsteps
+    states = torch.zeros((N + 1,) + tuple(prob.shape), device="cuda")  # states[k] = u^k
+    up = torch.zeros_like(v)
+    sc = torch.empty_like(v)
+    for k in range(N):
+        u = states[k].clone()
+        P.oocs_incore_run(desc, u.data_ptr(), up.data_ptr(), m.data_ptr(), sc.data_ptr(), 1, k,
+                          prob.src_xyz, w, s)
+        states[k + 1].copy_(u)
+        up.copy_(states[k])
+    res = torch.empty((N, ny, nx), device="cuda")
+    mis = torch.zeros(1, dtype=torch.float64, device="cuda")
+    plane = ny * nx
+    for k in range(N):
+        P.oocs_receiver_residual(states[k + 1].data_ptr() + 4 * prob.zr * plane, d[k].data_ptr(), plane,
+                                 res[k].data_ptr(), mis.data_ptr(), s)
+    lam, lp, mu, mo, g = (torch.zeros_like(v) for _ in range(5))
+    for k in range(N, 0, -1):
+        P.oocs_adjoint_step(desc, lam.data_ptr(), lp.data_ptr(), mu.data_ptr(), mo.data_ptr(), m.data_ptr(),
+                            res[k - 1].data_ptr(), prob.zr, s)
+        lam, lp = lp, lam
+        mu, mo = mo, mu
+        P.oocs_gradient_accumulate(desc, g.data_ptr(), lam.data_ptr(), states[k - 1].data_ptr(),
+                                   float(w[k - 1]), prob.src_xyz, s)
+    torch.cuda.synchronize()
+    return float(mis.item()), g
+
+
+@pytest.mark.parametrize("K", [10, 7, 1])
+def test_driver_matches_per_step_entry_points(P, K):
+    """oocs_misfit_forward / _backward with raw checkpoints give bit for bit the
+    misfit and dJ/dm of the per-step loop, for segment lengths that divide the
+    run, leave a short last segment, and hold a single state."""
+    torch = torch_cuda()
+    A, prob, v, v_true, w = _small_problem(P, 0, shape=(32, 28, 36), nsteps=40)
+    prob.checkpoint_every = K
+    vv = torch.from_numpy(v).cuda()
+    d = A.receiver_data(torch.from_numpy(v_true).cuda(), prob)
+    J_ref, g_ref = _granular_gradient(P, torch, prob, vv, d)
+    nbytes = prob.workspace_bytes()
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    m = torch.empty_like(vv)
+    s = torch.cuda.current_stream().cuda_stream
+    P.oocs_model_from_velocity(vv.data_ptr(), m.data_ptr(), vv.numel(), prob.dt / prob.dx, s)
+    res = torch.empty((prob.nsteps,) + tuple(prob.shape[1:]), device="cuda")
+    mis = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(vv)
+    P.oocs_misfit_forward(prob.desc(), m.data_ptr(), prob.src_xyz, prob.wavelet32(), prob.zr, d.data_ptr(),
+                          prob.nsteps, K, 0, ws.data_ptr(), nbytes, res.data_ptr(), mis.data_ptr(), s)
+    P.oocs_misfit_backward(prob.desc(), m.data_ptr(), prob.src_xyz, prob.wavelet32(), prob.zr, res.data_ptr(),
+                           prob.nsteps, K, 0, ws.data_ptr(), nbytes, g.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert J_ref > 0
+    assert abs(float(mis.item()) - J_ref) <= 1e-12 * J_ref  # double accumulation order may differ
+    assert torch.equal(g, g_ref)
