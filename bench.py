@@ -5,12 +5,15 @@ Workload (the metric's configuration): 25-point 8th-order acoustic wave
 (leapfrog), FP32, 512^3 grid, dx = 10 m, dt = 0.8 ms, seeded 8-layer velocity
 model 1500-4500 m/s with +-5 % noise, 15 Hz Ricker source at the centre,
 device budget 4 GiB, 8 z-slabs of 64 planes, temporal blocking depth k = 4,
-fixed-rate codec at 16 bits/value, single working buffer (Sec. 5).
+fixed-rate codec at 16 bits/value, single working buffer (Sec. 5).  The
+read-only model m is kept on the device (decoded once from its rate-16 store,
+inside the budget), so u and u_prev stream; ``compare`` also times the
+paper's dataflow, which streams m with every slab visit.
 
 One bench step = one oocs_step(100) from rest (the host stores are reset to
 the compressed initial state and the time index to 0 before each, untimed):
-100 time steps = 25 sweeps over the 8 slabs, every slab streamed host->GPU,
-decoded, advanced 4 steps, encoded and streamed back.  ``value`` = interior point-updates / s (Gpoint-updates/s) with
+100 time steps = 25 sweeps over the 8 slabs, every slab's u and u_prev
+streamed host->GPU, decoded, advanced 4 steps, encoded and streamed back.  ``value`` = interior point-updates / s (Gpoint-updates/s) with
 the fields already in the compressed host store (pinned host memory: where
 the method keeps them); ``e2e`` adds the conversion from and to raw FP32 host
 arrays through oocs_compress / oocs_decompress.
@@ -41,12 +44,14 @@ K_DEPTH = 4
 SLAB = 64
 BUDGET = 4 << 30
 RATE = 16
+RO_RESIDENT = 1  # keep m on the device (oocs_desc.readonly_resident)
 WAVE_BYTES_PER_POINT = 16  # read u, u_prev, m; write u_next (FP32)
-WORKLOAD = "wave25_512cubed_100steps_8slabs_k4_rate16_swb"
+WORKLOAD = "wave25_512cubed_100steps_8slabs_k4_rate16_swb_m_resident"
 # DRAM bytes (read + write) per updated point of the wave step kernel from one ncu
-# capture of a 512x512x192 case (profiles/k_star_step_and_codec_512x512x192.md);
-# scaled to a launch by its points.  Set to None whenever the kernel changes.
-STEP_TRAFFIC_B_PER_POINT = 15.53
+# capture of a 512x512x80 launch, the window size of the sweep's balanced step
+# launches (profiles/k_star_step_and_codec_512x512x192_512x512x80.md); scaled
+# to a launch by its points.  Set to None whenever the kernel changes.
+STEP_TRAFFIC_B_PER_POINT = 15.93
 
 
 def parse():
@@ -61,7 +66,8 @@ def parse():
     ap.add_argument("--profile-run", choices=["sweep", "kernels"], default=None,
                     help="run only the region to capture under ncu --profile-from-start off: "
                          "'sweep' = one oocs_step(100) of the workload; 'kernels' = one launch each "
-                         "of the wave step, encode and decode kernels on a 512x512x192 grid")
+                         "of the wave step, encode and decode kernels on a 512x512x192 grid, then "
+                         "one wave step on a 512x512x80 grid")
     return ap.parse_args()
 
 
@@ -190,15 +196,15 @@ def make_inputs(total_steps):
     return m, w, (cx, cy, cz), z
 
 
-def wave_desc(P, rate, wb=1):
+def wave_desc(P, rate, wb=1, ro=RO_RESIDENT):
     import synthetic
     return P.make_desc(N, N, N, P.OOCS_WAVE, synthetic.wave_star_coef(), BUDGET, rate_bits=rate,
-                       temporal_depth=K_DEPTH, slab_planes=SLAB, working_buffers=wb)
+                       temporal_depth=K_DEPTH, slab_planes=SLAB, working_buffers=wb, readonly_resident=ro)
 
 
-def open_ctx(P, torch, rate, wb, inputs):
+def open_ctx(P, torch, rate, wb, inputs, ro=RO_RESIDENT):
     m, w, src, z = inputs
-    st = P.OutOfCoreStencil(wave_desc(P, rate, wb))
+    st = P.OutOfCoreStencil(wave_desc(P, rate, wb, ro))
     pin = {}
     for name, arr in (("z", z), ("m", m)):
         t = torch.empty(arr.shape, dtype=torch.float32, pin_memory=True)
@@ -271,6 +277,8 @@ def base_line(args, world):
                        "time_steps_per_step": STEPS_PER_CALL, "slabs": N // SLAB,
                        "slab_planes": SLAB, "temporal_depth": K_DEPTH, "rate_bits": args.rate,
                        "working_buffers": 1, "device_budget_bytes": BUDGET,
+                       "model_m": "device-resident (decoded once from its store)" if RO_RESIDENT
+                       else "streamed with every slab visit",
                        "l2": "inputs larger than L2 (one 512^3 FP32 field = 537 MB)",
                        "parallelism": f"replicas{world}"}}
 
@@ -329,17 +337,21 @@ def run_ours(args):
                 "frac": (step_gbs / hbm_peak) if step_gbs else None,
                 "traffic": (STEP_TRAFFIC_B_PER_POINT * cls["step"]["units"] / max(cls["step"]["launches"], 1)
                             if STEP_TRAFFIC_B_PER_POINT else None),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 512x512x192 "
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 512x512x80 "
                                   "launch, scaled by points per launch",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": step_bytes / max(cls["step"]["launches"], 1),
                 "avg_launch_ms": cls["step"]["device_ms"] / max(cls["step"]["launches"], 1)}
-    # binding roofline of the whole sweep: HBM algorithmic bytes vs host link
+    # binding roofline of the whole sweep: HBM algorithmic bytes vs host link.
+    # Per sweep and grid value of a streamed field: in = H2D write (c) + decode
+    # read (c) + write (4); out = encode read (4) + write (c) + D2H read (c);
+    # c = 4 uncompressed (the decode / encode are copies).
     n_all = N ** 3
     c_bytes = args.rate / 8.0 if args.rate else 4.0
     passes = d["passes_done"]
+    f_in = st.plan.fields_in
     hbm_alg = STEPS_PER_CALL * args.steps * interior_points() * WAVE_BYTES_PER_POINT \
-        + passes * n_all * 2 * c_bytes * (3 + 2)
+        + passes * n_all * (f_in * (2 * c_bytes + 4) + 2 * (4 + 2 * c_bytes))
     t_hbm = hbm_alg / (hbm_peak * 1e9)
     t_h2d = d["h2d_bytes"] / (link["h2d_GBs"] * 1e9)
     t_d2h = d["d2h_bytes"] / (link["d2h_GBs"] * 1e9)
@@ -405,10 +417,14 @@ def run_ours(args):
     compare = None
     if not args.no_compare:
         compare = {}
-        for name, rate, wb in (("uncompressed_swb", 0, 1), ("uncompressed_classic", 0, 3),
-                               (f"rate{args.rate}_classic", args.rate, 3),
-                               ("rate8_swb", 8, 1), ("rate12_swb", 12, 1)):
-            st, pin = open_ctx(P, torch, rate, wb, inputs)
+        for name, rate, wb, ro in (("uncompressed_swb", 0, 1, RO_RESIDENT),
+                                   ("uncompressed_classic", 0, 3, RO_RESIDENT),
+                                   (f"rate{args.rate}_classic", args.rate, 3, RO_RESIDENT),
+                                   ("rate8_swb", 8, 1, RO_RESIDENT), ("rate12_swb", 12, 1, RO_RESIDENT),
+                                   (f"rate{args.rate}_swb_m_streamed", args.rate, 1, 0),
+                                   ("uncompressed_swb_m_streamed", 0, 1, 0),
+                                   ("uncompressed_classic_m_streamed", 0, 3, 0)):
+            st, pin = open_ctx(P, torch, rate, wb, inputs, ro)
             snap_u = st.snapshot_stores()
             timed_calls(torch, st, 1, snap_u)
             k = 2
@@ -418,11 +434,14 @@ def run_ours(args):
             st.close()
             del st, pin, snap_u
             torch.cuda.empty_cache()
-        ws_c = wave_desc(P, args.rate)
-        compressed_ws = P.oocs_query(ws_c).workspace_bytes
         compare["speedup_compressed_vs_uncompressed"] = value / world / compare["uncompressed_swb"]["value"]
+        compare["speedup_compressed_vs_uncompressed_m_streamed"] = \
+            compare[f"rate{args.rate}_swb_m_streamed"]["value"] / compare["uncompressed_swb_m_streamed"]["value"]
+        # the paper's memory comparison (Sec. 6.2): compressed SWB against
+        # uncompressed classic, both streaming m as the paper does
         compare["memory_reduction_vs_uncompressed_classic"] = \
-            1.0 - compressed_ws / compare["uncompressed_classic"]["workspace_bytes"]
+            1.0 - compare[f"rate{args.rate}_swb_m_streamed"]["workspace_bytes"] \
+            / compare["uncompressed_classic_m_streamed"]["workspace_bytes"]
         compare["paper_v100"] = {"speedup": 1.1, "memory_reduction": 0.330,
                                  "source": "Sec. 6.1 and Sec. 6.2 (V100-PCIe, FP64, context only)"}
 
@@ -546,11 +565,17 @@ def run_profile(args):
     s = torch.cuda.current_stream(dev).cuda_stream
     d = P.make_desc(N, N, nz, P.OOCS_WAVE, synthetic.wave_star_coef(), BUDGET, rate_bits=0,
                     temporal_depth=K_DEPTH, slab_planes=SLAB)
+    # an 80-plane grid: the window size of the sweep's balanced step launches
+    d80 = P.make_desc(N, N, 80, P.OOCS_WAVE, synthetic.wave_star_coef(), BUDGET, rate_bits=0,
+                      temporal_depth=K_DEPTH, slab_planes=SLAB)
+    u80, up80, sc80, m80 = (t[:80].clone() for t in (u, up, sc, m))
     torch.cuda.synchronize(dev)
     torch.cuda.profiler.start()
     P.oocs_incore_run(d, u.data_ptr(), up.data_ptr(), m.data_ptr(), sc.data_ptr(), 1, 0, None, None, s)
     P.oocs_encode_device(u.data_ptr(), N, N, nz, args.rate, blocks.data_ptr(), s)
     P.oocs_decode_device(blocks.data_ptr(), N, N, nz, args.rate, sc.data_ptr(), s)
+    P.oocs_incore_run(d80, u80.data_ptr(), up80.data_ptr(), m80.data_ptr(), sc80.data_ptr(), 1, 0, None, None,
+                      s)
     torch.cuda.synchronize(dev)
     torch.cuda.profiler.stop()
     print(json.dumps({"profile_run": "kernels", "grid": [N, N, nz], "rate": args.rate,

@@ -74,6 +74,12 @@ typedef struct {
     int32_t temporal_depth;      /* k >= 1 steps per slab visit; 0 = 4                        */
     int32_t slab_planes;         /* T, multiple of 4; 0 = largest T that fits device_budget  */
     int32_t working_buffers;     /* OOCS_SWB (1) or OOCS_CLASSIC (3)                          */
+    int32_t readonly_resident;   /* WAVE: 0 = stream the read-only model M with every slab
+                                  * visit, as the paper does (Sec. 6.2); 1 = keep M on the
+                                  * device as FP32 (decoded once from its store) for the
+                                  * context's life, counted in the workspace, so only U and
+                                  * U_PREV cross the host link.  Ignored for HEAT.           */
+    int32_t reserved;            /* 0                                                        */
 } oocs_desc;
 
 /* Resolved plan (Sec. 3.1 chunking and temporal blocking; Sec. 6.2 memory model). */
@@ -85,7 +91,7 @@ typedef struct {
     int32_t window_planes;       /* min(T + 2h, nz)                                          */
     int32_t fields_in;           /* streamed host->device fields (HEAT 1, WAVE 3)            */
     int32_t fields_out;          /* streamed device->host fields (HEAT 1, WAVE 2)            */
-    int32_t reserved;
+    int32_t readonly_resident;   /* 1 if M is kept on the device (fields_in is then 2)       */
     uint64_t layer_bytes;        /* bytes of one 4-plane layer of one field in the store     */
     uint64_t host_store_bytes;   /* bytes of one field's host store = nz/4 * layer_bytes     */
     uint64_t workspace_bytes;    /* device workspace for this desc                           */
@@ -141,7 +147,10 @@ oocs_status oocs_create(const oocs_desc *desc, void *workspace, uint64_t workspa
  * copies to overlap.  Layout: nz/4 layers of plan.layer_bytes; with
  * rate_bits > 0 a layer holds (nx/4)(ny/4) codec blocks of 8*rate_bits bytes,
  * block (bx, by) at ((by * nx/4) + bx) * 8*rate_bits; with rate_bits = 0 it is
- * the raw FP32 planes.  Updated in place by oocs_step.                      */
+ * the raw FP32 planes.  Updated in place by oocs_step.  With
+ * desc.readonly_resident the device copy of M is (re)made from its store at
+ * the first oocs_step after oocs_bind_field(M) or oocs_compress(M); later
+ * writes to the M store by other means are not seen until one of them.     */
 oocs_status oocs_bind_field(oocs_ctx *ctx, int32_t field, void *host_store, uint64_t bytes);
 
 /* Set the point source of the WAVE scheme: voxel (x, y, z) receives w[t] at

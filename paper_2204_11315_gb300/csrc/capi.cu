@@ -60,6 +60,8 @@ struct Layout {
     uint64_t w_off[3][3];     // [working buffer][buffer]
     uint64_t in_off[3][3];    // [slot][field_in]
     uint64_t out_off[3][2];   // [slot][field_out]
+    uint64_t ro_off;          // resident FP32 copy of M (readonly_resident), else 0
+    uint64_t ro_bytes;
     uint64_t total;
     int nwb;                  // working buffers (1 SWB, 3 classic)
     int nbuf;                 // buffers per working set (heat 2, wave 3)
@@ -70,6 +72,8 @@ struct Layout {
 
 struct Derived {
     int r, k, h, T, S, wp, fin, fout;
+    int fin_stream;  // fields crossing the link per visit (fin minus a resident M)
+    bool ro_res;     // M kept on the device
     uint64_t layer_bytes;
     int64_t slot_layers_in, slot_layers_out;
 };
@@ -85,6 +89,8 @@ Derived derive(const oocs_desc &d, int T)
     v.wp = (int)std::min<int64_t>(T + 2 * (int64_t)v.h, d.nz);
     v.fin = d.scheme == OOCS_WAVE ? 3 : 1;
     v.fout = d.scheme == OOCS_WAVE ? 2 : 1;
+    v.ro_res = d.scheme == OOCS_WAVE && d.readonly_resident != 0;
+    v.fin_stream = v.fin - (v.ro_res ? 1 : 0);
     v.layer_bytes = d.rate_bits > 0 ? (uint64_t)(d.nx / 4) * (d.ny / 4) * 8ull * d.rate_bits
                                     : (uint64_t)4 * d.nx * d.ny * 4;
     v.slot_layers_in = std::min<int64_t>(ceil_div(T + v.h, 4), d.nz / 4);
@@ -97,7 +103,9 @@ Layout layout_for(const oocs_desc &d, const Derived &v, int nwb)
     Layout L;
     memset(&L, 0, sizeof(L));
     L.nwb = nwb;
-    L.nbuf = d.scheme == OOCS_WAVE ? 3 : 2;
+    // window buffers: heat u, u'; wave u, u_prev and m (m lives in the
+    // resident copy when readonly_resident)
+    L.nbuf = d.scheme == OOCS_WAVE && !v.ro_res ? 3 : 2;
     L.buf_bytes = align_up((uint64_t)v.wp * d.nx * d.ny * 4, 256);
     L.in_slot_bytes = align_up((uint64_t)v.slot_layers_in * v.layer_bytes, 256);
     L.out_slot_bytes = align_up((uint64_t)v.slot_layers_out * v.layer_bytes, 256);
@@ -108,7 +116,7 @@ Layout layout_for(const oocs_desc &d, const Derived &v, int nwb)
             off += L.buf_bytes;
         }
     for (int q = 0; q < 3; ++q)
-        for (int f = 0; f < v.fin; ++f) {
+        for (int f = 0; f < v.fin_stream; ++f) {
             L.in_off[q][f] = off;
             off += L.in_slot_bytes;
         }
@@ -117,6 +125,11 @@ Layout layout_for(const oocs_desc &d, const Derived &v, int nwb)
             L.out_off[q][f] = off;
             off += L.out_slot_bytes;
         }
+    if (v.ro_res) {
+        L.ro_off = off;
+        L.ro_bytes = align_up((uint64_t)d.nz * d.nx * d.ny * 4, 256);
+        off += L.ro_bytes;
+    }
     L.total = off;
     return L;
 }
@@ -165,6 +178,10 @@ oocs_status validate_desc(const oocs_desc *d, std::string &err)
     }
     if (d->working_buffers != OOCS_SWB && d->working_buffers != OOCS_CLASSIC) {
         err = "working_buffers must be 1 (SWB) or 3 (classic)";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->readonly_resident != 0 && d->readonly_resident != 1) {
+        err = "readonly_resident must be 0 or 1";
         return OOCS_ERR_INVALID_ARG;
     }
     return OOCS_OK;
@@ -228,8 +245,9 @@ oocs_status plan_impl(const oocs_desc *d, oocs_plan *p, std::string &err)
     p->halo_planes = v.h;
     p->num_slabs = v.S;
     p->window_planes = v.wp;
-    p->fields_in = v.fin;
+    p->fields_in = v.fin_stream;
     p->fields_out = v.fout;
+    p->readonly_resident = v.ro_res ? 1 : 0;
     p->layer_bytes = v.layer_bytes;
     p->host_store_bytes = (uint64_t)(d->nz / 4) * v.layer_bytes;
     p->workspace_bytes = layout_for(*d, v, nwb).total;
@@ -264,6 +282,7 @@ struct oocs_ctx {
 
     uint64_t g = 0;  // slab visits enqueued
     oocs_stats stats;
+    bool ro_dirty = true;  // resident M must be (re)made from its store
 
     // trace mode (oocs_trace_schedule): scheduling operations are recorded
     // here instead of being issued to CUDA
@@ -284,6 +303,7 @@ struct oocs_ctx {
     float *wbuf(int wb, int b) const { return reinterpret_cast<float *>(ws + L.w_off[wb][b]); }
     char *in_slot(int q, int f) const { return ws + L.in_off[q][f]; }
     char *out_slot(int q, int f) const { return ws + L.out_off[q][f]; }
+    float *ro_m() const { return reinterpret_cast<float *>(ws + L.ro_off); }
 };
 
 namespace {
@@ -527,6 +547,37 @@ oocs_status store_layers(oocs_ctx *c, const float *src, int64_t w0, int64_t l0, 
     return ks.end(kClsStore, (uint64_t)(l1 - l0) * 4 * c->d.nx * c->d.ny);
 }
 
+// Make the resident FP32 copy of M (readonly_resident) from its host store,
+// on stream 0: raw planes are copied; compressed layers go in chunks of T
+// planes through staging slot 0 and are decoded into place, so the resident
+// values are exactly those a per-visit decode would produce.
+oocs_status upload_resident(oocs_ctx *c)
+{
+    const oocs_desc &d = c->d;
+    const Derived &v = c->v;
+    cudaStream_t st = c->st[0];
+    const int64_t plane_f = d.nx * d.ny;
+    const char *store = c->store[OOCS_FIELD_M];
+    if (d.rate_bits == 0) {
+        const uint64_t bytes = (uint64_t)d.nz * plane_f * 4;
+        CU(c, cudaMemcpyAsync(c->ro_m(), store, bytes, cudaMemcpyHostToDevice, st));
+        c->stats.h2d_bytes += bytes;
+    } else {
+        char *blk = c->in_slot(0, 0);  // holds slot_layers_in >= T/4 layers
+        for (int64_t z0 = 0; z0 < d.nz; z0 += v.T) {
+            const int64_t z1 = std::min<int64_t>(z0 + v.T, d.nz);
+            const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
+            CU(c, cudaMemcpyAsync(blk, store + (uint64_t)(z0 / 4) * v.layer_bytes, bytes, cudaMemcpyHostToDevice,
+                                  st));
+            CU(c, launch_decode_layers(blk, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, c->ro_m() + z0 * plane_f, st));
+            c->stats.h2d_bytes += bytes;
+            c->stats.kernel_launches++;
+        }
+    }
+    c->ro_dirty = false;
+    return OOCS_OK;
+}
+
 // Enqueue one slab visit (slab s, k_eff steps starting at global time t).
 oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
 {
@@ -558,14 +609,14 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     if (c->trace) {
         if (n1 > n0) {
             oocs_trace_access a[4] = {acc(OOCS_RES_IN_SLOT, q, n0 / 4, n1 / 4, true)};
-            for (int f = 0; f < v.fin; ++f)
+            for (int f = 0; f < v.fin_stream; ++f)
                 a[1 + f] = acc(OOCS_RES_HOST, in_field_id(c, f), n0 / 4, n1 / 4, false);
             trace_push(c, OOCS_OP_H2D, q, -1, (int64_t)g, {a[0], a[1]});
-            for (int f = 1; f < v.fin; ++f)
+            for (int f = 1; f < v.fin_stream; ++f)
                 c->trace->back().access[c->trace->back().naccess++] = a[1 + f];
         }
     } else {
-        for (int f = 0; f < v.fin; ++f) {
+        for (int f = 0; f < v.fin_stream; ++f) {
             const int id = in_field_id(c, f);
             const uint64_t bytes = (uint64_t)(n1 - n0) / 4 * v.layer_bytes;
             if (bytes) {
@@ -574,7 +625,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             }
         }
     }
-    c->stats.h2d_bytes += (uint64_t)v.fin * (uint64_t)(n1 - n0) / 4 * v.layer_bytes;
+    c->stats.h2d_bytes += (uint64_t)v.fin_stream * (uint64_t)(n1 - n0) / 4 * v.layer_bytes;
     SCHED(sched_record(c, q, kEvH2D + q));
     // 4. working buffer released by visit g-1 (single working buffer); the
     //    overlap borrowed from visit g-1's slot has landed
@@ -601,7 +652,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         // one decode launch for every field and both source slots
         CodecSegments sg;
         int64_t nl[kMaxCodecSegments];
-        for (int f = 0; f < v.fin; ++f) {
+        for (int f = 0; f < v.fin_stream; ++f) {
             float *dst = c->wbuf(wb, f);  // heat: U -> buf 0; wave: U, U_PREV, M -> 0, 1, 2
             if (s > 0 && n0 > w0) {
                 sg.blocks[sg.nseg] = c->in_slot(qp, f) + (w0 / 4 - pn0 / 4) * v.layer_bytes;
@@ -620,11 +671,11 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             return r;
         CU(c, launch_decode_segments(sg, nl, d.nx, d.ny, d.rate_bits, st));
         c->stats.kernel_launches++;
-        r = ks.end(kClsLoad, (uint64_t)v.fin * (w1 - w0) * plane_f);
+        r = ks.end(kClsLoad, (uint64_t)v.fin_stream * (w1 - w0) * plane_f);
         if (r != OOCS_OK)
             return r;
     } else {
-        for (int f = 0; f < v.fin; ++f) {
+        for (int f = 0; f < v.fin_stream; ++f) {
             float *dst = c->wbuf(wb, f);
             if (s > 0) {
                 oocs_status r = load_layers(c, c->in_slot(qp, f), pn0 / 4, w0 / 4, n0 / 4, dst, w0, st);
@@ -667,7 +718,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         Ls.z_hi = hi - w0;
         Ls.cur = c->wbuf(wb, cur);
         Ls.prev = c->wbuf(wb, oth);
-        Ls.m = d.scheme == OOCS_WAVE ? c->wbuf(wb, 2) : nullptr;
+        Ls.m = d.scheme != OOCS_WAVE ? nullptr : v.ro_res ? c->ro_m() + w0 * plane_f : c->wbuf(wb, 2);
         Ls.out = c->wbuf(wb, oth);
         const int64_t tstep = t + j - 1;
         Ls.src_z = -1;
@@ -842,6 +893,8 @@ oocs_status oocs_bind_field(oocs_ctx *ctx, int32_t field, void *host_store, uint
                     "host store needs " + std::to_string(ctx->p.host_store_bytes) + " bytes");
     ctx->store[field] = static_cast<char *>(host_store);
     ctx->store_bytes[field] = bytes;
+    if (field == OOCS_FIELD_M)
+        ctx->ro_dirty = true;
     return OOCS_OK;
 }
 
@@ -873,6 +926,8 @@ static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, f
         return fail(ctx, OOCS_ERR_STATE, "field is not bound");
     if (enc ? !src : !dst)
         return fail(ctx, OOCS_ERR_INVALID_ARG, "raw host array is NULL");
+    if (enc && field == OOCS_FIELD_M)
+        ctx->ro_dirty = true;
     const oocs_desc &d = ctx->d;
     const uint64_t plane_bytes = (uint64_t)d.nx * d.ny * 4;
     s = join_streams(ctx);
@@ -953,6 +1008,11 @@ oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
     s = sched_record(ctx, 0, kEvT0);
     if (s != OOCS_OK)
         return s;
+    if (ctx->v.ro_res && ctx->ro_dirty && !ctx->trace) {
+        s = upload_resident(ctx);
+        if (s != OOCS_OK)
+            return s;
+    }
     s = join_streams(ctx);
     if (s != OOCS_OK)
         return s;

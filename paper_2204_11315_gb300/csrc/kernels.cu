@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <utility>
 
 #include "codec.cuh"
@@ -81,23 +82,80 @@ struct StepArgs {
     int nx, ny, nz;
     int64_t plane;
     int gz0;
-    int z_lo, z_hi, zchunk;
+    int z_lo, z_hi;
+    int zchunk;         // > 0: chunked launch; 0: balanced launch
+    int tiles_y, ntiles;
     StarCoef c;
     int src_x, src_y, src_zw;
     float w;
 };
 
-// One time step over window planes [z_lo, z_hi).  CTA = 64 x 16 tile walking
-// a z chunk, warp-specialised: warp 4 is the producer, which streams u tiles
-// (with a 4-column / R-row halo) into an NSU-deep shared-memory ring and the
-// prev / m tiles (wave) into an NSC-deep ring by TMA, each stage guarded by a
-// "full" mbarrier (TMA bytes landed) and an "empty" mbarrier (all four
-// consumer warps done with it).  Consumer warps run decoupled, with no
+// A piece of a CTA's work: tile (x0, y0), window planes [zs, ze).
+struct StepSeg {
+    int x0, y0, zs, ze;
+};
+
+// The CTA's segments, in order.  Chunked launch: grid (tiles_x, tiles_y,
+// chunks), one segment per CTA.  Balanced launch: 1-D grid of G CTAs; the
+// ntiles * P tile-planes (P = z_hi - z_lo), in tile-major order with tiles
+// numbered y fastest, are split into G equal contiguous ranges, so every CTA
+// does the same work and a range may end one tile's z range and start the
+// next one's.  With y fastest, the tiles above and below (whose 2R-row halo
+// is most of the extra u reads) are walked about P - ntiles P / G planes
+// apart, so the shared halo rows are still in L2.
+struct SegCursor {
+    int64_t pos = 0, end = 0;
+    bool chunk_done = false;
+
+    OOCS_FN void init(const StepArgs &a)
+    {
+        if (a.zchunk == 0) {
+            const int64_t total = (int64_t)a.ntiles * (a.z_hi - a.z_lo);
+            pos = total * blockIdx.x / gridDim.x;
+            end = total * (blockIdx.x + 1) / gridDim.x;
+        }
+    }
+    OOCS_FN bool next(const StepArgs &a, StepSeg &s)
+    {
+        if (a.zchunk > 0) {
+            if (chunk_done)
+                return false;
+            chunk_done = true;
+            s.x0 = blockIdx.x * kTX;
+            s.y0 = blockIdx.y * kTY;
+            s.zs = a.z_lo + blockIdx.z * a.zchunk;
+            s.ze = min(s.zs + a.zchunk, a.z_hi);
+            return s.zs < s.ze;
+        }
+        if (pos >= end)
+            return false;
+        const int P = a.z_hi - a.z_lo;
+        const int64_t t = pos / P;
+        const int64_t e = min(end, (t + 1) * P);
+        s.x0 = (int)(t / a.tiles_y) * kTX;
+        s.y0 = (int)(t % a.tiles_y) * kTY;
+        s.zs = a.z_lo + (int)(pos - t * P);
+        s.ze = a.z_lo + (int)(e - t * P);
+        pos = e;
+        return true;
+    }
+};
+
+// One time step over window planes [z_lo, z_hi).  A CTA walks the z range of
+// one or more 64 x 16 tiles (segments, above), warp-specialised: warp 4 is
+// the producer, which streams u tiles (with a 4-column / R-row halo) into an
+// NSU-deep shared-memory ring and the centre fields (wave: prev, m) into an
+// NSC-deep ring by TMA, each stage guarded by a "full" mbarrier (TMA bytes
+// landed) and an "empty" mbarrier (all four consumer warps done with it);
+// ring positions come from running counts of planes, so the rings carry on
+// from one segment to the next.  Consumer warps run decoupled, with no
 // CTA-wide barrier per plane.  Consumer thread (tx, w) owns the 2 x 4 points
 // x = x0 + 2 tx + {0, 1}, y = y0 + 4 w + {0..3}; it keeps u(z-R .. z+R) of
 // them in a register queue, takes x neighbours from 64-bit shared loads and y
 // neighbours inside its four rows from the queue.  Planes outside the window
-// or grid arrive zero-filled from TMA.
+// or grid arrive zero-filled from TMA.  For R = 4, a warp whose 64 x 4 points
+// are all interior, on a plane without the source or receivers, takes a path
+// without per-point tests.
 //
 // kAdjoint and kGradient (the wave misfit's adjoint, see kernels.h) use the
 // same pipeline with three and two centre fields.
@@ -110,6 +168,7 @@ __global__ void __launch_bounds__(kStepThreads, 2)
     constexpr int NCF = centre_fields<SCHEME>();
     using C = StepCfg<R, NCF>;
     constexpr int Q = C::Q;
+    constexpr bool kFastPath = R == 4;
     extern __shared__ unsigned char smem_raw[];
     float *us = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *cs = us + C::NSU * C::kUStage;  // centre field f, stage st at cs + (f NSC + st) kCStage
@@ -119,11 +178,6 @@ __global__ void __launch_bounds__(kStepThreads, 2)
     uint64_t *cempty = cfull + C::NSC;
 
     const int tx = threadIdx.x, wid = threadIdx.y;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-    const int zs = a.z_lo + blockIdx.z * a.zchunk;
-    const int ze = min(zs + a.zchunk, a.z_hi);
-    const int pu0 = zs - R;   // first u plane of the queue
-    const int pu_end = ze + R;
 
     if (wid == 0 && tx == 0) {
         for (int i = 0; i < C::NSU; ++i) {
@@ -142,206 +196,236 @@ __global__ void __launch_bounds__(kStepThreads, 2)
     pdl_launch_dependents();
     pdl_wait_prior_grid();
 
+    SegCursor cur;
+    cur.init(a);
+    StepSeg sg;
+
     if (wid == kConsumerWarps) {
         // ------------------------------------------------ producer warp --
         if (tx != 0)
             return;
         bool good = true;
-        int u_next = pu0, c_next = zs;
-        auto put_u = [&](int p) {
-            const int st = (p - pu0) % C::NSU, n = (p - pu0) / C::NSU;
-            if (n > 0 && !mbar_wait(&uempty[st], (uint32_t)((n - 1) & 1)))
-                return false;
-            mbar_arrive_expect_tx(&ufull[st], C::kUBytes);
-            tma_load_3d(us + st * C::kUStage, &tm_cur, x0 - 4, y0 - R, p, &ufull[st]);
-            u_next = p + 1;
-            return true;
-        };
-        auto put_c = [&](int z) {
-            const int st = (z - zs) % C::NSC, n = (z - zs) / C::NSC;
-            if (n > 0 && !mbar_wait(&cempty[st], (uint32_t)((n - 1) & 1)))
-                return false;
-            mbar_arrive_expect_tx(&cfull[st], NCF * C::kCBytes);
-            tma_load_3d(cs + st * C::kCStage, &tm_prev, x0, y0, z, &cfull[st]);
-            tma_load_3d(cs + (C::NSC + st) * C::kCStage, &tm_m, x0, y0, z, &cfull[st]);
-            if constexpr (NCF == 3)
-                tma_load_3d(cs + (2 * C::NSC + st) * C::kCStage, &tm_c2, x0, y0, z, &cfull[st]);
-            c_next = z + 1;
-            return true;
-        };
-        // u planes are needed in order (queue prologue first), the c planes
-        // alongside the u plane R ahead of them
-        for (int p = pu0; good && p < pu_end; ++p) {
-            good = put_u(p);
-            const int z = p - R;
-            if (NCF > 0 && good && z >= zs && z < ze)
-                good = put_c(z);
+        uint32_t un = 0, cn = 0;  // u planes / centre-field planes issued so far
+        while (good && cur.next(a, sg)) {
+            // u planes in order (queue prologue first), the centre fields of
+            // plane z alongside the u plane R ahead of it
+            for (int p = sg.zs - R; p < sg.ze + R; ++p) {
+                const uint32_t st = un % C::NSU, n = un / C::NSU;
+                if (n > 0 && !mbar_wait(&uempty[st], (n - 1) & 1)) {
+                    good = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&ufull[st], C::kUBytes);
+                tma_load_3d(us + st * C::kUStage, &tm_cur, sg.x0 - 4, sg.y0 - R, p, &ufull[st]);
+                ++un;
+                const int z = p - R;
+                if (NCF > 0 && z >= sg.zs && z < sg.ze) {
+                    const uint32_t cst = cn % C::NSC, cnn = cn / C::NSC;
+                    if (cnn > 0 && !mbar_wait(&cempty[cst], (cnn - 1) & 1)) {
+                        good = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&cfull[cst], NCF * C::kCBytes);
+                    tma_load_3d(cs + cst * C::kCStage, &tm_prev, sg.x0, sg.y0, z, &cfull[cst]);
+                    tma_load_3d(cs + (C::NSC + cst) * C::kCStage, &tm_m, sg.x0, sg.y0, z, &cfull[cst]);
+                    if constexpr (NCF == 3)
+                        tma_load_3d(cs + (2 * C::NSC + cst) * C::kCStage, &tm_c2, sg.x0, sg.y0, z, &cfull[cst]);
+                    ++cn;
+                }
+            }
         }
         // drain: everything requested lands before the CTA may retire
-        for (int p = max(pu0, u_next - C::NSU); p < u_next; ++p)
-            mbar_wait(&ufull[(p - pu0) % C::NSU], (uint32_t)(((p - pu0) / C::NSU) & 1));
-        for (int z = max(zs, c_next - C::NSC); z < c_next; ++z)
-            mbar_wait(&cfull[(z - zs) % C::NSC], (uint32_t)(((z - zs) / C::NSC) & 1));
+        for (uint32_t i = un > (uint32_t)C::NSU ? un - C::NSU : 0; i < un; ++i)
+            mbar_wait(&ufull[i % C::NSU], (i / C::NSU) & 1);
+        for (uint32_t i = cn > (uint32_t)C::NSC ? cn - C::NSC : 0; i < cn; ++i)
+            mbar_wait(&cfull[i % C::NSC], (i / C::NSC) & 1);
         return;
     }
 
     // --------------------------------------------------- consumer warps --
-    auto u_stage = [&](int p) { return (p - pu0) % C::NSU; };
-    auto u_phase = [&](int p) { return (uint32_t)(((p - pu0) / C::NSU) & 1); };
-    auto release_u = [&](int p) {
-        __syncwarp();
-        if (tx == 0)
-            mbar_arrive(&uempty[u_stage(p)]);
-    };
     const int ucol = 4 + kVX * tx;
     auto urow = [&](int rel_row) { return (R + kRPT * wid + rel_row) * kBoxW + ucol; };
-
-    // register queue: in iteration z, q[r][i] = u(z - R + i) at row 4 wid + r
-    float2 q[kRPT][Q];
-#pragma unroll
-    for (int r = 0; r < kRPT; ++r)
-        q[r][2 * R] = make_float2(0.0f, 0.0f);
+    uint32_t ucn = 0, ccn = 0;  // u planes / centre-field planes consumed before this segment
     bool good = true;
-    for (int i = 0; i < 2 * R && good; ++i) {
-        const int p = pu0 + i;
-        good = mbar_wait(&ufull[u_stage(p)], u_phase(p));
-        if (!good)
-            break;
-        const float *P = us + u_stage(p) * C::kUStage;
+    while (good && cur.next(a, sg)) {
+        const int x0 = sg.x0, y0 = sg.y0, zs = sg.zs, ze = sg.ze;
+        const int pu0 = zs - R;  // first u plane of the queue
+        auto u_cnt = [&](int p) { return ucn + (uint32_t)(p - pu0); };
+        auto u_stage = [&](int p) { return u_cnt(p) % C::NSU; };
+        auto u_phase = [&](int p) { return (u_cnt(p) / C::NSU) & 1; };
+        auto release_u = [&](int p) {
+            __syncwarp();
+            if (tx == 0)
+                mbar_arrive(&uempty[u_stage(p)]);
+        };
+
+        // register queue: in iteration z, q[r][i] = u(z - R + i) at row 4 wid + r
+        float2 q[kRPT][Q];
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r)
+            q[r][2 * R] = make_float2(0.0f, 0.0f);
+        for (int i = 0; i < 2 * R && good; ++i) {
+            const int p = pu0 + i;
+            good = mbar_wait(&ufull[u_stage(p)], u_phase(p));
+            if (!good)
+                break;
+            const float *P = us + u_stage(p) * C::kUStage;
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) {
+#pragma unroll
+                for (int j = 0; j < 2 * R; ++j)  // shift towards 0, newest at 2R:
+                    q[r][j] = q[r][j + 1];       // ends with q[1 .. 2R] = u(zs-R .. zs+R-1)
+                q[r][2 * R] = *reinterpret_cast<const float2 *>(P + urow(r));
+            }
+            if (p < zs)  // planes before the segment are only queue inputs
+                release_u(p);
+        }
+
+        const int x = x0 + kVX * tx;  // first of the thread's two columns
+        const bool x_ok = x < a.nx;   // nx is a multiple of 4: both columns or neither
+        bool in_x[kVX];
+#pragma unroll
+        for (int c = 0; c < kVX; ++c)
+            in_x[c] = (x + c) >= R && (x + c) < a.nx - R;
+        const int wy0 = y0 + kRPT * wid;  // the warp's first row
+        bool row_ok[kRPT], in_y[kRPT];
 #pragma unroll
         for (int r = 0; r < kRPT; ++r) {
-#pragma unroll
-            for (int j = 0; j < 2 * R; ++j)  // shift towards 0, newest at 2R:
-                q[r][j] = q[r][j + 1];       // ends with q[1 .. 2R] = u(zs-R .. zs+R-1)
-            q[r][2 * R] = *reinterpret_cast<const float2 *>(P + urow(r));
+            row_ok[r] = x_ok && wy0 + r < a.ny;
+            in_y[r] = wy0 + r >= R && wy0 + r < a.ny - R;
         }
-        if (p < zs)  // planes before the chunk are only queue inputs
+        // every point of the warp's 64 x 4 block is interior in x and y
+        const bool warp_in = x0 >= R && x0 + kTX <= a.nx - R && wy0 >= R && wy0 + kRPT <= a.ny - R;
+        const bool src_in_warp =
+            a.src_x >= x0 && a.src_x < x0 + kTX && a.src_y >= wy0 && a.src_y < wy0 + kRPT;
+
+        for (int z = zs; good && z < ze; ++z) {
+            const int pn = z + R;
+            good = mbar_wait(&ufull[u_stage(pn)], u_phase(pn));
+            const uint32_t cc = ccn + (uint32_t)(z - zs);
+            const int cst = (int)(cc % C::NSC);
+            if (NCF > 0 && good)
+                good = mbar_wait(&cfull[cst], (cc / C::NSC) & 1);
+            if (!good)
+                break;
+            const float *Pn = us + u_stage(pn) * C::kUStage;
+            const float *P = us + u_stage(z) * C::kUStage;
+            const int gz = a.gz0 + z;
+            const bool z_interior = gz >= R && gz < a.nz - R;
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) {
+#pragma unroll
+                for (int j = 0; j < 2 * R; ++j)
+                    q[r][j] = q[r][j + 1];
+                q[r][2 * R] = *reinterpret_cast<const float2 *>(Pn + urow(r));
+            }
+            // y neighbours outside the thread's rows: R rows above, R below
+            float2 above[R], below[R];
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                above[d - 1] = *reinterpret_cast<const float2 *>(P + urow(-d));
+                below[d - 1] = *reinterpret_cast<const float2 *>(P + urow(kRPT - 1 + d));
+            }
+            [[maybe_unused]] const bool rcv_plane = SCHEME == kAdjoint && a.res != nullptr && gz == a.zr;
+            auto rows = [&](auto FAST) {
+                constexpr bool kFast = decltype(FAST)::value;
+#pragma unroll
+                for (int r = 0; r < kRPT; ++r) {
+                    if (!kFast && !row_ok[r])
+                        continue;
+                    float xv[10];  // columns x-4 .. x+5 of row r (five 64-bit loads)
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        const float2 v = *reinterpret_cast<const float2 *>(P + urow(r) - 4 + 2 * i);
+                        xv[2 * i] = v.x;
+                        xv[2 * i + 1] = v.y;
+                    }
+                    const float2 uc = q[r][R];
+                    const int y = wy0 + r;
+                    float2 cv[NCF > 0 ? NCF : 1];
+                    if constexpr (NCF > 0) {
+                        const int ci = cst * C::kCStage + (kRPT * wid + r) * kTX + kVX * tx;
+#pragma unroll
+                        for (int f = 0; f < NCF; ++f)
+                            cv[f] = *reinterpret_cast<const float2 *>(cs + f * C::NSC * C::kCStage + ci);
+                    }
+                    [[maybe_unused]] float2 rv = make_float2(0.0f, 0.0f);
+                    if constexpr (SCHEME == kAdjoint && !kFast) {
+                        if (rcv_plane)
+                            rv = __ldg(reinterpret_cast<const float2 *>(a.res + (int64_t)y * a.nx + x));
+                    }
+                    float res[kVX];
+                    [[maybe_unused]] float res2[kVX];
+#pragma unroll
+                    for (int c = 0; c < kVX; ++c) {
+                        const float u = c ? uc.y : uc.x;
+                        // shell: heat / wave keep u (Dirichlet), the adjoint is
+                        // zero there, the gradient keeps its value
+                        if constexpr (SCHEME == kAdjoint) {
+                            res[c] = 0.0f;
+                            res2[c] = 0.0f;
+                        } else if constexpr (SCHEME == kGradient) {
+                            res[c] = c ? cv[0].y : cv[0].x;
+                        } else {
+                            res[c] = u;
+                        }
+                        if (kFast || (z_interior && in_y[r] && in_x[c])) {
+                            float s[R + 1];
+                            s[0] = 0.0f;
+#pragma unroll
+                            for (int d = 1; d <= R; ++d) {
+                                const float2 ym = (r - d >= 0) ? q[(r - d) >= 0 ? r - d : 0][R]
+                                                               : above[(d - r - 1) >= 0 ? d - r - 1 : 0];
+                                const float2 yp = (r + d < kRPT) ? q[(r + d) < kRPT ? r + d : 0][R]
+                                                                 : below[(r + d - kRPT) >= 0 ? r + d - kRPT : 0];
+                                const float2 zm = q[r][R - d];
+                                const float2 zp = q[r][R + d];
+                                s[d] = nbr_sum(xv[4 + c - d], xv[4 + c + d], c ? ym.y : ym.x, c ? yp.y : yp.x,
+                                               c ? zm.y : zm.x, c ? zp.y : zp.x);
+                            }
+                            const float L = star_L<R>(a.c, u, s);
+                            [[maybe_unused]] const bool at_src =
+                                !kFast && (x + c == a.src_x && y == a.src_y && z == a.src_zw);
+                            if constexpr (SCHEME == kHeat) {
+                                res[c] = L;
+                            } else if constexpr (SCHEME == kWave) {
+                                res[c] = wave_update(L, u, c ? cv[0].y : cv[0].x, c ? cv[1].y : cv[1].x, at_src,
+                                                     a.w);
+                            } else if constexpr (SCHEME == kAdjoint) {
+                                res[c] = adjoint_update(L, c ? cv[2].y : cv[2].x, c ? cv[0].y : cv[0].x,
+                                                        !kFast && rcv_plane, c ? rv.y : rv.x);
+                                res2[c] = fmul_rn(c ? cv[1].y : cv[1].x, res[c]);
+                            } else {
+                                res[c] = gradient_update(L, c ? cv[1].y : cv[1].x, c ? cv[0].y : cv[0].x, at_src,
+                                                         a.w);
+                            }
+                        }
+                    }
+                    const int64_t o = (int64_t)z * a.plane + (int64_t)y * a.nx + x;
+                    *reinterpret_cast<float2 *>(a.out + o) = make_float2(res[0], res[1]);
+                    if constexpr (SCHEME == kAdjoint)
+                        *reinterpret_cast<float2 *>(a.out2 + o) = make_float2(res2[0], res2[1]);
+                }
+            };
+            if (kFastPath && warp_in && z_interior && !(src_in_warp && z == a.src_zw) && !rcv_plane)
+                rows(std::true_type{});
+            else
+                rows(std::false_type{});
+            // plane z (xy neighbours) and its centre-field stage are done
+            __syncwarp();
+            if (tx == 0) {
+                mbar_arrive(&uempty[u_stage(z)]);
+                if (NCF > 0)
+                    mbar_arrive(&cempty[cst]);
+            }
+        }
+        if (!good)
+            break;
+        // the last R planes only fed the queue
+        for (int p = ze; p < ze + R; ++p)
             release_u(p);
-    }
-
-    const int x = x0 + kVX * tx;  // first of the thread's two columns
-    const bool x_ok = x < a.nx;   // nx is a multiple of 4: both columns or neither
-    bool in_x[kVX];
-#pragma unroll
-    for (int c = 0; c < kVX; ++c)
-        in_x[c] = (x + c) >= R && (x + c) < a.nx - R;
-    bool row_ok[kRPT], in_y[kRPT];
-#pragma unroll
-    for (int r = 0; r < kRPT; ++r) {
-        const int y = y0 + kRPT * wid + r;
-        row_ok[r] = x_ok && y < a.ny;
-        in_y[r] = y >= R && y < a.ny - R;
-    }
-
-    for (int z = zs; good && z < ze; ++z) {
-        const int pn = z + R;
-        good = mbar_wait(&ufull[u_stage(pn)], u_phase(pn));
-        const int cst = (z - zs) % C::NSC;
-        if (NCF > 0 && good)
-            good = mbar_wait(&cfull[cst], (uint32_t)(((z - zs) / C::NSC) & 1));
-        if (!good)
-            break;
-        const float *Pn = us + u_stage(pn) * C::kUStage;
-        const float *P = us + u_stage(z) * C::kUStage;
-        const int gz = a.gz0 + z;
-        const bool z_interior = gz >= R && gz < a.nz - R;
-#pragma unroll
-        for (int r = 0; r < kRPT; ++r) {
-#pragma unroll
-            for (int j = 0; j < 2 * R; ++j)
-                q[r][j] = q[r][j + 1];
-            q[r][2 * R] = *reinterpret_cast<const float2 *>(Pn + urow(r));
-        }
-        // y neighbours outside the thread's rows: R rows above, R below
-        float2 above[R], below[R];
-#pragma unroll
-        for (int d = 1; d <= R; ++d) {
-            above[d - 1] = *reinterpret_cast<const float2 *>(P + urow(-d));
-            below[d - 1] = *reinterpret_cast<const float2 *>(P + urow(kRPT - 1 + d));
-        }
-#pragma unroll
-        for (int r = 0; r < kRPT; ++r) {
-            if (!row_ok[r])
-                continue;
-            float xv[10];  // columns x-4 .. x+5 of row r (five 64-bit loads)
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                const float2 v = *reinterpret_cast<const float2 *>(P + urow(r) - 4 + 2 * i);
-                xv[2 * i] = v.x;
-                xv[2 * i + 1] = v.y;
-            }
-            const float2 uc = q[r][R];
-            const int y = y0 + kRPT * wid + r;
-            float2 cv[NCF > 0 ? NCF : 1];
-            if constexpr (NCF > 0) {
-                const int ci = cst * C::kCStage + (kRPT * wid + r) * kTX + kVX * tx;
-#pragma unroll
-                for (int f = 0; f < NCF; ++f)
-                    cv[f] = *reinterpret_cast<const float2 *>(cs + f * C::NSC * C::kCStage + ci);
-            }
-            [[maybe_unused]] float2 rv = make_float2(0.0f, 0.0f);
-            [[maybe_unused]] bool at_rcv = false;
-            if constexpr (SCHEME == kAdjoint) {
-                at_rcv = a.res != nullptr && gz == a.zr;
-                if (at_rcv)
-                    rv = __ldg(reinterpret_cast<const float2 *>(a.res + (int64_t)y * a.nx + x));
-            }
-            float res[kVX];
-            [[maybe_unused]] float res2[kVX];
-#pragma unroll
-            for (int c = 0; c < kVX; ++c) {
-                const float u = c ? uc.y : uc.x;
-                // shell: heat / wave keep u (Dirichlet), the adjoint is zero
-                // there, the gradient keeps its value
-                if constexpr (SCHEME == kAdjoint) {
-                    res[c] = 0.0f;
-                    res2[c] = 0.0f;
-                } else if constexpr (SCHEME == kGradient) {
-                    res[c] = c ? cv[0].y : cv[0].x;
-                } else {
-                    res[c] = u;
-                }
-                if (z_interior && in_y[r] && in_x[c]) {
-                    float s[R + 1];
-                    s[0] = 0.0f;
-#pragma unroll
-                    for (int d = 1; d <= R; ++d) {
-                        const float2 ym = (r - d >= 0) ? q[(r - d) >= 0 ? r - d : 0][R]
-                                                       : above[(d - r - 1) >= 0 ? d - r - 1 : 0];
-                        const float2 yp = (r + d < kRPT) ? q[(r + d) < kRPT ? r + d : 0][R]
-                                                         : below[(r + d - kRPT) >= 0 ? r + d - kRPT : 0];
-                        const float2 zm = q[r][R - d];
-                        const float2 zp = q[r][R + d];
-                        s[d] = nbr_sum(xv[4 + c - d], xv[4 + c + d], c ? ym.y : ym.x, c ? yp.y : yp.x,
-                                       c ? zm.y : zm.x, c ? zp.y : zp.x);
-                    }
-                    const float L = star_L<R>(a.c, u, s);
-                    [[maybe_unused]] const bool at_src = (x + c == a.src_x && y == a.src_y && z == a.src_zw);
-                    if constexpr (SCHEME == kHeat) {
-                        res[c] = L;
-                    } else if constexpr (SCHEME == kWave) {
-                        res[c] = wave_update(L, u, c ? cv[0].y : cv[0].x, c ? cv[1].y : cv[1].x, at_src, a.w);
-                    } else if constexpr (SCHEME == kAdjoint) {
-                        res[c] = adjoint_update(L, c ? cv[2].y : cv[2].x, c ? cv[0].y : cv[0].x, at_rcv,
-                                                c ? rv.y : rv.x);
-                        res2[c] = fmul_rn(c ? cv[1].y : cv[1].x, res[c]);
-                    } else {
-                        res[c] = gradient_update(L, c ? cv[1].y : cv[1].x, c ? cv[0].y : cv[0].x, at_src, a.w);
-                    }
-                }
-            }
-            const int64_t o = (int64_t)z * a.plane + (int64_t)y * a.nx + x;
-            *reinterpret_cast<float2 *>(a.out + o) = make_float2(res[0], res[1]);
-            if constexpr (SCHEME == kAdjoint)
-                *reinterpret_cast<float2 *>(a.out2 + o) = make_float2(res2[0], res2[1]);
-        }
-        // plane z (xy neighbours) and its prev / m stage are done
-        __syncwarp();
-        if (tx == 0) {
-            mbar_arrive(&uempty[u_stage(z)]);
-            if (NCF > 0)
-                mbar_arrive(&cempty[cst]);
-        }
+        ucn += (uint32_t)(ze - zs + 2 * R);
+        ccn += NCF > 0 ? (uint32_t)(ze - zs) : 0u;
     }
 }
 
@@ -432,6 +516,8 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
     const int tiles_y = (int)((L.ny + kTY - 1) / kTY);
     const int tiles = tiles_x * tiles_y;
     const int nplanes = a.z_hi - a.z_lo;
+    a.tiles_y = tiles_y;
+    a.ntiles = tiles;
     // z chunks: keep >= 12 planes per CTA and choose the count whose last wave
     // of CTAs (sms x resident per wave) is fullest
     const int slots = dev_info().sms * resident;
@@ -449,9 +535,17 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
             best = nc;
         }
     }
-    a.zchunk = (nplanes + best - 1) / best;
-    const int nchunks = (nplanes + a.zchunk - 1) / a.zchunk;
-    dim3 grid(tiles_x, tiles_y, nchunks);
+    dim3 grid;
+    if (best_eff >= 0.9) {
+        a.zchunk = (nplanes + best - 1) / best;
+        grid = dim3(tiles_x, tiles_y, (nplanes + a.zchunk - 1) / a.zchunk);
+    } else {
+        // short windows on a plane whose tiles do not fill the SMs evenly
+        // (e.g. 256 tiles on 304 slots): one wave of equal tile-plane ranges
+        a.zchunk = 0;
+        const int64_t total = (int64_t)tiles * nplanes;
+        grid = dim3((unsigned)std::min<int64_t>(slots, (total + 15) / 16), 1, 1);
+    }
     dim3 block(32, kConsumerWarps + 1, 1);
     return launch_pdl(kern, grid, block, smem, s, mc, mp, mm, m2, a);
 }

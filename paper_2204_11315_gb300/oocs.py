@@ -40,20 +40,21 @@ class oocs_desc(ctypes.Structure):
                 ("coef", ctypes.c_float * (MAX_RADIUS + 1)),
                 ("device_budget", ctypes.c_uint64), ("rate_bits", ctypes.c_int32),
                 ("temporal_depth", ctypes.c_int32), ("slab_planes", ctypes.c_int32),
-                ("working_buffers", ctypes.c_int32)]
+                ("working_buffers", ctypes.c_int32), ("readonly_resident", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class oocs_plan(ctypes.Structure):
     _fields_ = [("slab_planes", ctypes.c_int32), ("temporal_depth", ctypes.c_int32),
                 ("halo_planes", ctypes.c_int32), ("num_slabs", ctypes.c_int32),
                 ("window_planes", ctypes.c_int32), ("fields_in", ctypes.c_int32),
-                ("fields_out", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("fields_out", ctypes.c_int32), ("readonly_resident", ctypes.c_int32),
                 ("layer_bytes", ctypes.c_uint64), ("host_store_bytes", ctypes.c_uint64),
                 ("workspace_bytes", ctypes.c_uint64), ("workspace_swb_bytes", ctypes.c_uint64),
                 ("workspace_classic_bytes", ctypes.c_uint64)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class oocs_kernel_stats(ctypes.Structure):
@@ -172,7 +173,7 @@ def _check(status: int, ctx=None):
 
 
 def make_desc(nx, ny, nz, scheme, coef, device_budget, rate_bits=0, temporal_depth=0,
-              slab_planes=0, working_buffers=OOCS_SWB, radius=None) -> oocs_desc:
+              slab_planes=0, working_buffers=OOCS_SWB, radius=None, readonly_resident=0) -> oocs_desc:
     coef = [float(c) for c in coef]
     d = oocs_desc()
     d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
@@ -185,6 +186,7 @@ def make_desc(nx, ny, nz, scheme, coef, device_budget, rate_bits=0, temporal_dep
     d.temporal_depth = int(temporal_depth)
     d.slab_planes = int(slab_planes)
     d.working_buffers = int(working_buffers)
+    d.readonly_resident = int(readonly_resident)
     return d
 
 

@@ -18,10 +18,11 @@ def heat_desc(P, shape, rate=0, k=1, T=32, wb=1, alpha=0.1, budget=8 << 30):
                        rate_bits=rate, temporal_depth=k, slab_planes=T, working_buffers=wb)
 
 
-def wave_desc(P, shape, rate=0, k=4, T=64, wb=1, budget=8 << 30):
+def wave_desc(P, shape, rate=0, k=4, T=64, wb=1, budget=8 << 30, ro=0):
     nz, ny, nx = shape
     return P.make_desc(nx, ny, nz, P.OOCS_WAVE, synthetic.wave_star_coef(), budget,
-                       rate_bits=rate, temporal_depth=k, slab_planes=T, working_buffers=wb)
+                       rate_bits=rate, temporal_depth=k, slab_planes=T, working_buffers=wb,
+                       readonly_resident=ro)
 
 
 def incore(P, desc, u0, nsteps, up0=None, m=None, src=None, w=None, t0=0):

@@ -74,6 +74,27 @@ def test_plan_wave_workload(P):
     assert p.workspace_swb_bytes == 3 * buf + 3 * 3 * slot_in + 3 * 2 * slot_out
 
 
+def test_plan_wave_resident_model(P):
+    """readonly_resident: m leaves the staging slots and the window buffers and
+    takes one FP32 grid in the workspace; heat ignores the flag."""
+    kw = dict(rate_bits=16, temporal_depth=4, slab_planes=64)
+    coef = synthetic.wave_star_coef()
+    p0 = P.oocs_query(P.make_desc(512, 512, 512, P.OOCS_WAVE, coef, 4 << 30, **kw))
+    p1 = P.oocs_query(P.make_desc(512, 512, 512, P.OOCS_WAVE, coef, 4 << 30, readonly_resident=1, **kw))
+    assert (p1.fields_in, p1.fields_out, p1.readonly_resident) == (2, 2, 1)
+    buf = 96 * 512 * 512 * 4
+    slot_in = (64 + 16) // 4 * p1.layer_bytes
+    grid = 512 ** 3 * 4
+    assert p1.workspace_swb_bytes == p0.workspace_swb_bytes - buf - 3 * slot_in + grid
+    assert p1.workspace_classic_bytes == p0.workspace_classic_bytes - 3 * buf - 3 * slot_in + grid
+    assert p1.workspace_bytes <= 4 << 30
+    h = P.oocs_query(P.make_desc(128, 128, 128, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), 1 << 30,
+                                 rate_bits=16, readonly_resident=1))
+    assert (h.fields_in, h.readonly_resident) == (1, 0)
+    with pytest.raises(P.OOCSError):
+        P.oocs_query(P.make_desc(128, 128, 128, P.OOCS_WAVE, coef, 1 << 30, readonly_resident=2))
+
+
 def test_auto_slab_thickness_from_budget(P):
     # the budget of the T = 32 plan makes the planner pick T = 32 (4 slabs)
     need = P.oocs_query(_c1(P)).workspace_bytes

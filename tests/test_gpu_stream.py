@@ -131,12 +131,32 @@ def test_wave_compressed_within_tolerance(P, orc, rate):
     assert rel_l2(gup, rup) <= synthetic.TOL_COMPRESSED[rate]
 
 
-def test_wave_full_size_uncompressed_bitexact(P):
-    """The benchmark workload's grid and plan (512^3, 8 slabs of 64, k = 4), uncompressed."""
+@pytest.mark.parametrize("rate,wb", [(0, 1), (16, 1), (12, 3)])
+def test_wave_resident_model_bitexact(P, rate, wb):
+    """readonly_resident keeps m on the device (decoded once): the stores after
+    the run are byte-identical to streaming m with every visit, and m crosses
+    the link once instead of once per sweep."""
+    shape = (128, 72, 40)
+    steps = 10
+    m, w, src, z = _wave_inputs(shape, steps)
+    runs = [streamed(P, wave_desc(P, shape, rate=rate, k=4, T=32, wb=wb, ro=ro), z, steps, up0=z, m=m,
+                     src=src, w=w) for ro in (0, 1)]
+    (_, _, st0, _, p0), (_, _, st1, stats1, p1) = runs
+    assert np.array_equal(st0[0], st1[0]) and np.array_equal(st0[1], st1[1])
+    assert (p0.fields_in, p0.readonly_resident) == (3, 0)
+    assert (p1.fields_in, p1.readonly_resident) == (2, 1)
+    passes = -(-steps // 4)
+    assert stats1["h2d_bytes"] == (2 * passes + 1) * p1.host_store_bytes
+
+
+@pytest.mark.parametrize("ro", [0, 1])
+def test_wave_full_size_uncompressed_bitexact(P, ro):
+    """The benchmark workload's grid and plan (512^3, 8 slabs of 64, k = 4), uncompressed,
+    with m streamed or resident."""
     shape = (512, 512, 512)
     steps = 12
     m, w, src, z = _wave_inputs(shape, steps)
-    desc = wave_desc(P, shape, rate=0, k=4, T=64, budget=4 << 30)
+    desc = wave_desc(P, shape, rate=0, k=4, T=64, budget=4 << 30, ro=ro)
     ru, rup = incore(P, desc, z, steps, up0=z, m=m, src=src, w=w)
     gu, gup, _, _, plan = streamed(P, desc, z, steps, up0=z, m=m, src=src, w=w)
     assert plan.num_slabs == 8 and plan.workspace_bytes <= 4 << 30

@@ -125,13 +125,14 @@ CASES = [
 ]
 
 
-def _desc(P, scheme, shape, rate, k, T, wb):
+def _desc(P, scheme, shape, rate, k, T, wb, ro=0):
     nz, ny, nx = shape
     if scheme == "heat":
         return P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), 8 << 30,
                            rate_bits=rate, temporal_depth=k, slab_planes=T, working_buffers=wb)
     return P.make_desc(nx, ny, nz, P.OOCS_WAVE, synthetic.wave_star_coef(), 8 << 30,
-                       rate_bits=rate, temporal_depth=k, slab_planes=T, working_buffers=wb)
+                       rate_bits=rate, temporal_depth=k, slab_planes=T, working_buffers=wb,
+                       readonly_resident=ro)
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -154,6 +155,19 @@ def test_schedule_is_race_free(P, case):
         expect = None if sweep == 0 else sweep - 1
         got = {None if w is None else w // plan.num_slabs for w in writers}
         assert got == {expect}, (visit, got)
+
+
+@pytest.mark.parametrize("wb", [1, 3])
+def test_schedule_with_resident_model(P, wb):
+    """m kept on the device: only U and U_PREV are copied per visit; the
+    schedule stays race-free and every streamed layer still crosses once."""
+    desc = _desc(P, "wave", (128, 72, 40), 16, 4, 32, wb, ro=1)
+    trace = P.oocs_trace_schedule(desc, [10])
+    assert check(trace, swb=(wb == 1)) is None
+    fields = {f for o in trace if o["op"] == "H2D" for (k, f, lo, hi, w) in o["access"] if k == "HOST"}
+    assert fields == {0, 1}
+    h2d_layers = sum(o["access"][0][3] - o["access"][0][2] for o in trace if o["op"] == "H2D")
+    assert h2d_layers == 3 * (128 // 4)
 
 
 @pytest.mark.parametrize("drop", ["d2h", "decoded", "wrel", "h2d"])
