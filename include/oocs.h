@@ -338,6 +338,57 @@ typedef struct {
 oocs_status oocs_trace_schedule(const oocs_desc *desc, const int32_t *nsteps, int32_t ncalls,
                                 oocs_trace_op *ops, int64_t capacity, int64_t *count);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent problems (any mix of HEAT and WAVE descs, each
+ * with its own grid, T, k and rate, all OOCS_SWB) advanced through ONE
+ * Algorithm-1 pipeline: one device workspace whose working buffer and staging
+ * slots are sized for the largest problem (plus one resident model per WAVE
+ * problem with readonly_resident), the same three streams, events and slab
+ * visit sequence.  A batch step runs rounds in which every unfinished problem
+ * sweeps its slabs once (k of its own steps), so copies of one problem's
+ * visits overlap the kernels of another's.  Results are those of running each
+ * problem alone with the same desc.  The paper has no batching; this is the
+ * serving pattern built on its pipeline.
+ * ------------------------------------------------------------------------- */
+typedef struct oocs_batch oocs_batch;
+
+/* Device workspace bytes a batch of the n descs needs. */
+oocs_status oocs_batch_query(const oocs_desc *descs, int32_t n, uint64_t *workspace_bytes);
+
+/* Create a batch on the current device: descs[0..n-1] (copied), a 256-byte
+ * aligned device workspace of >= oocs_batch_query bytes and three distinct
+ * streams, all owned by the caller and kept alive until oocs_batch_destroy.
+ * Each problem is a context (oocs_batch_context) used with oocs_bind_field,
+ * oocs_set_source, oocs_compress, oocs_decompress, oocs_set_time,
+ * oocs_get_stats, oocs_set_profiling and oocs_step (that problem alone, through
+ * the batch's pipeline); oocs_destroy refuses it.                          */
+oocs_status oocs_batch_create(const oocs_desc *descs, int32_t n, void *workspace, uint64_t workspace_bytes,
+                              void *const streams[3], oocs_batch **out);
+oocs_status oocs_batch_context(oocs_batch *batch, int32_t i, oocs_ctx **ctx);
+
+/* Advance every problem by nsteps (asynchronous; oocs_batch_synchronize). */
+oocs_status oocs_batch_step(oocs_batch *batch, int32_t nsteps);
+
+/* Capture one oocs_batch_step(nsteps) as a CUDA graph (nothing runs; the
+ * problems' time indices and stats are unchanged), and replay it with
+ * oocs_batch_launch, which advances every problem by nsteps per call with one
+ * graph launch instead of thousands of launches and copies.  A replay always
+ * follows all previously enqueued work.  OOCS_ERR_UNSUPPORTED if a problem has
+ * a source with amplitudes (they are kernel arguments of the captured steps);
+ * OOCS_ERR_STATE while profiling is on.  A new capture replaces the old one. */
+oocs_status oocs_batch_capture(oocs_batch *batch, int32_t nsteps);
+oocs_status oocs_batch_launch(oocs_batch *batch);
+
+/* Wait for everything enqueued on the batch (timeout_ns = 0: no limit). */
+oocs_status oocs_batch_synchronize(oocs_batch *batch, uint64_t timeout_ns);
+oocs_status oocs_batch_destroy(oocs_batch *batch);
+
+/* oocs_trace_schedule for a batch: ncalls successive oocs_batch_step calls.
+ * Host field ids are 3 i + field for problem i; d2h event ids are unique per
+ * problem and slab.  No GPU is touched.                                    */
+oocs_status oocs_batch_trace_schedule(const oocs_desc *descs, int32_t n, const int32_t *nsteps, int32_t ncalls,
+                                      oocs_trace_op *ops, int64_t capacity, int64_t *count);
+
 /* Library version string. */
 const char *oocs_version(void);
 

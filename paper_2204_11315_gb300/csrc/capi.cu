@@ -260,6 +260,8 @@ oocs_status plan_impl(const oocs_desc *d, oocs_plan *p, std::string &err)
 
 void oocs::set_last_error(const std::string &msg) { g_last_error = msg; }
 
+struct oocs_batch;
+
 struct oocs_ctx {
     oocs_desc d;
     oocs_plan p;
@@ -300,10 +302,39 @@ struct oocs_ctx {
     oocs_status sticky = OOCS_OK;
     std::string err = "no error";
 
+    // member of a batch (oocs_batch_create): the workspace, the three streams,
+    // the Algorithm-1 events and the visit counter belong to the batch
+    oocs_batch *batch = nullptr;
+    int host_base = 0;  // trace: host field ids of this problem start here
+    int d2h_base = 0;   // trace: d2h event ids of this problem start here
+
     float *wbuf(int wb, int b) const { return reinterpret_cast<float *>(ws + L.w_off[wb][b]); }
     char *in_slot(int q, int f) const { return ws + L.in_off[q][f]; }
     char *out_slot(int q, int f) const { return ws + L.out_off[q][f]; }
     float *ro_m() const { return reinterpret_cast<float *>(ws + L.ro_off); }
+};
+
+// A batch of independent problems advanced through one Algorithm-1 pipeline:
+// one workspace (every region sized for the largest problem, so visits of
+// different problems use the same staging slots and working buffer), three
+// streams, one set of events and one visit counter.
+struct oocs_batch {
+    std::vector<oocs_ctx *> ctx;
+    char *ws = nullptr;
+    cudaStream_t st[3] = {};
+    cudaEvent_t ev_decoded[3] = {}, ev_h2d[3] = {}, ev_wrel[3] = {}, ev_join[3] = {};
+    uint64_t g = 0;
+    std::vector<oocs_trace_op> *trace = nullptr;
+    // CUDA graph of one oocs_batch_step (oocs_batch_capture / oocs_batch_launch)
+    bool capturing = false;
+    std::vector<cudaEvent_t> cap_recorded;  // events recorded since the capture began
+    cudaGraphExec_t exec = nullptr;
+    int32_t graph_steps = 0;
+    std::vector<oocs_stats> graph_delta;  // per problem: what one replay enqueues
+    bool recorded_in_capture(cudaEvent_t e) const
+    {
+        return std::find(cap_recorded.begin(), cap_recorded.end(), e) != cap_recorded.end();
+    }
 };
 
 namespace {
@@ -373,7 +404,7 @@ enum : int { kEvDecoded = 100, kEvH2D = 200, kEvWrel = 300, kEvJoin = 400, kEvT0
 cudaEvent_t event_of(oocs_ctx *c, int id)
 {
     if (id >= kEvD2H)
-        return c->ev_d2h[id - kEvD2H];
+        return c->ev_d2h[id - kEvD2H - c->d2h_base];
     if (id == kEvT0)
         return c->ev_t0;
     if (id == kEvT1)
@@ -419,7 +450,13 @@ oocs_status sched_wait(oocs_ctx *c, int si, int ev)
         trace_push(c, OOCS_OP_WAIT, si, ev, -1, {});
         return OOCS_OK;
     }
-    CU(c, cudaStreamWaitEvent(c->st[si], event_of(c, ev), 0));
+    cudaEvent_t e = event_of(c, ev);
+    // inside a graph capture, an event last recorded before the capture began
+    // belongs to work that a replay always follows (oocs_batch_launch joins
+    // the streams first): its wait is dropped
+    if (c->batch && c->batch->capturing && !c->batch->recorded_in_capture(e))
+        return OOCS_OK;
+    CU(c, cudaStreamWaitEvent(c->st[si], e, 0));
     return OOCS_OK;
 }
 
@@ -429,7 +466,10 @@ oocs_status sched_record(oocs_ctx *c, int si, int ev)
         trace_push(c, OOCS_OP_RECORD, si, ev, -1, {});
         return OOCS_OK;
     }
-    CU(c, cudaEventRecord(event_of(c, ev), c->st[si]));
+    cudaEvent_t e = event_of(c, ev);
+    if (c->batch && c->batch->capturing)
+        c->batch->cap_recorded.push_back(e);
+    CU(c, cudaEventRecord(e, c->st[si]));
     return OOCS_OK;
 }
 
@@ -604,13 +644,13 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     // 2. host layers [n0, n1) were last written by slabs s and s+1 of the previous sweep
     for (int ss = s; ss <= s + 1 && ss < v.S; ++ss)
         if (c->d2h_recorded[ss])
-            SCHED(sched_wait(c, q, kEvD2H + ss));
+            SCHED(sched_wait(c, q, kEvD2H + c->d2h_base + ss));
     // 3. H2D of the new layers of every streamed field
     if (c->trace) {
         if (n1 > n0) {
             oocs_trace_access a[4] = {acc(OOCS_RES_IN_SLOT, q, n0 / 4, n1 / 4, true)};
             for (int f = 0; f < v.fin_stream; ++f)
-                a[1 + f] = acc(OOCS_RES_HOST, in_field_id(c, f), n0 / 4, n1 / 4, false);
+                a[1 + f] = acc(OOCS_RES_HOST, c->host_base + in_field_id(c, f), n0 / 4, n1 / 4, false);
             trace_push(c, OOCS_OP_H2D, q, -1, (int64_t)g, {a[0], a[1]});
             for (int f = 1; f < v.fin_stream; ++f)
                 c->trace->back().access[c->trace->back().naccess++] = a[1 + f];
@@ -779,9 +819,11 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     // 8. D2H into the host store, in place
     if (c->trace) {
         trace_push(c, OOCS_OP_D2H, q, -1, (int64_t)g,
-                   {acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, false), acc(OOCS_RES_HOST, 0, z0 / 4, z1 / 4, true)});
+                   {acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, false),
+                    acc(OOCS_RES_HOST, c->host_base, z0 / 4, z1 / 4, true)});
         if (v.fout == 2)
-            c->trace->back().access[c->trace->back().naccess++] = acc(OOCS_RES_HOST, 1, z0 / 4, z1 / 4, true);
+            c->trace->back().access[c->trace->back().naccess++] =
+                acc(OOCS_RES_HOST, c->host_base + 1, z0 / 4, z1 / 4, true);
     }
     for (int f = 0; f < v.fout; ++f) {
         const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
@@ -790,7 +832,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
                                   bytes, cudaMemcpyDeviceToHost, st));
         c->stats.d2h_bytes += bytes;
     }
-    SCHED(sched_record(c, q, kEvD2H + s));
+    SCHED(sched_record(c, q, kEvD2H + c->d2h_base + s));
     c->d2h_recorded[s] = 1;
     c->g++;
     c->stats.slabs_done++;
@@ -1002,6 +1044,11 @@ oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
             return fail(ctx, OOCS_ERR_STATE, "all fields of the scheme must be bound before oocs_step");
     if (nsteps == 0)
         return OOCS_OK;
+    if (ctx->batch) {  // one problem of a batch through the batch's pipeline
+        if (ctx->batch->capturing)
+            return fail(ctx, OOCS_ERR_STATE, "the batch is capturing a graph");
+        ctx->g = ctx->batch->g;
+    }
     s = join_streams(ctx);
     if (s != OOCS_OK)
         return s;
@@ -1036,6 +1083,8 @@ oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
     s = sched_record(ctx, 0, kEvT1);
     if (s != OOCS_OK)
         return s;
+    if (ctx->batch)
+        ctx->batch->g = ctx->g;
     ctx->timing_pending = !ctx->trace;
     return OOCS_OK;
 }
@@ -1156,24 +1205,23 @@ const char *oocs_last_error(const oocs_ctx *ctx)
     return ctx ? ctx->err.c_str() : g_last_error.c_str();
 }
 
-oocs_status oocs_destroy(oocs_ctx *ctx)
+static void destroy_ctx(oocs_ctx *ctx)
 {
-    if (!ctx)
-        return OOCS_OK;
     for (int i = 0; i < 3; ++i)
-        if (ctx->st[i])
+        if (ctx->st[i] && !ctx->trace)
             cudaStreamSynchronize(ctx->st[i]);
     auto kill = [](cudaEvent_t &e) {
         if (e)
             cudaEventDestroy(e);
         e = nullptr;
     };
-    for (int i = 0; i < 3; ++i) {
-        kill(ctx->ev_decoded[i]);
-        kill(ctx->ev_h2d[i]);
-        kill(ctx->ev_wrel[i]);
-        kill(ctx->ev_join[i]);
-    }
+    if (!ctx->batch)  // a batch owns the shared pipeline events
+        for (int i = 0; i < 3; ++i) {
+            kill(ctx->ev_decoded[i]);
+            kill(ctx->ev_h2d[i]);
+            kill(ctx->ev_wrel[i]);
+            kill(ctx->ev_join[i]);
+        }
     for (auto &e : ctx->ev_d2h)
         kill(e);
     for (auto &e : ctx->ev_pool)
@@ -1181,6 +1229,15 @@ oocs_status oocs_destroy(oocs_ctx *ctx)
     kill(ctx->ev_t0);
     kill(ctx->ev_t1);
     delete ctx;
+}
+
+oocs_status oocs_destroy(oocs_ctx *ctx)
+{
+    if (!ctx)
+        return OOCS_OK;
+    if (ctx->batch)
+        return fail(ctx, OOCS_ERR_STATE, "this context belongs to a batch (oocs_batch_destroy)");
+    destroy_ctx(ctx);
     return OOCS_OK;
 }
 
@@ -1290,6 +1347,507 @@ oocs_status oocs_decode_device(const void *blocks, int64_t nx, int64_t ny, int64
                                          static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess)
         return fail(nullptr, OOCS_ERR_CUDA, std::string("decode: ") + cudaGetErrorString(e));
+    return OOCS_OK;
+}
+
+}  // extern "C"
+
+// ============================================================ batches ======
+
+namespace {
+
+// Shared layout of a batch: every region sized for the largest problem (so
+// all problems' visits use the same working buffer and staging slots), then
+// one resident FP32 model per problem that keeps it on the device.
+Layout batch_layout(const std::vector<oocs_desc> &d, const std::vector<Derived> &v, std::vector<uint64_t> &ro_off,
+                    std::vector<uint64_t> &ro_bytes)
+{
+    Layout L;
+    memset(&L, 0, sizeof(L));
+    L.nwb = 1;
+    int fin = 0, fout = 0;
+    for (size_t i = 0; i < d.size(); ++i) {
+        const Layout Li = layout_for(d[i], v[i], 1);
+        L.nbuf = std::max(L.nbuf, Li.nbuf);
+        L.buf_bytes = std::max(L.buf_bytes, Li.buf_bytes);
+        L.in_slot_bytes = std::max(L.in_slot_bytes, Li.in_slot_bytes);
+        L.out_slot_bytes = std::max(L.out_slot_bytes, Li.out_slot_bytes);
+        fin = std::max(fin, v[i].fin_stream);
+        fout = std::max(fout, v[i].fout);
+    }
+    uint64_t off = 0;
+    for (int b = 0; b < L.nbuf; ++b) {
+        L.w_off[0][b] = off;
+        off += L.buf_bytes;
+    }
+    for (int q = 0; q < 3; ++q)
+        for (int f = 0; f < fin; ++f) {
+            L.in_off[q][f] = off;
+            off += L.in_slot_bytes;
+        }
+    for (int q = 0; q < 3; ++q)
+        for (int f = 0; f < fout; ++f) {
+            L.out_off[q][f] = off;
+            off += L.out_slot_bytes;
+        }
+    ro_off.assign(d.size(), 0);
+    ro_bytes.assign(d.size(), 0);
+    for (size_t i = 0; i < d.size(); ++i)
+        if (v[i].ro_res) {
+            ro_off[i] = off;
+            ro_bytes[i] = align_up((uint64_t)d[i].nz * d[i].nx * d[i].ny * 4, 256);
+            off += ro_bytes[i];
+        }
+    L.total = off;
+    return L;
+}
+
+oocs_status batch_plans(const oocs_desc *descs, int32_t n, std::vector<oocs_desc> &d, std::vector<oocs_plan> &p,
+                        std::vector<Derived> &v, std::string &err)
+{
+    if (!descs || n < 1 || n > 4096) {
+        err = "need 1..4096 problem descriptions";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    d.assign(descs, descs + n);
+    p.resize(n);
+    v.resize(n);
+    for (int32_t i = 0; i < n; ++i) {
+        oocs_status s = plan_impl(&d[i], &p[i], err);
+        if (s != OOCS_OK) {
+            err = "problem " + std::to_string(i) + ": " + err;
+            return s;
+        }
+        if (d[i].working_buffers != OOCS_SWB) {
+            err = "problem " + std::to_string(i) + ": a batch runs one working buffer (OOCS_SWB)";
+            return OOCS_ERR_INVALID_ARG;
+        }
+        if (d[i].temporal_depth == 0)
+            d[i].temporal_depth = p[i].temporal_depth;
+        v[i] = derive(d[i], p[i].slab_planes);
+    }
+    return OOCS_OK;
+}
+
+// Members are plain contexts whose workspace regions, streams and pipeline
+// events are the batch's.  With `trace`, nothing touches CUDA.
+oocs_status batch_build(oocs_batch *b, const std::vector<oocs_desc> &d, const std::vector<oocs_plan> &p,
+                        const std::vector<Derived> &v, char *ws)
+{
+    std::vector<uint64_t> ro_off, ro_bytes;
+    const Layout L = batch_layout(d, v, ro_off, ro_bytes);
+    b->ws = ws;
+    int d2h_base = 0;
+    for (size_t i = 0; i < d.size(); ++i) {
+        oocs_ctx *c = new (std::nothrow) oocs_ctx();
+        if (!c)
+            return fail(nullptr, OOCS_ERR_HOST_ALLOC, "cannot allocate a context");
+        b->ctx.push_back(c);
+        c->batch = b;
+        c->trace = b->trace;
+        c->d = d[i];
+        c->p = p[i];
+        c->v = v[i];
+        c->L = L;
+        c->L.ro_off = ro_off[i];
+        c->L.ro_bytes = ro_bytes[i];
+        c->ws = ws;
+        for (int k = 0; k < 3; ++k) {
+            c->st[k] = b->st[k];
+            c->ev_decoded[k] = b->ev_decoded[k];
+            c->ev_h2d[k] = b->ev_h2d[k];
+            c->ev_wrel[k] = b->ev_wrel[k];
+            c->ev_join[k] = b->ev_join[k];
+        }
+        memset(&c->stats, 0, sizeof(c->stats));
+        c->stats.workspace_bytes = L.total;
+        c->host_base = 3 * (int)i;
+        c->d2h_base = d2h_base;
+        d2h_base += c->v.S;
+        c->ev_d2h.assign(c->v.S, nullptr);
+        c->d2h_recorded.assign(c->v.S, 0);
+        if (b->trace)
+            continue;
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < c->v.S && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&c->ev_d2h[k], cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreate(&c->ev_t0);
+        if (e == cudaSuccess)
+            e = cudaEventCreate(&c->ev_t1);
+        if (e != cudaSuccess)
+            return fail(nullptr, OOCS_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    }
+    return OOCS_OK;
+}
+
+void batch_free(oocs_batch *b)
+{
+    if (!b)
+        return;
+    if (!b->trace)
+        for (int i = 0; i < 3; ++i)
+            if (b->st[i])
+                cudaStreamSynchronize(b->st[i]);
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    for (oocs_ctx *c : b->ctx)
+        destroy_ctx(c);
+    auto kill = [](cudaEvent_t &e) {
+        if (e)
+            cudaEventDestroy(e);
+        e = nullptr;
+    };
+    for (int i = 0; i < 3; ++i) {
+        kill(b->ev_decoded[i]);
+        kill(b->ev_h2d[i]);
+        kill(b->ev_wrel[i]);
+        kill(b->ev_join[i]);
+    }
+    delete b;
+}
+
+oocs_status batch_ready(oocs_batch *b)
+{
+    if (!b)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "batch is NULL");
+    for (oocs_ctx *c : b->ctx) {
+        oocs_status s = check_ready(c);
+        if (s != OOCS_OK)
+            return fail(nullptr, s, c->err);
+        const int nf = c->d.scheme == OOCS_WAVE ? 3 : 1;
+        for (int f = 0; f < nf; ++f)
+            if (!c->store[f])
+                return fail(nullptr, OOCS_ERR_STATE, "every field of every problem must be bound");
+    }
+    return OOCS_OK;
+}
+
+// Enqueue nsteps of every problem: rounds in which each unfinished problem
+// sweeps its slabs once (k of its own steps), all through the batch's
+// pipeline.  In a capture the streams fork from and join back into stream 0.
+oocs_status batch_enqueue(oocs_batch *b, int32_t nsteps, bool capture)
+{
+    oocs_ctx *c0 = b->ctx[0];
+    if (capture) {
+        SCHED(sched_record(c0, 0, kEvJoin + 0));
+        SCHED(sched_wait(c0, 1, kEvJoin + 0));
+        SCHED(sched_wait(c0, 2, kEvJoin + 0));
+    } else {
+        SCHED(join_streams(c0));
+    }
+    std::vector<int32_t> left(b->ctx.size(), nsteps);
+    for (bool more = true; more;) {
+        more = false;
+        for (size_t i = 0; i < b->ctx.size(); ++i) {
+            oocs_ctx *c = b->ctx[i];
+            if (left[i] <= 0)
+                continue;
+            const int k_eff = std::min(left[i], c->v.k);
+            const int64_t t = (int64_t)c->stats.steps_done;
+            c->g = b->g;
+            for (int sl = 0; sl < c->v.S; ++sl) {
+                oocs_status s = enqueue_slab(c, sl, k_eff, t);
+                if (s != OOCS_OK) {
+                    b->g = c->g;
+                    return fail(nullptr, s, c->err);
+                }
+            }
+            b->g = c->g;
+            c->stats.steps_done = (uint64_t)(t + k_eff);
+            c->stats.passes_done++;
+            left[i] -= k_eff;
+            more = more || left[i] > 0;
+        }
+    }
+    if (capture) {
+        SCHED(sched_record(c0, 1, kEvJoin + 1));
+        SCHED(sched_record(c0, 2, kEvJoin + 2));
+        SCHED(sched_wait(c0, 0, kEvJoin + 1));
+        SCHED(sched_wait(c0, 0, kEvJoin + 2));
+        return OOCS_OK;
+    }
+    return join_streams(c0);
+}
+
+oocs_status batch_uploads(oocs_batch *b)
+{
+    for (oocs_ctx *c : b->ctx)
+        if (c->v.ro_res && c->ro_dirty && !c->trace) {
+            oocs_status s = upload_resident(c);
+            if (s != OOCS_OK)
+                return fail(nullptr, s, c->err);
+        }
+    return OOCS_OK;
+}
+
+void add_stats(oocs_stats &a, const oocs_stats &d, int sign)
+{
+    auto f = [&](uint64_t &x, uint64_t y) { x = sign > 0 ? x + y : x - y; };
+    f(a.h2d_bytes, d.h2d_bytes);
+    f(a.d2h_bytes, d.d2h_bytes);
+    f(a.kernel_launches, d.kernel_launches);
+    f(a.steps_done, d.steps_done);
+    f(a.passes_done, d.passes_done);
+    f(a.slabs_done, d.slabs_done);
+    for (int k = 0; k < 3; ++k) {
+        oocs_kernel_stats &x = k == 0 ? a.load : k == 1 ? a.step : a.store;
+        const oocs_kernel_stats &y = k == 0 ? d.load : k == 1 ? d.step : d.store;
+        f(x.launches, y.launches);
+        f(x.units, y.units);
+    }
+}
+
+oocs_stats stats_diff(const oocs_stats &after, const oocs_stats &before)
+{
+    oocs_stats d = after;
+    add_stats(d, before, -1);
+    d.workspace_bytes = 0;
+    d.last_step_ms = 0.0;
+    d.load.device_ms = d.step.device_ms = d.store.device_ms = 0.0;
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+oocs_status oocs_batch_query(const oocs_desc *descs, int32_t n, uint64_t *workspace_bytes)
+{
+    if (!workspace_bytes)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "workspace_bytes is NULL");
+    std::vector<oocs_desc> d;
+    std::vector<oocs_plan> p;
+    std::vector<Derived> v;
+    std::string err;
+    oocs_status s = batch_plans(descs, n, d, p, v, err);
+    if (s != OOCS_OK)
+        return fail(nullptr, s, err);
+    std::vector<uint64_t> ro_off, ro_bytes;
+    *workspace_bytes = batch_layout(d, v, ro_off, ro_bytes).total;
+    return OOCS_OK;
+}
+
+oocs_status oocs_batch_create(const oocs_desc *descs, int32_t n, void *workspace, uint64_t workspace_bytes,
+                              void *const streams[3], oocs_batch **out)
+{
+    if (!out)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    std::vector<oocs_desc> d;
+    std::vector<oocs_plan> p;
+    std::vector<Derived> v;
+    std::string err;
+    oocs_status s = batch_plans(descs, n, d, p, v, err);
+    if (s != OOCS_OK)
+        return fail(nullptr, s, err);
+    std::vector<uint64_t> ro_off, ro_bytes;
+    const uint64_t need = batch_layout(d, v, ro_off, ro_bytes).total;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
+    if (workspace_bytes < need)
+        return fail(nullptr, OOCS_ERR_BUDGET,
+                    "workspace of " + std::to_string(workspace_bytes) + " bytes < batch's " + std::to_string(need));
+    if (!streams || !streams[0] || !streams[1] || !streams[2] || streams[0] == streams[1] ||
+        streams[1] == streams[2] || streams[0] == streams[2])
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "three distinct non-null streams are required");
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, workspace) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "workspace is not device memory");
+    }
+    oocs_batch *b = new (std::nothrow) oocs_batch();
+    if (!b)
+        return fail(nullptr, OOCS_ERR_HOST_ALLOC, "cannot allocate the batch");
+    for (int i = 0; i < 3; ++i)
+        b->st[i] = static_cast<cudaStream_t>(streams[i]);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&b->ev_decoded[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_h2d[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_wrel[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return fail(nullptr, OOCS_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    }
+    s = batch_build(b, d, p, v, static_cast<char *>(workspace));
+    if (s != OOCS_OK) {
+        std::string msg = g_last_error;
+        batch_free(b);
+        return fail(nullptr, s, msg);
+    }
+    *out = b;
+    return OOCS_OK;
+}
+
+oocs_status oocs_batch_context(oocs_batch *b, int32_t i, oocs_ctx **ctx)
+{
+    if (!b || !ctx || i < 0 || i >= (int32_t)b->ctx.size())
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "bad batch, index or output pointer");
+    *ctx = b->ctx[i];
+    return OOCS_OK;
+}
+
+oocs_status oocs_batch_step(oocs_batch *b, int32_t nsteps)
+{
+    oocs_status s = batch_ready(b);
+    if (s != OOCS_OK)
+        return s;
+    if (nsteps < 0)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if (b->capturing)
+        return fail(nullptr, OOCS_ERR_STATE, "the batch is capturing a graph");
+    if (nsteps == 0)
+        return OOCS_OK;
+    SCHED(join_streams(b->ctx[0]));
+    SCHED(batch_uploads(b));
+    return batch_enqueue(b, nsteps, false);
+}
+
+oocs_status oocs_batch_capture(oocs_batch *b, int32_t nsteps)
+{
+    oocs_status s = batch_ready(b);
+    if (s != OOCS_OK)
+        return s;
+    if (nsteps < 1)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "nsteps must be >= 1");
+    for (oocs_ctx *c : b->ctx) {
+        if (c->has_src && !c->w.empty())
+            return fail(nullptr, OOCS_ERR_UNSUPPORTED,
+                        "a problem has a time-dependent source: its amplitudes are kernel arguments, "
+                        "so a replayed graph would repeat them; use oocs_batch_step");
+        if (c->prof)
+            return fail(nullptr, OOCS_ERR_STATE, "turn profiling off before capturing");
+    }
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    // everything before, and the uploads of resident models, run now
+    SCHED(join_streams(b->ctx[0]));
+    SCHED(batch_uploads(b));
+    SCHED(join_streams(b->ctx[0]));
+    std::vector<oocs_stats> before;
+    std::vector<std::vector<char>> d2h_before;
+    for (oocs_ctx *c : b->ctx) {
+        before.push_back(c->stats);
+        d2h_before.push_back(c->d2h_recorded);
+        std::fill(c->d2h_recorded.begin(), c->d2h_recorded.end(), 0);
+    }
+    const uint64_t g0 = b->g;
+    b->cap_recorded.clear();
+    cudaError_t e = cudaStreamBeginCapture(b->st[0], cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess)
+        return fail(nullptr, OOCS_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    b->capturing = true;
+    s = batch_enqueue(b, nsteps, true);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->st[0], &graph);
+    b->capturing = false;
+    if (s == OOCS_OK && e == cudaSuccess)
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph)
+        cudaGraphDestroy(graph);
+    // nothing ran: the host-side state goes back to before the capture
+    b->graph_delta.clear();
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        oocs_ctx *c = b->ctx[i];
+        b->graph_delta.push_back(stats_diff(c->stats, before[i]));
+        c->stats = before[i];
+        if (s != OOCS_OK || e != cudaSuccess)
+            c->d2h_recorded = d2h_before[i];
+    }
+    if (s != OOCS_OK || e != cudaSuccess) {
+        b->g = g0;
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        cudaGetLastError();
+        if (s != OOCS_OK)
+            return s;
+        return fail(nullptr, OOCS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    b->graph_steps = nsteps;
+    return OOCS_OK;
+}
+
+oocs_status oocs_batch_launch(oocs_batch *b)
+{
+    oocs_status s = batch_ready(b);
+    if (s != OOCS_OK)
+        return s;
+    if (!b->exec)
+        return fail(nullptr, OOCS_ERR_STATE, "no captured graph (oocs_batch_capture)");
+    oocs_ctx *c0 = b->ctx[0];
+    SCHED(join_streams(c0));
+    SCHED(batch_uploads(b));
+    SCHED(join_streams(c0));
+    CU(c0, cudaGraphLaunch(b->exec, b->st[0]));
+    // later work on streams 1 and 2 follows the graph
+    SCHED(sched_record(c0, 0, kEvJoin + 0));
+    SCHED(sched_wait(c0, 1, kEvJoin + 0));
+    SCHED(sched_wait(c0, 2, kEvJoin + 0));
+    for (size_t i = 0; i < b->ctx.size(); ++i)
+        add_stats(b->ctx[i]->stats, b->graph_delta[i], +1);
+    return OOCS_OK;
+}
+
+oocs_status oocs_batch_synchronize(oocs_batch *b, uint64_t timeout_ns)
+{
+    if (!b)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "batch is NULL");
+    for (oocs_ctx *c : b->ctx) {
+        oocs_status s = oocs_synchronize(c, timeout_ns);
+        if (s != OOCS_OK)
+            return fail(nullptr, s, c->err);
+    }
+    return OOCS_OK;
+}
+
+oocs_status oocs_batch_destroy(oocs_batch *b)
+{
+    batch_free(b);
+    return OOCS_OK;
+}
+
+oocs_status oocs_batch_trace_schedule(const oocs_desc *descs, int32_t n, const int32_t *nsteps, int32_t ncalls,
+                                      oocs_trace_op *ops, int64_t capacity, int64_t *count)
+{
+    if (!count || (ncalls > 0 && !nsteps) || ncalls < 0 || capacity < 0 || (capacity > 0 && !ops))
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "bad trace arguments");
+    *count = 0;
+    std::vector<oocs_desc> d;
+    std::vector<oocs_plan> p;
+    std::vector<Derived> v;
+    std::string err;
+    oocs_status s = batch_plans(descs, n, d, p, v, err);
+    if (s != OOCS_OK)
+        return fail(nullptr, s, err);
+    std::vector<oocs_trace_op> trace;
+    oocs_batch *b = new (std::nothrow) oocs_batch();
+    if (!b)
+        return fail(nullptr, OOCS_ERR_HOST_ALLOC, "cannot allocate the batch");
+    b->trace = &trace;
+    s = batch_build(b, d, p, v, nullptr);
+    static char dummy;
+    for (oocs_ctx *c : b->ctx)
+        for (int f = 0; f < 3; ++f)
+            c->store[f] = &dummy;  // never dereferenced in trace mode
+    for (int32_t i = 0; i < ncalls && s == OOCS_OK; ++i)
+        if (nsteps[i] > 0)
+            s = batch_enqueue(b, nsteps[i], false);
+    std::string msg = g_last_error;
+    batch_free(b);
+    if (s != OOCS_OK)
+        return fail(nullptr, s, msg);
+    *count = (int64_t)trace.size();
+    if ((int64_t)trace.size() > capacity)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "trace needs " + std::to_string(trace.size()) + " entries");
+    for (size_t i = 0; i < trace.size(); ++i)
+        ops[i] = trace[i];
     return OOCS_OK;
 }
 

@@ -135,6 +135,17 @@ SIGNATURES = {
                                    _i32, _vp, _i64, _vp, _vp, _vp]),
     "oocs_misfit_backward": (_i32, [ctypes.POINTER(oocs_desc), _vp, _vp, _vp, _i32, _i64, _vp, _i32, _i32,
                                     _i32, _vp, _i64, _vp, _vp]),
+    "oocs_batch_query": (_i32, [ctypes.POINTER(oocs_desc), _i32, ctypes.POINTER(_u64)]),
+    "oocs_batch_create": (_i32, [ctypes.POINTER(oocs_desc), _i32, _vp, _u64, ctypes.POINTER(_vp),
+                                 ctypes.POINTER(_vp)]),
+    "oocs_batch_context": (_i32, [_vp, _i32, ctypes.POINTER(_vp)]),
+    "oocs_batch_step": (_i32, [_vp, _i32]),
+    "oocs_batch_capture": (_i32, [_vp, _i32]),
+    "oocs_batch_launch": (_i32, [_vp]),
+    "oocs_batch_synchronize": (_i32, [_vp, _u64]),
+    "oocs_batch_destroy": (_i32, [_vp]),
+    "oocs_batch_trace_schedule": (_i32, [ctypes.POINTER(oocs_desc), _i32, ctypes.POINTER(_i32), _i32,
+                                         ctypes.POINTER(oocs_trace_op), _i64, ctypes.POINTER(_i64)]),
     "oocs_encode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
     "oocs_decode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
 }
@@ -300,6 +311,42 @@ def oocs_trace_schedule(desc, nsteps_calls):
     return out
 
 
+def _trace_ops(buf, n):
+    out = []
+    for i in range(n):
+        o = buf[i]
+        out.append({"op": OOCS_OP_NAMES[o.op], "stream": o.stream, "event": o.event,
+                    "visit": o.visit,
+                    "access": [(OOCS_RES_NAMES[a.kind], a.index, a.lo, a.hi, bool(a.write))
+                               for a in o.access[:o.naccess]]})
+    return out
+
+
+def _desc_array(descs):
+    arr = (oocs_desc * len(descs))()
+    for i, d in enumerate(descs):
+        arr[i] = d
+    return arr
+
+
+def oocs_batch_trace_schedule(descs, nsteps_calls):
+    """oocs_trace_schedule for successive oocs_batch_step calls of a batch."""
+    arr = _desc_array(descs)
+    calls = (_i32 * len(nsteps_calls))(*[int(n) for n in nsteps_calls])
+    count = _i64(0)
+    lib().oocs_batch_trace_schedule(arr, len(descs), calls, len(nsteps_calls), None, 0, ctypes.byref(count))
+    buf = (oocs_trace_op * max(count.value, 1))()
+    _check(lib().oocs_batch_trace_schedule(arr, len(descs), calls, len(nsteps_calls), buf, count.value,
+                                           ctypes.byref(count)))
+    return _trace_ops(buf, count.value)
+
+
+def oocs_batch_query(descs) -> int:
+    n = _u64(0)
+    _check(lib().oocs_batch_query(_desc_array(descs), len(descs), ctypes.byref(n)))
+    return n.value
+
+
 def oocs_adjoint_step(desc, lam_ptr, lam_prev_ptr, mu_ptr, mu_out_ptr, m_ptr, res_ptr=0, zr=-1,
                       stream=0):
     _check(lib().oocs_adjoint_step(ctypes.byref(desc), _vp(lam_ptr), _vp(lam_prev_ptr), _vp(mu_ptr),
@@ -458,6 +505,79 @@ class OutOfCoreStencil:
         if getattr(self, "ctx", None):
             oocs_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchProblem(OutOfCoreStencil):
+    """One problem of an OutOfCoreBatch: a context owned by the batch, with its
+    own pinned host stores (the OutOfCoreStencil methods apply to it)."""
+
+    def __init__(self, batch, i: int, desc: oocs_desc):
+        import torch
+        self.torch = torch
+        self.desc = desc
+        self.plan = oocs_query(desc)
+        self.device = batch.device
+        self.streams = batch.streams
+        c = _vp()
+        _check(lib().oocs_batch_context(_vp(batch.handle), int(i), ctypes.byref(c)))
+        self.ctx = c.value
+        nfields = 3 if desc.scheme == OOCS_WAVE else 1
+        self.stores = []
+        for f in range(nfields):
+            st = torch.zeros(self.plan.host_store_bytes, dtype=torch.uint8, pin_memory=True)
+            oocs_bind_field(self.ctx, f, st.data_ptr(), st.numel())
+            self.stores.append(st)
+        self._keep = []
+
+    def close(self):
+        self.ctx = None  # owned by the batch
+
+
+class OutOfCoreBatch:
+    """A batch (oocs_batch_*) plus its workspace and streams, allocated through
+    PyTorch; problems[i] are BatchProblem objects."""
+
+    def __init__(self, descs, device: int = 0):
+        import torch
+        self.torch = torch
+        self.descs = list(descs)
+        self.device = torch.device("cuda", device)
+        self.workspace_bytes = oocs_batch_query(self.descs)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+            ws = (self.workspace.data_ptr() + 255) // 256 * 256
+            self.streams = [torch.cuda.Stream(device=self.device) for _ in range(3)]
+            arr = (_vp * 3)(*[s.cuda_stream for s in self.streams])
+            out = _vp()
+            _check(lib().oocs_batch_create(_desc_array(self.descs), len(self.descs), _vp(ws),
+                                           self.workspace_bytes, arr, ctypes.byref(out)))
+            self.handle = out.value
+        self.problems = [BatchProblem(self, i, d) for i, d in enumerate(self.descs)]
+
+    def step(self, nsteps: int):
+        _check(lib().oocs_batch_step(_vp(self.handle), int(nsteps)))
+
+    def capture(self, nsteps: int):
+        _check(lib().oocs_batch_capture(_vp(self.handle), int(nsteps)))
+
+    def launch(self):
+        _check(lib().oocs_batch_launch(_vp(self.handle)))
+
+    def synchronize(self, timeout_s: float = 0.0):
+        _check(lib().oocs_batch_synchronize(_vp(self.handle), int(timeout_s * 1e9)))
+        for p in self.problems:
+            p._keep.clear()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().oocs_batch_destroy(_vp(self.handle))
+            self.handle = None
 
     def __del__(self):
         try:

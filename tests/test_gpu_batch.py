@@ -1,0 +1,158 @@
+"""Batches of independent problems through one pipeline (oocs_batch_*), on the GPU.
+
+Every problem of a batch must end with the host stores it gets when it runs
+alone with the same desc (same kernels, same arithmetic, byte for byte), for
+mixed heat / wave problems with different grids, slab thicknesses, temporal
+depths, rates, sources and resident models; split calls continue each
+problem's time; a captured CUDA graph replayed twice equals two direct batch
+steps; a problem with a time-dependent source cannot be captured.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from gpu_util import heat_desc, torch_cuda, wave_desc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2204_11315_gb300 as P
+    P.lib()
+    return P
+
+
+def _problems(P, with_source=True):
+    """(desc, inputs) pairs; inputs: dict field -> FP32 array, optional source."""
+    out = []
+    u = synthetic.heat_initial(64)
+    out.append((heat_desc(P, u.shape, rate=16, k=2, T=32), {0: u}, None))
+    u = synthetic.uniform_field((96, 40, 128), 7)
+    out.append((heat_desc(P, u.shape, rate=0, k=3, T=32, alpha=0.12), {0: u}, None))
+    for shape, rate, k, T, ro, seed in (((128, 72, 40), 16, 4, 32, 0, 11), ((96, 48, 64), 12, 3, 24, 1, 12),
+                                        ((80, 40, 40), 0, 1, 16, 1, 13)):
+        m = synthetic.wave_model(shape)
+        if with_source:
+            z = np.zeros(shape, np.float32)
+            src = (synthetic.centre(shape)[::-1], synthetic.ricker(40))
+            fields = {0: z, 1: z, 2: m}
+        else:
+            u0 = (1e-3 * synthetic.uniform_field(shape, seed)).astype(np.float32)
+            fields = {0: u0, 1: u0, 2: m}
+            src = None
+        out.append((wave_desc(P, shape, rate=rate, k=k, T=T, ro=ro), fields, src))
+    return out
+
+
+def _load(prob, fields, src):
+    for f, a in fields.items():
+        prob.compress(f, a)
+    if src is not None:
+        (x, y, z), w = src
+        prob.set_source(x, y, z, w)
+
+
+def _alone(P, desc, fields, src, calls):
+    st = P.OutOfCoreStencil(desc)
+    try:
+        _load(st, fields, src)
+        for n in calls:
+            st.step(n)
+        st.synchronize(120.0)
+        return [s.numpy().copy() for s in st.stores], st.stats()
+    finally:
+        st.close()
+
+
+def _batch(P, probs):
+    b = P.OutOfCoreBatch([d for d, _, _ in probs])
+    for bp, (d, fields, src) in zip(b.problems, probs):
+        _load(bp, fields, src)
+    b.synchronize(120.0)
+    return b
+
+
+@pytest.mark.parametrize("calls", [[10], [4, 6]])
+def test_batch_matches_problems_run_alone(P, calls):
+    torch_cuda()
+    probs = _problems(P)
+    b = _batch(P, probs)
+    try:
+        for n in calls:
+            b.step(n)
+        b.synchronize(120.0)
+        got = [[s.numpy().copy() for s in bp.stores] for bp in b.problems]
+        stats = [bp.stats() for bp in b.problems]
+    finally:
+        b.close()
+    for i, (d, fields, src) in enumerate(probs):
+        # the same calls: with a lossy rate the sweep boundaries (where the
+        # codec rounds) depend on how the steps are split into calls
+        ref, rstats = _alone(P, d, fields, src, calls)
+        nout = 2 if d.scheme == P.OOCS_WAVE else 1
+        for f in range(nout):
+            assert np.array_equal(got[i][f], ref[f]), (i, f)
+        assert stats[i]["steps_done"] == sum(calls)
+        assert stats[i]["h2d_bytes"] == rstats["h2d_bytes"] and stats[i]["d2h_bytes"] == rstats["d2h_bytes"]
+
+
+def test_one_problem_of_a_batch_steps_alone(P):
+    """oocs_step on a batch member advances that problem only, through the batch's pipeline."""
+    torch_cuda()
+    probs = _problems(P)
+    b = _batch(P, probs)
+    try:
+        b.problems[2].step(8)
+        b.synchronize(120.0)
+        got = [s.numpy().copy() for s in b.problems[2].stores]
+        assert b.problems[0].stats()["steps_done"] == 0
+        with pytest.raises(P.OOCSError):
+            P.oocs_destroy(b.problems[0].ctx)
+    finally:
+        b.close()
+    d, fields, src = probs[2]
+    ref, _ = _alone(P, d, fields, src, [8])
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+def test_graph_replay_equals_direct_steps(P):
+    torch_cuda()
+    probs = _problems(P, with_source=False)
+    outs = []
+    for mode in ("direct", "graph"):
+        b = _batch(P, probs)
+        try:
+            if mode == "direct":
+                b.step(6)
+                b.step(6)
+            else:
+                b.capture(6)
+                assert all(bp.stats()["steps_done"] == 0 for bp in b.problems)
+                b.launch()
+                b.launch()
+            b.synchronize(120.0)
+            outs.append(([[s.numpy().copy() for s in bp.stores] for bp in b.problems],
+                         [bp.stats() for bp in b.problems]))
+        finally:
+            b.close()
+    (sd, std), (sg, stg) = outs
+    for i in range(len(probs)):
+        for a, c in zip(sd[i], sg[i]):
+            assert np.array_equal(a, c), i
+        for key in ("steps_done", "h2d_bytes", "d2h_bytes", "kernel_launches", "slabs_done"):
+            assert std[i][key] == stg[i][key], (i, key)
+    assert std[0]["steps_done"] == 12
+
+
+def test_capture_refuses_a_time_dependent_source(P):
+    torch_cuda()
+    b = _batch(P, _problems(P, with_source=True))
+    try:
+        with pytest.raises(P.OOCSError) as e:
+            b.capture(4)
+        assert e.value.status == 7
+        b.step(2)  # the batch stays usable
+        b.synchronize(60.0)
+    finally:
+        b.close()

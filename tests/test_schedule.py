@@ -202,3 +202,103 @@ def test_trace_capacity_error(P):
     buf = (P.oocs.oocs_trace_op * 2)()
     st = P.lib().oocs_trace_schedule(ctypes.byref(desc), calls, 1, buf, 2, ctypes.byref(count))
     assert st == 1 and count.value > 2
+
+
+# ----------------------------------------------------------------- batches
+
+BATCH = [("heat", (128, 128, 128), 16, 2, 32, 0), ("wave", (128, 72, 40), 16, 4, 32, 0),
+         ("heat", (64, 36, 100), 0, 3, 16, 0), ("wave", (96, 48, 64), 12, 3, 24, 1),
+         ("wave", (40, 16, 24), 8, 4, 64, 0)]
+
+
+def _batch_descs(P, spec=BATCH):
+    return [_desc(P, sc, sh, rate, k, T, 1, ro) for sc, sh, rate, k, T, ro in spec]
+
+
+@pytest.mark.parametrize("calls", [[10], [3, 4], [1, 7, 2]])
+def test_batch_schedule_is_race_free(P, calls):
+    """Several problems through one pipeline: no race on the shared working
+    buffer and staging slots, kernels of all visits ordered (one working
+    buffer), and per problem every host layer read in sweep p+1 was written
+    back in sweep p."""
+    descs = _batch_descs(P)
+    trace = P.oocs_batch_trace_schedule(descs, calls)
+    assert check(trace, swb=True) is None
+    plans = [P.oocs_query(d) for d in descs]
+    h2d = {}
+    for o in trace:
+        if o["op"] == "H2D":
+            i = o["access"][1][1] // 3
+            h2d[i] = h2d.get(i, 0) + o["access"][0][3] - o["access"][0][2]
+    for i, (sc, sh, rate, k, T, ro) in enumerate(BATCH):
+        sweeps = sum(-(-c // k) for c in calls)
+        assert h2d[i] == sweeps * (sh[0] // 4)
+    # host dataflow per problem: the last writer of every layer read is the previous sweep
+    writer, sweep_of = {}, {}
+    visits = sorted({o["visit"] for o in trace if o["visit"] >= 0})
+    for o in trace:
+        for (kd, idx, lo, hi, w) in o["access"]:
+            if kd == "HOST":
+                sweep_of.setdefault((idx // 3, o["visit"]), None)
+    count = {}
+    order = []
+    for o in trace:
+        if o["op"] == "H2D":
+            order.append((o["access"][1][1] // 3, o["visit"]))
+    seen = {}
+    for i, v in order:
+        seen.setdefault(i, []).append(v)
+    for i, vs in seen.items():
+        S = plans[i].num_slabs
+        for n, v in enumerate(vs):
+            sweep_of[(i, v)] = n // S
+    for o in trace:
+        if o["op"] == "H2D":
+            i = o["access"][1][1] // 3
+            sw = sweep_of[(i, o["visit"])]
+            for (kd, idx, lo, hi, w) in o["access"][1:]:
+                if idx % 3 >= (2 if BATCH[i][0] == "wave" else 1):
+                    continue
+                got = {writer.get((idx, l)) for l in range(lo, hi)}
+                assert got == {None if sw == 0 else sw - 1}, (i, o["visit"], got)
+        if o["op"] == "D2H":
+            for (kd, idx, lo, hi, w) in o["access"]:
+                if kd == "HOST" and w:
+                    for l in range(lo, hi):
+                        writer[(idx, l)] = sweep_of[(idx // 3, o["visit"])]
+    assert len(visits) == sum(sum(-(-c // BATCH[i][3]) for c in calls) * plans[i].num_slabs
+                              for i in range(len(BATCH)))
+
+
+@pytest.mark.parametrize("drop", ["decoded", "wrel"])
+def test_batch_check_detects_missing_waits(P, drop):
+    base = {"decoded": range(100, 103), "wrel": range(300, 303)}[drop]
+    trace = P.oocs_batch_trace_schedule(_batch_descs(P), [6])
+    cut = [o for o in trace if not (o["op"] == "WAIT" and o["event"] in base)]
+    assert len(cut) < len(trace)
+    assert check(cut, swb=True) is not None
+
+
+def test_batch_workspace_is_per_region_maximum(P):
+    """One working buffer and one slot set, each region sized for the largest
+    problem's, plus the resident models: the exact sum of the layout."""
+    descs = _batch_descs(P)
+    a256 = lambda b: -(-b // 256) * 256
+    buf = slot_in = slot_out = 0
+    nbuf = fin = fout = 0
+    resident = 0
+    for (sc, (nz, ny, nx), rate, k, T, ro), d in zip(BATCH, descs):
+        p = P.oocs_query(d)
+        wave = sc == "wave"
+        buf = max(buf, a256(p.window_planes * nx * ny * 4))
+        slot_in = max(slot_in, a256(min(-(-(T + p.halo_planes) // 4), nz // 4) * p.layer_bytes))
+        slot_out = max(slot_out, a256(min(T // 4, nz // 4) * p.layer_bytes))
+        nbuf = max(nbuf, 3 if wave and not ro else 2)
+        fin = max(fin, p.fields_in)
+        fout = max(fout, p.fields_out)
+        resident += a256(nz * ny * nx * 4) if wave and ro else 0
+    want = nbuf * buf + 3 * fin * slot_in + 3 * fout * slot_out + resident
+    assert P.oocs_batch_query(descs) == want
+    # many copies of one problem cost one problem's pipeline
+    one = [descs[1]]
+    assert P.oocs_batch_query(one * 16) == P.oocs_query(descs[1]).workspace_bytes
