@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--rate", type=int, default=RATE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--profile-run", choices=["sweep", "kernels"], default=None,
                     help="run only the region to capture under ncu --profile-from-start off: "
                          "'sweep' = one oocs_step(100) of the workload; 'kernels' = one launch each "
@@ -413,6 +415,12 @@ def run_ours(args):
     # ---- accuracy at the stated configuration: 100 steps from rest
     accuracy = check_accuracy(P, torch, dev, args.rate, inputs)
 
+    # ---- the adjoint workload (gradient of a receiver misfit)
+    adjoint = None if args.no_adjoint else run_adjoint(P, torch, dev, float(peaks["hbm_gbs"]))
+
+    # ---- the batched workload (many independent problems, one pipeline)
+    batched = None if args.no_batch else run_batched(P, torch, dev)
+
     # ---- comparison: uncompressed streaming, SWB and classic (Fig. 9, Fig. 11 analogues)
     compare = None
     if not args.no_compare:
@@ -449,7 +457,7 @@ def run_ours(args):
     line.update({"value": value, "ms_per_step": ms / args.steps, "dtype": "f32",
                  "gpu_launches": int(d["kernel_launches"]), "e2e": e2e, "roofline": roofline,
                  "clocks": clk, "sweep_roofline": sweep_roofline, "kernels": kernels,
-                 "accuracy": accuracy, "compare": compare,
+                 "accuracy": accuracy, "compare": compare, "adjoint": adjoint, "batched": batched,
                  "workspace_bytes": P.oocs_query(wave_desc(P, args.rate)).workspace_bytes})
     if rank == 0 and not args.no_cpu_baseline:
         tot, pts_cpu = 0.0, 0
@@ -467,6 +475,181 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+BATCH_N, BATCH_STEPS, BATCH_BUDGET, BATCH_TOL = 64, 50, 8 << 30, 1e-4
+
+
+def run_batched(P, torch, dev):
+    """64 independent problems (heat and wave alternating, every side seeded
+    in 64..384 by 16), 50 steps each, one shared 8 GiB workspace, (slabs, k,
+    rate) autotuned per size class at the rate-16 tolerance.  Timed three ways
+    on the same problems from the same compressed state: each problem alone
+    (its own context, one after another), one batch step through the shared
+    pipeline, and a replay of the batch step captured as a CUDA graph."""
+    import numpy as np
+
+    import synthetic
+    from paper_2204_11315_gb300 import autotune
+    t0 = time.time()
+    descs = []
+    for sc, (nz, ny, nx) in synthetic.batch_shapes(BATCH_N):
+        if sc == "heat":
+            descs.append(P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), BATCH_BUDGET))
+        else:
+            descs.append(P.make_desc(nx, ny, nz, P.OOCS_WAVE, synthetic.wave_star_coef(), BATCH_BUDGET))
+    cache = os.path.join(tempfile.gettempdir(), f"oocs_autotune_{os.getpid()}.json")
+    tuned, report = autotune.tune(descs, BATCH_TOL, BATCH_BUDGET, cache)
+    t_tune = time.time() - t0
+    b = P.OutOfCoreBatch(tuned)
+    for i, (bp, d) in enumerate(zip(b.problems, tuned)):
+        shape = (d.nz, d.ny, d.nx)
+        if d.scheme == P.OOCS_HEAT:
+            bp.compress(P.OOCS_FIELD_U, synthetic.uniform_field(shape, 100 + i))
+        else:
+            u0 = synthetic.wave_initial(shape, 200 + i)
+            bp.compress(P.OOCS_FIELD_U, u0)
+            bp.compress(P.OOCS_FIELD_U_PREV, u0)
+            bp.compress(P.OOCS_FIELD_M, synthetic.wave_model(shape))
+        bp.synchronize(600.0)
+    snaps = [bp.snapshot_stores() for bp in b.problems]
+
+    def restore():
+        for bp, sn in zip(b.problems, snaps):
+            bp.restore_stores(sn, 0)
+
+    def timed(fn, stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        b.synchronize(600.0)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    s0 = b.streams[0]
+    restore()
+    b.step(BATCH_STEPS)  # warm-up
+    b.synchronize(600.0)
+    restore()
+    l0 = sum(bp.stats()["kernel_launches"] for bp in b.problems)
+    ms_batch = timed(lambda: b.step(BATCH_STEPS), s0)
+    launches_per_step = sum(bp.stats()["kernel_launches"] for bp in b.problems) - l0
+    restore()
+    b.capture(BATCH_STEPS)
+    b.launch()  # warm-up replay
+    b.synchronize(600.0)
+    restore()
+    ms_graph = timed(b.launch, s0)
+    # each problem alone: a context of its own over the same host stores
+    restore()
+    ms_alone, ws_alone = 0.0, []
+    for bp, d in zip(b.problems, tuned):
+        st = P.OutOfCoreStencil(d, stores=bp.stores)
+        try:
+            ws_alone.append(st.plan.workspace_bytes)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st.streams[0])
+            st.step(BATCH_STEPS)
+            e1.record(st.streams[0])
+            st.synchronize(600.0)
+            e1.synchronize()
+            ms_alone += e0.elapsed_time(e1)
+        finally:
+            st.close()
+    b.close()
+    pts = sum((int(d.nx) - 2 * d.radius) * (int(d.ny) - 2 * d.radius) * (int(d.nz) - 2 * d.radius)
+              for d in tuned) * BATCH_STEPS
+    gpts = lambda ms: pts / (ms / 1e3) / 1e9
+    rates, slabs, depths = {}, {}, {}
+    for r in report["problems"]:
+        rates[r["rate"]] = rates.get(r["rate"], 0) + 1
+        slabs[r["slabs"]] = slabs.get(r["slabs"], 0) + 1
+        depths[r["k"]] = depths.get(r["k"], 0) + 1
+    return {"workload": f"{BATCH_N}_problems_heat_wave_sides64to384_{BATCH_STEPS}steps_budget8GiB_tol1e-4",
+            "unit": UNIT, "value": gpts(ms_graph),
+            "graph_replay": {"value": gpts(ms_graph), "ms": ms_graph},
+            "batch_step": {"value": gpts(ms_batch), "ms": ms_batch},
+            "each_alone": {"value": gpts(ms_alone), "ms": ms_alone},
+            "speedup_graph_vs_alone": ms_alone / ms_graph,
+            "interior_point_updates": pts, "workspace_bytes": P.oocs_batch_query(tuned),
+            "sum_of_alone_workspaces": int(sum(ws_alone)), "kernel_launches_per_batch_step": launches_per_step,
+            "tuning": {"seconds": t_tune, "classes": report["classes"],
+                       "candidates_timed": report["candidates_timed"], "rates": rates, "slabs": slabs,
+                       "temporal_depths": depths}}
+
+
+ADJ_N, ADJ_STEPS, ADJ_EVERY, ADJ_RATE = 256, 400, 10, 16
+
+
+def run_adjoint(P, torch, dev, hbm_peak):
+    """dJ/dv of J = 1/2 sum_n |u^n(z = 8) - d^n|^2 on a 256^3 wave grid, 400
+    steps, (u^n, u^(n-1)) checkpointed every 10 steps at 16 bits/value, through
+    the autograd Function (one forward + one backward call of the library's
+    driver).  Target data d from a smooth +5 % velocity bump.  Also the live
+    bandwidth of the adjoint-step kernel (24 B per point: read m lam^(n+1)
+    (stencil), lam^(n+1), lam^(n+2), m; write lam^n, m lam^n)."""
+    import numpy as np
+
+    import paper_2204_11315_gb300.adjoint as A
+    import synthetic
+    n = ADJ_N
+    shape = (n, n, n)
+    w = synthetic.ricker(ADJ_STEPS)
+    v = synthetic.layered_velocity(shape, seed=4).astype(np.float32)
+    z, y, x = np.ogrid[:n, :n, :n]
+    bump = np.exp(-((x - 140.0) ** 2 + (y - 120.0) ** 2 + (z - 40.0) ** 2) / 400.0)
+    v_true = (v * (1.0 + 0.05 * bump)).astype(np.float32)
+    prob = A.WaveProblem(shape=shape, dt=synthetic.WAVE_DT, dx=synthetic.WAVE_DX,
+                         coef=synthetic.wave_star_coef(), src_xyz=(n // 2, n // 2, 32), wavelet=w, zr=8,
+                         nsteps=ADJ_STEPS, checkpoint_every=ADJ_EVERY, rate=ADJ_RATE)
+    d = A.receiver_data(torch.from_numpy(v_true).to(dev), prob)
+    v_dev = torch.from_numpy(v).to(dev)
+    times = []
+    for rep_i in range(3):
+        vt = v_dev.clone().requires_grad_(True)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize(dev)
+        e[0].record()
+        J = A.wave_misfit(vt, d, prob)
+        e[1].record()
+        J.backward()
+        e[2].record()
+        torch.cuda.synchronize(dev)
+        if rep_i:  # the first is a warm-up
+            times.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])))
+        grad_norm = float(vt.grad.norm())
+    fwd = float(np.median([t[0] for t in times]))
+    bwd = float(np.median([t[1] for t in times]))
+    interior = (n - 8) ** 3
+    # live bandwidth of the adjoint-step kernel on the same grid
+    desc = prob.desc()
+    f = [torch.zeros(shape, device=dev) for _ in range(4)]
+    m = torch.full(shape, 0.1, device=dev)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    reps = 40
+    for _ in range(3):
+        P.oocs_adjoint_step(desc, f[0].data_ptr(), f[1].data_ptr(), f[2].data_ptr(), f[3].data_ptr(),
+                            m.data_ptr(), 0, -1, s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(reps):
+        a, b = (2, 3) if i % 2 == 0 else (3, 2)
+        P.oocs_adjoint_step(desc, f[0].data_ptr(), f[1].data_ptr(), f[a].data_ptr(), f[b].data_ptr(),
+                            m.data_ptr(), 0, -1, s)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    k_ms = e0.elapsed_time(e1) / reps
+    k_gbs = 24 * n ** 3 / (k_ms / 1e3) / 1e9
+    return {"workload": f"wave25_{n}cubed_{ADJ_STEPS}steps_misfit_gradient_checkpoints{ADJ_EVERY}_rate{ADJ_RATE}",
+            "value": interior * ADJ_STEPS / ((fwd + bwd) / 1e3) / 1e9,
+            "unit": "Gpoint-steps/s of the whole gradient (forward + backward)",
+            "ms_per_gradient": fwd + bwd, "forward_ms": fwd, "backward_ms": bwd,
+            "grad_norm": grad_norm, "misfit": float(J.detach()),
+            "workspace_bytes": prob.workspace_bytes(),
+            "roofline": {"bound": "hbm", "kernel": "k_star_step<4,adjoint>", "achieved": k_gbs, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": k_gbs / hbm_peak, "bytes_per_point": 24,
+                         "avg_launch_ms": k_ms, "grid": [n, n, n]}}
 
 
 def check_accuracy(P, torch, dev, rate, inputs):

@@ -1,0 +1,174 @@
+"""Autotuner of a problem's slab thickness T, temporal depth k and codec rate.
+
+The knobs of the out-of-core sweep (Sec. 3.1 temporal blocking, Sec. 4.2
+fixed rate) trade redundant halo work, pipeline depth and link bytes against
+each other differently for every grid, so they are measured, not modelled:
+
+* rates: those whose error bar meets the requested tolerance (the bars the
+  test suite holds each rate to, rel-L2 against the FP64 oracle: 1e-4 at 16
+  bits/value, 2e-3 at 12, 3e-2 at 8; rate 0 is exact);
+* slabs: S in {1, 2, 4} (T = nz / S rounded up to the 4-plane layer), kept
+  only when T >= 2 h so region sharing holds and the plan fits the budget;
+* temporal depth: k in {2, 4, 8} for the 7-point heat stencil, {2, 4} for the
+  25-point wave stencil.
+
+Each candidate runs `steps` time steps of the problem's own grid on seeded
+data through a fresh context (one warm-up call, one call timed with CUDA
+events) and the fastest is kept.  Problems are grouped into classes (scheme
+and the rounded cube root of the volume); one problem per class is timed and
+its (S, k, rate) is applied to the class.  Choices are cached in a JSON file
+keyed by class, budget and tolerance.  The tile shape of the step kernel is
+fixed (64 x 16, the layout of its TMA rings); its launch geometry is chosen
+per launch by the occupancy model in the library.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+from . import oocs as O
+
+RATE_REL_L2 = {0: 0.0, 16: 1e-4, 12: 2e-3, 8: 3e-2}
+SLABS = (1, 2, 4)
+DEPTHS = {O.OOCS_HEAT: (2, 4, 8), O.OOCS_WAVE: (2, 4)}
+
+
+def rates_for(tol: float):
+    """Compressed rates whose error bar meets tol; uncompressed (0) when none does."""
+    r = [q for q in (8, 12, 16) if RATE_REL_L2[q] <= tol]
+    return r or [0]
+
+
+def with_plan(desc, slabs: int, k: int, rate: int):
+    """desc with S = slabs slabs (T rounded up to 4 planes), depth k, rate; None if invalid."""
+    d = O.oocs_desc.from_buffer_copy(desc)
+    T = -(-int(d.nz) // slabs)
+    T = -(-T // 4) * 4
+    h = 4 * -(-(k * d.radius) // 4)
+    if slabs > 1 and T < 2 * h:
+        return None
+    d.slab_planes = min(T, int(d.nz))
+    d.temporal_depth = k
+    d.rate_bits = rate
+    try:
+        O.oocs_query(d)
+    except O.OOCSError:
+        return None
+    return d
+
+
+def class_key(desc, budget: int, tol: float) -> str:
+    vol = int(desc.nx) * int(desc.ny) * int(desc.nz)
+    side = int(round(vol ** (1.0 / 3.0) / 32.0)) * 32
+    scheme = "heat" if desc.scheme == O.OOCS_HEAT else "wave"
+    return f"{scheme}:{side}:{budget}:{tol:g}:ro{int(desc.readonly_resident)}"
+
+
+class _Probe:
+    """Seeded FP32 fields of one grid and host stores, pinned once and reused
+    by every candidate of the grid."""
+
+    def __init__(self, desc, seed: int = 0):
+        import torch
+        shape = (int(desc.nz), int(desc.ny), int(desc.nx))
+        rng = np.random.default_rng(seed)
+        nf = 1 if desc.scheme == O.OOCS_HEAT else 3
+        self.fields = {}
+        for f in range(nf):
+            t = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+            a = t.numpy()
+            if desc.scheme == O.OOCS_HEAT:
+                a[...] = rng.random(shape, dtype=np.float32)
+            elif f == O.OOCS_FIELD_M:
+                a[...] = 0.02 + 0.1 * rng.random(shape, dtype=np.float32)
+            else:
+                a[...] = 1e-3 * rng.random(shape, dtype=np.float32)
+            self.fields[f] = t
+        raw = 4 * int(desc.nx) * int(desc.ny) * int(desc.nz)  # the largest store (rate 0)
+        self.stores = [torch.empty(raw, dtype=torch.uint8, pin_memory=True) for _ in range(nf)]
+
+
+def time_candidate(desc, steps: int, probe: _Probe | None = None) -> float:
+    """Milliseconds per time step of one oocs_step(steps) call on seeded data."""
+    import torch
+    probe = probe or _Probe(desc)
+    st = O.OutOfCoreStencil(desc, stores=probe.stores)
+    try:
+        for f, t in probe.fields.items():
+            st.compress(f, t)
+        st.synchronize(600.0)
+        st.step(steps)
+        st.synchronize(600.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st.streams[0])
+        st.step(steps)
+        e1.record(st.streams[0])
+        st.synchronize(600.0)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+    finally:
+        st.close()
+
+
+def tune_one(desc, tol: float, steps: int = 4):
+    """(best desc, ms per step, every candidate timed) for one problem."""
+    tried = []
+    best, best_ms = None, math.inf
+    probe = _Probe(desc)
+    for rate in rates_for(tol):
+        for slabs in SLABS:
+            for k in DEPTHS[desc.scheme]:
+                d = with_plan(desc, slabs, k, rate)
+                if d is None:
+                    continue
+                ms = time_candidate(d, max(steps, k), probe)
+                tried.append({"slabs": slabs, "k": k, "rate": rate, "ms_per_step": ms})
+                if ms < best_ms:
+                    best, best_ms = d, ms
+    return best, best_ms, tried
+
+
+def tune(descs, tol: float, budget: int, cache_path: str | None = None, steps: int = 4):
+    """Tuned copies of descs (and a report).  The batch of the tuned descs is
+    kept within `budget` bytes of shared workspace by adding slabs to the
+    largest problems if needed."""
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    out, report, timed = [], [], 0
+    for d in descs:
+        d = O.oocs_desc.from_buffer_copy(d)
+        d.device_budget = budget
+        key = class_key(d, budget, tol)
+        if key not in cache:
+            best, ms, tried = tune_one(d, tol, steps)
+            timed += len(tried)
+            if best is None:
+                raise O.OOCSError(2, f"no plan of {key} fits the budget")
+            cache[key] = {"slabs": -(-int(d.nz) // int(best.slab_planes)), "k": int(best.temporal_depth),
+                          "rate": int(best.rate_bits), "ms_per_step": ms, "tried": tried}
+        c = cache[key]
+        t = with_plan(d, c["slabs"], c["k"], c["rate"])
+        slabs = c["slabs"]
+        while t is None and slabs < 64:  # this member of the class needs more slabs
+            slabs *= 2
+            t = with_plan(d, slabs, c["k"], c["rate"])
+        out.append(t)
+        report.append({"class": key, "slabs": slabs, "k": c["k"], "rate": c["rate"]})
+    # shared workspace of the batch within the budget: split the largest windows
+    while O.oocs_batch_query(out) > budget:
+        i = max(range(len(out)), key=lambda j: int(out[j].nx) * int(out[j].ny) * int(out[j].slab_planes))
+        slabs = 2 * -(-int(out[i].nz) // int(out[i].slab_planes))
+        t = with_plan(out[i], slabs, int(out[i].temporal_depth), int(out[i].rate_bits))
+        if t is None:
+            raise O.OOCSError(2, "the batch does not fit the budget")
+        out[i] = t
+        report[i]["slabs"] = slabs
+    if cache_path:
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    return out, {"problems": report, "candidates_timed": timed, "classes": len({r["class"] for r in report})}

@@ -426,7 +426,9 @@ class OutOfCoreStencil:
     Streams: three ``torch.cuda.Stream`` objects.
     """
 
-    def __init__(self, desc: oocs_desc, device: int = 0):
+    def __init__(self, desc: oocs_desc, device: int = 0, stores=None):
+        """stores: optional pinned uint8 tensors (one per field, each at least
+        plan.host_store_bytes) to bind instead of allocating new ones."""
         import torch
         self.torch = torch
         self.desc = desc
@@ -443,7 +445,10 @@ class OutOfCoreStencil:
         nfields = 3 if desc.scheme == OOCS_WAVE else 1
         self.stores = []
         for f in range(nfields):
-            st = torch.zeros(self.plan.host_store_bytes, dtype=torch.uint8, pin_memory=True)
+            if stores is not None:
+                st = stores[f][:self.plan.host_store_bytes]
+            else:
+                st = torch.zeros(self.plan.host_store_bytes, dtype=torch.uint8, pin_memory=True)
             oocs_bind_field(self.ctx, f, st.data_ptr(), st.numel())
             self.stores.append(st)
         self._keep = []

@@ -196,3 +196,26 @@ def blocks_field(shape, seed: int, kind: str) -> np.ndarray:
 
 TOL_UNCOMPRESSED = {"heat": 1e-6, "wave": 1e-5}
 TOL_COMPRESSED = {16: 1e-4, 12: 2e-3, 8: 3e-2}
+
+
+# ----------------------------------------------------------------------------
+# Batched workload: many independent problems of uneven size
+# ----------------------------------------------------------------------------
+
+def batch_shapes(n: int, seed: int = 9, lo: int = 64, hi: int = 384, step: int = 16):
+    """n (scheme, (nz, ny, nx)) pairs: every side drawn independently from
+    {lo, lo + step, ..., hi}, heat and wave alternating."""
+    k = (hi - lo) // step + 1
+    u = uniform01(seed, 3 * n)
+    sides = (lo + step * np.minimum((u * k).astype(np.int64), k - 1)).reshape(n, 3)
+    return [("heat" if i % 2 == 0 else "wave", tuple(int(v) for v in sides[i])) for i in range(n)]
+
+
+def wave_initial(shape, seed: int, amplitude: float = 1e-3) -> np.ndarray:
+    """FP32 amplitude * U[0,1) field with the 4-wide shell of the 25-point star zeroed."""
+    nz, ny, nx = shape
+    f = (amplitude * uniform01(seed, nz * ny * nx)).astype(np.float32).reshape(nz, ny, nx)
+    f[:4] = f[-4:] = 0.0
+    f[:, :4] = f[:, -4:] = 0.0
+    f[:, :, :4] = f[:, :, -4:] = 0.0
+    return f

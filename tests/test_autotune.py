@@ -1,0 +1,90 @@
+"""Host logic of the autotuner (no GPU): candidate plans, classes, the cache,
+and fitting a batch into its budget.  Timing is replaced by a cost model."""
+import json
+
+import pytest
+
+import synthetic
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2204_11315_gb300 as P
+    P.lib()
+    return P
+
+
+@pytest.fixture
+def A(monkeypatch):
+    from paper_2204_11315_gb300 import autotune as A
+    calls = []
+
+    def fake_time(desc, steps, probe=None):
+        # cheaper with fewer slabs, k = 4 and lower rates
+        S = -(-int(desc.nz) // int(desc.slab_planes))
+        calls.append((int(desc.nz), S, int(desc.temporal_depth), int(desc.rate_bits)))
+        return 1.0 * S + abs(int(desc.temporal_depth) - 4) * 0.1 + int(desc.rate_bits) * 0.01
+
+    class NoProbe:
+        def __init__(self, desc, seed=0):
+            pass
+
+    monkeypatch.setattr(A, "time_candidate", fake_time)
+    monkeypatch.setattr(A, "_Probe", NoProbe)
+    A.calls = calls
+    return A
+
+
+def _wave(P, nz, ny, nx, budget=8 << 30):
+    return P.make_desc(nx, ny, nz, P.OOCS_WAVE, synthetic.wave_star_coef(), budget)
+
+
+def _heat(P, nz, ny, nx, budget=8 << 30):
+    return P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), budget)
+
+
+def test_rates_follow_the_tolerance(A):
+    assert A.rates_for(1e-4) == [16]
+    assert A.rates_for(2e-3) == [12, 16]
+    assert A.rates_for(0.05) == [8, 12, 16]
+    assert A.rates_for(1e-6) == [0]
+
+
+def test_candidate_plans_respect_region_sharing(P, A):
+    d = _wave(P, 64, 64, 64)
+    # k = 4, r = 4: h = 16, so four slabs of 16 planes (< 2h) are not a plan
+    assert A.with_plan(d, 4, 4, 16) is None
+    two = A.with_plan(d, 2, 4, 16)
+    assert (two.slab_planes, two.temporal_depth, two.rate_bits) == (32, 4, 16)
+    assert P.oocs_query(two).num_slabs == 2
+    one = A.with_plan(_heat(P, 100, 36, 44), 1, 8, 12)
+    assert P.oocs_query(one).num_slabs == 1
+
+
+def test_tune_picks_the_fastest_and_reuses_classes(P, A, tmp_path):
+    cache = tmp_path / "tune.json"
+    descs = [_wave(P, 128, 128, 128), _wave(P, 128, 128, 124), _heat(P, 96, 96, 96)]
+    out, rep = A.tune(descs, 2e-3, 8 << 30, str(cache))
+    assert rep["classes"] == 2  # the two wave grids share a class
+    for d in out:
+        assert P.oocs_query(d).num_slabs == 1
+        assert int(d.temporal_depth) == 4 and int(d.rate_bits) == 12
+    n_timed = len(A.calls)
+    assert rep["candidates_timed"] == n_timed
+    # cached: nothing is timed again
+    out2, rep2 = A.tune(descs, 2e-3, 8 << 30, str(cache))
+    assert rep2["candidates_timed"] == 0 and len(A.calls) == n_timed
+    assert [(int(a.slab_planes), int(a.temporal_depth)) for a in out] == \
+        [(int(a.slab_planes), int(a.temporal_depth)) for a in out2]
+    assert set(json.loads(cache.read_text())) == {r["class"] for r in rep["problems"]}
+
+
+def test_batch_is_fitted_into_the_budget(P, A):
+    """One slab each is fastest, but the shared workspace must fit: the largest
+    windows are split into more slabs until it does."""
+    descs = [_wave(P, 384, 384, 384), _wave(P, 64, 64, 64), _heat(P, 256, 256, 256)]
+    loose, _ = A.tune(descs, 1e-4, 8 << 30)
+    budget = P.oocs_batch_query(loose) // 2
+    tight, rep = A.tune(descs, 1e-4, budget)
+    assert P.oocs_batch_query(tight) <= budget
+    assert P.oocs_query(tight[0]).num_slabs > 1

@@ -156,3 +156,25 @@ def test_capture_refuses_a_time_dependent_source(P):
         b.synchronize(60.0)
     finally:
         b.close()
+
+
+def test_tuned_problems_run_as_a_batch(P, tmp_path):
+    """The autotuner times real candidates and returns plans that run as a batch
+    (and give the stores of each problem run alone)."""
+    torch_cuda()
+    from paper_2204_11315_gb300 import autotune
+    probs = _problems(P, with_source=False)[1:3]
+    descs, rep = autotune.tune([d for d, _, _ in probs], 2e-3, 2 << 30, str(tmp_path / "t.json"), steps=2)
+    assert rep["candidates_timed"] > 0
+    assert all(r["rate"] in (12, 16) for r in rep["problems"])
+    tuned = [(d, f, s) for d, (_, f, s) in zip(descs, probs)]
+    b = _batch(P, tuned)
+    try:
+        b.step(6)
+        b.synchronize(120.0)
+        got = [[s.numpy().copy() for s in bp.stores] for bp in b.problems]
+    finally:
+        b.close()
+    for i, (d, fields, src) in enumerate(tuned):
+        ref, _ = _alone(P, d, fields, src, [6])
+        assert np.array_equal(got[i][0], ref[0])
