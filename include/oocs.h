@@ -169,6 +169,22 @@ oocs_status oocs_compress(oocs_ctx *ctx, int32_t field, const float *src);
  * FP32 host array `dst` of nx*ny*nz values.  Asynchronous.                 */
 oocs_status oocs_decompress(oocs_ctx *ctx, int32_t field, float *dst);
 
+/* Planes [z0, z0 + nplanes) (whole 4-plane layers) of `field` between a
+ * device FP32 array holding exactly those planes and the bound host store:
+ * oocs_compress_device encodes them into their store layers (a copy at rate
+ * 0), oocs_decompress_device decodes them back.  For filling or reading a
+ * store larger than any host staging array.  Runs on streams[0], so the
+ * device array must be complete in that stream's order (data written on
+ * another stream: synchronize it first); asynchronous (the array must stay
+ * valid until oocs_synchronize).                                           */
+oocs_status oocs_compress_device(oocs_ctx *ctx, int32_t field, const float *src, int64_t z0, int64_t nplanes);
+oocs_status oocs_decompress_device(oocs_ctx *ctx, int32_t field, float *dst, int64_t z0, int64_t nplanes);
+
+/* Page-locked host memory of exactly `bytes` (cudaHostAlloc, portable) for
+ * host stores; free with oocs_host_free.  OOCS_ERR_HOST_ALLOC if it fails.  */
+oocs_status oocs_host_alloc(uint64_t bytes, void **ptr);
+oocs_status oocs_host_free(void *ptr);
+
 /* Set the context's global time index t (the index of the source sample the
  * next step adds; 0 after oocs_create).  For restarting from a stored state.
  * Takes effect for work enqueued after the call.                           */

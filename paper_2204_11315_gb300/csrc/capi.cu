@@ -1020,6 +1020,87 @@ oocs_status oocs_decompress(oocs_ctx *ctx, int32_t field, float *dst)
     return codec_field(ctx, field, nullptr, dst, false);
 }
 
+// Planes [z0, z0 + nplanes) of `field` between a device array holding them
+// and the host store, in chunks of T planes through working buffer 0 and the
+// first out (encode) or in (decode) slot of field 0, on stream 0.
+static oocs_status codec_range_device(oocs_ctx *ctx, int32_t field, const float *src, float *dst, int64_t z0,
+                                      int64_t nplanes, bool enc)
+{
+    oocs_status s = check_ready(ctx);
+    if (s != OOCS_OK)
+        return s;
+    const int nf = ctx->d.scheme == OOCS_WAVE ? 3 : 1;
+    if (field < 0 || field >= nf || !ctx->store[field])
+        return fail(ctx, OOCS_ERR_STATE, "field is not bound");
+    const oocs_desc &d = ctx->d;
+    if ((enc ? !src : !dst) || (reinterpret_cast<uintptr_t>(enc ? (const void *)src : (const void *)dst) & 15))
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "device array must be non-null and 16-byte aligned");
+    if (z0 < 0 || nplanes < 0 || z0 % 4 || nplanes % 4 || z0 + nplanes > d.nz)
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "planes must be whole 4-plane layers inside the grid");
+    if (enc && field == OOCS_FIELD_M)
+        ctx->ro_dirty = true;
+    s = join_streams(ctx);
+    if (s != OOCS_OK)
+        return s;
+    cudaStream_t st = ctx->st[0];
+    const int64_t plane = d.nx * d.ny;
+    const int64_t T = ctx->v.T;  // the slots hold at least T/4 layers
+    for (int64_t c0 = 0; c0 < nplanes; c0 += T) {
+        const int64_t n = std::min<int64_t>(T, nplanes - c0);
+        char *host = ctx->store[field] + (uint64_t)((z0 + c0) / 4) * ctx->v.layer_bytes;
+        const uint64_t cbytes = (uint64_t)n / 4 * ctx->v.layer_bytes;
+        if (d.rate_bits == 0) {
+            if (enc)
+                CU(ctx, cudaMemcpyAsync(host, src + c0 * plane, cbytes, cudaMemcpyDeviceToHost, st));
+            else
+                CU(ctx, cudaMemcpyAsync(dst + c0 * plane, host, cbytes, cudaMemcpyHostToDevice, st));
+        } else if (enc) {
+            char *blk = ctx->out_slot(0, 0);
+            CU(ctx, launch_encode_layers(src + c0 * plane, d.nx, d.ny, n / 4, d.rate_bits, blk, st));
+            CU(ctx, cudaMemcpyAsync(host, blk, cbytes, cudaMemcpyDeviceToHost, st));
+        } else {
+            char *blk = ctx->in_slot(0, 0);
+            CU(ctx, cudaMemcpyAsync(blk, host, cbytes, cudaMemcpyHostToDevice, st));
+            CU(ctx, launch_decode_layers(blk, d.nx, d.ny, n / 4, d.rate_bits, dst + c0 * plane, st));
+        }
+    }
+    return join_streams(ctx);
+}
+
+oocs_status oocs_compress_device(oocs_ctx *ctx, int32_t field, const float *src, int64_t z0, int64_t nplanes)
+{
+    return codec_range_device(ctx, field, src, nullptr, z0, nplanes, true);
+}
+
+oocs_status oocs_decompress_device(oocs_ctx *ctx, int32_t field, float *dst, int64_t z0, int64_t nplanes)
+{
+    return codec_range_device(ctx, field, nullptr, dst, z0, nplanes, false);
+}
+
+oocs_status oocs_host_alloc(uint64_t bytes, void **ptr)
+{
+    if (!ptr || bytes == 0)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "bytes > 0 and an output pointer are required");
+    *ptr = nullptr;
+    cudaError_t e = cudaHostAlloc(ptr, bytes, cudaHostAllocPortable);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(nullptr, OOCS_ERR_HOST_ALLOC,
+                    "cudaHostAlloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+    return OOCS_OK;
+}
+
+oocs_status oocs_host_free(void *ptr)
+{
+    if (ptr && cudaFreeHost(ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "not a pointer from oocs_host_alloc");
+    }
+    return OOCS_OK;
+}
+
 oocs_status oocs_set_time(oocs_ctx *ctx, int64_t t)
 {
     oocs_status s = check_ready(ctx);

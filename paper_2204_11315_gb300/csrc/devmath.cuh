@@ -17,6 +17,44 @@ OOCS_FN float fmul_rn(float a, float b) { return __fmul_rn(a, b); }
 OOCS_FN float fadd_rn(float a, float b) { return __fadd_rn(a, b); }
 OOCS_FN float fsub_rn(float a, float b) { return __fsub_rn(a, b); }
 OOCS_FN float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// Packed pairs (sm_100 family f32x2 instructions): each lane of a pair is one
+// IEEE round-to-nearest FP32 operation, exactly the scalar forms above.
+OOCS_FN unsigned long long pk2(float2 v)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+OOCS_FN float2 upk2(unsigned long long r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+OOCS_FN float2 fadd2_rn(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+OOCS_FN float2 fsub2_rn(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+OOCS_FN float2 fmul2_rn(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+OOCS_FN float2 fma2_rn(float2 a, float2 b, float2 c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+    return upk2(d);
+}
 // index of the lowest set bit of a non-zero word
 OOCS_FN int ctz64(uint64_t x) { return __ffsll((long long)x) - 1; }
 OOCS_FN int ctz32(uint32_t x) { return __ffs((int)x) - 1; }

@@ -354,6 +354,37 @@ __global__ void __launch_bounds__(kStepThreads, 2)
                         if (rcv_plane)
                             rv = __ldg(reinterpret_cast<const float2 *>(a.res + (int64_t)y * a.nx + x));
                     }
+                    if constexpr (kFast) {
+                        // every point interior, no source or receiver: the pair of
+                        // x-adjacent points in packed f32x2 operations
+                        float2 s2[R + 1];
+                        s2[0] = make_float2(0.0f, 0.0f);
+#pragma unroll
+                        for (int d = 1; d <= R; ++d) {
+                            const float2 ym = (r - d >= 0) ? q[(r - d) >= 0 ? r - d : 0][R]
+                                                           : above[(d - r - 1) >= 0 ? d - r - 1 : 0];
+                            const float2 yp = (r + d < kRPT) ? q[(r + d) < kRPT ? r + d : 0][R]
+                                                             : below[(r + d - kRPT) >= 0 ? r + d - kRPT : 0];
+                            s2[d] = nbr_sum2(make_float2(xv[4 - d], xv[5 - d]), make_float2(xv[4 + d], xv[5 + d]),
+                                             ym, yp, q[r][R - d], q[r][R + d]);
+                        }
+                        const float2 L2 = star_L2<R>(a.c, uc, s2);
+                        float2 o2;
+                        if constexpr (SCHEME == kHeat) {
+                            o2 = L2;
+                        } else if constexpr (SCHEME == kWave) {
+                            o2 = wave_update2(L2, uc, cv[0], cv[1]);
+                        } else if constexpr (SCHEME == kAdjoint) {
+                            o2 = adjoint_update2(L2, cv[2], cv[0]);
+                        } else {
+                            o2 = fma2_rn(cv[1], L2, cv[0]);
+                        }
+                        const int64_t o = (int64_t)z * a.plane + (int64_t)y * a.nx + x;
+                        *reinterpret_cast<float2 *>(a.out + o) = o2;
+                        if constexpr (SCHEME == kAdjoint)
+                            *reinterpret_cast<float2 *>(a.out2 + o) = fmul2_rn(cv[1], o2);
+                        continue;
+                    }
                     float res[kVX];
                     [[maybe_unused]] float res2[kVX];
 #pragma unroll

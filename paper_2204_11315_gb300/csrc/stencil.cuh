@@ -58,4 +58,31 @@ OOCS_FN float gradient_update(float L, float lam, float g, bool at_src, float w)
     return fma_rn(lam, at_src ? fadd_rn(L, w) : L, g);
 }
 
+// The same operations on a pair of x-adjacent points (f32x2), for points
+// without a source or receiver term: lane by lane the scalar forms above.
+OOCS_FN float2 nbr_sum2(float2 xm, float2 xp, float2 ym, float2 yp, float2 zm, float2 zp)
+{
+    return fadd2_rn(fadd2_rn(fadd2_rn(xm, xp), fadd2_rn(ym, yp)), fadd2_rn(zm, zp));
+}
+
+template <int R>
+OOCS_FN float2 star_L2(const StarCoef &c, float2 u, const float2 (&s)[R + 1])
+{
+    float2 L = fmul2_rn(make_float2(c.c[0], c.c[0]), u);
+#pragma unroll
+    for (int d = 1; d <= R; ++d)
+        L = fma2_rn(make_float2(c.c[d], c.c[d]), s[d], L);
+    return L;
+}
+
+OOCS_FN float2 wave_update2(float2 L, float2 u, float2 up, float2 m)
+{
+    return fma2_rn(m, L, fsub2_rn(fadd2_rn(u, u), up));
+}
+
+OOCS_FN float2 adjoint_update2(float2 L, float2 lam, float2 lam_pp)
+{
+    return fadd2_rn(fsub2_rn(fadd2_rn(lam, lam), lam_pp), L);
+}
+
 }  // namespace oocs

@@ -146,6 +146,10 @@ SIGNATURES = {
     "oocs_batch_destroy": (_i32, [_vp]),
     "oocs_batch_trace_schedule": (_i32, [ctypes.POINTER(oocs_desc), _i32, ctypes.POINTER(_i32), _i32,
                                          ctypes.POINTER(oocs_trace_op), _i64, ctypes.POINTER(_i64)]),
+    "oocs_compress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
+    "oocs_decompress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
+    "oocs_host_alloc": (_i32, [_u64, ctypes.POINTER(_vp)]),
+    "oocs_host_free": (_i32, [_vp]),
     "oocs_encode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
     "oocs_decode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
 }
@@ -406,6 +410,40 @@ def oocs_misfit_backward(desc, m_ptr, src, w, zr, res_ptr, nsteps, checkpoint_ev
                                       wv.ctypes.data_as(_vp), int(wv.size), int(zr), _vp(res_ptr),
                                       int(nsteps), int(checkpoint_every), int(rate_bits), _vp(ws_ptr),
                                       int(ws_bytes), _vp(grad_ptr), _vp(stream)))
+
+
+def oocs_compress_device(ctx, field, src_ptr, z0, nplanes):
+    _check(lib().oocs_compress_device(_vp(ctx), int(field), _vp(src_ptr), int(z0), int(nplanes)), ctx)
+
+
+def oocs_decompress_device(ctx, field, dst_ptr, z0, nplanes):
+    _check(lib().oocs_decompress_device(_vp(ctx), int(field), _vp(dst_ptr), int(z0), int(nplanes)), ctx)
+
+
+class HostBuffer:
+    """Page-locked host memory of an exact size (oocs_host_alloc), viewable as
+    a uint8 torch tensor; freed by close() or garbage collection."""
+
+    def __init__(self, nbytes: int):
+        p = _vp()
+        _check(lib().oocs_host_alloc(int(nbytes), ctypes.byref(p)))
+        self.ptr, self.nbytes = p.value, int(nbytes)
+
+    def tensor(self):
+        import torch
+        arr = np.ctypeslib.as_array((ctypes.c_uint8 * self.nbytes).from_address(self.ptr))
+        return torch.from_numpy(arr)
+
+    def close(self):
+        if self.ptr:
+            lib().oocs_host_free(_vp(self.ptr))
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def oocs_encode_device(field_ptr, nx, ny, nz, rate, blocks_ptr, stream=0):

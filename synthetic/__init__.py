@@ -219,3 +219,46 @@ def wave_initial(shape, seed: int, amplitude: float = 1e-3) -> np.ndarray:
     f[:, :4] = f[:, -4:] = 0.0
     f[:, :, :4] = f[:, :, -4:] = 0.0
     return f
+
+
+# ----------------------------------------------------------------------------
+# The same generator in PyTorch (for fields too large to draw on the host)
+# ----------------------------------------------------------------------------
+
+def _signed(u: int) -> int:
+    return u - (1 << 64) if u >= (1 << 63) else u
+
+
+def _srl(torch, x, k: int):
+    """Logical right shift of int64 lanes holding uint64 bit patterns."""
+    return (x >> k) & ((1 << (64 - k)) - 1)
+
+
+def uniform01_torch(seed: int, n: int, offset: int = 0, stream: int = 0, device="cpu"):
+    """uniform01(seed, n, stream, offset) as an FP32 torch tensor on `device`,
+    bit for bit (int64 lanes wrap like uint64 for +, *, ^ and masked shifts)."""
+    import torch
+    key = _signed(int(_key(seed, stream)))
+    z = torch.arange(offset, offset + n, dtype=torch.int64, device=device) + key
+    z = z + _signed(int(_GOLDEN))
+    z = (z ^ _srl(torch, z, 30)) * _signed(int(_M1))
+    z = (z ^ _srl(torch, z, 27)) * _signed(int(_M2))
+    z = z ^ _srl(torch, z, 31)
+    bits = _srl(torch, z, 40)
+    return bits.to(torch.float32) * (1.0 / 16777216.0)
+
+
+def uniform_field_planes_torch(shape, seed: int, z0: int, z1: int, device="cpu"):
+    """Planes [z0, z1) of uniform_field(shape, seed) as a torch tensor on `device`."""
+    nz, ny, nx = shape
+    plane = ny * nx
+    f = uniform01_torch(seed, (z1 - z0) * plane, offset=z0 * plane, device=device).reshape(z1 - z0, ny, nx)
+    if z0 == 0:
+        f[0] = 0.0
+    if z1 == nz:
+        f[-1] = 0.0
+    f[:, 0] = 0.0
+    f[:, -1] = 0.0
+    f[:, :, 0] = 0.0
+    f[:, :, -1] = 0.0
+    return f
