@@ -557,6 +557,7 @@ def run_batched(P, torch, dev):
     l0 = sum(bp.stats()["kernel_launches"] for bp in b.problems)
     ms_batch = timed(lambda: b.step(BATCH_STEPS), s0)
     launches_per_step = sum(bp.stats()["kernel_launches"] for bp in b.problems) - l0
+    after_batch = [[s.clone() for s in bp.stores] for bp in b.problems]
     restore()
     b.capture(BATCH_STEPS)
     b.launch()  # warm-up replay
@@ -579,6 +580,8 @@ def run_batched(P, torch, dev):
             ms_alone += e0.elapsed_time(e1)
         finally:
             st.close()
+    # every problem ends with the same host store bytes either way
+    identical = all(torch.equal(a, s) for ab, bp in zip(after_batch, b.problems) for a, s in zip(ab, bp.stores))
     b.close()
     pts = sum((int(d.nx) - 2 * d.radius) * (int(d.ny) - 2 * d.radius) * (int(d.nz) - 2 * d.radius)
               for d in tuned) * BATCH_STEPS
@@ -594,6 +597,7 @@ def run_batched(P, torch, dev):
             "batch_step": {"value": gpts(ms_batch), "ms": ms_batch},
             "each_alone": {"value": gpts(ms_alone), "ms": ms_alone},
             "speedup_graph_vs_alone": ms_alone / ms_graph,
+            "stores_identical_batch_vs_alone": identical,
             "interior_point_updates": pts, "workspace_bytes": P.oocs_batch_query(tuned),
             "sum_of_alone_workspaces": int(sum(ws_alone)), "kernel_launches_per_batch_step": launches_per_step,
             "tuning": {"seconds": t_tune, "classes": report["classes"],

@@ -276,3 +276,33 @@ def test_driver_matches_per_step_entry_points(P, K):
     assert J_ref > 0
     assert abs(float(mis.item()) - J_ref) <= 1e-12 * J_ref  # double accumulation order may differ
     assert torch.equal(g, g_ref)
+
+
+@pytest.mark.slow
+def test_dot_product_at_workload_size(P):
+    """<F^N x, y> = <x, (F^T)^N y> on the adjoint workload's grid and length
+    (256^3, N = 400 GPU steps, FP32; x, y seeded interior fields)."""
+    torch = torch_cuda()
+    shape = (256, 256, 256)
+    N = 400
+    rng = np.random.default_rng(11)
+    desc = _desc(P, shape)
+    m = synthetic.wave_model(shape)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    s = torch.cuda.current_stream().cuda_stream
+    u0, up0, y1, y2 = (_interior(shape, rng) for _ in range(4))
+    U, UP, M, SC = T(u0), T(up0), T(m), torch.empty(shape, device="cuda")
+    P.oocs_incore_run(desc, U.data_ptr(), UP.data_ptr(), M.data_ptr(), SC.data_ptr(), N, 0, None, None, s)
+    LAM, LP = T(y1), T(-y2)
+    MU, MO = T(m * y1), torch.empty(shape, device="cuda")
+    for _ in range(N):
+        P.oocs_adjoint_step(desc, LAM.data_ptr(), LP.data_ptr(), MU.data_ptr(), MO.data_ptr(), M.data_ptr(),
+                            0, -1, s)
+        LAM, LP = LP, LAM
+        MU, MO = MO, MU
+    torch.cuda.synchronize()
+    d = lambda a, b: float(torch.dot(a.double().ravel(), b.double().ravel()))
+    lhs = d(U, T(y1)) + d(UP, T(y2))
+    rhs = d(T(u0), LAM) - d(T(up0), LP)
+    scale = (float(U.double().norm()) * np.linalg.norm(y1) + float(UP.double().norm()) * np.linalg.norm(y2))
+    assert abs(lhs - rhs) <= 1e-4 * scale, (lhs, rhs, scale)

@@ -197,3 +197,19 @@ def test_restore_and_set_time_repeat_the_run(P):
     for a, b in zip(outs[0], outs[1]):
         assert np.array_equal(a, b)
     assert not np.array_equal(outs[0][0], snap[0].numpy())
+
+
+@pytest.mark.slow
+def test_wave_benchmark_plan_within_tolerance_of_oracle(P, orc):
+    """The benchmark's exact configuration and plan (512^3, 100 steps, rate 16,
+    m on the device, 8 slabs of 64, k = 4, one working buffer) against the
+    FP64 oracle over the whole grid."""
+    shape = (512, 512, 512)
+    steps = 100
+    m, w, src, z = _wave_inputs(shape, steps)
+    desc = wave_desc(P, shape, rate=16, k=4, T=64, budget=4 << 30, ro=1)
+    gu, gup, _, stats, plan = streamed(P, desc, z, steps, up0=z, m=m, src=src, w=w)
+    assert plan.num_slabs == 8 and plan.readonly_resident == 1 and plan.workspace_bytes <= 4 << 30
+    ru, rup = orc.wave_run(z, z, m, synthetic.wave_star_coef(), steps, src=synthetic.centre(shape), w=w)
+    assert rel_l2(gu, ru) <= synthetic.TOL_COMPRESSED[16]
+    assert rel_l2(gup, rup) <= synthetic.TOL_COMPRESSED[16]
