@@ -389,9 +389,12 @@ oocs_status oocs_batch_step(oocs_batch *batch, int32_t nsteps);
  * problems' time indices and stats are unchanged), and replay it with
  * oocs_batch_launch, which advances every problem by nsteps per call with one
  * graph launch instead of thousands of launches and copies.  A replay always
- * follows all previously enqueued work.  OOCS_ERR_UNSUPPORTED if a problem has
- * a source with amplitudes (they are kernel arguments of the captured steps);
- * OOCS_ERR_STATE while profiling is on.  A new capture replaces the old one. */
+ * follows all previously enqueued work, and may be mixed with direct steps.
+ * Source amplitudes are read at replay time from a device copy of the
+ * wavelet (made by oocs_set_source) at each problem's current time index, so
+ * replays give the same results as direct steps.  OOCS_ERR_UNSUPPORTED if a
+ * wavelet has more than 65536 samples; OOCS_ERR_STATE while profiling is on.
+ * A new capture replaces the old one.                                      */
 oocs_status oocs_batch_capture(oocs_batch *batch, int32_t nsteps);
 oocs_status oocs_batch_launch(oocs_batch *batch);
 

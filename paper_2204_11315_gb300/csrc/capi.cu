@@ -62,6 +62,7 @@ struct Layout {
     uint64_t out_off[3][2];   // [slot][field_out]
     uint64_t ro_off;          // resident FP32 copy of M (readonly_resident), else 0
     uint64_t ro_bytes;
+    uint64_t src_off;         // wave: device time index + wavelet (graph replays), else 0
     uint64_t total;
     int nwb;                  // working buffers (1 SWB, 3 classic)
     int nbuf;                 // buffers per working set (heat 2, wave 3)
@@ -69,6 +70,10 @@ struct Layout {
     uint64_t in_slot_bytes;   // one staging slot of one field
     uint64_t out_slot_bytes;
 };
+
+// wavelet samples a context keeps on the device for replayed graphs
+constexpr int64_t kMaxDeviceWavelet = 1 << 16;
+constexpr uint64_t kSrcRegionBytes = 256 + (uint64_t)kMaxDeviceWavelet * 4;
 
 struct Derived {
     int r, k, h, T, S, wp, fin, fout;
@@ -129,6 +134,10 @@ Layout layout_for(const oocs_desc &d, const Derived &v, int nwb)
         L.ro_off = off;
         L.ro_bytes = align_up((uint64_t)d.nz * d.nx * d.ny * 4, 256);
         off += L.ro_bytes;
+    }
+    if (d.scheme == OOCS_WAVE) {
+        L.src_off = off;
+        off += kSrcRegionBytes;
     }
     L.total = off;
     return L;
@@ -312,6 +321,9 @@ struct oocs_ctx {
     char *in_slot(int q, int f) const { return ws + L.in_off[q][f]; }
     char *out_slot(int q, int f) const { return ws + L.out_off[q][f]; }
     float *ro_m() const { return reinterpret_cast<float *>(ws + L.ro_off); }
+    int64_t *t_dev() const { return reinterpret_cast<int64_t *>(ws + L.src_off); }
+    float *w_dev() const { return reinterpret_cast<float *>(ws + L.src_off + 256); }
+    int64_t t_capture = 0;  // time index when the batch's graph was captured
 };
 
 // A batch of independent problems advanced through one Algorithm-1 pipeline:
@@ -763,7 +775,19 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         const int64_t tstep = t + j - 1;
         Ls.src_z = -1;
         Ls.w = 0.0f;
-        if (c->has_src && tstep < (int64_t)c->w.size()) {
+        Ls.w_dev = nullptr;
+        Ls.t_dev = nullptr;
+        if (c->has_src && c->batch && c->batch->capturing) {
+            // recorded in a graph: the amplitude is read at replay time from
+            // the device wavelet at the replay's own time index
+            Ls.src_x = c->src[0];
+            Ls.src_y = c->src[1];
+            Ls.src_z = c->src[2];
+            Ls.w_dev = c->w_dev();
+            Ls.t_dev = c->t_dev();
+            Ls.t_rel = tstep - c->t_capture;
+            Ls.nw = (int64_t)c->w.size();
+        } else if (c->has_src && tstep < (int64_t)c->w.size()) {
             Ls.src_x = c->src[0];
             Ls.src_y = c->src[1];
             Ls.src_z = c->src[2];
@@ -955,6 +979,10 @@ oocs_status oocs_set_source(oocs_ctx *ctx, int64_t x, int64_t y, int64_t z, cons
     ctx->src[1] = y;
     ctx->src[2] = z;
     ctx->w.assign(w, w + nw);
+    // the device copy read by replayed graphs (at most kMaxDeviceWavelet samples)
+    const int64_t nd = std::min<int64_t>(nw, kMaxDeviceWavelet);
+    if (nd > 0 && !ctx->trace && ctx->L.src_off)
+        CU(ctx, cudaMemcpyAsync(ctx->w_dev(), ctx->w.data(), (size_t)nd * 4, cudaMemcpyHostToDevice, ctx->st[0]));
     return OOCS_OK;
 }
 
@@ -1441,7 +1469,7 @@ namespace {
 // all problems' visits use the same working buffer and staging slots), then
 // one resident FP32 model per problem that keeps it on the device.
 Layout batch_layout(const std::vector<oocs_desc> &d, const std::vector<Derived> &v, std::vector<uint64_t> &ro_off,
-                    std::vector<uint64_t> &ro_bytes)
+                    std::vector<uint64_t> &ro_bytes, std::vector<uint64_t> &src_off)
 {
     Layout L;
     memset(&L, 0, sizeof(L));
@@ -1479,6 +1507,12 @@ Layout batch_layout(const std::vector<oocs_desc> &d, const std::vector<Derived> 
             ro_bytes[i] = align_up((uint64_t)d[i].nz * d[i].nx * d[i].ny * 4, 256);
             off += ro_bytes[i];
         }
+    src_off.assign(d.size(), 0);
+    for (size_t i = 0; i < d.size(); ++i)
+        if (d[i].scheme == OOCS_WAVE) {
+            src_off[i] = off;
+            off += kSrcRegionBytes;
+        }
     L.total = off;
     return L;
 }
@@ -1515,8 +1549,8 @@ oocs_status batch_plans(const oocs_desc *descs, int32_t n, std::vector<oocs_desc
 oocs_status batch_build(oocs_batch *b, const std::vector<oocs_desc> &d, const std::vector<oocs_plan> &p,
                         const std::vector<Derived> &v, char *ws)
 {
-    std::vector<uint64_t> ro_off, ro_bytes;
-    const Layout L = batch_layout(d, v, ro_off, ro_bytes);
+    std::vector<uint64_t> ro_off, ro_bytes, src_off;
+    const Layout L = batch_layout(d, v, ro_off, ro_bytes, src_off);
     b->ws = ws;
     int d2h_base = 0;
     for (size_t i = 0; i < d.size(); ++i) {
@@ -1532,6 +1566,7 @@ oocs_status batch_build(oocs_batch *b, const std::vector<oocs_desc> &d, const st
         c->L = L;
         c->L.ro_off = ro_off[i];
         c->L.ro_bytes = ro_bytes[i];
+        c->L.src_off = src_off[i];
         c->ws = ws;
         for (int k = 0; k < 3; ++k) {
             c->st[k] = b->st[k];
@@ -1704,8 +1739,8 @@ oocs_status oocs_batch_query(const oocs_desc *descs, int32_t n, uint64_t *worksp
     oocs_status s = batch_plans(descs, n, d, p, v, err);
     if (s != OOCS_OK)
         return fail(nullptr, s, err);
-    std::vector<uint64_t> ro_off, ro_bytes;
-    *workspace_bytes = batch_layout(d, v, ro_off, ro_bytes).total;
+    std::vector<uint64_t> ro_off, ro_bytes, src_off;
+    *workspace_bytes = batch_layout(d, v, ro_off, ro_bytes, src_off).total;
     return OOCS_OK;
 }
 
@@ -1722,8 +1757,8 @@ oocs_status oocs_batch_create(const oocs_desc *descs, int32_t n, void *workspace
     oocs_status s = batch_plans(descs, n, d, p, v, err);
     if (s != OOCS_OK)
         return fail(nullptr, s, err);
-    std::vector<uint64_t> ro_off, ro_bytes;
-    const uint64_t need = batch_layout(d, v, ro_off, ro_bytes).total;
+    std::vector<uint64_t> ro_off, ro_bytes, src_off;
+    const uint64_t need = batch_layout(d, v, ro_off, ro_bytes, src_off).total;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
     if (workspace_bytes < need)
@@ -1795,12 +1830,13 @@ oocs_status oocs_batch_capture(oocs_batch *b, int32_t nsteps)
     if (nsteps < 1)
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "nsteps must be >= 1");
     for (oocs_ctx *c : b->ctx) {
-        if (c->has_src && !c->w.empty())
+        if (c->has_src && (int64_t)c->w.size() > kMaxDeviceWavelet)
             return fail(nullptr, OOCS_ERR_UNSUPPORTED,
-                        "a problem has a time-dependent source: its amplitudes are kernel arguments, "
-                        "so a replayed graph would repeat them; use oocs_batch_step");
+                        "a source wavelet longer than " + std::to_string(kMaxDeviceWavelet) +
+                            " samples cannot be read by a replayed graph; use oocs_batch_step");
         if (c->prof)
             return fail(nullptr, OOCS_ERR_STATE, "turn profiling off before capturing");
+        c->t_capture = (int64_t)c->stats.steps_done;
     }
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
@@ -1827,6 +1863,12 @@ oocs_status oocs_batch_capture(oocs_batch *b, int32_t nsteps)
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(b->st[0], &graph);
     b->capturing = false;
+    // an event last recorded inside a capture cannot be waited on outside it:
+    // record each again, for real, on stream 0 (the capture ran nothing, and
+    // later calls are ordered by their opening join anyway)
+    for (cudaEvent_t ev : b->cap_recorded)
+        if (cudaEventRecord(ev, b->st[0]) != cudaSuccess && e == cudaSuccess)
+            e = cudaGetLastError();
     if (s == OOCS_OK && e == cudaSuccess)
         e = cudaGraphInstantiate(&b->exec, graph, 0);
     if (graph)
@@ -1865,6 +1907,10 @@ oocs_status oocs_batch_launch(oocs_batch *b)
     oocs_ctx *c0 = b->ctx[0];
     SCHED(join_streams(c0));
     SCHED(batch_uploads(b));
+    // the time index each problem's replayed source steps count from
+    for (oocs_ctx *c : b->ctx)
+        if (c->has_src)
+            CU(c0, launch_set_i64(c->t_dev(), (int64_t)c->stats.steps_done, b->st[0]));
     SCHED(join_streams(c0));
     CU(c0, cudaGraphLaunch(b->exec, b->st[0]));
     // later work on streams 1 and 2 follows the graph

@@ -88,7 +88,25 @@ struct StepArgs {
     StarCoef c;
     int src_x, src_y, src_zw;
     float w;
+    const float *w_dev;  // device-side amplitude (see StepLaunch)
+    const int64_t *t_dev;
+    int64_t t_rel, nw;
 };
+
+// Whether the step adds a source amplitude, and which (read only by the
+// thread at the source voxel).
+OOCS_FN bool source_amplitude(const StepArgs &a, float &w)
+{
+    if (!a.w_dev) {
+        w = a.w;
+        return true;
+    }
+    const int64_t t = *a.t_dev + a.t_rel;
+    if (t < 0 || t >= a.nw)
+        return false;
+    w = a.w_dev[t];
+    return true;
+}
 
 // A piece of a CTA's work: tile (x0, y0), window planes [zs, ze).
 struct StepSeg {
@@ -415,20 +433,24 @@ __global__ void __launch_bounds__(kStepThreads, 2)
                                                c ? zm.y : zm.x, c ? zp.y : zp.x);
                             }
                             const float L = star_L<R>(a.c, u, s);
-                            [[maybe_unused]] const bool at_src =
+                            [[maybe_unused]] bool at_src =
                                 !kFast && (x + c == a.src_x && y == a.src_y && z == a.src_zw);
+                            [[maybe_unused]] float w_src = 0.0f;
+                            if constexpr (SCHEME == kWave || SCHEME == kGradient)
+                                if (at_src)
+                                    at_src = source_amplitude(a, w_src);
                             if constexpr (SCHEME == kHeat) {
                                 res[c] = L;
                             } else if constexpr (SCHEME == kWave) {
                                 res[c] = wave_update(L, u, c ? cv[0].y : cv[0].x, c ? cv[1].y : cv[1].x, at_src,
-                                                     a.w);
+                                                     w_src);
                             } else if constexpr (SCHEME == kAdjoint) {
                                 res[c] = adjoint_update(L, c ? cv[2].y : cv[2].x, c ? cv[0].y : cv[0].x,
                                                         !kFast && rcv_plane, c ? rv.y : rv.x);
                                 res2[c] = fmul_rn(c ? cv[1].y : cv[1].x, res[c]);
                             } else {
                                 res[c] = gradient_update(L, c ? cv[1].y : cv[1].x, c ? cv[0].y : cv[0].x, at_src,
-                                                         a.w);
+                                                         w_src);
                             }
                         }
                     }
@@ -604,6 +626,10 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
     a.src_y = (int)L.src_y;
     a.src_zw = L.src_z >= 0 ? (int)(L.src_z - L.gz0) : -1;
     a.w = L.w;
+    a.w_dev = L.w_dev;
+    a.t_dev = L.t_dev;
+    a.t_rel = L.t_rel;
+    a.nw = L.nw;
     if (L.radius == 1 && L.scheme == kHeat)
         return launch_step_t<1, kHeat>(L, a, s);
     if (L.radius == 4 && L.scheme == kHeat)
@@ -617,6 +643,14 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
     if (L.radius == 4 && L.scheme == kGradient)
         return launch_step_t<4, kGradient>(L, a, s);
     return cudaErrorInvalidValue;
+}
+
+__global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
+
+cudaError_t launch_set_i64(int64_t *p, int64_t v, cudaStream_t s)
+{
+    k_set_i64<<<1, 1, 0, s>>>(p, v);
+    return cudaGetLastError();
 }
 
 cudaError_t read_device_error(unsigned int *code, bool clear)

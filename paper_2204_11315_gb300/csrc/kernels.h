@@ -37,9 +37,19 @@ struct StepLaunch {
     float coef[5];
     int64_t src_x, src_y, src_z;  // global source voxel, src_z < 0: none
     float w;                      // source amplitude for this step
+    // device-side amplitude (for launches recorded in a CUDA graph): if w_dev
+    // is set, the step at time t = *t_dev + t_rel adds w_dev[t] when
+    // 0 <= t < nw and nothing otherwise, instead of `w`
+    const float *w_dev;
+    const int64_t *t_dev;
+    int64_t t_rel;
+    int64_t nw;
 };
 
 cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s);
+
+// *p = v in stream order (one thread).
+cudaError_t launch_set_i64(int64_t *p, int64_t v, cudaStream_t s);
 
 // Read (and optionally clear) the device error word set by kernels whose
 // bounded waits ran out (0 = no error).

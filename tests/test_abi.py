@@ -71,7 +71,9 @@ def test_plan_wave_workload(P):
     # workspace = 3 window buffers + 3 staging slots per field in + 3 per field out
     slot_in = (64 + 16) // 4 * p.layer_bytes
     slot_out = 64 // 4 * p.layer_bytes
-    assert p.workspace_swb_bytes == 3 * buf + 3 * 3 * slot_in + 3 * 2 * slot_out
+    # + the device wavelet and time index read by replayed graphs
+    src = 256 + 65536 * 4
+    assert p.workspace_swb_bytes == 3 * buf + 3 * 3 * slot_in + 3 * 2 * slot_out + src
 
 
 def test_plan_wave_resident_model(P):

@@ -116,9 +116,13 @@ def test_one_problem_of_a_batch_steps_alone(P):
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
 
 
-def test_graph_replay_equals_direct_steps(P):
+@pytest.mark.parametrize("with_source", [False, True])
+def test_graph_replay_equals_direct_steps(P, with_source):
+    """Two replays of a captured 6-step batch equal two direct batch steps; with
+    sources, each replay reads the wavelet at its own time index (steps 0-5,
+    then 6-11), byte for byte."""
     torch_cuda()
-    probs = _problems(P, with_source=False)
+    probs = _problems(P, with_source=with_source)
     outs = []
     for mode in ("direct", "graph"):
         b = _batch(P, probs)
@@ -145,9 +149,12 @@ def test_graph_replay_equals_direct_steps(P):
     assert std[0]["steps_done"] == 12
 
 
-def test_capture_refuses_a_time_dependent_source(P):
+def test_capture_refuses_a_wavelet_the_device_cannot_hold(P):
     torch_cuda()
-    b = _batch(P, _problems(P, with_source=True))
+    probs = _problems(P, with_source=True)
+    d, fields, ((x, y, z), w) = probs[2]
+    probs[2] = (d, fields, ((x, y, z), np.zeros(70000, np.float32)))
+    b = _batch(P, probs)
     try:
         with pytest.raises(P.OOCSError) as e:
             b.capture(4)
@@ -156,6 +163,32 @@ def test_capture_refuses_a_time_dependent_source(P):
         b.synchronize(60.0)
     finally:
         b.close()
+
+
+def test_replays_and_direct_steps_interleave(P):
+    """Direct steps between replays move every problem's time index; the next
+    replay continues from it (source included)."""
+    torch_cuda()
+    probs = _problems(P, with_source=True)
+    outs = []
+    for mode in ("direct", "mixed"):
+        b = _batch(P, probs)
+        try:
+            if mode == "direct":
+                for n in (4, 3, 4):
+                    b.step(n)
+            else:
+                b.capture(4)
+                b.launch()
+                b.step(3)
+                b.launch()
+            b.synchronize(120.0)
+            outs.append([[s.numpy().copy() for s in bp.stores] for bp in b.problems])
+        finally:
+            b.close()
+    for i in range(len(probs)):
+        for a, c in zip(outs[0][i], outs[1][i]):
+            assert np.array_equal(a, c), i
 
 
 def test_tuned_problems_run_as_a_batch(P, tmp_path):

@@ -297,8 +297,10 @@ def test_batch_workspace_is_per_region_maximum(P):
         fin = max(fin, p.fields_in)
         fout = max(fout, p.fields_out)
         resident += a256(nz * ny * nx * 4) if wave and ro else 0
+        resident += (256 + 65536 * 4) if wave else 0  # device wavelet and time index
     want = nbuf * buf + 3 * fin * slot_in + 3 * fout * slot_out + resident
     assert P.oocs_batch_query(descs) == want
-    # many copies of one problem cost one problem's pipeline
+    # many copies of one problem cost one problem's pipeline (plus each wave
+    # problem's own device wavelet)
     one = [descs[1]]
-    assert P.oocs_batch_query(one * 16) == P.oocs_query(descs[1]).workspace_bytes
+    assert P.oocs_batch_query(one * 16) == P.oocs_query(descs[1]).workspace_bytes + 15 * (256 + 65536 * 4)
