@@ -93,8 +93,8 @@ struct StepArgs {
     int64_t t_rel, nw;
 };
 
-// Whether the step adds a source amplitude, and which (read only by the
-// thread at the source voxel).
+// Whether the step adds a source amplitude, and which (resolved once per
+// thread before the z march).
 OOCS_FN bool source_amplitude(const StepArgs &a, float &w)
 {
     if (!a.w_dev) {
@@ -261,6 +261,13 @@ __global__ void __launch_bounds__(kStepThreads, 2)
     }
 
     // --------------------------------------------------- consumer warps --
+    // the source term of this step: its voxel's x (-1 when the step adds
+    // nothing) and amplitude
+    [[maybe_unused]] float w_src = 0.0f;
+    [[maybe_unused]] int src_x = a.src_x;
+    if constexpr (SCHEME == kWave || SCHEME == kGradient)
+        if (src_x >= 0 && !source_amplitude(a, w_src))
+            src_x = -1;
     const int ucol = 4 + kVX * tx;
     auto urow = [&](int rel_row) { return (R + kRPT * wid + rel_row) * kBoxW + ucol; };
     uint32_t ucn = 0, ccn = 0;  // u planes / centre-field planes consumed before this segment
@@ -433,12 +440,8 @@ __global__ void __launch_bounds__(kStepThreads, 2)
                                                c ? zm.y : zm.x, c ? zp.y : zp.x);
                             }
                             const float L = star_L<R>(a.c, u, s);
-                            [[maybe_unused]] bool at_src =
-                                !kFast && (x + c == a.src_x && y == a.src_y && z == a.src_zw);
-                            [[maybe_unused]] float w_src = 0.0f;
-                            if constexpr (SCHEME == kWave || SCHEME == kGradient)
-                                if (at_src)
-                                    at_src = source_amplitude(a, w_src);
+                            [[maybe_unused]] const bool at_src =
+                                !kFast && (x + c == src_x && y == a.src_y && z == a.src_zw);
                             if constexpr (SCHEME == kHeat) {
                                 res[c] = L;
                             } else if constexpr (SCHEME == kWave) {
