@@ -51,12 +51,26 @@ typedef enum {
  *  OOCS_HEAT: u' = c0 u + sum_{d=1..r} c_d s_d(u)                 (first order in time)
  *  OOCS_WAVE: u' = 2u - up + m (c0 u + sum_d c_d s_d(u) + w[t] at the source)  (leapfrog)
  * with s_d(u)(p) = (u[p-d ex] + u[p+d ex]) + (u[p-d ey] + u[p+d ey]) + (u[p-d ez] + u[p+d ez]). */
-enum { OOCS_HEAT = 0, OOCS_WAVE = 1 };
+enum { OOCS_HEAT = 0, OOCS_WAVE = 1, OOCS_WAVE_ADJOINT = 2 };
 
 /* Fields of a context.  HEAT streams U.  WAVE streams U (u^t), U_PREV (u^(t-1))
  * and the read-only model M = (v dt/dx)^2 (the paper's read-only dataset,
  * Sec. 6.2); the write-only dataset is device-only.                        */
 enum { OOCS_FIELD_U = 0, OOCS_FIELD_U_PREV = 1, OOCS_FIELD_M = 2 };
+
+/* OOCS_WAVE_ADJOINT: one time step of the WAVE scheme's discrete adjoint per
+ * oocs_step(ctx, 1), slab by slab in reverse z order, with the gradient of a
+ * receiver misfit accumulated on the device.  At time index k (oocs_set_time)
+ * the step reads lam^k (field LAM), lam^(k+1) (LAM_PREV, interior only) and
+ * the forward state u^(k-1) (FWD), adds lam^k (L u^(k-1) + w[k-1] at the
+ * source) to dJ/dm (field GRAD, on the device, zero at create), writes
+ * lam^(k-1) = 2 lam^k - lam^(k+1) + L(m lam^k) + r^(k-2) at the receiver plane
+ * into LAM_PREV's store, then swaps the LAM and LAM_PREV stores and sets the
+ * time index to k-1.  r^n = planes[n] of oocs_set_receiver.  m (field M) is
+ * kept on the device (readonly_resident must be 1); temporal_depth is 1; the
+ * halo is one 4-plane layer; no region sharing (whole windows are copied).
+ * GRAD is read with oocs_decompress_device.                                 */
+enum { OOCS_FIELD_LAM = 0, OOCS_FIELD_LAM_PREV = 1, OOCS_FIELD_FWD = 3, OOCS_FIELD_GRAD = 4 };
 
 /* Working-buffer schemes (Sec. 5): 1 = single working buffer shared by the
  * three streams (the paper's method); 3 = classic, one per stream (Fig. 6a). */
@@ -158,6 +172,14 @@ oocs_status oocs_bind_field(oocs_ctx *ctx, int32_t field, void *host_store, uint
  * life).  w (host, nw values) is copied.  Steps t >= nw add nothing.        */
 oocs_status oocs_set_source(oocs_ctx *ctx, int64_t x, int64_t y, int64_t z, const float *w,
                             int32_t nw);
+
+/* WAVE: after every step t < nplanes (t counted over the context's life, as
+ * for the source), copy plane zr of the new state u^(t+1) to planes[t]
+ * (device array of nplanes * nx * ny FP32, written on the visit's stream in
+ * step order).  nplanes = 0 stops recording.  WAVE_ADJOINT: planes[n] is the
+ * residual r^n added at plane zr (read).  The receiver record a misfit and its
+ * adjoint need (no counterpart in the paper's forward-only runs).          */
+oocs_status oocs_set_receiver(oocs_ctx *ctx, int64_t zr, float *planes, int64_t nplanes);
 
 /* Fill the bound store of `field` from a raw FP32 host array of nx*ny*nz
  * values (initial compression of the chunks, Algorithm 1 input (1)): copies

@@ -11,6 +11,15 @@ memory holds the compressed checkpoints plus one segment of states.
 Both passes are single calls of the library's native driver
 (oocs_misfit_forward / oocs_misfit_backward, include/oocs.h); this module only
 allocates the workspace with PyTorch and marshals arguments.
+
+With `device_budget` set, the same gradient is computed out of core, for grids
+that do not fit the device: the forward run is the slab sweep (Sec. 3.1, k
+steps per visit) recording the receiver plane, its checkpoints are snapshots
+of the compressed host stores every `checkpoint_every` steps; the backward
+pass recomputes each segment's states one step per sweep (snapshotting the
+compressed u store after each), then runs one adjoint sweep per time step
+(scheme OOCS_WAVE_ADJOINT: slabs in reverse z order, lam streamed through the
+codec, m and dJ/dm on the device).
 """
 from __future__ import annotations
 
@@ -34,6 +43,9 @@ class WaveProblem:
     nsteps: int
     checkpoint_every: int = 10
     rate: int = 16               # codec rate of the checkpoints; 0 = raw copies
+    device_budget: int | None = None  # set: out-of-core sweeps within this many bytes
+    slab_planes: int = 0         # out of core: T (0 = from the budget)
+    forward_depth: int = 4       # out of core: temporal depth of the forward sweep
     _desc: object = field(default=None, repr=False)
 
     def desc(self):
@@ -54,6 +66,94 @@ def _ptr(t):
     return t.data_ptr()
 
 
+# ------------------------------------------------------------ out of core --
+
+def _ooc_desc(prob: WaveProblem, scheme: int, depth: int):
+    nz, ny, nx = prob.shape
+    return O.make_desc(nx, ny, nz, scheme, prob.coef, prob.device_budget, rate_bits=prob.rate,
+                       temporal_depth=depth, slab_planes=prob.slab_planes, readonly_resident=1)
+
+
+def _ooc_forward(torch, m, d_obs, prob: WaveProblem):
+    """Slab-swept forward run from rest: the receiver record, the residuals, J
+    and the checkpoints (pinned copies of the compressed u, u_prev stores)."""
+    nz, ny, nx = prob.shape
+    plane = ny * nx
+    N, K = prob.nsteps, prob.checkpoint_every
+    dev = m.device
+    st = O.OutOfCoreStencil(_ooc_desc(prob, O.OOCS_WAVE, prob.forward_depth), device=dev.index or 0)
+    try:
+        zero = torch.zeros(prob.shape, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize(dev)  # m and zero are written on torch's stream
+        for f, src in ((O.OOCS_FIELD_U, zero), (O.OOCS_FIELD_U_PREV, zero), (O.OOCS_FIELD_M, m)):
+            O.oocs_compress_device(st.ctx, f, _ptr(src), 0, nz)
+        st.set_source(*prob.src_xyz, prob.wavelet32())
+        rec = torch.empty((N, ny, nx), dtype=torch.float32, device=dev)
+        O.oocs_set_receiver(st.ctx, prob.zr, _ptr(rec), N)
+        st.synchronize(600.0)
+        ckpt = {}
+        for s0 in range(0, N, K):
+            ckpt[s0] = [st.stores[f].clone().pin_memory() for f in (O.OOCS_FIELD_U, O.OOCS_FIELD_U_PREV)]
+            st.step(min(K, N - s0))
+            st.synchronize(3600.0)
+        res = torch.empty_like(rec)
+        misfit = torch.zeros(1, dtype=torch.float64, device=dev)
+        O.oocs_receiver_residual(_ptr(rec), _ptr(d_obs), N * plane, _ptr(res), _ptr(misfit),
+                                 torch.cuda.current_stream(dev).cuda_stream)
+        torch.cuda.synchronize(dev)
+    finally:
+        st.close()
+    return misfit, res, ckpt
+
+
+def _ooc_backward(torch, m, res, ckpt, prob: WaveProblem):
+    """dJ/dm by adjoint sweeps, each segment's forward states recomputed from its checkpoint."""
+    nz, ny, nx = prob.shape
+    N, K = prob.nsteps, prob.checkpoint_every
+    dev = m.device
+    fwd = O.OutOfCoreStencil(_ooc_desc(prob, O.OOCS_WAVE, 1), device=dev.index or 0)
+    adj = O.OutOfCoreStencil(_ooc_desc(prob, O.OOCS_WAVE_ADJOINT, 1), device=dev.index or 0)
+    try:
+        torch.cuda.synchronize(dev)
+        O.oocs_compress_device(fwd.ctx, O.OOCS_FIELD_M, _ptr(m), 0, nz)
+        O.oocs_compress_device(adj.ctx, O.OOCS_FIELD_M, _ptr(m), 0, nz)
+        fwd.set_source(*prob.src_xyz, prob.wavelet32())
+        adj.set_source(*prob.src_xyz, prob.wavelet32())
+        O.oocs_set_receiver(adj.ctx, prob.zr, _ptr(res), N)
+        # lam^N = r^(N-1) on the receiver plane's interior, lam^(N+1) = 0
+        lam = torch.zeros(prob.shape, dtype=torch.float32, device=dev)
+        lam[prob.zr, 4:ny - 4, 4:nx - 4] = res[N - 1, 4:ny - 4, 4:nx - 4]
+        zero = torch.zeros_like(lam)
+        torch.cuda.synchronize(dev)
+        O.oocs_compress_device(adj.ctx, O.OOCS_FIELD_LAM, _ptr(lam), 0, nz)
+        O.oocs_compress_device(adj.ctx, O.OOCS_FIELD_LAM_PREV, _ptr(zero), 0, nz)
+        adj.synchronize(600.0)
+        del lam, zero
+        for s0 in reversed(range(0, N, K)):
+            e0 = min(s0 + K, N)
+            # the segment's states u^s0 .. u^(e0-1), one sweep per step
+            for f, snap in zip((O.OOCS_FIELD_U, O.OOCS_FIELD_U_PREV), ckpt[s0]):
+                fwd.stores[f].copy_(snap)
+            fwd.set_time(s0)
+            states = {s0: fwd.stores[O.OOCS_FIELD_U].clone().pin_memory()}
+            for t in range(s0, e0 - 1):
+                fwd.step(1)
+                fwd.synchronize(3600.0)
+                states[t + 1] = fwd.stores[O.OOCS_FIELD_U].clone().pin_memory()
+            for k in range(e0, s0, -1):  # lam^k, u^(k-1) -> dJ/dm term k-1 and lam^(k-1)
+                adj.bind(O.OOCS_FIELD_FWD, states[k - 1])
+                adj.set_time(k)
+                adj.step(1)
+            adj.synchronize(3600.0)
+        grad_m = torch.empty_like(m)
+        O.oocs_decompress_device(adj.ctx, O.OOCS_FIELD_GRAD, _ptr(grad_m), 0, nz)
+        adj.synchronize(600.0)
+    finally:
+        fwd.close()
+        adj.close()
+    return grad_m
+
+
 def _make_function():
     import torch
 
@@ -67,6 +167,11 @@ def _make_function():
             stream = torch.cuda.current_stream(v.device).cuda_stream
             m = torch.empty_like(v)
             O.oocs_model_from_velocity(_ptr(v), _ptr(m), n, prob.dt / prob.dx, stream)
+            if prob.device_budget is not None:
+                misfit, res, ckpt = _ooc_forward(torch, m, d_obs, prob)
+                ctx.prob, ctx.ckpt, ctx.ws = prob, ckpt, None
+                ctx.save_for_backward(v, m, res)
+                return misfit[0]
             nbytes = prob.workspace_bytes()
             ws = torch.empty(nbytes, dtype=torch.uint8, device=v.device)
             res = torch.empty((prob.nsteps, ny, nx), dtype=torch.float32, device=v.device)
@@ -85,10 +190,14 @@ def _make_function():
             prob, ws = ctx.prob, ctx.ws
             n = v.numel()
             stream = torch.cuda.current_stream(v.device).cuda_stream
-            grad_m = torch.empty_like(v)
-            O.oocs_misfit_backward(prob.desc(), _ptr(m), prob.src_xyz, prob.wavelet32(), prob.zr, _ptr(res),
-                                   prob.nsteps, prob.checkpoint_every, prob.rate, _ptr(ws), ws.numel(),
-                                   _ptr(grad_m), stream)
+            if prob.device_budget is not None:
+                grad_m = _ooc_backward(torch, m, res, ctx.ckpt, prob)
+                ctx.ckpt = None
+            else:
+                grad_m = torch.empty_like(v)
+                O.oocs_misfit_backward(prob.desc(), _ptr(m), prob.src_xyz, prob.wavelet32(), prob.zr, _ptr(res),
+                                       prob.nsteps, prob.checkpoint_every, prob.rate, _ptr(ws), ws.numel(),
+                                       _ptr(grad_m), stream)
             ctx.ws = None
             grad_v = torch.empty_like(v)
             O.oocs_velocity_gradient(_ptr(grad_m), _ptr(v), _ptr(grad_v), n, prob.dt / prob.dx, stream)

@@ -57,15 +57,16 @@ uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
     // byte offsets inside the workspace
-    uint64_t w_off[3][3];     // [working buffer][buffer]
+    uint64_t w_off[3][4];     // [working buffer][buffer]
     uint64_t in_off[3][3];    // [slot][field_in]
     uint64_t out_off[3][2];   // [slot][field_out]
     uint64_t ro_off;          // resident FP32 copy of M (readonly_resident), else 0
     uint64_t ro_bytes;
     uint64_t src_off;         // wave: device time index + wavelet (graph replays), else 0
+    uint64_t g_off;           // adjoint: dJ/dm on the device, else 0
     uint64_t total;
     int nwb;                  // working buffers (1 SWB, 3 classic)
-    int nbuf;                 // buffers per working set (heat 2, wave 3)
+    int nbuf;                 // buffers per working set (heat 2, wave 3, adjoint 4)
     uint64_t buf_bytes;       // one window buffer
     uint64_t in_slot_bytes;   // one staging slot of one field
     uint64_t out_slot_bytes;
@@ -83,11 +84,14 @@ struct Derived {
     int64_t slot_layers_in, slot_layers_out;
 };
 
+// fields bound to host stores: heat U; wave U, U_PREV, M; adjoint LAM, LAM_PREV, M, FWD
+int bound_fields(const oocs_desc &d) { return d.scheme == OOCS_HEAT ? 1 : d.scheme == OOCS_WAVE ? 3 : 4; }
+
 Derived derive(const oocs_desc &d, int T)
 {
     Derived v;
     v.r = d.radius;
-    v.k = d.temporal_depth > 0 ? d.temporal_depth : 4;
+    v.k = d.scheme == OOCS_WAVE_ADJOINT ? 1 : d.temporal_depth > 0 ? d.temporal_depth : 4;
     v.h = (int)(4 * ceil_div((int64_t)v.k * v.r, 4));
     v.T = T;
     v.S = (int)ceil_div(d.nz, T);
@@ -96,9 +100,15 @@ Derived derive(const oocs_desc &d, int T)
     v.fout = d.scheme == OOCS_WAVE ? 2 : 1;
     v.ro_res = d.scheme == OOCS_WAVE && d.readonly_resident != 0;
     v.fin_stream = v.fin - (v.ro_res ? 1 : 0);
+    if (d.scheme == OOCS_WAVE_ADJOINT) {  // in: LAM, LAM_PREV, FWD; out: LAM_PREV; M resident
+        v.fin = v.fin_stream = 3;
+        v.fout = 1;
+        v.ro_res = true;
+    }
     v.layer_bytes = d.rate_bits > 0 ? (uint64_t)(d.nx / 4) * (d.ny / 4) * 8ull * d.rate_bits
                                     : (uint64_t)4 * d.nx * d.ny * 4;
-    v.slot_layers_in = std::min<int64_t>(ceil_div(T + v.h, 4), d.nz / 4);
+    // region sharing leaves T + h new planes per visit; the adjoint copies whole windows
+    v.slot_layers_in = std::min<int64_t>(ceil_div(d.scheme == OOCS_WAVE_ADJOINT ? v.wp : T + v.h, 4), d.nz / 4);
     v.slot_layers_out = std::min<int64_t>(T / 4, d.nz / 4);
     return v;
 }
@@ -111,6 +121,8 @@ Layout layout_for(const oocs_desc &d, const Derived &v, int nwb)
     // window buffers: heat u, u'; wave u, u_prev and m (m lives in the
     // resident copy when readonly_resident)
     L.nbuf = d.scheme == OOCS_WAVE && !v.ro_res ? 3 : 2;
+    if (d.scheme == OOCS_WAVE_ADJOINT)
+        L.nbuf = 4;  // lam^k, lam^(k+1) -> lam^(k-1), u^(k-1), m lam^k
     L.buf_bytes = align_up((uint64_t)v.wp * d.nx * d.ny * 4, 256);
     L.in_slot_bytes = align_up((uint64_t)v.slot_layers_in * v.layer_bytes, 256);
     L.out_slot_bytes = align_up((uint64_t)v.slot_layers_out * v.layer_bytes, 256);
@@ -139,6 +151,10 @@ Layout layout_for(const oocs_desc &d, const Derived &v, int nwb)
         L.src_off = off;
         off += kSrcRegionBytes;
     }
+    if (d.scheme == OOCS_WAVE_ADJOINT) {  // dJ/dm, accumulated on the device
+        L.g_off = off;
+        off += align_up((uint64_t)d.nz * d.nx * d.ny * 4, 256);
+    }
     L.total = off;
     return L;
 }
@@ -157,8 +173,13 @@ oocs_status validate_desc(const oocs_desc *d, std::string &err)
         err = "grid dimension too large";
         return OOCS_ERR_INVALID_ARG;
     }
-    if (d->scheme != OOCS_HEAT && d->scheme != OOCS_WAVE) {
-        err = "scheme must be OOCS_HEAT or OOCS_WAVE";
+    if (d->scheme != OOCS_HEAT && d->scheme != OOCS_WAVE && d->scheme != OOCS_WAVE_ADJOINT) {
+        err = "scheme must be OOCS_HEAT, OOCS_WAVE or OOCS_WAVE_ADJOINT";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->scheme == OOCS_WAVE_ADJOINT &&
+        (d->radius != 4 || d->temporal_depth > 1 || d->readonly_resident != 1 || d->working_buffers != OOCS_SWB)) {
+        err = "the wave adjoint needs radius 4, temporal_depth 1, readonly_resident 1 and one working buffer";
         return OOCS_ERR_INVALID_ARG;
     }
     if (d->radius != 1 && d->radius != 4) {
@@ -278,12 +299,17 @@ struct oocs_ctx {
     Layout L;
     char *ws = nullptr;
     cudaStream_t st[3] = {};
-    char *store[3] = {};
-    uint64_t store_bytes[3] = {};
+    char *store[4] = {};  // by field id (bound_fields of the scheme)
+    uint64_t store_bytes[4] = {};
 
     bool has_src = false;
     int64_t src[3] = {0, 0, -1};
     std::vector<float> w;
+
+    // receiver plane: WAVE records plane zr of u^(t+1) into planes[t] after
+    // every step t < nplanes (device array [nplanes][ny][nx])
+    float *rec = nullptr;
+    int64_t rec_z = -1, rec_n = 0;
 
     cudaEvent_t ev_decoded[3] = {}, ev_h2d[3] = {}, ev_wrel[3] = {}, ev_join[3] = {};
     std::vector<cudaEvent_t> ev_d2h;
@@ -321,6 +347,7 @@ struct oocs_ctx {
     char *in_slot(int q, int f) const { return ws + L.in_off[q][f]; }
     char *out_slot(int q, int f) const { return ws + L.out_off[q][f]; }
     float *ro_m() const { return reinterpret_cast<float *>(ws + L.ro_off); }
+    float *grad() const { return reinterpret_cast<float *>(ws + L.g_off); }
     int64_t *t_dev() const { return reinterpret_cast<int64_t *>(ws + L.src_off); }
     float *w_dev() const { return reinterpret_cast<float *>(ws + L.src_off + 256); }
     int64_t t_capture = 0;  // time index when the batch's graph was captured
@@ -799,6 +826,11 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             CU(c, launch_star_step(Ls, st));
         c->stats.kernel_launches++;
         step_units += (uint64_t)(hi - lo) * d.nx * d.ny;
+        // the receiver plane lies in this slab's interior, which every step of
+        // the visit computes: record u^(tstep+1) there
+        if (c->rec && c->rec_z >= z0 && c->rec_z < z1 && tstep < c->rec_n && !c->trace)
+            CU(c, cudaMemcpyAsync(c->rec + tstep * plane_f, Ls.out + (c->rec_z - w0) * plane_f,
+                                  (size_t)plane_f * 4, cudaMemcpyDeviceToDevice, st));
         std::swap(cur, oth);
     }
     {
@@ -858,6 +890,158 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     }
     SCHED(sched_record(c, q, kEvD2H + c->d2h_base + s));
     c->d2h_recorded[s] = 1;
+    c->g++;
+    c->stats.slabs_done++;
+    return OOCS_OK;
+}
+
+// One slab visit of the wave adjoint at time index k (temporal depth 1, the
+// time walk of Sec. 3.1 run backwards): copy the windows of lam^k and u^(k-1)
+// and the interior of lam^(k+1) to the device, decode them into the working
+// buffer, form m lam^k, add the gradient term lam^k (L u^(k-1) + w[k-1] e_src)
+// to the device-resident dJ/dm, take the adjoint step on the interior, encode
+// lam^(k-1) and copy it back over lam^(k+1)'s host layers.
+oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k)
+{
+    const Derived &v = c->v;
+    const oocs_desc &d = c->d;
+    const uint64_t g = c->g;
+    const int q = (int)(g % 3);
+    cudaStream_t st = c->st[q];
+    const int64_t z0 = (int64_t)s * v.T;
+    const int64_t z1 = std::min<int64_t>(z0 + v.T, d.nz);
+    const int64_t w0 = std::max<int64_t>(z0 - v.h, 0);
+    const int64_t w1 = std::min<int64_t>(z1 + v.h, d.nz);
+    const int64_t plane_f = d.nx * d.ny;
+    // slot q, field f: 0 = lam^k (window), 1 = lam^(k+1) (interior), 2 = u^(k-1) (window)
+    const int store_of[3] = {OOCS_FIELD_LAM, OOCS_FIELD_LAM_PREV, OOCS_FIELD_FWD};
+    const int64_t l0[3] = {w0 / 4, z0 / 4, w0 / 4}, l1[3] = {w1 / 4, z1 / 4, w1 / 4};
+    float *W0 = c->wbuf(0, 0), *W1 = c->wbuf(0, 1), *W2 = c->wbuf(0, 2), *W3 = c->wbuf(0, 3);
+
+    // 1. staging slot q is free once visit g-2 has decoded it
+    if (g >= 2)
+        SCHED(sched_wait(c, q, kEvDecoded + (int)((g - 2) % 3)));
+    // 2. H2D (host stores read only, or read and written by this visit alone;
+    //    across steps the call's opening join orders everything)
+    if (c->trace) {
+        trace_push(c, OOCS_OP_H2D, q, -1, (int64_t)g,
+                   {acc(OOCS_RES_IN_SLOT, q, w0 / 4, w1 / 4, true), acc(OOCS_RES_HOST, c->host_base + 0, l0[0], l1[0], false),
+                    acc(OOCS_RES_HOST, c->host_base + 1, l0[1], l1[1], false),
+                    acc(OOCS_RES_HOST, c->host_base + 3, l0[2], l1[2], false)});
+    } else {
+        for (int f = 0; f < 3; ++f)
+            CU(c, cudaMemcpyAsync(c->in_slot(q, f), c->store[store_of[f]] + (uint64_t)l0[f] * v.layer_bytes,
+                                  (uint64_t)(l1[f] - l0[f]) * v.layer_bytes, cudaMemcpyHostToDevice, st));
+    }
+    for (int f = 0; f < 3; ++f)
+        c->stats.h2d_bytes += (uint64_t)(l1[f] - l0[f]) * v.layer_bytes;
+    // 3. the working buffer is free once visit g-1 has encoded from it
+    if (g >= 1)
+        SCHED(sched_wait(c, q, kEvWrel + (int)((g - 1) % 3)));
+    // 4. decode lam^k, lam^(k+1) (interior planes, at their window positions), u^(k-1)
+    float *dst[3] = {W0, W1 + (z0 - w0) * plane_f, W2};
+    if (c->trace) {
+        trace_push(c, OOCS_OP_LOAD, q, -1, (int64_t)g,
+                   {acc(OOCS_RES_IN_SLOT, q, w0 / 4, w1 / 4, false), acc(OOCS_RES_WORK, 0, w0 / 4, w1 / 4, true)});
+    } else {
+        KernelScope ks;
+        oocs_status r = ks.begin(c, st, kClsLoad);
+        if (r != OOCS_OK)
+            return r;
+        if (d.rate_bits > 0) {
+            CodecSegments sg;
+            int64_t nl[kMaxCodecSegments];
+            for (int f = 0; f < 3; ++f) {
+                sg.blocks[sg.nseg] = c->in_slot(q, f);
+                sg.planes[sg.nseg] = dst[f];
+                nl[sg.nseg++] = l1[f] - l0[f];
+            }
+            CU(c, launch_decode_segments(sg, nl, d.nx, d.ny, d.rate_bits, st));
+            c->stats.kernel_launches++;
+        } else {
+            for (int f = 0; f < 3; ++f)
+                CU(c, cudaMemcpyAsync(dst[f], c->in_slot(q, f), (uint64_t)(l1[f] - l0[f]) * v.layer_bytes,
+                                      cudaMemcpyDeviceToDevice, st));
+        }
+        r = ks.end(kClsLoad, (uint64_t)(2 * (w1 - w0) + (z1 - z0)) * plane_f);
+        if (r != OOCS_OK)
+            return r;
+    }
+    SCHED(sched_record(c, q, kEvDecoded + q));
+    // 5. m lam^k over the window, the gradient term, the adjoint step
+    StepLaunch G;
+    memset(&G, 0, sizeof(G));
+    G.radius = 4;
+    G.nx = d.nx;
+    G.ny = d.ny;
+    G.nz = d.nz;
+    G.gz0 = w0;
+    G.wp = w1 - w0;
+    G.z_lo = z0 - w0;
+    G.z_hi = z1 - w0;
+    for (int i = 0; i <= 4; ++i)
+        G.coef[i] = d.coef[i];
+    G.src_z = -1;
+    StepLaunch A = G;
+    G.scheme = kGradient;
+    G.cur = W2;
+    G.prev = c->grad() + w0 * plane_f;
+    G.m = W0;
+    G.out = c->grad() + w0 * plane_f;
+    if (c->has_src && k - 1 >= 0 && k - 1 < (int64_t)c->w.size()) {
+        G.src_x = c->src[0];
+        G.src_y = c->src[1];
+        G.src_z = c->src[2];
+        G.w = c->w[k - 1];
+    }
+    A.scheme = kAdjoint;
+    A.cur = W3;
+    A.prev = W1;
+    A.m = c->ro_m() + w0 * plane_f;
+    A.c2 = W0;
+    A.out = W1;
+    A.out2 = nullptr;
+    A.zr = -1;
+    if (c->rec && k - 2 >= 0 && k - 2 < c->rec_n) {
+        A.res = c->rec + (k - 2) * plane_f;
+        A.zr = c->rec_z;
+    }
+    if (c->trace) {
+        for (int i = 0; i < 3; ++i)
+            trace_push(c, OOCS_OP_STEP, q, -1, (int64_t)g, {acc(OOCS_RES_WORK, 0, w0 / 4, w1 / 4, true)});
+    } else {
+        KernelScope ks;
+        oocs_status r = ks.begin(c, st, kClsStep);
+        if (r != OOCS_OK)
+            return r;
+        CU(c, launch_product(W3, c->ro_m() + w0 * plane_f, W0, (w1 - w0) * plane_f, st));
+        CU(c, launch_star_step(G, st));
+        CU(c, launch_star_step(A, st));
+        c->stats.kernel_launches += 3;
+        r = ks.end(kClsStep, (uint64_t)(z1 - z0) * plane_f, 2);
+        if (r != OOCS_OK)
+            return r;
+    }
+    // 6. encode lam^(k-1) on the interior into the out slot
+    if (c->trace) {
+        trace_push(c, OOCS_OP_STORE, q, -1, (int64_t)g,
+                   {acc(OOCS_RES_WORK, 0, z0 / 4, z1 / 4, false), acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, true)});
+    } else {
+        oocs_status r = store_layers(c, W1, w0, z0 / 4, z1 / 4, c->out_slot(q, 0), st);
+        if (r != OOCS_OK)
+            return r;
+    }
+    SCHED(sched_record(c, q, kEvWrel + q));
+    // 7. D2H over lam^(k+1)'s layers of the host store
+    const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
+    if (c->trace)
+        trace_push(c, OOCS_OP_D2H, q, -1, (int64_t)g,
+                   {acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, false),
+                    acc(OOCS_RES_HOST, c->host_base + 1, z0 / 4, z1 / 4, true)});
+    else
+        CU(c, cudaMemcpyAsync(c->store[OOCS_FIELD_LAM_PREV] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, 0),
+                              bytes, cudaMemcpyDeviceToHost, st));
+    c->stats.d2h_bytes += bytes;
     c->g++;
     c->stats.slabs_done++;
     return OOCS_OK;
@@ -937,6 +1121,8 @@ oocs_status oocs_create(const oocs_desc *desc, void *workspace, uint64_t workspa
         e = cudaEventCreate(&c->ev_t0);
     if (e == cudaSuccess)
         e = cudaEventCreate(&c->ev_t1);
+    if (e == cudaSuccess && c->d.scheme == OOCS_WAVE_ADJOINT)  // dJ/dm starts at zero
+        e = cudaMemsetAsync(c->grad(), 0, (size_t)c->d.nz * c->d.nx * c->d.ny * 4, c->st[0]);
     if (e != cudaSuccess) {
         std::string msg = std::string("cudaEventCreate: ") + cudaGetErrorString(e);
         oocs_destroy(c);
@@ -951,7 +1137,7 @@ oocs_status oocs_bind_field(oocs_ctx *ctx, int32_t field, void *host_store, uint
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
-    const int nf = ctx->d.scheme == OOCS_WAVE ? 3 : 1;
+    const int nf = bound_fields(ctx->d);
     if (field < 0 || field >= nf)
         return fail(ctx, OOCS_ERR_INVALID_ARG, "field id not used by this scheme");
     if (!host_store || bytes < ctx->p.host_store_bytes)
@@ -969,7 +1155,7 @@ oocs_status oocs_set_source(oocs_ctx *ctx, int64_t x, int64_t y, int64_t z, cons
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
-    if (ctx->d.scheme != OOCS_WAVE)
+    if (ctx->d.scheme == OOCS_HEAT)
         return fail(ctx, OOCS_ERR_INVALID_ARG, "a point source needs the wave scheme");
     if (x < 0 || y < 0 || z < 0 || x >= ctx->d.nx || y >= ctx->d.ny || z >= ctx->d.nz || nw < 0 ||
         (nw > 0 && !w))
@@ -986,12 +1172,27 @@ oocs_status oocs_set_source(oocs_ctx *ctx, int64_t x, int64_t y, int64_t z, cons
     return OOCS_OK;
 }
 
+oocs_status oocs_set_receiver(oocs_ctx *ctx, int64_t zr, float *planes, int64_t nplanes)
+{
+    oocs_status s = check_ready(ctx);
+    if (s != OOCS_OK)
+        return s;
+    if (ctx->d.scheme == OOCS_HEAT)
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "receiver planes belong to the wave scheme and its adjoint");
+    if (nplanes < 0 || (nplanes > 0 && (!planes || zr < 0 || zr >= ctx->d.nz)))
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "receiver plane outside the grid or no device array");
+    ctx->rec = nplanes > 0 ? planes : nullptr;
+    ctx->rec_z = zr;
+    ctx->rec_n = nplanes;
+    return OOCS_OK;
+}
+
 static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, float *dst, bool enc)
 {
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
-    const int nf = ctx->d.scheme == OOCS_WAVE ? 3 : 1;
+    const int nf = bound_fields(ctx->d);
     if (field < 0 || field >= nf || !ctx->store[field])
         return fail(ctx, OOCS_ERR_STATE, "field is not bound");
     if (enc ? !src : !dst)
@@ -1057,14 +1258,23 @@ static oocs_status codec_range_device(oocs_ctx *ctx, int32_t field, const float 
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
-    const int nf = ctx->d.scheme == OOCS_WAVE ? 3 : 1;
-    if (field < 0 || field >= nf || !ctx->store[field])
-        return fail(ctx, OOCS_ERR_STATE, "field is not bound");
     const oocs_desc &d = ctx->d;
     if ((enc ? !src : !dst) || (reinterpret_cast<uintptr_t>(enc ? (const void *)src : (const void *)dst) & 15))
         return fail(ctx, OOCS_ERR_INVALID_ARG, "device array must be non-null and 16-byte aligned");
     if (z0 < 0 || nplanes < 0 || z0 % 4 || nplanes % 4 || z0 + nplanes > d.nz)
         return fail(ctx, OOCS_ERR_INVALID_ARG, "planes must be whole 4-plane layers inside the grid");
+    if (d.scheme == OOCS_WAVE_ADJOINT && field == OOCS_FIELD_GRAD) {  // lives on the device
+        s = join_streams(ctx);
+        if (s != OOCS_OK)
+            return s;
+        float *g = ctx->grad() + z0 * d.nx * d.ny;
+        CU(ctx, cudaMemcpyAsync(enc ? g : dst, enc ? src : g, (size_t)nplanes * d.nx * d.ny * 4,
+                                cudaMemcpyDeviceToDevice, ctx->st[0]));
+        return join_streams(ctx);
+    }
+    const int nf = bound_fields(ctx->d);
+    if (field < 0 || field >= nf || !ctx->store[field])
+        return fail(ctx, OOCS_ERR_STATE, "field is not bound");
     if (enc && field == OOCS_FIELD_M)
         ctx->ro_dirty = true;
     s = join_streams(ctx);
@@ -1147,7 +1357,7 @@ oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
         return s;
     if (nsteps < 0)
         return fail(ctx, OOCS_ERR_INVALID_ARG, "nsteps must be >= 0");
-    const int nf = ctx->d.scheme == OOCS_WAVE ? 3 : 1;
+    const int nf = bound_fields(ctx->d);
     for (int f = 0; f < nf; ++f)
         if (!ctx->store[f])
             return fail(ctx, OOCS_ERR_STATE, "all fields of the scheme must be bound before oocs_step");
@@ -1173,6 +1383,31 @@ oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
     if (s != OOCS_OK)
         return s;
     int64_t t = (int64_t)ctx->stats.steps_done;
+    if (ctx->d.scheme == OOCS_WAVE_ADJOINT) {
+        // one adjoint step at time index t, slabs in reverse z order; then the
+        // stores of lam^t and the new lam^(t-1) take their next roles
+        if (nsteps != 1)
+            return fail(ctx, OOCS_ERR_INVALID_ARG, "the wave adjoint advances one step per oocs_step call");
+        if (t < 1)
+            return fail(ctx, OOCS_ERR_STATE, "the adjoint's time index must be >= 1 (oocs_set_time)");
+        for (int sl = ctx->v.S - 1; sl >= 0; --sl) {
+            s = enqueue_adjoint_slab(ctx, sl, t);
+            if (s != OOCS_OK)
+                return s;
+        }
+        std::swap(ctx->store[OOCS_FIELD_LAM], ctx->store[OOCS_FIELD_LAM_PREV]);
+        std::swap(ctx->store_bytes[OOCS_FIELD_LAM], ctx->store_bytes[OOCS_FIELD_LAM_PREV]);
+        ctx->stats.steps_done = (uint64_t)(t - 1);
+        ctx->stats.passes_done++;
+        s = join_streams(ctx);
+        if (s != OOCS_OK)
+            return s;
+        s = sched_record(ctx, 0, kEvT1);
+        if (s != OOCS_OK)
+            return s;
+        ctx->timing_pending = !ctx->trace;
+        return OOCS_OK;
+    }
     int left = nsteps;
     while (left > 0) {
         const int k_eff = std::min(left, ctx->v.k);
@@ -1290,8 +1525,14 @@ oocs_status oocs_trace_schedule(const oocs_desc *desc, const int32_t *nsteps, in
     c->ev_d2h.assign(c->v.S, nullptr);
     c->d2h_recorded.assign(c->v.S, 0);
     static char dummy;
-    for (int f = 0; f < 3; ++f)
+    for (int f = 0; f < 4; ++f)
         c->store[f] = &dummy;  // never dereferenced in trace mode
+    if (c->d.scheme == OOCS_WAVE_ADJOINT) {  // adjoint steps count down from here
+        int64_t total = 0;
+        for (int i = 0; i < ncalls; ++i)
+            total += nsteps[i];
+        c->stats.steps_done = (uint64_t)total;
+    }
     for (int i = 0; i < ncalls && s == OOCS_OK; ++i)
         s = oocs_step(c, nsteps[i]);
     if (s != OOCS_OK) {
@@ -1537,6 +1778,10 @@ oocs_status batch_plans(const oocs_desc *descs, int32_t n, std::vector<oocs_desc
             err = "problem " + std::to_string(i) + ": a batch runs one working buffer (OOCS_SWB)";
             return OOCS_ERR_INVALID_ARG;
         }
+        if (d[i].scheme == OOCS_WAVE_ADJOINT) {
+            err = "problem " + std::to_string(i) + ": the wave adjoint runs in a context of its own";
+            return OOCS_ERR_INVALID_ARG;
+        }
         if (d[i].temporal_depth == 0)
             d[i].temporal_depth = p[i].temporal_depth;
         v[i] = derive(d[i], p[i].slab_planes);
@@ -1631,7 +1876,7 @@ oocs_status batch_ready(oocs_batch *b)
         oocs_status s = check_ready(c);
         if (s != OOCS_OK)
             return fail(nullptr, s, c->err);
-        const int nf = c->d.scheme == OOCS_WAVE ? 3 : 1;
+        const int nf = bound_fields(c->d);
         for (int f = 0; f < nf; ++f)
             if (!c->store[f])
                 return fail(nullptr, OOCS_ERR_STATE, "every field of every problem must be bound");
@@ -1961,7 +2206,7 @@ oocs_status oocs_batch_trace_schedule(const oocs_desc *descs, int32_t n, const i
     s = batch_build(b, d, p, v, nullptr);
     static char dummy;
     for (oocs_ctx *c : b->ctx)
-        for (int f = 0; f < 3; ++f)
+        for (int f = 0; f < 4; ++f)
             c->store[f] = &dummy;  // never dereferenced in trace mode
     for (int32_t i = 0; i < ncalls && s == OOCS_OK; ++i)
         if (nsteps[i] > 0)

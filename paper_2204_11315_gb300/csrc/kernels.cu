@@ -407,7 +407,8 @@ __global__ void __launch_bounds__(kStepThreads, 2)
                         const int64_t o = (int64_t)z * a.plane + (int64_t)y * a.nx + x;
                         *reinterpret_cast<float2 *>(a.out + o) = o2;
                         if constexpr (SCHEME == kAdjoint)
-                            *reinterpret_cast<float2 *>(a.out2 + o) = fmul2_rn(cv[1], o2);
+                            if (a.out2)
+                                *reinterpret_cast<float2 *>(a.out2 + o) = fmul2_rn(cv[1], o2);
                         continue;
                     }
                     float res[kVX];
@@ -460,7 +461,8 @@ __global__ void __launch_bounds__(kStepThreads, 2)
                     const int64_t o = (int64_t)z * a.plane + (int64_t)y * a.nx + x;
                     *reinterpret_cast<float2 *>(a.out + o) = make_float2(res[0], res[1]);
                     if constexpr (SCHEME == kAdjoint)
-                        *reinterpret_cast<float2 *>(a.out2 + o) = make_float2(res2[0], res2[1]);
+                        if (a.out2)
+                            *reinterpret_cast<float2 *>(a.out2 + o) = make_float2(res2[0], res2[1]);
                 }
             };
             if (kFastPath && warp_in && z_interior && !(src_in_warp && z == a.src_zw) && !rcv_plane)
@@ -641,7 +643,7 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
         return launch_step_t<1, kWave>(L, a, s);
     if (L.radius == 4 && L.scheme == kWave)
         return launch_step_t<4, kWave>(L, a, s);
-    if (L.radius == 4 && L.scheme == kAdjoint && L.c2 && L.out2)
+    if (L.radius == 4 && L.scheme == kAdjoint && L.c2)
         return launch_step_t<4, kAdjoint>(L, a, s);
     if (L.radius == 4 && L.scheme == kGradient)
         return launch_step_t<4, kGradient>(L, a, s);
@@ -649,6 +651,29 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
 }
 
 __global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
+
+// out[i] = a[i] * b[i] (one rounding), n a multiple of 4, 16-byte aligned arrays
+__global__ void __launch_bounds__(256) k_product(float *__restrict__ out, const float *__restrict__ a,
+                                                 const float *__restrict__ b, int64_t n4)
+{
+    pdl_launch_dependents();
+    pdl_wait_prior_grid();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 x = reinterpret_cast<const float4 *>(a)[i];
+        const float4 y = reinterpret_cast<const float4 *>(b)[i];
+        reinterpret_cast<float4 *>(out)[i] =
+            make_float4(fmul_rn(x.x, y.x), fmul_rn(x.y, y.y), fmul_rn(x.z, y.z), fmul_rn(x.w, y.w));
+    }
+}
+
+cudaError_t launch_product(float *out, const float *a, const float *b, int64_t n, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    const int64_t n4 = n / 4;
+    const unsigned grid = (unsigned)std::min<int64_t>((n4 + 255) / 256, (int64_t)dev_info().sms * 8);
+    return launch_pdl(k_product, dim3(grid), dim3(256), 0, s, out, a, b, n4);
+}
 
 cudaError_t launch_set_i64(int64_t *p, int64_t v, cudaStream_t s)
 {

@@ -15,7 +15,7 @@ namespace oocs {
 //   scheme     cur (stencil)   prev          m       c2     out           out2
 //   kHeat      u^n             -             -       -      u^(n+1)       -
 //   kWave      u^n             u^(n-1)       m       -      u^(n+1)       -
-//   kAdjoint   m lam^(n+1)     lam^(n+2)     m       lam^(n+1)  lam^n     m lam^n
+//   kAdjoint   m lam^(n+1)     lam^(n+2)     m       lam^(n+1)  lam^n     m lam^n (or null)
 //   kGradient  u^n             dJ/dm         lam^(n+1)  -   dJ/dm         -
 // (out may alias prev; kAdjoint adds res at global plane zr, kGradient adds w
 // at the source voxel.)
@@ -47,6 +47,9 @@ struct StepLaunch {
 };
 
 cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s);
+
+// out = a * b elementwise (FP32, one rounding each); n a multiple of 4.
+cudaError_t launch_product(float *out, const float *a, const float *b, int64_t n, cudaStream_t s);
 
 // *p = v in stream order (one thread).
 cudaError_t launch_set_i64(int64_t *p, int64_t v, cudaStream_t s);

@@ -22,8 +22,10 @@ OOCS_OK = 0
 STATUS_NAMES = {0: "OOCS_OK", 1: "OOCS_ERR_INVALID_ARG", 2: "OOCS_ERR_BUDGET",
                 3: "OOCS_ERR_HOST_ALLOC", 4: "OOCS_ERR_CUDA", 5: "OOCS_ERR_TIMEOUT",
                 6: "OOCS_ERR_STATE", 7: "OOCS_ERR_UNSUPPORTED"}
-OOCS_HEAT, OOCS_WAVE = 0, 1
+OOCS_HEAT, OOCS_WAVE, OOCS_WAVE_ADJOINT = 0, 1, 2
 OOCS_FIELD_U, OOCS_FIELD_U_PREV, OOCS_FIELD_M = 0, 1, 2
+OOCS_FIELD_LAM, OOCS_FIELD_LAM_PREV, OOCS_FIELD_FWD, OOCS_FIELD_GRAD = 0, 1, 3, 4
+BOUND_FIELDS = {OOCS_HEAT: 1, OOCS_WAVE: 3, OOCS_WAVE_ADJOINT: 4}
 OOCS_SWB, OOCS_CLASSIC = 1, 3
 MAX_RADIUS = 4
 
@@ -146,6 +148,7 @@ SIGNATURES = {
     "oocs_batch_destroy": (_i32, [_vp]),
     "oocs_batch_trace_schedule": (_i32, [ctypes.POINTER(oocs_desc), _i32, ctypes.POINTER(_i32), _i32,
                                          ctypes.POINTER(oocs_trace_op), _i64, ctypes.POINTER(_i64)]),
+    "oocs_set_receiver": (_i32, [_vp, _i64, _vp, _i64]),
     "oocs_compress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
     "oocs_decompress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
     "oocs_host_alloc": (_i32, [_u64, ctypes.POINTER(_vp)]),
@@ -412,6 +415,10 @@ def oocs_misfit_backward(desc, m_ptr, src, w, zr, res_ptr, nsteps, checkpoint_ev
                                       int(ws_bytes), _vp(grad_ptr), _vp(stream)))
 
 
+def oocs_set_receiver(ctx, zr, planes_ptr, nplanes):
+    _check(lib().oocs_set_receiver(_vp(ctx), int(zr), _vp(planes_ptr) if planes_ptr else None, int(nplanes)), ctx)
+
+
 def oocs_compress_device(ctx, field, src_ptr, z0, nplanes):
     _check(lib().oocs_compress_device(_vp(ctx), int(field), _vp(src_ptr), int(z0), int(nplanes)), ctx)
 
@@ -480,7 +487,7 @@ class OutOfCoreStencil:
             self.streams = [torch.cuda.Stream(device=self.device) for _ in range(3)]
             self.ctx = oocs_create(desc, self._ws_ptr, self.plan.workspace_bytes,
                                    [s.cuda_stream for s in self.streams])
-        nfields = 3 if desc.scheme == OOCS_WAVE else 1
+        nfields = BOUND_FIELDS[desc.scheme]
         self.stores = []
         for f in range(nfields):
             if stores is not None:
@@ -523,6 +530,11 @@ class OutOfCoreStencil:
 
     def set_time(self, t: int):
         oocs_set_time(self.ctx, t)
+
+    def bind(self, field: int, store):
+        """Bind a pinned uint8 tensor (at least plan.host_store_bytes) as the store of `field`."""
+        oocs_bind_field(self.ctx, field, store.data_ptr(), store.numel())
+        self.stores[field] = store
 
     def snapshot_stores(self):
         """Pinned host copies of the current stores (call after synchronize)."""
@@ -570,7 +582,7 @@ class BatchProblem(OutOfCoreStencil):
         c = _vp()
         _check(lib().oocs_batch_context(_vp(batch.handle), int(i), ctypes.byref(c)))
         self.ctx = c.value
-        nfields = 3 if desc.scheme == OOCS_WAVE else 1
+        nfields = BOUND_FIELDS[desc.scheme]
         self.stores = []
         for f in range(nfields):
             st = torch.zeros(self.plan.host_store_bytes, dtype=torch.uint8, pin_memory=True)

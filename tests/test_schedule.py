@@ -304,3 +304,23 @@ def test_batch_workspace_is_per_region_maximum(P):
     # problem's own device wavelet)
     one = [descs[1]]
     assert P.oocs_batch_query(one * 16) == P.oocs_query(descs[1]).workspace_bytes + 15 * (256 + 65536 * 4)
+
+
+@pytest.mark.parametrize("rate", [16, 0])
+def test_adjoint_sweep_schedule(P, rate):
+    """Adjoint sweeps (slabs in reverse z order, whole windows copied): race-free,
+    kernels of different visits ordered, every layer of lam^(k+1) overwritten
+    once per step with lam^(k-1), nothing written to lam^k or u^(k-1)."""
+    nz, ny, nx = 96, 40, 48
+    d = P.make_desc(nx, ny, nz, P.OOCS_WAVE_ADJOINT, synthetic.wave_star_coef(), 8 << 30, rate_bits=rate,
+                    temporal_depth=1, slab_planes=32, readonly_resident=1)
+    plan = P.oocs_query(d)
+    assert (plan.num_slabs, plan.halo_planes, plan.temporal_depth) == (3, 4, 1)
+    trace = P.oocs_trace_schedule(d, [1, 1, 1])
+    assert check(trace, swb=True) is None
+    order = [o["visit"] for o in trace if o["op"] == "H2D"]
+    firsts = [lo for o in trace if o["op"] == "H2D" for (k, i, lo, hi, w) in o["access"] if k == "HOST" and i == 1]
+    assert firsts[:3] == [64 // 4, 32 // 4, 0]  # slabs in reverse z order
+    writes = [(i, lo, hi) for o in trace if o["op"] == "D2H" for (k, i, lo, hi, w) in o["access"] if w]
+    assert {i for i, _, _ in writes} == {1}
+    assert sum(hi - lo for _, lo, hi in writes) == 3 * (nz // 4)
