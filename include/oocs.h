@@ -181,6 +181,23 @@ oocs_status oocs_set_source(oocs_ctx *ctx, int64_t x, int64_t y, int64_t z, cons
  * adjoint need (no counterpart in the paper's forward-only runs).          */
 oocs_status oocs_set_receiver(oocs_ctx *ctx, int64_t zr, float *planes, int64_t nplanes);
 
+/* HEAT and WAVE: record the compressed states the sweep writes.  A slab visit
+ * that advances the field from time t to t+k copies the encoded interior of
+ * its new u^(t+k) (and, for WAVE, of u^(t+k-1)) into stores[t+k - t0]
+ * (stores[t+k-1 - t0]) as well as into the field's own store, when that index
+ * lies in [0, n) and the entry is non-null; after the call's work is done a
+ * recorded store holds exactly the bytes U's store held after that state was
+ * written.  So with temporal_depth 1 (HEAT) or <= 2 (WAVE) every state a call
+ * passes through is recorded; with deeper blocking, those at the ends of the
+ * visits.  stores: n pointers to caller-owned pinned host memory of at least
+ * host_store_bytes each (the list is copied; the memory must stay valid until
+ * the work is synchronized).  Copies run on the visit's stream after its own
+ * device->host copy and count in d2h_bytes.  n = 0 stops recording.  A batch
+ * member with a record (or receiver planes) cannot be captured as a graph
+ * (OOCS_ERR_UNSUPPORTED).  The checkpoints and recomputed forward states of the
+ * out-of-core misfit gradient (no counterpart in the paper).                */
+oocs_status oocs_set_state_record(oocs_ctx *ctx, void *const *stores, int64_t t0, int64_t n);
+
 /* Fill the bound store of `field` from a raw FP32 host array of nx*ny*nz
  * values (initial compression of the chunks, Algorithm 1 input (1)): copies
  * go through the workspace and the codec kernels, using streams[0..1].
@@ -215,7 +232,10 @@ oocs_status oocs_set_time(oocs_ctx *ctx, int64_t t);
 /* Advance the bound fields `nsteps` time steps: ceil(nsteps/k) sweeps over
  * the S slabs (the last with the remainder), each slab streamed through the
  * three-stream pipeline of Algorithm 1 with the single working buffer.
- * Asynchronous; the host stores hold the new state after oocs_synchronize. */
+ * Asynchronous; the host stores hold the new state after oocs_synchronize.
+ * The call's work opens and closes with a join of the three streams: it
+ * starts after whatever the caller ordered before it on streams[0], and an
+ * event the caller records on streams[0] after the call completes with it. */
 oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps);
 
 /* Wait for all work of the context, at most timeout_ns nanoseconds

@@ -76,7 +76,8 @@ def _ooc_desc(prob: WaveProblem, scheme: int, depth: int):
 
 def _ooc_forward(torch, m, d_obs, prob: WaveProblem):
     """Slab-swept forward run from rest: the receiver record, the residuals, J
-    and the checkpoints (pinned copies of the compressed u, u_prev stores)."""
+    and the checkpoints, the compressed (u^s, u^(s-1)) stores at every segment
+    start s, which the sweep ending at s writes into the state record."""
     nz, ny, nx = prob.shape
     plane = ny * nx
     N, K = prob.nsteps, prob.checkpoint_every
@@ -90,12 +91,18 @@ def _ooc_forward(torch, m, d_obs, prob: WaveProblem):
         st.set_source(*prob.src_xyz, prob.wavelet32())
         rec = torch.empty((N, ny, nx), dtype=torch.float32, device=dev)
         O.oocs_set_receiver(st.ctx, prob.zr, _ptr(rec), N)
+        starts = list(range(0, N, K))
+        pool = torch.empty((len(starts), 2, st.plan.host_store_bytes), dtype=torch.uint8, pin_memory=True)
         st.synchronize(600.0)
-        ckpt = {}
-        for s0 in range(0, N, K):
-            ckpt[s0] = [st.stores[f].clone().pin_memory() for f in (O.OOCS_FIELD_U, O.OOCS_FIELD_U_PREV)]
+        pool[0, 0].copy_(st.stores[O.OOCS_FIELD_U])
+        pool[0, 1].copy_(st.stores[O.OOCS_FIELD_U_PREV])
+        ptrs = [0] * (N + 1)  # entry t + 1: state u^t, t = -1 .. N - 1
+        for i, s0 in enumerate(starts[1:], 1):
+            ptrs[s0 + 1], ptrs[s0] = pool[i, 0].data_ptr(), pool[i, 1].data_ptr()
+        O.oocs_set_state_record(st.ctx, ptrs, -1)
+        for s0 in starts:  # each call ends its last sweep at the next segment start
             st.step(min(K, N - s0))
-            st.synchronize(3600.0)
+        st.synchronize(3600.0)
         res = torch.empty_like(rec)
         misfit = torch.zeros(1, dtype=torch.float64, device=dev)
         O.oocs_receiver_residual(_ptr(rec), _ptr(d_obs), N * plane, _ptr(res), _ptr(misfit),
@@ -103,15 +110,19 @@ def _ooc_forward(torch, m, d_obs, prob: WaveProblem):
         torch.cuda.synchronize(dev)
     finally:
         st.close()
-    return misfit, res, ckpt
+    return misfit, res, {s0: (pool[i, 0], pool[i, 1]) for i, s0 in enumerate(starts)}
 
 
 def _ooc_backward(torch, m, res, ckpt, prob: WaveProblem):
-    """dJ/dm by adjoint sweeps, each segment's forward states recomputed from its checkpoint."""
+    """dJ/dm by adjoint sweeps over the segments in reverse.  Each segment's
+    states u^s .. u^(e-1) are recomputed from its checkpoint by sweeps of
+    depth 2 (the first of depth 1), whose two outputs the state record keeps;
+    the recomputation of one segment overlaps the adjoint sweeps of the
+    segment after it (two record rings, ordered by events on stream 0)."""
     nz, ny, nx = prob.shape
     N, K = prob.nsteps, prob.checkpoint_every
     dev = m.device
-    fwd = O.OutOfCoreStencil(_ooc_desc(prob, O.OOCS_WAVE, 1), device=dev.index or 0)
+    fwd = O.OutOfCoreStencil(_ooc_desc(prob, O.OOCS_WAVE, 2), device=dev.index or 0)
     adj = O.OutOfCoreStencil(_ooc_desc(prob, O.OOCS_WAVE_ADJOINT, 1), device=dev.index or 0)
     try:
         torch.cuda.synchronize(dev)
@@ -129,22 +140,39 @@ def _ooc_backward(torch, m, res, ckpt, prob: WaveProblem):
         O.oocs_compress_device(adj.ctx, O.OOCS_FIELD_LAM_PREV, _ptr(zero), 0, nz)
         adj.synchronize(600.0)
         del lam, zero
-        for s0 in reversed(range(0, N, K)):
+        nb = fwd.plan.host_store_bytes
+        rings = [torch.empty((K, nb), dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        ring_free = [None, None]  # event after the adjoint sweeps that last read each ring
+        for j, s0 in enumerate(reversed(range(0, N, K))):
             e0 = min(s0 + K, N)
-            # the segment's states u^s0 .. u^(e0-1), one sweep per step
-            for f, snap in zip((O.OOCS_FIELD_U, O.OOCS_FIELD_U_PREV), ckpt[s0]):
-                fwd.stores[f].copy_(snap)
-            fwd.set_time(s0)
-            states = {s0: fwd.stores[O.OOCS_FIELD_U].clone().pin_memory()}
-            for t in range(s0, e0 - 1):
-                fwd.step(1)
-                fwd.synchronize(3600.0)
-                states[t + 1] = fwd.stores[O.OOCS_FIELD_U].clone().pin_memory()
+            ring = rings[j % 2]
+            ck_u, ck_p = ckpt[s0]
+            if e0 - s0 == 1:
+                states = [ck_u]
+            else:
+                if ring_free[j % 2] is not None:
+                    fwd.streams[0].wait_event(ring_free[j % 2])
+                # the checkpoint stores are consumed: the sweeps overwrite them
+                fwd.bind(O.OOCS_FIELD_U, ck_u)
+                fwd.bind(O.OOCS_FIELD_U_PREV, ck_p)
+                fwd.set_time(s0)
+                O.oocs_set_state_record(fwd.ctx, [ring[i].data_ptr() for i in range(K)], s0)
+                fwd.step(1)                # u^(s0+1) and u^s0
+                if e0 - s0 > 2:
+                    fwd.step(e0 - s0 - 2)  # u^(s0+2) .. u^(e0-1), two per sweep
+                done = torch.cuda.Event()
+                done.record(fwd.streams[0])
+                adj.streams[0].wait_event(done)
+                states = [ring[i] for i in range(e0 - s0)]
             for k in range(e0, s0, -1):  # lam^k, u^(k-1) -> dJ/dm term k-1 and lam^(k-1)
-                adj.bind(O.OOCS_FIELD_FWD, states[k - 1])
+                adj.bind(O.OOCS_FIELD_FWD, states[k - 1 - s0])
                 adj.set_time(k)
                 adj.step(1)
-            adj.synchronize(3600.0)
+            ev = torch.cuda.Event()
+            ev.record(adj.streams[0])
+            ring_free[j % 2] = ev
+        adj.synchronize(3600.0)
+        fwd.synchronize(600.0)
         grad_m = torch.empty_like(m)
         O.oocs_decompress_device(adj.ctx, O.OOCS_FIELD_GRAD, _ptr(grad_m), 0, nz)
         adj.synchronize(600.0)

@@ -311,6 +311,11 @@ struct oocs_ctx {
     float *rec = nullptr;
     int64_t rec_z = -1, rec_n = 0;
 
+    // state record (oocs_set_state_record): host stores receiving the encoded
+    // states u^t a visit writes, srec[t - srec_t0] (null entries skipped)
+    std::vector<char *> srec;
+    int64_t srec_t0 = 0;
+
     cudaEvent_t ev_decoded[3] = {}, ev_h2d[3] = {}, ev_wrel[3] = {}, ev_join[3] = {};
     std::vector<cudaEvent_t> ev_d2h;
     std::vector<char> d2h_recorded;
@@ -888,6 +893,19 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
                                   bytes, cudaMemcpyDeviceToHost, st));
         c->stats.d2h_bytes += bytes;
     }
+    // 8b. the same layers into the state record: out slot f holds u^(t+k-f);
+    //     nothing in the pipeline reads the record, and the out slot is
+    //     rewritten only by visit g+3 on this stream
+    for (int f = 0; f < v.fout && !c->srec.empty(); ++f) {
+        const int64_t i = t + k_eff - f - c->srec_t0;
+        if (i < 0 || i >= (int64_t)c->srec.size() || !c->srec[i])
+            continue;
+        const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
+        if (!c->trace)
+            CU(c, cudaMemcpyAsync(c->srec[i] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, f), bytes,
+                                  cudaMemcpyDeviceToHost, st));
+        c->stats.d2h_bytes += bytes;
+    }
     SCHED(sched_record(c, q, kEvD2H + c->d2h_base + s));
     c->d2h_recorded[s] = 1;
     c->g++;
@@ -1184,6 +1202,22 @@ oocs_status oocs_set_receiver(oocs_ctx *ctx, int64_t zr, float *planes, int64_t 
     ctx->rec = nplanes > 0 ? planes : nullptr;
     ctx->rec_z = zr;
     ctx->rec_n = nplanes;
+    return OOCS_OK;
+}
+
+oocs_status oocs_set_state_record(oocs_ctx *ctx, void *const *stores, int64_t t0, int64_t n)
+{
+    oocs_status s = check_ready(ctx);
+    if (s != OOCS_OK)
+        return s;
+    if (ctx->d.scheme == OOCS_WAVE_ADJOINT)
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "the state record belongs to the forward schemes");
+    if (n < 0 || (n > 0 && !stores))
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "n must be >= 0 and stores non-null when n > 0");
+    // the copies already enqueued read the old list's pointers by value
+    ctx->srec.assign(n > 0 ? reinterpret_cast<char *const *>(stores) : nullptr,
+                     n > 0 ? reinterpret_cast<char *const *>(stores) + n : nullptr);
+    ctx->srec_t0 = t0;
     return OOCS_OK;
 }
 
@@ -2081,6 +2115,10 @@ oocs_status oocs_batch_capture(oocs_batch *b, int32_t nsteps)
                             " samples cannot be read by a replayed graph; use oocs_batch_step");
         if (c->prof)
             return fail(nullptr, OOCS_ERR_STATE, "turn profiling off before capturing");
+        if (c->rec || !c->srec.empty())
+            return fail(nullptr, OOCS_ERR_UNSUPPORTED,
+                        "receiver planes and state records are indexed by the time step, which a replayed "
+                        "graph does not advance; use oocs_batch_step");
         c->t_capture = (int64_t)c->stats.steps_done;
     }
     if (b->exec) {

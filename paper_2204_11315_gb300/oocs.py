@@ -149,6 +149,7 @@ SIGNATURES = {
     "oocs_batch_trace_schedule": (_i32, [ctypes.POINTER(oocs_desc), _i32, ctypes.POINTER(_i32), _i32,
                                          ctypes.POINTER(oocs_trace_op), _i64, ctypes.POINTER(_i64)]),
     "oocs_set_receiver": (_i32, [_vp, _i64, _vp, _i64]),
+    "oocs_set_state_record": (_i32, [_vp, ctypes.POINTER(_vp), _i64, _i64]),
     "oocs_compress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
     "oocs_decompress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
     "oocs_host_alloc": (_i32, [_u64, ctypes.POINTER(_vp)]),
@@ -419,6 +420,13 @@ def oocs_set_receiver(ctx, zr, planes_ptr, nplanes):
     _check(lib().oocs_set_receiver(_vp(ctx), int(zr), _vp(planes_ptr) if planes_ptr else None, int(nplanes)), ctx)
 
 
+def oocs_set_state_record(ctx, store_ptrs, t0=0):
+    """store_ptrs[i]: host address receiving the compressed state u^(t0 + i), or 0 to skip it."""
+    n = len(store_ptrs)
+    arr = (_vp * max(n, 1))(*[p or None for p in store_ptrs])
+    _check(lib().oocs_set_state_record(_vp(ctx), arr if n else None, int(t0), n), ctx)
+
+
 def oocs_compress_device(ctx, field, src_ptr, z0, nplanes):
     _check(lib().oocs_compress_device(_vp(ctx), int(field), _vp(src_ptr), int(z0), int(nplanes)), ctx)
 
@@ -527,6 +535,9 @@ class OutOfCoreStencil:
 
     def step(self, nsteps: int):
         oocs_step(self.ctx, nsteps)
+        if self.desc.scheme == OOCS_WAVE_ADJOINT:  # the library swapped the two stores
+            self.stores[OOCS_FIELD_LAM], self.stores[OOCS_FIELD_LAM_PREV] = \
+                self.stores[OOCS_FIELD_LAM_PREV], self.stores[OOCS_FIELD_LAM]
 
     def set_time(self, t: int):
         oocs_set_time(self.ctx, t)

@@ -324,11 +324,13 @@ def _ooc_problem(P, rate, K, nsteps=60, budget=None, slab=32):
     return A, prob, v, v_true
 
 
-@pytest.mark.parametrize("K,nsteps", [(10, 60), (7, 55)])
+@pytest.mark.parametrize("K,nsteps", [(10, 60), (7, 55), (10, 51)])
 def test_out_of_core_gradient_equals_in_core_uncompressed(P, K, nsteps):
-    """Uncompressed, the slab-swept forward, the one-step-per-sweep recomputation
-    and the adjoint sweeps (3 slabs, reverse z order) perform the in-core
-    driver's operations on the same values: J to double rounding, dJ/dv bit for bit."""
+    """Uncompressed, the slab-swept forward, the recomputation of each segment
+    (sweeps of depth 1 and 2, states kept by the state record) and the adjoint
+    sweeps (3 slabs, reverse z order) perform the in-core driver's operations
+    on the same values: J to double rounding, dJ/dv bit for bit.  Segments of
+    7 steps end on a depth-1 sweep; 51 = 5 x 10 + 1 ends on a one-step segment."""
     torch = torch_cuda()
     A, prob_in, v, v_true = _ooc_problem(P, 0, K, nsteps)
     _, prob_oc, _, _ = _ooc_problem(P, 0, K, nsteps, budget=8 << 30)
