@@ -94,6 +94,12 @@ def _declare(L):
     L.oracle_decode_block.restype = _i32
     L.oracle_encode_field.argtypes = [_fp, _i64, _i64, _i64, _i32, _u32p]
     L.oracle_decode_field.argtypes = [_u32p, _i64, _i64, _i64, _i32, _fp, _i8p]
+    L.oracle_bq_header.argtypes = [_fp]
+    L.oracle_bq_header.restype = _i32
+    L.oracle_bq_encode_block.argtypes = [_fp, _i32, _u32p]
+    L.oracle_bq_decode_block.argtypes = [_u32p, _i32, _fp]
+    L.oracle_bq_encode_field.argtypes = [_fp, _i64, _i64, _i64, _i32, _u32p]
+    L.oracle_bq_decode_field.argtypes = [_u32p, _i64, _i64, _i64, _i32, _fp]
 
 
 def _p(a, t):
@@ -337,3 +343,46 @@ def decode_field(words, shape, rate, with_planes=False):
     low = np.empty(nb, np.int8)
     lib().oracle_decode_field(_p(w, _u32p), nx, ny, nz, int(rate), _p(f, _fp), _p(low, _i8p))
     return (f, low) if with_planes else f
+
+
+# ---------------------------------------------------------------------------
+# block quantiser (oracle.c item 3; Sec. 7 future work (1))
+# ---------------------------------------------------------------------------
+
+def bq_header(v64) -> int:
+    v = np.ascontiguousarray(v64, dtype=np.float32).reshape(64)
+    return int(lib().oracle_bq_header(_p(v, _fp)))
+
+
+def bq_encode_block(v64, rate):
+    v = np.ascontiguousarray(v64, dtype=np.float32).reshape(64)
+    words = np.zeros(2 * rate, np.uint32)
+    lib().oracle_bq_encode_block(_p(v, _fp), int(rate), _p(words, _u32p))
+    return words
+
+
+def bq_decode_block(words, rate):
+    w = np.ascontiguousarray(words, dtype=np.uint32).reshape(2 * rate)
+    v = np.empty(64, np.float32)
+    lib().oracle_bq_decode_block(_p(w, _u32p), int(rate), _p(v, _fp))
+    return v
+
+
+def bq_encode_field(f, rate):
+    """Block-quantise an [nz][ny][nx] FP32 field; same block layout as encode_field."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    nz, ny, nx = f.shape
+    assert nx % 4 == 0 and ny % 4 == 0 and nz % 4 == 0 and 2 <= rate <= 32
+    nb = (nx // 4) * (ny // 4) * (nz // 4)
+    out = np.zeros(nb * 2 * rate, np.uint32)
+    lib().oracle_bq_encode_field(_p(f, _fp), nx, ny, nz, int(rate), _p(out, _u32p))
+    return out
+
+
+def bq_decode_field(words, shape, rate):
+    nz, ny, nx = shape
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    assert w.size == (nx // 4) * (ny // 4) * (nz // 4) * 2 * rate
+    f = np.empty((nz, ny, nx), np.float32)
+    lib().oracle_bq_decode_field(_p(w, _u32p), nx, ny, nz, int(rate), _p(f, _fp))
+    return f

@@ -36,6 +36,17 @@
  *            exactly 64*rate bits (8 header bits included).
  *      Decoding is the inverse, with v = float(q) * 2^(emax - 29).
  *
+ *   3. A plain block quantiser, the simpler fixed-rate codec the comparison of
+ *      compression libraries (Sec. 7, future work (1)) sets against the
+ *      transform codec.  Same 4x4x4 block, same 64*rate bits per block:
+ *        header: 8 bits, 0 for an all-zero block, else emax + 127, where
+ *                emax = max(frexp exponent of max|v|, -126), so max|v| < 2^emax;
+ *        values: q = rate - 1 bits each, in block index order, two's
+ *                complement n = clamp(rint(v 2^(q-1-emax)), -(2^(q-1)-1),
+ *                2^(q-1)-1), rint rounding half to even; the last 56 bits of
+ *                the block are zero.
+ *      Decoding gives v = fl32(fl32(n) 2^(emax-q+1)) (round to nearest).
+ *
  * Readings where the paper is silent are listed with the project design notes;
  * they are: the header is the 8-bit biased exponent emax+127 (0 = all-zero
  * block); emax is clamped to >= -95, so |v| < 2^-124 quantises to 0; the
@@ -625,4 +636,107 @@ double oracle_wave_misfit_gradient(int64_t nx, int64_t ny, int64_t nz, const dou
     free(scratch);
     free(res);
     return J;
+}
+
+/* ---------------------------------------------------------------------------
+ * Block quantiser (item 3 of the header): the bits of a block are numbered
+ * from bit 0 of word 0 upwards (bit p is bit p % 32 of word p / 32), and are
+ * written and read one at a time.
+ * ------------------------------------------------------------------------- */
+static void bq_put_bit(uint32_t *words, int p, unsigned bit)
+{
+    if (bit)
+        words[p / 32] |= 1u << (p % 32);
+}
+
+static unsigned bq_get_bit(const uint32_t *words, int p) { return (words[p / 32] >> (p % 32)) & 1u; }
+
+/* 0 for an all-zero block, else emax + 127 (in 1 .. 255) */
+int oracle_bq_header(const float *v)
+{
+    float mx = 0.0f;
+    for (int i = 0; i < 64; i++)
+        if (fabsf(v[i]) > mx)
+            mx = fabsf(v[i]);
+    if (mx == 0.0f)
+        return 0;
+    int e;
+    frexpf(mx, &e); /* mx = f 2^e, f in [0.5, 1) */
+    if (e < -126)
+        e = -126;
+    return e + 127;
+}
+
+void oracle_bq_encode_block(const float *v, int rate, uint32_t *words)
+{
+    const int q = rate - 1;
+    const int64_t lim = ((int64_t)1 << (q - 1)) - 1;
+    memset(words, 0, (size_t)(2 * rate) * sizeof(uint32_t));
+    const int hdr = oracle_bq_header(v);
+    for (int b = 0; b < 8; b++)
+        bq_put_bit(words, b, (hdr >> b) & 1);
+    if (hdr == 0)
+        return;
+    const int emax = hdr - 127;
+    for (int j = 0; j < 64; j++) {
+        /* v 2^(q-1-emax) is exact in double for every finite float */
+        double x = rint(ldexp((double)v[j], q - 1 - emax));
+        int64_t n = (int64_t)x;
+        if (n > lim)
+            n = lim;
+        if (n < -lim)
+            n = -lim;
+        const uint64_t u = (uint64_t)n; /* two's complement, low q bits kept */
+        for (int b = 0; b < q; b++)
+            bq_put_bit(words, 8 + j * q + b, (unsigned)((u >> b) & 1u));
+    }
+}
+
+void oracle_bq_decode_block(const uint32_t *words, int rate, float *v)
+{
+    const int q = rate - 1;
+    int hdr = 0;
+    for (int b = 0; b < 8; b++)
+        hdr |= (int)bq_get_bit(words, b) << b;
+    if (hdr == 0) {
+        for (int j = 0; j < 64; j++)
+            v[j] = 0.0f;
+        return;
+    }
+    const int emax = hdr - 127;
+    for (int j = 0; j < 64; j++) {
+        int64_t n = 0;
+        for (int b = 0; b < q; b++)
+            n |= (int64_t)bq_get_bit(words, 8 + j * q + b) << b;
+        if (n >> (q - 1)) /* sign bit of the q-bit field */
+            n -= (int64_t)1 << q;
+        const float fn = (float)n; /* round to nearest */
+        v[j] = (float)((double)fn * ldexp(1.0, emax - q + 1)); /* exact product, one rounding */
+    }
+}
+
+void oracle_bq_encode_field(const float *f, int64_t nx, int64_t ny, int64_t nz, int rate, uint32_t *out)
+{
+    int64_t bnx = nx / 4, bny = ny / 4, bnz = nz / 4, b;
+    int64_t nb = bnx * bny * bnz;
+#pragma omp parallel for schedule(static)
+    for (b = 0; b < nb; b++) {
+        int64_t bx = b % bnx, by = (b / bnx) % bny, bz = b / (bnx * bny);
+        float v[64];
+        gather(f, nx, ny, bx, by, bz, v);
+        oracle_bq_encode_block(v, rate, out + b * 2 * rate);
+    }
+}
+
+void oracle_bq_decode_field(const uint32_t *in, int64_t nx, int64_t ny, int64_t nz, int rate, float *f)
+{
+    int64_t bnx = nx / 4, bny = ny / 4, bnz = nz / 4, b;
+    int64_t nb = bnx * bny * bnz;
+#pragma omp parallel for schedule(static)
+    for (b = 0; b < nb; b++) {
+        int64_t bx = b % bnx, by = (b / bnx) % bny, bz = b / (bnx * bny);
+        float v[64];
+        oracle_bq_decode_block(in + b * 2 * rate, rate, v);
+        scatter(f, nx, ny, bx, by, bz, v);
+    }
 }
