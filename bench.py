@@ -215,15 +215,16 @@ def make_inputs(total_steps):
     return m, w, (cx, cy, cz), z
 
 
-def wave_desc(P, rate, wb=1, ro=RO_RESIDENT):
+def wave_desc(P, rate, wb=1, ro=RO_RESIDENT, codec=0):
     import synthetic
     return P.make_desc(N, N, N, P.OOCS_WAVE, synthetic.wave_star_coef(), BUDGET, rate_bits=rate,
-                       temporal_depth=K_DEPTH, slab_planes=SLAB, working_buffers=wb, readonly_resident=ro)
+                       temporal_depth=K_DEPTH, slab_planes=SLAB, working_buffers=wb, readonly_resident=ro,
+                       codec=codec)
 
 
-def open_ctx(P, torch, rate, wb, inputs, ro=RO_RESIDENT):
+def open_ctx(P, torch, rate, wb, inputs, ro=RO_RESIDENT, codec=0):
     m, w, src, z = inputs
-    st = P.OutOfCoreStencil(wave_desc(P, rate, wb, ro))
+    st = P.OutOfCoreStencil(wave_desc(P, rate, wb, ro, codec))
     pin = {}
     for name, arr in (("z", z), ("m", m)):
         t = torch.empty(arr.shape, dtype=torch.float32, pin_memory=True)
@@ -446,14 +447,19 @@ def run_ours(args):
     compare = None
     if single and not args.no_compare:
         compare = {}
-        for name, rate, wb, ro in (("uncompressed_swb", 0, 1, RO_RESIDENT),
-                                   ("uncompressed_classic", 0, 3, RO_RESIDENT),
-                                   (f"rate{args.rate}_classic", args.rate, 3, RO_RESIDENT),
-                                   ("rate8_swb", 8, 1, RO_RESIDENT), ("rate12_swb", 12, 1, RO_RESIDENT),
-                                   (f"rate{args.rate}_swb_m_streamed", args.rate, 1, 0),
-                                   ("uncompressed_swb_m_streamed", 0, 1, 0),
-                                   ("uncompressed_classic_m_streamed", 0, 3, 0)):
-            st, pin = open_ctx(P, torch, rate, wb, inputs, ro)
+        ref = incore_reference(P, torch, dev, inputs)
+        for name, rate, wb, ro, codec in (("uncompressed_swb", 0, 1, RO_RESIDENT, 0),
+                                          ("uncompressed_classic", 0, 3, RO_RESIDENT, 0),
+                                          (f"rate{args.rate}_classic", args.rate, 3, RO_RESIDENT, 0),
+                                          ("rate8_swb", 8, 1, RO_RESIDENT, 0), ("rate12_swb", 12, 1, RO_RESIDENT, 0),
+                                          (f"rate{args.rate}_swb_m_streamed", args.rate, 1, 0, 0),
+                                          ("uncompressed_swb_m_streamed", 0, 1, 0, 0),
+                                          ("uncompressed_classic_m_streamed", 0, 3, 0, 0),
+                                          # the simpler codec of the Sec. 7 (1) comparison
+                                          ("quant12_swb", 12, 1, RO_RESIDENT, 1),
+                                          ("quant16_swb", 16, 1, RO_RESIDENT, 1),
+                                          ("quant20_swb", 20, 1, RO_RESIDENT, 1)):
+            st, pin = open_ctx(P, torch, rate, wb, inputs, ro, codec)
             snap_u = st.snapshot_stores()
             timed_calls(torch, st, 1, snap_u)
             k = 2
@@ -463,6 +469,10 @@ def run_ours(args):
             st.close()
             del st, pin, snap_u
             torch.cuda.empty_cache()
+            if rate and wb == 1 and ro == RO_RESIDENT:  # accuracy of each codec and rate
+                compare[name]["rel_l2_vs_uncompressed_fp32"] = check_accuracy(
+                    P, torch, dev, rate, inputs, codec, ref)["rel_l2_vs_uncompressed_fp32"]
+        del ref
         # the same workload as a batch of one, its 100-step call replayed as one CUDA graph
         m, w, src, z = inputs
         b = P.OutOfCoreBatch([wave_desc(P, args.rate)])
@@ -818,15 +828,14 @@ def run_adjoint(P, torch, dev, hbm_peak):
             "out_of_core": ooc}
 
 
-def check_accuracy(P, torch, dev, rate, inputs):
+def check_accuracy(P, torch, dev, rate, inputs, codec=0, ref=None):
     """Compressed run of the workload (100 steps from rest) against the
     uncompressed in-core GPU run of the same FP32 arithmetic (which the tests
-    hold within 1e-5 of the FP64 oracle)."""
+    hold within 1e-5 of the FP64 oracle); `ref` reuses that run."""
     import numpy as np
 
     import synthetic
-    m, w, src, z = inputs
-    st, pin = open_ctx(P, torch, rate, 1, inputs)
+    st, pin = open_ctx(P, torch, rate, 1, inputs, codec=codec)
     st.step(STEPS_PER_CALL)
     st.synchronize(600.0)
     out = st.decompress(P.OOCS_FIELD_U)
@@ -835,6 +844,19 @@ def check_accuracy(P, torch, dev, rate, inputs):
     st.close()
     del st, pin
     torch.cuda.empty_cache()
+    if ref is None:
+        ref = incore_reference(P, torch, dev, inputs)
+    rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    tol = synthetic.TOL_COMPRESSED.get(rate) if rate else synthetic.TOL_UNCOMPRESSED["wave"]
+    return {"rel_l2_vs_uncompressed_fp32": rel, "max_abs": float(np.max(np.abs(got - ref))),
+            "max_ref": float(np.max(np.abs(ref))), "stated_max_rel_l2": tol,
+            "within": bool(tol is not None and rel <= tol)}
+
+
+def incore_reference(P, torch, dev, inputs):
+    """The workload's 100 steps from rest, uncompressed and in core on the GPU (FP64 copy of u)."""
+    import numpy as np
+    m, w, src, z = inputs
     u = torch.zeros((N, N, N), device=dev)
     up = torch.zeros((N, N, N), device=dev)
     mm = torch.from_numpy(m).to(dev)
@@ -845,11 +867,7 @@ def check_accuracy(P, torch, dev, rate, inputs):
     ref = u.cpu().numpy().astype(np.float64)
     del u, up, mm, sc
     torch.cuda.empty_cache()
-    rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-    tol = synthetic.TOL_COMPRESSED.get(rate) if rate else synthetic.TOL_UNCOMPRESSED["wave"]
-    return {"rel_l2_vs_uncompressed_fp32": rel, "max_abs": float(np.max(np.abs(got - ref))),
-            "max_ref": float(np.max(np.abs(ref))), "stated_max_rel_l2": tol,
-            "within": bool(tol is not None and rel <= tol)}
+    return ref
 
 
 # ------------------------------------------------------------ reference --

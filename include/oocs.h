@@ -72,6 +72,18 @@ enum { OOCS_FIELD_U = 0, OOCS_FIELD_U_PREV = 1, OOCS_FIELD_M = 2 };
  * GRAD is read with oocs_decompress_device.                                 */
 enum { OOCS_FIELD_LAM = 0, OOCS_FIELD_LAM_PREV = 1, OOCS_FIELD_FWD = 3, OOCS_FIELD_GRAD = 4 };
 
+/* Fixed-rate codecs of the host store.  Both code each 4x4x4 block of FP32
+ * values (index i + 4j + 16k) into exactly 8*rate bytes, so they share the
+ * store layout, the plan and the schedule.
+ *  TRANSFORM: the ZFP method (block-floating-point quantisation, decorrelating
+ *   lifting transform, embedded bit-plane coding; cuZFP in the paper, Sec. 4.2),
+ *   with this library's own bitstream.
+ *  QUANT: an 8-bit header (0 = all-zero block, else emax + 127 with
+ *   emax = max(frexp exponent of max|v|, -126)), then 64 two's complement
+ *   fields of q = rate - 1 bits, n = clamp(rint(v 2^(q-1-emax)), +-(2^(q-1)-1)),
+ *   bits numbered from bit 0 of word 0; decodes to RN(RN(n) 2^(emax-q+1)).  */
+enum { OOCS_CODEC_TRANSFORM = 0, OOCS_CODEC_QUANT = 1 };
+
 /* Working-buffer schemes (Sec. 5): 1 = single working buffer shared by the
  * three streams (the paper's method); 3 = classic, one per stream (Fig. 6a). */
 enum { OOCS_SWB = 1, OOCS_CLASSIC = 3 };
@@ -93,7 +105,9 @@ typedef struct {
                                   * device as FP32 (decoded once from its store) for the
                                   * context's life, counted in the workspace, so only U and
                                   * U_PREV cross the host link.  Ignored for HEAT.           */
-    int32_t reserved;            /* 0                                                        */
+    int32_t codec;               /* rate_bits > 0: OOCS_CODEC_TRANSFORM (0, the paper's kind of
+                                  * codec, Sec. 4.2; rate 1..32) or OOCS_CODEC_QUANT (1, a plain
+                                  * block quantiser, the comparison of Sec. 7 (1); rate 2..32) */
 } oocs_desc;
 
 /* Resolved plan (Sec. 3.1 chunking and temporal blocking; Sec. 6.2 memory model). */
@@ -356,11 +370,12 @@ oocs_status oocs_misfit_backward(const oocs_desc *desc, const float *m, const in
 /* Fixed-rate block codec (Sec. 4.2) on device arrays.  encode: field
  * [nz][ny][nx] FP32 -> (nx/4)(ny/4)(nz/4) blocks of 8*rate bytes in layer
  * order (block (bx,by,bz) at ((bz*(ny/4)+by)*(nx/4)+bx)).  decode: inverse.
- * rate in [1, 32]; dims multiples of 4; pointers 16-byte aligned.          */
+ * codec OOCS_CODEC_TRANSFORM with rate in [1, 32] or OOCS_CODEC_QUANT with
+ * rate in [2, 32]; dims multiples of 4; pointers 16-byte aligned.          */
 oocs_status oocs_encode_device(const float *field, int64_t nx, int64_t ny, int64_t nz,
-                               int32_t rate, void *blocks, void *stream);
+                               int32_t rate, int32_t codec, void *blocks, void *stream);
 oocs_status oocs_decode_device(const void *blocks, int64_t nx, int64_t ny, int64_t nz,
-                               int32_t rate, float *field, void *stream);
+                               int32_t rate, int32_t codec, float *field, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Schedule trace (no GPU needed): the operations oocs_step would enqueue, in

@@ -189,14 +189,14 @@ cudaError_t save_field(const float *f, const oocs_desc *d, int32_t rate, void *d
 {
     if (!rate)
         return cudaMemcpyAsync(dst, f, d->nx * d->ny * d->nz * 4, cudaMemcpyDeviceToDevice, st);
-    return launch_encode_layers(f, d->nx, d->ny, d->nz / 4, rate, dst, st);
+    return launch_encode_layers(f, d->nx, d->ny, d->nz / 4, rate, kCodecTransform, dst, st);
 }
 
 cudaError_t load_field(const void *src, const oocs_desc *d, int32_t rate, float *f, cudaStream_t st)
 {
     if (!rate)
         return cudaMemcpyAsync(f, src, d->nx * d->ny * d->nz * 4, cudaMemcpyDeviceToDevice, st);
-    return launch_decode_layers(src, d->nx, d->ny, d->nz / 4, rate, f, st);
+    return launch_decode_layers(src, d->nx, d->ny, d->nz / 4, rate, kCodecTransform, f, st);
 }
 
 unsigned grid1d(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16); }

@@ -198,6 +198,14 @@ oocs_status validate_desc(const oocs_desc *d, std::string &err)
         err = "rate_bits must be 0 (uncompressed) or 1..32";
         return OOCS_ERR_INVALID_ARG;
     }
+    if (d->codec != OOCS_CODEC_TRANSFORM && d->codec != OOCS_CODEC_QUANT) {
+        err = "codec must be OOCS_CODEC_TRANSFORM (0) or OOCS_CODEC_QUANT (1)";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->codec == OOCS_CODEC_QUANT && d->rate_bits == 1) {
+        err = "the block quantiser needs rate_bits >= 2";
+        return OOCS_ERR_INVALID_ARG;
+    }
     if (d->temporal_depth < 0 || d->temporal_depth > 64) {
         err = "temporal_depth must be 0 (auto) or 1..64";
         return OOCS_ERR_INVALID_ARG;
@@ -605,7 +613,7 @@ oocs_status load_layers(oocs_ctx *c, const char *src, int64_t src_l0, int64_t l0
     if (c->d.rate_bits == 0) {
         CU(c, cudaMemcpyAsync(to, from, (l1 - l0) * c->v.layer_bytes, cudaMemcpyDeviceToDevice, s));
     } else {
-        CU(c, launch_decode_layers(from, c->d.nx, c->d.ny, l1 - l0, c->d.rate_bits, to, s));
+        CU(c, launch_decode_layers(from, c->d.nx, c->d.ny, l1 - l0, c->d.rate_bits, c->d.codec, to, s));
         c->stats.kernel_launches++;
     }
     return ks.end(kClsLoad, (uint64_t)(l1 - l0) * 4 * c->d.nx * c->d.ny);
@@ -625,7 +633,7 @@ oocs_status store_layers(oocs_ctx *c, const float *src, int64_t w0, int64_t l0, 
     if (c->d.rate_bits == 0) {
         CU(c, cudaMemcpyAsync(dst, from, (l1 - l0) * c->v.layer_bytes, cudaMemcpyDeviceToDevice, s));
     } else {
-        CU(c, launch_encode_layers(from, c->d.nx, c->d.ny, l1 - l0, c->d.rate_bits, dst, s));
+        CU(c, launch_encode_layers(from, c->d.nx, c->d.ny, l1 - l0, c->d.rate_bits, c->d.codec, dst, s));
         c->stats.kernel_launches++;
     }
     return ks.end(kClsStore, (uint64_t)(l1 - l0) * 4 * c->d.nx * c->d.ny);
@@ -653,7 +661,7 @@ oocs_status upload_resident(oocs_ctx *c)
             const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
             CU(c, cudaMemcpyAsync(blk, store + (uint64_t)(z0 / 4) * v.layer_bytes, bytes, cudaMemcpyHostToDevice,
                                   st));
-            CU(c, launch_decode_layers(blk, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, c->ro_m() + z0 * plane_f, st));
+            CU(c, launch_decode_layers(blk, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, d.codec, c->ro_m() + z0 * plane_f, st));
             c->stats.h2d_bytes += bytes;
             c->stats.kernel_launches++;
         }
@@ -753,7 +761,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         oocs_status r = ks.begin(c, st, kClsLoad);
         if (r != OOCS_OK)
             return r;
-        CU(c, launch_decode_segments(sg, nl, d.nx, d.ny, d.rate_bits, st));
+        CU(c, launch_decode_segments(sg, nl, d.nx, d.ny, d.rate_bits, d.codec, st));
         c->stats.kernel_launches++;
         r = ks.end(kClsLoad, (uint64_t)v.fin_stream * (w1 - w0) * plane_f);
         if (r != OOCS_OK)
@@ -861,7 +869,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         oocs_status r = ks.begin(c, st, kClsStore);
         if (r != OOCS_OK)
             return r;
-        CU(c, launch_encode_segments(sg, nl, d.nx, d.ny, d.rate_bits, st));
+        CU(c, launch_encode_segments(sg, nl, d.nx, d.ny, d.rate_bits, d.codec, st));
         c->stats.kernel_launches++;
         r = ks.end(kClsStore, (uint64_t)v.fout * (z1 - z0) * plane_f);
         if (r != OOCS_OK)
@@ -974,7 +982,7 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k)
                 sg.planes[sg.nseg] = dst[f];
                 nl[sg.nseg++] = l1[f] - l0[f];
             }
-            CU(c, launch_decode_segments(sg, nl, d.nx, d.ny, d.rate_bits, st));
+            CU(c, launch_decode_segments(sg, nl, d.nx, d.ny, d.rate_bits, d.codec, st));
             c->stats.kernel_launches++;
         } else {
             for (int f = 0; f < 3; ++f)
@@ -1261,11 +1269,11 @@ static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, f
         if (enc) {
             CU(ctx, cudaMemcpyAsync(raw, src + z0 * d.nx * d.ny, (z1 - z0) * plane_bytes,
                                     cudaMemcpyHostToDevice, st));
-            CU(ctx, launch_encode_layers(raw, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, blk, st));
+            CU(ctx, launch_encode_layers(raw, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, d.codec, blk, st));
             CU(ctx, cudaMemcpyAsync(host_blk, blk, cbytes, cudaMemcpyDeviceToHost, st));
         } else {
             CU(ctx, cudaMemcpyAsync(blk, host_blk, cbytes, cudaMemcpyHostToDevice, st));
-            CU(ctx, launch_decode_layers(blk, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, raw, st));
+            CU(ctx, launch_decode_layers(blk, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, d.codec, raw, st));
             CU(ctx, cudaMemcpyAsync(dst + z0 * d.nx * d.ny, raw, (z1 - z0) * plane_bytes,
                                     cudaMemcpyDeviceToHost, st));
         }
@@ -1328,12 +1336,12 @@ static oocs_status codec_range_device(oocs_ctx *ctx, int32_t field, const float 
                 CU(ctx, cudaMemcpyAsync(dst + c0 * plane, host, cbytes, cudaMemcpyHostToDevice, st));
         } else if (enc) {
             char *blk = ctx->out_slot(0, 0);
-            CU(ctx, launch_encode_layers(src + c0 * plane, d.nx, d.ny, n / 4, d.rate_bits, blk, st));
+            CU(ctx, launch_encode_layers(src + c0 * plane, d.nx, d.ny, n / 4, d.rate_bits, d.codec, blk, st));
             CU(ctx, cudaMemcpyAsync(host, blk, cbytes, cudaMemcpyDeviceToHost, st));
         } else {
             char *blk = ctx->in_slot(0, 0);
             CU(ctx, cudaMemcpyAsync(blk, host, cbytes, cudaMemcpyHostToDevice, st));
-            CU(ctx, launch_decode_layers(blk, d.nx, d.ny, n / 4, d.rate_bits, dst + c0 * plane, st));
+            CU(ctx, launch_decode_layers(blk, d.nx, d.ny, n / 4, d.rate_bits, d.codec, dst + c0 * plane, st));
         }
     }
     return join_streams(ctx);
@@ -1696,25 +1704,27 @@ oocs_status oocs_incore_run(const oocs_desc *desc, float *u, float *u_prev, cons
     return OOCS_OK;
 }
 
-static oocs_status codec_args(int64_t nx, int64_t ny, int64_t nz, int32_t rate, const void *a,
+static oocs_status codec_args(int64_t nx, int64_t ny, int64_t nz, int32_t rate, int32_t codec, const void *a,
                               const void *b)
 {
     if (nx < 4 || ny < 4 || nz < 4 || nx % 4 || ny % 4 || nz % 4)
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "dims must be positive multiples of 4");
-    if (rate < 1 || rate > 32)
-        return fail(nullptr, OOCS_ERR_INVALID_ARG, "rate must be in [1, 32]");
+    if (codec != OOCS_CODEC_TRANSFORM && codec != OOCS_CODEC_QUANT)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "codec must be OOCS_CODEC_TRANSFORM or OOCS_CODEC_QUANT");
+    if (rate < (codec == OOCS_CODEC_QUANT ? 2 : 1) || rate > 32)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "rate must be in [1, 32] (transform) or [2, 32] (quantiser)");
     if (!a || !b || (reinterpret_cast<uintptr_t>(a) & 15) || (reinterpret_cast<uintptr_t>(b) & 15))
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "pointers must be non-null and 16-byte aligned");
     return OOCS_OK;
 }
 
 oocs_status oocs_encode_device(const float *field, int64_t nx, int64_t ny, int64_t nz, int32_t rate,
-                               void *blocks, void *stream)
+                               int32_t codec, void *blocks, void *stream)
 {
-    oocs_status s = codec_args(nx, ny, nz, rate, field, blocks);
+    oocs_status s = codec_args(nx, ny, nz, rate, codec, field, blocks);
     if (s != OOCS_OK)
         return s;
-    cudaError_t e = launch_encode_layers(field, nx, ny, nz / 4, rate, blocks,
+    cudaError_t e = launch_encode_layers(field, nx, ny, nz / 4, rate, codec, blocks,
                                          static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess)
         return fail(nullptr, OOCS_ERR_CUDA, std::string("encode: ") + cudaGetErrorString(e));
@@ -1722,12 +1732,12 @@ oocs_status oocs_encode_device(const float *field, int64_t nx, int64_t ny, int64
 }
 
 oocs_status oocs_decode_device(const void *blocks, int64_t nx, int64_t ny, int64_t nz, int32_t rate,
-                               float *field, void *stream)
+                               int32_t codec, float *field, void *stream)
 {
-    oocs_status s = codec_args(nx, ny, nz, rate, blocks, field);
+    oocs_status s = codec_args(nx, ny, nz, rate, codec, blocks, field);
     if (s != OOCS_OK)
         return s;
-    cudaError_t e = launch_decode_layers(blocks, nx, ny, nz / 4, rate, field,
+    cudaError_t e = launch_decode_layers(blocks, nx, ny, nz / 4, rate, codec, field,
                                          static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess)
         return fail(nullptr, OOCS_ERR_CUDA, std::string("decode: ") + cudaGetErrorString(e));

@@ -20,6 +20,7 @@
 
 #include "codec.cuh"
 #include "kernels.h"
+#include "quant.cuh"
 #include "stencil.cuh"
 #include "tma.cuh"
 
@@ -725,6 +726,7 @@ OOCS_FN uint32_t *segment_word(const CodecSegments &sg, int64_t blk, int rate, i
     return static_cast<uint32_t *>(sg.blocks[g]) + (blk - sg.first[g]) * (int64_t)(2 * rate) + wi;
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(kCodecThreads)
     k_encode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
@@ -754,7 +756,10 @@ __global__ void __launch_bounds__(kCodecThreads)
                 v[16 * k + 4 * j + 3] = f.w;
             }
         uint32_t *row = sw + threadIdx.x * stride;
-        encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
+        if constexpr (KIND == kCodecQuant)
+            bq_encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
+        else
+            encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
     }
     __syncthreads();
     // each warp copies whole blocks out, its lanes over the block's words
@@ -767,6 +772,7 @@ __global__ void __launch_bounds__(kCodecThreads)
     }
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(kCodecThreads)
     k_decode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
@@ -785,7 +791,10 @@ __global__ void __launch_bounds__(kCodecThreads)
         static_cast<const uint32_t *>(sg.blocks[g]) + (b - sg.first[g]) * (int64_t)(2 * rate);
     const int nw = 2 * rate;
     float v[64];
-    decode_block(rate, [&](int i) -> uint32_t { return i < nw ? __ldg(src + i) : 0u; }, v);
+    if constexpr (KIND == kCodecQuant)
+        bq_decode_block(rate, [&](int i) -> uint32_t { return __ldg(src + i); }, v);
+    else
+        decode_block(rate, [&](int i) -> uint32_t { return i < nw ? __ldg(src + i) : 0u; }, v);
     float *base = sg.planes[g] + 4 * bl * plane + (int64_t)(4 * by) * nx + 4 * bx;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -806,51 +815,67 @@ static cudaError_t seal_segments(CodecSegments &sg, int64_t nx, int64_t ny, cons
     return cudaSuccess;
 }
 
-cudaError_t launch_encode_segments(CodecSegments sg, const int64_t *nlayers, int64_t nx, int64_t ny,
-                                   int rate, cudaStream_t s)
+static bool codec_ok(int rate, int kind)
 {
+    return (kind == kCodecTransform && rate >= 1 && rate <= 32) || (kind == kCodecQuant && rate >= 2 && rate <= 32);
+}
+
+cudaError_t launch_encode_segments(CodecSegments sg, const int64_t *nlayers, int64_t nx, int64_t ny,
+                                   int rate, int kind, cudaStream_t s)
+{
+    if (!codec_ok(rate, kind))
+        return cudaErrorInvalidValue;
     cudaError_t e = seal_segments(sg, nx, ny, nlayers);
     if (e != cudaSuccess)
         return e;
     const int64_t nb = sg.first[sg.nseg];
     if (nb == 0)
         return cudaSuccess;
-    return launch_pdl(k_encode_layers, dim3((unsigned)((nb + kCodecThreads - 1) / kCodecThreads)),
-                      dim3(kCodecThreads), (size_t)kCodecThreads * (2 * rate + 1) * 4, s, sg, (int)nx,
-                      (int)ny, rate);
+    const dim3 grid((unsigned)((nb + kCodecThreads - 1) / kCodecThreads));
+    const size_t smem = (size_t)kCodecThreads * (2 * rate + 1) * 4;
+    if (kind == kCodecQuant)
+        return launch_pdl(k_encode_layers<kCodecQuant>, grid, dim3(kCodecThreads), smem, s, sg, (int)nx, (int)ny,
+                          rate);
+    return launch_pdl(k_encode_layers<kCodecTransform>, grid, dim3(kCodecThreads), smem, s, sg, (int)nx, (int)ny,
+                      rate);
 }
 
 cudaError_t launch_decode_segments(CodecSegments sg, const int64_t *nlayers, int64_t nx, int64_t ny,
-                                   int rate, cudaStream_t s)
+                                   int rate, int kind, cudaStream_t s)
 {
+    if (!codec_ok(rate, kind))
+        return cudaErrorInvalidValue;
     cudaError_t e = seal_segments(sg, nx, ny, nlayers);
     if (e != cudaSuccess)
         return e;
     const int64_t nb = sg.first[sg.nseg];
     if (nb == 0)
         return cudaSuccess;
-    return launch_pdl(k_decode_layers, dim3((unsigned)((nb + kCodecThreads - 1) / kCodecThreads)),
-                      dim3(kCodecThreads), 0, s, sg, (int)nx, (int)ny, rate);
+    const dim3 grid((unsigned)((nb + kCodecThreads - 1) / kCodecThreads));
+    if (kind == kCodecQuant)
+        return launch_pdl(k_decode_layers<kCodecQuant>, grid, dim3(kCodecThreads), 0, s, sg, (int)nx, (int)ny, rate);
+    return launch_pdl(k_decode_layers<kCodecTransform>, grid, dim3(kCodecThreads), 0, s, sg, (int)nx, (int)ny,
+                      rate);
 }
 
 cudaError_t launch_encode_layers(const float *planes, int64_t nx, int64_t ny, int64_t nlayers,
-                                 int rate, void *blocks, cudaStream_t s)
+                                 int rate, int kind, void *blocks, cudaStream_t s)
 {
     CodecSegments sg;
     sg.nseg = 1;
     sg.planes[0] = const_cast<float *>(planes);
     sg.blocks[0] = blocks;
-    return launch_encode_segments(sg, &nlayers, nx, ny, rate, s);
+    return launch_encode_segments(sg, &nlayers, nx, ny, rate, kind, s);
 }
 
 cudaError_t launch_decode_layers(const void *blocks, int64_t nx, int64_t ny, int64_t nlayers,
-                                 int rate, float *planes, cudaStream_t s)
+                                 int rate, int kind, float *planes, cudaStream_t s)
 {
     CodecSegments sg;
     sg.nseg = 1;
     sg.planes[0] = planes;
     sg.blocks[0] = const_cast<void *>(blocks);
-    return launch_decode_segments(sg, &nlayers, nx, ny, rate, s);
+    return launch_decode_segments(sg, &nlayers, nx, ny, rate, kind, s);
 }
 
 }  // namespace oocs

@@ -69,16 +69,21 @@ struct CodecSegments {
     int nseg = 0;
 };
 
+// Codec of a block (8 rate bytes per 4x4x4 block either way): the transform
+// codec (codec.cuh, rate 1..32) or the block quantiser (quant.cuh, rate 2..32).
+// The launchers return cudaErrorInvalidValue for another kind or rate.
+enum CodecKind { kCodecTransform = 0, kCodecQuant = 1 };
+
 cudaError_t launch_encode_segments(CodecSegments sg, const int64_t *nlayers, int64_t nx, int64_t ny,
-                                   int rate, cudaStream_t s);
+                                   int rate, int kind, cudaStream_t s);
 cudaError_t launch_decode_segments(CodecSegments sg, const int64_t *nlayers, int64_t nx, int64_t ny,
-                                   int rate, cudaStream_t s);
+                                   int rate, int kind, cudaStream_t s);
 
 // Fixed-rate codec over whole 4-plane layers.  planes: first FP32 plane of the
 // first layer; blocks: first block of the first layer.
 cudaError_t launch_encode_layers(const float *planes, int64_t nx, int64_t ny, int64_t nlayers,
-                                 int rate, void *blocks, cudaStream_t s);
+                                 int rate, int kind, void *blocks, cudaStream_t s);
 cudaError_t launch_decode_layers(const void *blocks, int64_t nx, int64_t ny, int64_t nlayers,
-                                 int rate, float *planes, cudaStream_t s);
+                                 int rate, int kind, float *planes, cudaStream_t s);
 
 }  // namespace oocs

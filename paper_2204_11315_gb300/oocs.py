@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "OOCS_OK", 1: "OOCS_ERR_INVALID_ARG", 2: "OOCS_ERR_BUDGET",
                 3: "OOCS_ERR_HOST_ALLOC", 4: "OOCS_ERR_CUDA", 5: "OOCS_ERR_TIMEOUT",
                 6: "OOCS_ERR_STATE", 7: "OOCS_ERR_UNSUPPORTED"}
 OOCS_HEAT, OOCS_WAVE, OOCS_WAVE_ADJOINT = 0, 1, 2
+OOCS_CODEC_TRANSFORM, OOCS_CODEC_QUANT = 0, 1
 OOCS_FIELD_U, OOCS_FIELD_U_PREV, OOCS_FIELD_M = 0, 1, 2
 OOCS_FIELD_LAM, OOCS_FIELD_LAM_PREV, OOCS_FIELD_FWD, OOCS_FIELD_GRAD = 0, 1, 3, 4
 BOUND_FIELDS = {OOCS_HEAT: 1, OOCS_WAVE: 3, OOCS_WAVE_ADJOINT: 4}
@@ -43,7 +44,7 @@ class oocs_desc(ctypes.Structure):
                 ("device_budget", ctypes.c_uint64), ("rate_bits", ctypes.c_int32),
                 ("temporal_depth", ctypes.c_int32), ("slab_planes", ctypes.c_int32),
                 ("working_buffers", ctypes.c_int32), ("readonly_resident", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("codec", ctypes.c_int32)]
 
 
 class oocs_plan(ctypes.Structure):
@@ -154,8 +155,8 @@ SIGNATURES = {
     "oocs_decompress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
     "oocs_host_alloc": (_i32, [_u64, ctypes.POINTER(_vp)]),
     "oocs_host_free": (_i32, [_vp]),
-    "oocs_encode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
-    "oocs_decode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _vp, _vp]),
+    "oocs_encode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _i32, _vp, _vp]),
+    "oocs_decode_device": (_i32, [_vp, _i64, _i64, _i64, _i32, _i32, _vp, _vp]),
 }
 
 _lock = threading.Lock()
@@ -192,7 +193,8 @@ def _check(status: int, ctx=None):
 
 
 def make_desc(nx, ny, nz, scheme, coef, device_budget, rate_bits=0, temporal_depth=0,
-              slab_planes=0, working_buffers=OOCS_SWB, radius=None, readonly_resident=0) -> oocs_desc:
+              slab_planes=0, working_buffers=OOCS_SWB, radius=None, readonly_resident=0,
+              codec=0) -> oocs_desc:
     coef = [float(c) for c in coef]
     d = oocs_desc()
     d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
@@ -206,6 +208,7 @@ def make_desc(nx, ny, nz, scheme, coef, device_budget, rate_bits=0, temporal_dep
     d.slab_planes = int(slab_planes)
     d.working_buffers = int(working_buffers)
     d.readonly_resident = int(readonly_resident)
+    d.codec = int(codec)
     return d
 
 
@@ -461,12 +464,12 @@ class HostBuffer:
             pass
 
 
-def oocs_encode_device(field_ptr, nx, ny, nz, rate, blocks_ptr, stream=0):
-    _check(lib().oocs_encode_device(_vp(field_ptr), nx, ny, nz, rate, _vp(blocks_ptr), _vp(stream)))
+def oocs_encode_device(field_ptr, nx, ny, nz, rate, blocks_ptr, stream=0, codec=0):
+    _check(lib().oocs_encode_device(_vp(field_ptr), nx, ny, nz, rate, codec, _vp(blocks_ptr), _vp(stream)))
 
 
-def oocs_decode_device(blocks_ptr, nx, ny, nz, rate, field_ptr, stream=0):
-    _check(lib().oocs_decode_device(_vp(blocks_ptr), nx, ny, nz, rate, _vp(field_ptr), _vp(stream)))
+def oocs_decode_device(blocks_ptr, nx, ny, nz, rate, field_ptr, stream=0, codec=0):
+    _check(lib().oocs_decode_device(_vp(blocks_ptr), nx, ny, nz, rate, codec, _vp(field_ptr), _vp(stream)))
 
 
 # ------------------------------------------------- torch-plumbed helper --

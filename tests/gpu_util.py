@@ -12,17 +12,17 @@ def torch_cuda():
     return torch
 
 
-def heat_desc(P, shape, rate=0, k=1, T=32, wb=1, alpha=0.1, budget=8 << 30):
+def heat_desc(P, shape, rate=0, k=1, T=32, wb=1, alpha=0.1, budget=8 << 30, codec=0):
     nz, ny, nx = shape
     return P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(alpha), budget,
-                       rate_bits=rate, temporal_depth=k, slab_planes=T, working_buffers=wb)
+                       rate_bits=rate, temporal_depth=k, slab_planes=T, working_buffers=wb, codec=codec)
 
 
-def wave_desc(P, shape, rate=0, k=4, T=64, wb=1, budget=8 << 30, ro=0):
+def wave_desc(P, shape, rate=0, k=4, T=64, wb=1, budget=8 << 30, ro=0, codec=0):
     nz, ny, nx = shape
     return P.make_desc(nx, ny, nz, P.OOCS_WAVE, synthetic.wave_star_coef(), budget,
                        rate_bits=rate, temporal_depth=k, slab_planes=T, working_buffers=wb,
-                       readonly_resident=ro)
+                       readonly_resident=ro, codec=codec)
 
 
 def incore(P, desc, u0, nsteps, up0=None, m=None, src=None, w=None, t0=0):
