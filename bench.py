@@ -473,6 +473,7 @@ def run_ours(args):
                 compare[name]["rel_l2_vs_uncompressed_fp32"] = check_accuracy(
                     P, torch, dev, rate, inputs, codec, ref)["rel_l2_vs_uncompressed_fp32"]
         del ref
+        compare["codec_kernels"] = codec_kernel_rates(P, torch, dev, args.rate, float(peaks["hbm_gbs"]))
         # the same workload as a batch of one, its 100-step call replayed as one CUDA graph
         m, w, src, z = inputs
         b = P.OutOfCoreBatch([wave_desc(P, args.rate)])
@@ -828,6 +829,40 @@ def run_adjoint(P, torch, dev, hbm_peak):
             "out_of_core": ooc}
 
 
+def codec_kernel_rates(P, torch, dev, rate, hbm_peak, reps=10):
+    """Live rates of the codec kernels alone: encode and decode of a 512 x 512
+    x 192 field (201 MB FP32, above the 129 MB L2) at `rate`, each codec,
+    CUDA events over `reps` launches after a warm-up.  Algorithmic bytes per
+    value: 4 (FP32) + rate/8 (compressed)."""
+    nz = 192
+    f = torch.randn((nz, N, N), device=dev) * 1e-3
+    g = torch.empty_like(f)
+    blocks = torch.empty(N * N * nz * rate // 32, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    vals = N * N * nz
+    out = {}
+    for name, codec in (("transform", 0), ("quant", 1)):
+        enc = lambda: P.oocs_encode_device(f.data_ptr(), N, N, nz, rate, blocks.data_ptr(), s, codec=codec)
+        dec = lambda: P.oocs_decode_device(blocks.data_ptr(), N, N, nz, rate, g.data_ptr(), s, codec=codec)
+        r = {}
+        for kind, fn in (("encode", enc), ("decode", dec)):
+            fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / reps
+            gbs = vals * (4 + rate / 8) / (ms / 1e3) / 1e9
+            r[kind] = {"avg_launch_ms": ms, "gvalues_per_s": vals / (ms / 1e3) / 1e9, "achieved_gbs": gbs,
+                       "frac_of_hbm": gbs / hbm_peak}
+        out[name] = r
+    del f, g, blocks
+    torch.cuda.empty_cache()
+    return {"grid": [N, N, nz], "rate": rate, "bytes_per_value": 4 + rate / 8, **out}
+
+
 def check_accuracy(P, torch, dev, rate, inputs, codec=0, ref=None):
     """Compressed run of the workload (100 steps from rest) against the
     uncompressed in-core GPU run of the same FP32 arithmetic (which the tests
@@ -943,6 +978,9 @@ def run_profile(args):
     P.oocs_decode_device(blocks.data_ptr(), N, N, nz, args.rate, sc.data_ptr(), s)
     P.oocs_incore_run(d80, u80.data_ptr(), up80.data_ptr(), m80.data_ptr(), sc80.data_ptr(), 1, 0, None, None,
                       s)
+    # the block quantiser's kernels on the same field and rate
+    P.oocs_encode_device(u.data_ptr(), N, N, nz, args.rate, blocks.data_ptr(), s, codec=1)
+    P.oocs_decode_device(blocks.data_ptr(), N, N, nz, args.rate, sc.data_ptr(), s, codec=1)
     torch.cuda.synchronize(dev)
     torch.cuda.profiler.stop()
     print(json.dumps({"profile_run": "kernels", "grid": [N, N, nz], "rate": args.rate,
