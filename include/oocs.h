@@ -252,6 +252,15 @@ oocs_status oocs_set_time(oocs_ctx *ctx, int64_t t);
  * event the caller records on streams[0] after the call completes with it. */
 oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps);
 
+/* Failure detection without a GPU fault: enqueue on streams[0] a one-thread
+ * kernel that waits on an mbarrier no thread ever arrives on, through the
+ * bounded wait every kernel of the library uses.  After about one second the
+ * wait gives up and records its timeout in the device error word; the next
+ * oocs_synchronize returns OOCS_ERR_CUDA ("a kernel's bounded wait ran out"),
+ * sticky on this context, and clears the word, so other contexts (and the
+ * GPU) stay usable.  For tests of the error path.                          */
+oocs_status oocs_selftest_stuck_wait(oocs_ctx *ctx);
+
 /* Wait for all work of the context, at most timeout_ns nanoseconds
  * (0 = no limit).  OOCS_ERR_TIMEOUT if it is still running (sticky);
  * OOCS_ERR_CUDA on a device error.                                         */

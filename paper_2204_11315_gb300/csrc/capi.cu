@@ -1213,6 +1213,18 @@ oocs_status oocs_set_receiver(oocs_ctx *ctx, int64_t zr, float *planes, int64_t 
     return OOCS_OK;
 }
 
+oocs_status oocs_selftest_stuck_wait(oocs_ctx *ctx)
+{
+    oocs_status s = check_ready(ctx);
+    if (s != OOCS_OK)
+        return s;
+    s = join_streams(ctx);
+    if (s != OOCS_OK)
+        return s;
+    CU(ctx, launch_stuck_wait(ctx->st[0]));
+    return OOCS_OK;
+}
+
 oocs_status oocs_set_state_record(oocs_ctx *ctx, void *const *stores, int64_t t0, int64_t n)
 {
     oocs_status s = check_ready(ctx);

@@ -676,6 +676,24 @@ cudaError_t launch_product(float *out, const float *a, const float *b, int64_t n
     return launch_pdl(k_product, dim3(grid), dim3(256), 0, s, out, a, b, n4);
 }
 
+// One thread waits on an mbarrier that no thread arrives on, through the
+// bounded wait every kernel here uses: after kWaitLimitNs it records
+// kErrWaitTimeout in the device error word and returns.  Failure detection
+// exercised without a GPU fault.
+__global__ void k_stuck_wait()
+{
+    __shared__ uint64_t bar;
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    mbar_wait(&bar, 0);  // phase 0 never completes
+}
+
+cudaError_t launch_stuck_wait(cudaStream_t s)
+{
+    k_stuck_wait<<<1, 1, 0, s>>>();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_set_i64(int64_t *p, int64_t v, cudaStream_t s)
 {
     k_set_i64<<<1, 1, 0, s>>>(p, v);

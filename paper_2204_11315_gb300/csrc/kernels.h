@@ -51,6 +51,10 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s);
 // out = a * b elementwise (FP32, one rounding each); n a multiple of 4.
 cudaError_t launch_product(float *out, const float *a, const float *b, int64_t n, cudaStream_t s);
 
+// A kernel whose only wait never completes: it ends after the bounded-wait
+// limit with kErrWaitTimeout in the device error word (failure-detection test).
+cudaError_t launch_stuck_wait(cudaStream_t s);
+
 // *p = v in stream order (one thread).
 cudaError_t launch_set_i64(int64_t *p, int64_t v, cudaStream_t s);
 

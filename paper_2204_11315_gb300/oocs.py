@@ -151,6 +151,7 @@ SIGNATURES = {
                                          ctypes.POINTER(oocs_trace_op), _i64, ctypes.POINTER(_i64)]),
     "oocs_set_receiver": (_i32, [_vp, _i64, _vp, _i64]),
     "oocs_set_state_record": (_i32, [_vp, ctypes.POINTER(_vp), _i64, _i64]),
+    "oocs_selftest_stuck_wait": (_i32, [_vp]),
     "oocs_compress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
     "oocs_decompress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
     "oocs_host_alloc": (_i32, [_u64, ctypes.POINTER(_vp)]),
@@ -421,6 +422,10 @@ def oocs_misfit_backward(desc, m_ptr, src, w, zr, res_ptr, nsteps, checkpoint_ev
 
 def oocs_set_receiver(ctx, zr, planes_ptr, nplanes):
     _check(lib().oocs_set_receiver(_vp(ctx), int(zr), _vp(planes_ptr) if planes_ptr else None, int(nplanes)), ctx)
+
+
+def oocs_selftest_stuck_wait(ctx):
+    _check(lib().oocs_selftest_stuck_wait(_vp(ctx)), ctx)
 
 
 def oocs_set_state_record(ctx, store_ptrs, t0=0):
