@@ -835,13 +835,14 @@ def codec_kernel_rates(P, torch, dev, rate, hbm_peak, reps=10):
     CUDA events over `reps` launches after a warm-up.  Algorithmic bytes per
     value: 4 (FP32) + rate/8 (compressed)."""
     nz = 192
-    f = torch.randn((nz, N, N), device=dev) * 1e-3
-    g = torch.empty_like(f)
+    noise = torch.randn((nz, N, N), device=dev) * 1e-3
+    zero = torch.zeros_like(noise)  # the sweep's fields are mostly all-zero blocks (a point source from rest)
+    g = torch.empty_like(noise)
     blocks = torch.empty(N * N * nz * rate // 32, dtype=torch.int32, device=dev)
     s = torch.cuda.current_stream(dev).cuda_stream
     vals = N * N * nz
     out = {}
-    for name, codec in (("transform", 0), ("quant", 1)):
+    for name, codec, f in (("transform", 0, noise), ("quant", 1, noise), ("transform_zero_field", 0, zero)):
         enc = lambda: P.oocs_encode_device(f.data_ptr(), N, N, nz, rate, blocks.data_ptr(), s, codec=codec)
         dec = lambda: P.oocs_decode_device(blocks.data_ptr(), N, N, nz, rate, g.data_ptr(), s, codec=codec)
         r = {}
@@ -858,7 +859,7 @@ def codec_kernel_rates(P, torch, dev, rate, hbm_peak, reps=10):
             r[kind] = {"avg_launch_ms": ms, "gvalues_per_s": vals / (ms / 1e3) / 1e9, "achieved_gbs": gbs,
                        "frac_of_hbm": gbs / hbm_peak}
         out[name] = r
-    del f, g, blocks
+    del noise, zero, g, blocks
     torch.cuda.empty_cache()
     return {"grid": [N, N, nz], "rate": rate, "bytes_per_value": 4 + rate / 8, **out}
 

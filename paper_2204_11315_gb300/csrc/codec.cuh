@@ -284,9 +284,19 @@ OOCS_FN void encode_block(const float (&v)[64], int rate, Sink &&sink)
     const float scale = bits_f32((uint32_t)(156 - emax) << 23);  // 2^(29 - emax)
 
     int32_t q[64];
+    uint32_t any = 0;
 #pragma unroll
-    for (int i = 0; i < 64; ++i)
+    for (int i = 0; i < 64; ++i) {
         q[i] = f2i_rz(fmul_rn(v[i], scale));
+        any |= (uint32_t)q[i];
+    }
+    if (any == 0) {
+        // only a block clamped at emax = -95 (all |v| < 2^-124) quantises to
+        // zero: every plane is one group-test 0, which the zero padding writes
+        bw.put((uint32_t)hdr, 8);
+        bw.finish();
+        return;
+    }
     xform_fwd(q);
 
     uint32_t lo[32], hi[32];  // negabinary coefficients in sequency order
@@ -348,6 +358,15 @@ OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64])
         return;
     }
     const int emax = max(hdr, 32) - 127;  // headers 1..31 are never written: clamp as the encoder does
+    if ((w0 >> 8) == 0u && (src(1) & 0xFFu) == 0u) {
+        // bits 8..39 zero: each of the 32 planes is a group-test 0 with no
+        // significant coefficient (the budget holds >= 56 bits), so every
+        // coefficient is 0 and every value +0
+#pragma unroll
+        for (int i = 0; i < 64; ++i)
+            v[i] = 0.0f;
+        return;
+    }
     BitReader<Src> br(src);
     br.skip(8);
 

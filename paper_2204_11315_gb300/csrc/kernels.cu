@@ -715,7 +715,8 @@ cudaError_t read_device_error(unsigned int *code, bool clear)
 constexpr int kCodecThreads = 128;
 
 // Locate global block b in a segment list; returns the segment and the block's
-// (bx, by, layer) inside it.
+// (bx, by, layer) inside it.  A launch codes fewer than 2^31 blocks (checked
+// by the launchers), so the index arithmetic is 32-bit.
 OOCS_FN int find_segment(const CodecSegments &sg, int64_t b, int bnx, int bny, int &bx, int &by,
                          int64_t &bl)
 {
@@ -723,11 +724,12 @@ OOCS_FN int find_segment(const CodecSegments &sg, int64_t b, int bnx, int bny, i
 #pragma unroll 1
     while (g + 1 < sg.nseg && b >= sg.first[g + 1])
         ++g;
-    const int64_t lb = b - sg.first[g];
-    bx = (int)(lb % bnx);
-    const int64_t t = lb / bnx;
-    by = (int)(t % bny);
-    bl = t / bny;
+    const uint32_t lb = (uint32_t)(b - sg.first[g]);
+    const uint32_t t = lb / (uint32_t)bnx;
+    bx = (int)(lb - t * (uint32_t)bnx);
+    const uint32_t l = t / (uint32_t)bny;
+    by = (int)(t - l * (uint32_t)bny);
+    bl = l;
     return g;
 }
 
@@ -745,7 +747,7 @@ OOCS_FN uint32_t *segment_word(const CodecSegments &sg, int64_t blk, int rate, i
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kCodecThreads)
+__global__ void __launch_bounds__(kCodecThreads, 6)
     k_encode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
     extern __shared__ uint32_t sw[];
@@ -783,15 +785,27 @@ __global__ void __launch_bounds__(kCodecThreads)
     // each warp copies whole blocks out, its lanes over the block's words
     const int nblk = (int)(total - b0 < kCodecThreads ? total - b0 : kCodecThreads);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int blk = warp; blk < nblk; blk += kCodecThreads / 32) {
-        uint32_t *dst = segment_word(sg, b0 + blk, rate, 0);
-        for (int wi = lane; wi < nw; wi += 32)
-            dst[wi] = sw[blk * stride + wi];
+    int g0 = 0;
+#pragma unroll 1
+    while (g0 + 1 < sg.nseg && b0 >= sg.first[g0 + 1])
+        ++g0;
+    if (b0 + nblk <= sg.first[g0 + 1]) {
+        // all of the CTA's blocks in one segment: their words are contiguous
+        uint32_t *dst = static_cast<uint32_t *>(sg.blocks[g0]) + (b0 - sg.first[g0]) * (int64_t)nw;
+        for (int blk = warp; blk < nblk; blk += kCodecThreads / 32)
+            for (int wi = lane; wi < nw; wi += 32)
+                dst[blk * nw + wi] = sw[blk * stride + wi];
+    } else {
+        for (int blk = warp; blk < nblk; blk += kCodecThreads / 32) {
+            uint32_t *dst = segment_word(sg, b0 + blk, rate, 0);
+            for (int wi = lane; wi < nw; wi += 32)
+                dst[wi] = sw[blk * stride + wi];
+        }
     }
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kCodecThreads)
+__global__ void __launch_bounds__(kCodecThreads, 6)
     k_decode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
     pdl_launch_dependents();
@@ -849,6 +863,8 @@ cudaError_t launch_encode_segments(CodecSegments sg, const int64_t *nlayers, int
     const int64_t nb = sg.first[sg.nseg];
     if (nb == 0)
         return cudaSuccess;
+    if (nb >= (int64_t)1 << 31)  // the kernels' block indices are 32-bit within a segment
+        return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((nb + kCodecThreads - 1) / kCodecThreads));
     const size_t smem = (size_t)kCodecThreads * (2 * rate + 1) * 4;
     if (kind == kCodecQuant)
@@ -869,6 +885,8 @@ cudaError_t launch_decode_segments(CodecSegments sg, const int64_t *nlayers, int
     const int64_t nb = sg.first[sg.nseg];
     if (nb == 0)
         return cudaSuccess;
+    if (nb >= (int64_t)1 << 31)  // the kernels' block indices are 32-bit within a segment
+        return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((nb + kCodecThreads - 1) / kCodecThreads));
     if (kind == kCodecQuant)
         return launch_pdl(k_decode_layers<kCodecQuant>, grid, dim3(kCodecThreads), 0, s, sg, (int)nx, (int)ny, rate);
