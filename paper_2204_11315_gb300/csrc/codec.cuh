@@ -220,16 +220,26 @@ struct BitReader {
     Src &src;
     uint64_t win = 0;   // unread bits, least significant first
     int nwin = 0;       // valid bits in win
-    int ridx = 0;       // index of `next`
-    uint32_t next;      // the following word, loaded one refill ahead
+    int ridx = 0;       // index of n0
+    uint32_t n0, n1, n2, n3;  // the next four words, loaded ahead so that a
+                              // refill seldom waits for a load
 
-    OOCS_FN explicit BitReader(Src &s) : src(s) { next = src(0); }
+    OOCS_FN explicit BitReader(Src &s) : src(s)
+    {
+        n0 = src(0);
+        n1 = src(1);
+        n2 = src(2);
+        n3 = src(3);
+    }
     OOCS_FN void fill()
     {
         if (nwin < 32) {
-            win |= (uint64_t)next << nwin;
+            win |= (uint64_t)n0 << nwin;
             nwin += 32;
-            next = src(++ridx);
+            n0 = n1;
+            n1 = n2;
+            n2 = n3;
+            n3 = src(++ridx + 3);
         }
     }
     OOCS_FN uint32_t peek(int n)  // n in [1, 32]
