@@ -177,8 +177,10 @@ oocs_status oocs_create(const oocs_desc *desc, void *workspace, uint64_t workspa
  * block (bx, by) at ((by * nx/4) + bx) * 8*rate_bits; with rate_bits = 0 it is
  * the raw FP32 planes.  Updated in place by oocs_step.  With
  * desc.readonly_resident the device copy of M is (re)made from its store at
- * the first oocs_step after oocs_bind_field(M) or oocs_compress(M); later
- * writes to the M store by other means are not seen until one of them.     */
+ * the first oocs_step after oocs_bind_field(M); oocs_compress(M) and
+ * oocs_compress_device(M) update it as they code (the values the store
+ * decodes to; oocs_compress at rate 0 leaves it to the next oocs_step);
+ * later writes to the M store by other means are not seen until one of them. */
 oocs_status oocs_bind_field(oocs_ctx *ctx, int32_t field, void *host_store, uint64_t bytes);
 
 /* Set the point source of the WAVE scheme: voxel (x, y, z) receives w[t] at

@@ -1255,6 +1255,9 @@ static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, f
         ctx->ro_dirty = true;
     const oocs_desc &d = ctx->d;
     const uint64_t plane_bytes = (uint64_t)d.nx * d.ny * 4;
+    // a resident M is decoded from each chunk's blocks while they are on the
+    // device (the values the store decodes to), so no step has to upload it
+    const bool ro_keep = enc && field == OOCS_FIELD_M && ctx->v.ro_res && d.rate_bits > 0;
     s = join_streams(ctx);
     if (s != OOCS_OK)
         return s;
@@ -1283,6 +1286,9 @@ static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, f
                                     cudaMemcpyHostToDevice, st));
             CU(ctx, launch_encode_layers(raw, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, d.codec, blk, st));
             CU(ctx, cudaMemcpyAsync(host_blk, blk, cbytes, cudaMemcpyDeviceToHost, st));
+            if (ro_keep)
+                CU(ctx, launch_decode_layers(blk, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, d.codec,
+                                             ctx->ro_m() + z0 * d.nx * d.ny, st));
         } else {
             CU(ctx, cudaMemcpyAsync(blk, host_blk, cbytes, cudaMemcpyHostToDevice, st));
             CU(ctx, launch_decode_layers(blk, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, d.codec, raw, st));
@@ -1290,7 +1296,10 @@ static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, f
                                     cudaMemcpyDeviceToHost, st));
         }
     }
-    return join_streams(ctx);
+    s = join_streams(ctx);
+    if (s == OOCS_OK && ro_keep)
+        ctx->ro_dirty = false;
+    return s;
 }
 
 oocs_status oocs_compress(oocs_ctx *ctx, int32_t field, const float *src)
@@ -1329,7 +1338,10 @@ static oocs_status codec_range_device(oocs_ctx *ctx, int32_t field, const float 
     const int nf = bound_fields(ctx->d);
     if (field < 0 || field >= nf || !ctx->store[field])
         return fail(ctx, OOCS_ERR_STATE, "field is not bound");
-    if (enc && field == OOCS_FIELD_M)
+    // a resident M takes the written planes' decoded values as they are
+    // coded (a copy at rate 0); if it was not made yet, the next step makes it
+    const bool ro_keep = enc && field == OOCS_FIELD_M && ctx->v.ro_res;
+    if (enc && field == OOCS_FIELD_M && !ro_keep)
         ctx->ro_dirty = true;
     s = join_streams(ctx);
     if (s != OOCS_OK)
@@ -1346,10 +1358,16 @@ static oocs_status codec_range_device(oocs_ctx *ctx, int32_t field, const float 
                 CU(ctx, cudaMemcpyAsync(host, src + c0 * plane, cbytes, cudaMemcpyDeviceToHost, st));
             else
                 CU(ctx, cudaMemcpyAsync(dst + c0 * plane, host, cbytes, cudaMemcpyHostToDevice, st));
+            if (ro_keep)
+                CU(ctx, cudaMemcpyAsync(ctx->ro_m() + (z0 + c0) * plane, src + c0 * plane, cbytes,
+                                        cudaMemcpyDeviceToDevice, st));
         } else if (enc) {
             char *blk = ctx->out_slot(0, 0);
             CU(ctx, launch_encode_layers(src + c0 * plane, d.nx, d.ny, n / 4, d.rate_bits, d.codec, blk, st));
             CU(ctx, cudaMemcpyAsync(host, blk, cbytes, cudaMemcpyDeviceToHost, st));
+            if (ro_keep)
+                CU(ctx, launch_decode_layers(blk, d.nx, d.ny, n / 4, d.rate_bits, d.codec,
+                                             ctx->ro_m() + (z0 + c0) * plane, st));
         } else {
             char *blk = ctx->in_slot(0, 0);
             CU(ctx, cudaMemcpyAsync(blk, host, cbytes, cudaMemcpyHostToDevice, st));

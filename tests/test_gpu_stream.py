@@ -135,7 +135,8 @@ def test_wave_compressed_within_tolerance(P, orc, rate):
 def test_wave_resident_model_bitexact(P, rate, wb):
     """readonly_resident keeps m on the device (decoded once): the stores after
     the run are byte-identical to streaming m with every visit, and m crosses
-    the link once instead of once per sweep."""
+    the link once instead of once per sweep (compressed, oocs_compress already
+    decodes it into the device copy; raw, the first step copies it)."""
     shape = (128, 72, 40)
     steps = 10
     m, w, src, z = _wave_inputs(shape, steps)
@@ -146,7 +147,7 @@ def test_wave_resident_model_bitexact(P, rate, wb):
     assert (p0.fields_in, p0.readonly_resident) == (3, 0)
     assert (p1.fields_in, p1.readonly_resident) == (2, 1)
     passes = -(-steps // 4)
-    assert stats1["h2d_bytes"] == (2 * passes + 1) * p1.host_store_bytes
+    assert stats1["h2d_bytes"] == (2 * passes + (1 if rate == 0 else 0)) * p1.host_store_bytes
 
 
 @pytest.mark.parametrize("ro", [0, 1])
