@@ -1374,7 +1374,10 @@ static oocs_status codec_range_device(oocs_ctx *ctx, int32_t field, const float 
             CU(ctx, launch_decode_layers(blk, d.nx, d.ny, n / 4, d.rate_bits, d.codec, dst + c0 * plane, st));
         }
     }
-    return join_streams(ctx);
+    s = join_streams(ctx);
+    if (s == OOCS_OK && ro_keep && z0 == 0 && nplanes == d.nz)  // the whole device copy was written
+        ctx->ro_dirty = false;
+    return s;
 }
 
 oocs_status oocs_compress_device(oocs_ctx *ctx, int32_t field, const float *src, int64_t z0, int64_t nplanes)
