@@ -804,29 +804,11 @@ __global__ void __launch_bounds__(kCodecThreads, 6)
     }
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(kCodecThreads, 6)
-    k_decode_layers(const CodecSegments sg, int nx, int ny, int rate)
+// Writes a decoded block's 64 values to its 4 x 4 x 4 place in the planes.
+OOCS_FN void store_block(const CodecSegments &sg, int g, int nx, int ny, int bx, int by, int64_t bl,
+                         const float (&v)[64])
 {
-    pdl_launch_dependents();
-    pdl_wait_prior_grid();
-    const int64_t b = (int64_t)blockIdx.x * kCodecThreads + threadIdx.x;
-    if (b >= sg.first[sg.nseg])
-        return;
-    int bx, by;
-    int64_t bl;
-    const int g = find_segment(sg, b, nx >> 2, ny >> 2, bx, by, bl);
     const int64_t plane = (int64_t)nx * ny;
-    // a thread's words share its block's cache lines: the first load of each
-    // line brings the rest into L1
-    const uint32_t *src =
-        static_cast<const uint32_t *>(sg.blocks[g]) + (b - sg.first[g]) * (int64_t)(2 * rate);
-    const int nw = 2 * rate;
-    float v[64];
-    if constexpr (KIND == kCodecQuant)
-        bq_decode_block(rate, [&](int i) -> uint32_t { return __ldg(src + i); }, v);
-    else
-        decode_block(rate, [&](int i) -> uint32_t { return i < nw ? __ldg(src + i) : 0u; }, v);
     float *base = sg.planes[g] + 4 * bl * plane + (int64_t)(4 * by) * nx + 4 * bx;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -835,6 +817,97 @@ __global__ void __launch_bounds__(kCodecThreads, 6)
             *reinterpret_cast<float4 *>(base + k * plane + (int64_t)j * nx) =
                 make_float4(v[16 * k + 4 * j + 0], v[16 * k + 4 * j + 1], v[16 * k + 4 * j + 2],
                             v[16 * k + 4 * j + 3]);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kCodecThreads, 6)
+    k_decode_layers(const CodecSegments sg, int nx, int ny, int rate)
+{
+    extern __shared__ uint32_t sw[];
+    pdl_launch_dependents();
+    pdl_wait_prior_grid();
+    const int64_t b = (int64_t)blockIdx.x * kCodecThreads + threadIdx.x;
+    const int nw = 2 * rate;
+    if constexpr (KIND == kCodecTransform) {
+        if (b >= sg.first[sg.nseg])
+            return;
+        int bx, by;
+        int64_t bl;
+        const int g = find_segment(sg, b, nx >> 2, ny >> 2, bx, by, bl);
+        // a thread's words share its block's cache lines: the first load of
+        // each line brings the rest into L1
+        const uint32_t *src = static_cast<const uint32_t *>(sg.blocks[g]) + (b - sg.first[g]) * (int64_t)nw;
+        float v[64];
+        decode_block(rate, [&](int i) -> uint32_t { return i < nw ? __ldg(src + i) : 0u; }, v);
+        store_block(sg, g, nx, ny, bx, by, bl, v);
+    } else {
+        // quantiser: a warp with a coded block copies its 32 blocks' words to
+        // shared memory (coalesced, eight blocks' loads in flight), so that
+        // the bit streams are not read by chains of dependent global loads;
+        // an all-zero warp needs nothing more than the headers
+        const bool live = b < sg.first[sg.nseg];
+        const int stride = 2 * rate + 1, lane = threadIdx.x & 31;
+        int bx = 0, by = 0, g = 0;
+        int64_t bl = 0;
+        const uint32_t *src = nullptr;
+        uint32_t w0 = 0u;
+        if (live) {
+            g = find_segment(sg, b, nx >> 2, ny >> 2, bx, by, bl);
+            src = static_cast<const uint32_t *>(sg.blocks[g]) + (b - sg.first[g]) * (int64_t)nw;
+            w0 = __ldg(src);
+        }
+        const unsigned coded = __ballot_sync(0xffffffffu, live && (w0 & 0xFFu) != 0u);
+        uint32_t *row = sw + threadIdx.x * stride;
+        if (coded) {
+            uint32_t *wrows = sw + (threadIdx.x & ~31) * stride;
+            // lane 0's block starts the warp's run of blocks
+            const uint32_t *wsrc = reinterpret_cast<const uint32_t *>(
+                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(src), 0));
+            const unsigned alive = __ballot_sync(0xffffffffu, live);  // a prefix of the lanes
+            const int nlive = __popc(alive);
+            // the live blocks are consecutive when the last one is in lane 0's
+            // segment (the common case); else each lane copies its own words
+            const int g_last = __shfl_sync(0xffffffffu, g, nlive - 1);
+            const int g_first = __shfl_sync(0xffffffffu, g, 0);
+            if (g_first == g_last) {
+                constexpr int kDepth = 8;
+                for (int base = 0; base < nlive; base += kDepth) {
+                    uint32_t r0[kDepth], r1[kDepth];
+#pragma unroll
+                    for (int u = 0; u < kDepth; ++u) {
+                        const int blk = base + u;
+                        r0[u] = (blk < nlive && lane < nw) ? __ldg(wsrc + blk * nw + lane) : 0u;
+                        r1[u] = (blk < nlive && lane + 32 < nw) ? __ldg(wsrc + blk * nw + lane + 32) : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kDepth; ++u) {
+                        const int blk = base + u;
+                        if (blk < nlive) {
+                            if (lane < nw)
+                                wrows[blk * stride + lane] = r0[u];
+                            if (lane + 32 < nw)
+                                wrows[blk * stride + lane + 32] = r1[u];
+                        }
+                    }
+                }
+            } else if (live) {
+                for (int i = 0; i < nw; ++i)
+                    row[i] = __ldg(src + i);
+            }
+            __syncwarp();
+        }
+        if (!live)
+            return;
+        float v[64];
+        if (coded) {
+            bq_decode_block(rate, [&](int i) -> uint32_t { return row[i]; }, v);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 64; ++i)
+                v[i] = 0.0f;
+        }
+        store_block(sg, g, nx, ny, bx, by, bl, v);
+    }
 }
 
 static cudaError_t seal_segments(CodecSegments &sg, int64_t nx, int64_t ny, const int64_t *nlayers)
@@ -888,8 +961,9 @@ cudaError_t launch_decode_segments(CodecSegments sg, const int64_t *nlayers, int
     if (nb >= (int64_t)1 << 31)  // the kernels' block indices are 32-bit within a segment
         return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((nb + kCodecThreads - 1) / kCodecThreads));
-    if (kind == kCodecQuant)
-        return launch_pdl(k_decode_layers<kCodecQuant>, grid, dim3(kCodecThreads), 0, s, sg, (int)nx, (int)ny, rate);
+    if (kind == kCodecQuant)  // staging rows for the warps with coded blocks
+        return launch_pdl(k_decode_layers<kCodecQuant>, grid, dim3(kCodecThreads),
+                          (size_t)kCodecThreads * (2 * rate + 1) * 4, s, sg, (int)nx, (int)ny, rate);
     return launch_pdl(k_decode_layers<kCodecTransform>, grid, dim3(kCodecThreads), 0, s, sg, (int)nx, (int)ny,
                       rate);
 }
