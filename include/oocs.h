@@ -58,18 +58,23 @@ enum { OOCS_HEAT = 0, OOCS_WAVE = 1, OOCS_WAVE_ADJOINT = 2 };
  * Sec. 6.2); the write-only dataset is device-only.                        */
 enum { OOCS_FIELD_U = 0, OOCS_FIELD_U_PREV = 1, OOCS_FIELD_M = 2 };
 
-/* OOCS_WAVE_ADJOINT: one time step of the WAVE scheme's discrete adjoint per
- * oocs_step(ctx, 1), slab by slab in reverse z order, with the gradient of a
- * receiver misfit accumulated on the device.  At time index k (oocs_set_time)
- * the step reads lam^k (field LAM), lam^(k+1) (LAM_PREV, interior only) and
- * the forward state u^(k-1) (FWD), adds lam^k (L u^(k-1) + w[k-1] at the
- * source) to dJ/dm (field GRAD, on the device, zero at create), writes
- * lam^(k-1) = 2 lam^k - lam^(k+1) + L(m lam^k) + r^(k-2) at the receiver plane
- * into LAM_PREV's store, then swaps the LAM and LAM_PREV stores and sets the
- * time index to k-1.  r^n = planes[n] of oocs_set_receiver.  m (field M) is
- * kept on the device (readonly_resident must be 1); temporal_depth is 1; the
- * halo is one 4-plane layer; no region sharing (whole windows are copied).
- * GRAD is read with oocs_decompress_device.                                 */
+/* OOCS_WAVE_ADJOINT: oocs_step(ctx, n) takes n time steps of the WAVE
+ * scheme's discrete adjoint, each a sweep over the slabs in reverse z order,
+ * with the gradient of a receiver misfit accumulated on the device.  At time
+ * index k (oocs_set_time, then counting down) a step reads lam^k (field LAM),
+ * lam^(k+1) (LAM_PREV, interior only) and the forward state u^(k-1), adds
+ * lam^k (L u^(k-1) + w[k-1] at the source) to dJ/dm (field GRAD, on the
+ * device, zero at create), writes lam^(k-1) = 2 lam^k - lam^(k+1) +
+ * L(m lam^k) + r^(k-2) at the receiver plane into LAM_PREV's store, then the
+ * LAM and LAM_PREV stores trade roles and the time index becomes k-1.
+ * u^(k-1) is read from the state record (oocs_set_state_record: entry
+ * k-1-t0) when one is set, else from the FWD store (then n must be 1).  The
+ * steps of one call are pipelined: a slab visit waits only for the previous
+ * step's copies of the slabs its window touches.  r^n = planes[n] of
+ * oocs_set_receiver.  m (field M) is kept on the device (readonly_resident
+ * must be 1); temporal_depth is 1; the halo is one 4-plane layer; no region
+ * sharing (whole windows are copied).  GRAD is read with
+ * oocs_decompress_device.                                                   */
 enum { OOCS_FIELD_LAM = 0, OOCS_FIELD_LAM_PREV = 1, OOCS_FIELD_FWD = 3, OOCS_FIELD_GRAD = 4 };
 
 /* Fixed-rate codecs of the host store.  Both code each 4x4x4 block of FP32
@@ -197,7 +202,9 @@ oocs_status oocs_set_source(oocs_ctx *ctx, int64_t x, int64_t y, int64_t z, cons
  * adjoint need (no counterpart in the paper's forward-only runs).          */
 oocs_status oocs_set_receiver(oocs_ctx *ctx, int64_t zr, float *planes, int64_t nplanes);
 
-/* HEAT and WAVE: record the compressed states the sweep writes.  A slab visit
+/* HEAT and WAVE: record the compressed states the sweep writes (for
+ * WAVE_ADJOINT the record is read instead: entry k-1-t0 is the forward state
+ * u^(k-1) of the adjoint step at time index k, see OOCS_WAVE_ADJOINT).  A slab visit
  * that advances the field from time t to t+k copies the encoded interior of
  * its new u^(t+k) (and, for WAVE, of u^(t+k-1)) into stores[t+k - t0]
  * (stores[t+k-1 - t0]) as well as into the field's own store, when that index

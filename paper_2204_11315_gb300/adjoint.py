@@ -164,10 +164,11 @@ def _ooc_backward(torch, m, res, ckpt, prob: WaveProblem):
                 done.record(fwd.streams[0])
                 adj.streams[0].wait_event(done)
                 states = [ring[i] for i in range(e0 - s0)]
-            for k in range(e0, s0, -1):  # lam^k, u^(k-1) -> dJ/dm term k-1 and lam^(k-1)
-                adj.bind(O.OOCS_FIELD_FWD, states[k - 1 - s0])
-                adj.set_time(k)
-                adj.step(1)
+            # the segment's adjoint steps k = e0 .. s0+1 in one call: lam^k and
+            # u^(k-1) -> the dJ/dm term k-1 and lam^(k-1)
+            O.oocs_set_state_record(adj.ctx, [st.data_ptr() for st in states], s0)
+            adj.set_time(e0)
+            adj.step(e0 - s0)
             ev = torch.cuda.Event()
             ev.record(adj.streams[0])
             ring_free[j % 2] = ev

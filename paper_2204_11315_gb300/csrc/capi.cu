@@ -308,6 +308,8 @@ struct oocs_ctx {
     char *ws = nullptr;
     cudaStream_t st[3] = {};
     char *store[4] = {};  // by field id (bound_fields of the scheme)
+    int store_id[4] = {0, 1, 2, 3};  // trace: the physical store behind each field (the
+                                     // adjoint's LAM and LAM_PREV stores trade roles every step)
     uint64_t store_bytes[4] = {};
 
     bool has_src = false;
@@ -927,7 +929,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
 // buffer, form m lam^k, add the gradient term lam^k (L u^(k-1) + w[k-1] e_src)
 // to the device-resident dJ/dm, take the adjoint step on the interior, encode
 // lam^(k-1) and copy it back over lam^(k+1)'s host layers.
-oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k)
+oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k, const char *fwd, bool chained)
 {
     const Derived &v = c->v;
     const oocs_desc &d = c->d;
@@ -944,27 +946,37 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k)
     const int64_t l0[3] = {w0 / 4, z0 / 4, w0 / 4}, l1[3] = {w1 / 4, z1 / 4, w1 / 4};
     float *W0 = c->wbuf(0, 0), *W1 = c->wbuf(0, 1), *W2 = c->wbuf(0, 2), *W3 = c->wbuf(0, 3);
 
+    const int par = (int)(k & 1);  // this step's set of per-slab D2H events
     // 1. staging slot q is free once visit g-2 has decoded it
     if (g >= 2)
         SCHED(sched_wait(c, q, kEvDecoded + (int)((g - 2) % 3)));
-    // 2. H2D (host stores read only, or read and written by this visit alone;
-    //    across steps the call's opening join orders everything)
+    // 2. the window of lam^k was written by the previous step (k+1) of this
+    //    call over slabs s-1 .. s+1; waiting for those copies also orders this
+    //    visit's later write of lam^(k-1) after the previous step's reads of
+    //    the store it overwrites (each of those visits read before it wrote)
+    if (chained)
+        for (int ss = std::max(s - 1, 0); ss <= std::min(s + 1, v.S - 1); ++ss)
+            if (c->d2h_recorded[(1 - par) * v.S + ss])
+                SCHED(sched_wait(c, q, kEvD2H + c->d2h_base + (1 - par) * v.S + ss));
+    // 3. H2D of the windows of lam^k and u^(k-1) and the interior of lam^(k+1)
     if (c->trace) {
         trace_push(c, OOCS_OP_H2D, q, -1, (int64_t)g,
-                   {acc(OOCS_RES_IN_SLOT, q, w0 / 4, w1 / 4, true), acc(OOCS_RES_HOST, c->host_base + 0, l0[0], l1[0], false),
-                    acc(OOCS_RES_HOST, c->host_base + 1, l0[1], l1[1], false),
+                   {acc(OOCS_RES_IN_SLOT, q, w0 / 4, w1 / 4, true),
+                    acc(OOCS_RES_HOST, c->host_base + c->store_id[OOCS_FIELD_LAM], l0[0], l1[0], false),
+                    acc(OOCS_RES_HOST, c->host_base + c->store_id[OOCS_FIELD_LAM_PREV], l0[1], l1[1], false),
                     acc(OOCS_RES_HOST, c->host_base + 3, l0[2], l1[2], false)});
     } else {
+        const char *src[3] = {c->store[store_of[0]], c->store[store_of[1]], fwd};
         for (int f = 0; f < 3; ++f)
-            CU(c, cudaMemcpyAsync(c->in_slot(q, f), c->store[store_of[f]] + (uint64_t)l0[f] * v.layer_bytes,
+            CU(c, cudaMemcpyAsync(c->in_slot(q, f), src[f] + (uint64_t)l0[f] * v.layer_bytes,
                                   (uint64_t)(l1[f] - l0[f]) * v.layer_bytes, cudaMemcpyHostToDevice, st));
     }
     for (int f = 0; f < 3; ++f)
         c->stats.h2d_bytes += (uint64_t)(l1[f] - l0[f]) * v.layer_bytes;
-    // 3. the working buffer is free once visit g-1 has encoded from it
+    // 4. the working buffer is free once visit g-1 has encoded from it
     if (g >= 1)
         SCHED(sched_wait(c, q, kEvWrel + (int)((g - 1) % 3)));
-    // 4. decode lam^k, lam^(k+1) (interior planes, at their window positions), u^(k-1)
+    // 5. decode lam^k, lam^(k+1) (interior planes, at their window positions), u^(k-1)
     float *dst[3] = {W0, W1 + (z0 - w0) * plane_f, W2};
     if (c->trace) {
         trace_push(c, OOCS_OP_LOAD, q, -1, (int64_t)g,
@@ -994,7 +1006,7 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k)
             return r;
     }
     SCHED(sched_record(c, q, kEvDecoded + q));
-    // 5. m lam^k over the window, the gradient term, the adjoint step
+    // 6. m lam^k over the window, the gradient term, the adjoint step
     StepLaunch G;
     memset(&G, 0, sizeof(G));
     G.radius = 4;
@@ -1048,7 +1060,7 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k)
         if (r != OOCS_OK)
             return r;
     }
-    // 6. encode lam^(k-1) on the interior into the out slot
+    // 7. encode lam^(k-1) on the interior into the out slot
     if (c->trace) {
         trace_push(c, OOCS_OP_STORE, q, -1, (int64_t)g,
                    {acc(OOCS_RES_WORK, 0, z0 / 4, z1 / 4, false), acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, true)});
@@ -1058,16 +1070,18 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k)
             return r;
     }
     SCHED(sched_record(c, q, kEvWrel + q));
-    // 7. D2H over lam^(k+1)'s layers of the host store
+    // 8. D2H over lam^(k+1)'s layers of the host store
     const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
     if (c->trace)
         trace_push(c, OOCS_OP_D2H, q, -1, (int64_t)g,
                    {acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, false),
-                    acc(OOCS_RES_HOST, c->host_base + 1, z0 / 4, z1 / 4, true)});
+                    acc(OOCS_RES_HOST, c->host_base + c->store_id[OOCS_FIELD_LAM_PREV], z0 / 4, z1 / 4, true)});
     else
         CU(c, cudaMemcpyAsync(c->store[OOCS_FIELD_LAM_PREV] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, 0),
                               bytes, cudaMemcpyDeviceToHost, st));
     c->stats.d2h_bytes += bytes;
+    SCHED(sched_record(c, q, kEvD2H + c->d2h_base + par * v.S + s));
+    c->d2h_recorded[par * v.S + s] = 1;
     c->g++;
     c->stats.slabs_done++;
     return OOCS_OK;
@@ -1129,8 +1143,10 @@ oocs_status oocs_create(const oocs_desc *desc, void *workspace, uint64_t workspa
         c->st[i] = static_cast<cudaStream_t>(streams[i]);
     memset(&c->stats, 0, sizeof(c->stats));
     c->stats.workspace_bytes = p.workspace_bytes;
-    c->ev_d2h.assign(c->v.S, nullptr);
-    c->d2h_recorded.assign(c->v.S, 0);
+    // the adjoint keeps the last D2H of each slab for two steps (step parity)
+    const int nd2h = c->d.scheme == OOCS_WAVE_ADJOINT ? 2 * c->v.S : c->v.S;
+    c->ev_d2h.assign(nd2h, nullptr);
+    c->d2h_recorded.assign(nd2h, 0);
     auto mk = [&](cudaEvent_t *e) {
         return cudaEventCreateWithFlags(e, cudaEventDisableTiming);
     };
@@ -1141,7 +1157,7 @@ oocs_status oocs_create(const oocs_desc *desc, void *workspace, uint64_t workspa
         if (e == cudaSuccess) e = mk(&c->ev_wrel[i]);
         if (e == cudaSuccess) e = mk(&c->ev_join[i]);
     }
-    for (int i = 0; i < c->v.S && e == cudaSuccess; ++i)
+    for (int i = 0; i < nd2h && e == cudaSuccess; ++i)
         e = mk(&c->ev_d2h[i]);
     if (e == cudaSuccess)
         e = cudaEventCreate(&c->ev_t0);
@@ -1230,8 +1246,6 @@ oocs_status oocs_set_state_record(oocs_ctx *ctx, void *const *stores, int64_t t0
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
-    if (ctx->d.scheme == OOCS_WAVE_ADJOINT)
-        return fail(ctx, OOCS_ERR_INVALID_ARG, "the state record belongs to the forward schemes");
     if (n < 0 || (n > 0 && !stores))
         return fail(ctx, OOCS_ERR_INVALID_ARG, "n must be >= 0 and stores non-null when n > 0");
     // the copies already enqueued read the old list's pointers by value
@@ -1459,21 +1473,39 @@ oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
         return s;
     int64_t t = (int64_t)ctx->stats.steps_done;
     if (ctx->d.scheme == OOCS_WAVE_ADJOINT) {
-        // one adjoint step at time index t, slabs in reverse z order; then the
-        // stores of lam^t and the new lam^(t-1) take their next roles
-        if (nsteps != 1)
-            return fail(ctx, OOCS_ERR_INVALID_ARG, "the wave adjoint advances one step per oocs_step call");
-        if (t < 1)
-            return fail(ctx, OOCS_ERR_STATE, "the adjoint's time index must be >= 1 (oocs_set_time)");
-        for (int sl = ctx->v.S - 1; sl >= 0; --sl) {
-            s = enqueue_adjoint_slab(ctx, sl, t);
-            if (s != OOCS_OK)
-                return s;
+        // nsteps adjoint steps from time index t down, each a sweep over the
+        // slabs in reverse z order; after each, the stores of lam^k and the
+        // new lam^(k-1) trade roles.  Steps of one call are chained by the
+        // per-slab D2H events of the previous step (parity sets), not joined.
+        if (t < nsteps)
+            return fail(ctx, OOCS_ERR_STATE, "the adjoint's time index must be >= nsteps (oocs_set_time)");
+        std::vector<const char *> fwd(nsteps, ctx->store[OOCS_FIELD_FWD]);
+        if (!ctx->srec.empty()) {
+            for (int j = 0; j < nsteps; ++j) {
+                const int64_t i = t - j - 1 - ctx->srec_t0;
+                if (i < 0 || i >= (int64_t)ctx->srec.size() || !ctx->srec[i])
+                    return fail(ctx, OOCS_ERR_STATE,
+                                "the state record holds no forward state u^" + std::to_string(t - j - 1));
+                fwd[j] = ctx->srec[i];
+            }
+        } else if (nsteps > 1 && !ctx->trace) {
+            return fail(ctx, OOCS_ERR_INVALID_ARG,
+                        "more than one adjoint step per call reads the forward states from a state record");
         }
-        std::swap(ctx->store[OOCS_FIELD_LAM], ctx->store[OOCS_FIELD_LAM_PREV]);
-        std::swap(ctx->store_bytes[OOCS_FIELD_LAM], ctx->store_bytes[OOCS_FIELD_LAM_PREV]);
-        ctx->stats.steps_done = (uint64_t)(t - 1);
-        ctx->stats.passes_done++;
+        std::fill(ctx->d2h_recorded.begin(), ctx->d2h_recorded.end(), 0);  // the opening join orders the rest
+        for (int j = 0; j < nsteps; ++j) {
+            const int64_t k = t - j;
+            for (int sl = ctx->v.S - 1; sl >= 0; --sl) {
+                s = enqueue_adjoint_slab(ctx, sl, k, fwd[j], j > 0);
+                if (s != OOCS_OK)
+                    return s;
+            }
+            std::swap(ctx->store[OOCS_FIELD_LAM], ctx->store[OOCS_FIELD_LAM_PREV]);
+            std::swap(ctx->store_bytes[OOCS_FIELD_LAM], ctx->store_bytes[OOCS_FIELD_LAM_PREV]);
+            std::swap(ctx->store_id[OOCS_FIELD_LAM], ctx->store_id[OOCS_FIELD_LAM_PREV]);
+            ctx->stats.passes_done++;
+        }
+        ctx->stats.steps_done = (uint64_t)(t - nsteps);
         s = join_streams(ctx);
         if (s != OOCS_OK)
             return s;
@@ -1597,8 +1629,8 @@ oocs_status oocs_trace_schedule(const oocs_desc *desc, const int32_t *nsteps, in
     c->v = derive(c->d, p.slab_planes);
     c->L = layout_for(c->d, c->v, c->d.working_buffers);
     memset(&c->stats, 0, sizeof(c->stats));
-    c->ev_d2h.assign(c->v.S, nullptr);
-    c->d2h_recorded.assign(c->v.S, 0);
+    c->ev_d2h.assign(c->d.scheme == OOCS_WAVE_ADJOINT ? 2 * c->v.S : c->v.S, nullptr);
+    c->d2h_recorded.assign(c->ev_d2h.size(), 0);
     static char dummy;
     for (int f = 0; f < 4; ++f)
         c->store[f] = &dummy;  // never dereferenced in trace mode

@@ -543,7 +543,7 @@ class OutOfCoreStencil:
 
     def step(self, nsteps: int):
         oocs_step(self.ctx, nsteps)
-        if self.desc.scheme == OOCS_WAVE_ADJOINT:  # the library swapped the two stores
+        if self.desc.scheme == OOCS_WAVE_ADJOINT and nsteps % 2:  # the library swapped the two stores
             self.stores[OOCS_FIELD_LAM], self.stores[OOCS_FIELD_LAM_PREV] = \
                 self.stores[OOCS_FIELD_LAM_PREV], self.stores[OOCS_FIELD_LAM]
 

@@ -322,5 +322,27 @@ def test_adjoint_sweep_schedule(P, rate):
     firsts = [lo for o in trace if o["op"] == "H2D" for (k, i, lo, hi, w) in o["access"] if k == "HOST" and i == 1]
     assert firsts[:3] == [64 // 4, 32 // 4, 0]  # slabs in reverse z order
     writes = [(i, lo, hi) for o in trace if o["op"] == "D2H" for (k, i, lo, hi, w) in o["access"] if w]
-    assert {i for i, _, _ in writes} == {1}
+    # the two lam stores trade roles every step: steps alternate between them
+    assert [i for i, _, _ in writes] == [1] * 3 + [0] * 3 + [1] * 3
     assert sum(hi - lo for _, lo, hi in writes) == 3 * (nz // 4)
+
+
+@pytest.mark.parametrize("calls", [[3], [2, 2], [5]])
+def test_adjoint_steps_in_one_call(P, calls):
+    """Several adjoint steps per call are chained by the previous step's
+    per-slab D2H events instead of a join: still race-free on the host stores
+    (whose roles alternate) and the device buffers, kernels of different
+    visits still ordered; without the chained waits the check finds a race."""
+    nz, ny, nx = 96, 40, 48
+    d = P.make_desc(nx, ny, nz, P.OOCS_WAVE_ADJOINT, synthetic.wave_star_coef(), 8 << 30, rate_bits=16,
+                    temporal_depth=1, slab_planes=32, readonly_resident=1)
+    trace = P.oocs_trace_schedule(d, calls)
+    assert check(trace, swb=True) is None
+    steps = sum(calls)
+    writes = [(i, hi - lo) for o in trace if o["op"] == "D2H" for (k, i, lo, hi, w) in o["access"] if w]
+    assert sum(n for _, n in writes) == steps * (nz // 4)  # every layer of lam once per step
+    assert [i for i, _ in writes] == [(j + 1) % 2 for j in range(steps) for _ in range(3)]
+    cut = [o for o in trace if not (o["op"] == "WAIT" and 1000 <= o["event"] < 2000)]
+    if max(calls) > 1:
+        assert len(cut) < len(trace)
+        assert check(cut, swb=True) is not None
