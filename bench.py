@@ -391,6 +391,15 @@ def run_ours(args):
         kernels[c] = k
     kernels["note"] = "one extra oocs_step(100) with all classes event-timed; ms per call"
     st.set_profiling(0)
+    # what binds the call as measured: the serial chain of kernels (one working
+    # buffer: the visits' kernels never overlap) or the host-link floor
+    chain_ms = sum(kernels[c]["device_ms"] for c in ("load", "step", "store"))
+    t_call = ms / world if world else ms
+    sweep_roofline["kernel_chain_ms_per_call"] = chain_ms
+    sweep_roofline["link_floor_ms_per_call"] = t_roof * 1e3 / args.steps
+    sweep_roofline["measured_binding"] = ("kernel chain" if chain_ms > t_roof * 1e3 / args.steps
+                                          else "host link")
+    sweep_roofline["ms_per_call"] = t_call / args.steps
 
     # ---- e2e: raw FP32 host arrays in, result back in host memory
     e2e_ms = []
