@@ -211,3 +211,29 @@ def test_tuned_problems_run_as_a_batch(P, tmp_path):
     for i, (d, fields, src) in enumerate(tuned):
         ref, _ = _alone(P, d, fields, src, [6])
         assert np.array_equal(got[i][0], ref[0])
+
+
+def test_batch_mixing_codecs_matches_problems_run_alone(P):
+    """Members of one batch keep their own codec (transform or block quantiser):
+    each ends with the stores it gets when it runs alone."""
+    torch_cuda()
+    probs = []
+    u = synthetic.heat_initial(64)
+    probs.append((heat_desc(P, u.shape, rate=16, k=2, T=32, codec=1), {0: u}, None))
+    probs.append((heat_desc(P, u.shape, rate=16, k=2, T=32, codec=0), {0: u}, None))
+    shape = (96, 48, 64)
+    m = synthetic.wave_model(shape)
+    z = np.zeros(shape, np.float32)
+    src = (synthetic.centre(shape)[::-1], synthetic.ricker(40))
+    probs.append((wave_desc(P, shape, rate=20, k=3, T=24, ro=1, codec=1), {0: z, 1: z, 2: m}, src))
+    b = _batch(P, probs)
+    try:
+        b.step(8)
+        b.synchronize(120.0)
+        got = [[s.numpy().copy() for s in bp.stores] for bp in b.problems]
+    finally:
+        b.close()
+    for i, (d, fields, s) in enumerate(probs):
+        ref, _ = _alone(P, d, fields, s, [8])
+        for f in range(2 if d.scheme == P.OOCS_WAVE else 1):
+            assert np.array_equal(got[i][f], ref[f]), (i, f)
