@@ -362,3 +362,29 @@ def test_out_of_core_gradient_rate16_vs_oracle(P, orc):
     J.backward()
     assert J_ref > 0 and abs(float(J.detach()) - J_ref) <= 1e-3 * J_ref
     assert rel_l2(vt.grad.cpu().numpy(), gv_ref) <= 2e-3
+
+
+def test_adjoint_multi_step_needs_the_forward_states(P):
+    """More than one adjoint step per call reads u^(k-1) from a state record:
+    without one the call is refused, and a record that lacks a needed state is
+    refused before anything is enqueued (the context stays usable)."""
+    torch = torch_cuda()
+    A, prob, v, _ = _ooc_problem(P, 16, 10, 20, budget=8 << 30)
+    adj = P.OutOfCoreStencil(A._ooc_desc(prob, P.OOCS_WAVE_ADJOINT, 1))
+    try:
+        adj.synchronize(60.0)
+        adj.set_time(6)
+        with pytest.raises(P.OOCSError) as e:
+            adj.step(2)
+        assert e.value.status == 1
+        nb = adj.plan.host_store_bytes
+        ring = torch.zeros((3, nb), dtype=torch.uint8, pin_memory=True)
+        P.oocs_set_state_record(adj.ctx, [ring[i].data_ptr() for i in range(3)], 4)  # u^4 .. u^6
+        with pytest.raises(P.OOCSError) as e:
+            adj.step(3)  # k = 6, 5, 4 needs u^5, u^4, u^3
+        assert e.value.status == 6
+        adj.step(2)  # u^5, u^4: allowed
+        adj.synchronize(60.0)
+        assert adj.stats()["steps_done"] == 4
+    finally:
+        adj.close()
