@@ -81,6 +81,19 @@ def dist_env():
     return rank, world, local
 
 
+def guarded(fn, *args):
+    """Run one of the sections measured after the headline; a failure (say a
+    host with too little free memory for a 134 GB pinned store) is reported
+    in its place instead of losing the whole line."""
+    try:
+        return fn(*args)
+    except Exception as e:  # noqa: BLE001 - any failure of an optional section
+        import torch
+        if torch.cuda.is_available():
+            torch.cuda.empty_cache()
+        return {"error": f"{type(e).__name__}: {e}"[:400]}
+
+
 def max_over_ranks(torch, value: float, device) -> float:
     """The largest of every rank's value (the slowest replica's time)."""
     import torch.distributed as dist
@@ -441,91 +454,21 @@ def run_ours(args):
     single = world == 1
 
     # ---- accuracy at the stated configuration: 100 steps from rest
-    accuracy = check_accuracy(P, torch, dev, args.rate, inputs) if single else None
+    accuracy = guarded(check_accuracy, P, torch, dev, args.rate, inputs) if single else None
 
     # ---- the adjoint workload (gradient of a receiver misfit)
-    adjoint = run_adjoint(P, torch, dev, float(peaks["hbm_gbs"])) if single and not args.no_adjoint else None
+    adjoint = guarded(run_adjoint, P, torch, dev, float(peaks["hbm_gbs"])) \
+        if single and not args.no_adjoint else None
 
     # ---- the batched workload (many independent problems, one pipeline)
-    batched = run_batched(P, torch, dev) if single and not args.no_batch else None
+    batched = guarded(run_batched, P, torch, dev) if single and not args.no_batch else None
 
     # ---- a grid larger than the device budget by far (two 134 GB arrays)
-    true_ooc = run_true_out_of_core(P, torch, dev) if single and not args.no_true_ooc else None
+    true_ooc = guarded(run_true_out_of_core, P, torch, dev) if single and not args.no_true_ooc else None
 
     # ---- comparison: uncompressed streaming, SWB and classic (Fig. 9, Fig. 11 analogues)
-    compare = None
-    if single and not args.no_compare:
-        compare = {}
-        ref = incore_reference(P, torch, dev, inputs)
-        for name, rate, wb, ro, codec in (("uncompressed_swb", 0, 1, RO_RESIDENT, 0),
-                                          ("uncompressed_classic", 0, 3, RO_RESIDENT, 0),
-                                          (f"rate{args.rate}_classic", args.rate, 3, RO_RESIDENT, 0),
-                                          ("rate8_swb", 8, 1, RO_RESIDENT, 0), ("rate12_swb", 12, 1, RO_RESIDENT, 0),
-                                          (f"rate{args.rate}_swb_m_streamed", args.rate, 1, 0, 0),
-                                          ("uncompressed_swb_m_streamed", 0, 1, 0, 0),
-                                          ("uncompressed_classic_m_streamed", 0, 3, 0, 0),
-                                          # the simpler codec of the Sec. 7 (1) comparison
-                                          ("quant12_swb", 12, 1, RO_RESIDENT, 1),
-                                          ("quant16_swb", 16, 1, RO_RESIDENT, 1),
-                                          ("quant20_swb", 20, 1, RO_RESIDENT, 1)):
-            st, pin = open_ctx(P, torch, rate, wb, inputs, ro, codec)
-            snap_u = st.snapshot_stores()
-            timed_calls(torch, st, 1, snap_u)
-            k = 2
-            cms = timed_calls(torch, st, k, snap_u)
-            compare[name] = {"value": interior_points() * STEPS_PER_CALL * k / (cms / 1e3) / 1e9,
-                             "workspace_bytes": st.plan.workspace_bytes}
-            st.close()
-            del st, pin, snap_u
-            torch.cuda.empty_cache()
-            if rate and wb == 1 and ro == RO_RESIDENT:  # accuracy of each codec and rate
-                compare[name]["rel_l2_vs_uncompressed_fp32"] = check_accuracy(
-                    P, torch, dev, rate, inputs, codec, ref)["rel_l2_vs_uncompressed_fp32"]
-        del ref
-        compare["codec_kernels"] = codec_kernel_rates(P, torch, dev, args.rate, float(peaks["hbm_gbs"]))
-        # the same workload as a batch of one, its 100-step call replayed as one CUDA graph
-        m, w, src, z = inputs
-        b = P.OutOfCoreBatch([wave_desc(P, args.rate)])
-        bp = b.problems[0]
-        pin = {}
-        for name, arr in (("z", z), ("m", m)):
-            t = torch.empty(arr.shape, dtype=torch.float32, pin_memory=True)
-            t.numpy()[...] = arr
-            pin[name] = t
-        bp.compress(P.OOCS_FIELD_U, pin["z"])
-        bp.compress(P.OOCS_FIELD_U_PREV, pin["z"])
-        bp.compress(P.OOCS_FIELD_M, pin["m"])
-        bp.set_source(src[0], src[1], src[2], w)
-        b.synchronize(600.0)
-        snap_g = bp.snapshot_stores()
-        b.capture(STEPS_PER_CALL)
-        gms = []
-        for i in range(3):
-            bp.restore_stores(snap_g, 0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(b.streams[0])
-            b.launch()
-            e1.record(b.streams[0])
-            b.synchronize(600.0)
-            e1.synchronize()
-            if i:
-                gms.append(e0.elapsed_time(e1))
-        compare[f"rate{args.rate}_swb_graph_replay"] = {
-            "value": interior_points() * STEPS_PER_CALL * len(gms) / (sum(gms) / 1e3) / 1e9,
-            "note": "the 100-step call captured once (oocs_batch_capture) and replayed"}
-        b.close()
-        del b, bp, pin, snap_g
-        torch.cuda.empty_cache()
-        compare["speedup_compressed_vs_uncompressed"] = value / world / compare["uncompressed_swb"]["value"]
-        compare["speedup_compressed_vs_uncompressed_m_streamed"] = \
-            compare[f"rate{args.rate}_swb_m_streamed"]["value"] / compare["uncompressed_swb_m_streamed"]["value"]
-        # the paper's memory comparison (Sec. 6.2): compressed SWB against
-        # uncompressed classic, both streaming m as the paper does
-        compare["memory_reduction_vs_uncompressed_classic"] = \
-            1.0 - compare[f"rate{args.rate}_swb_m_streamed"]["workspace_bytes"] \
-            / compare["uncompressed_classic_m_streamed"]["workspace_bytes"]
-        compare["paper_v100"] = {"speedup": 1.1, "memory_reduction": 0.330,
-                                 "source": "Sec. 6.1 and Sec. 6.2 (V100-PCIe, FP64, context only)"}
+    compare = guarded(run_compare, P, torch, dev, args, inputs, peaks, value, world) \
+        if single and not args.no_compare else None
 
     line = base_line(args, world)
     line.update({"value": value, "ms_per_step": ms / args.steps, "dtype": "f32",
@@ -666,6 +609,84 @@ def ooc_samples(shape, n=64, seed=32, margin=24):
     import synthetic
     u = synthetic.uniform01(seed, 3 * n).reshape(n, 3)
     return [tuple(int(margin + u[i, a] * (shape[a] - 2 * margin)) for a in range(3)) for i in range(n)]
+
+
+def run_compare(P, torch, dev, args, inputs, peaks, value, world):
+    """Comparison on the same GPU (Fig. 9, Fig. 11 analogues): uncompressed
+    streaming, SWB and classic, other rates and the block quantiser with their
+    accuracy, the codec kernels alone, and the call replayed as a CUDA graph."""
+    compare = {}
+    ref = incore_reference(P, torch, dev, inputs)
+    for name, rate, wb, ro, codec in (("uncompressed_swb", 0, 1, RO_RESIDENT, 0),
+                                      ("uncompressed_classic", 0, 3, RO_RESIDENT, 0),
+                                      (f"rate{args.rate}_classic", args.rate, 3, RO_RESIDENT, 0),
+                                      ("rate8_swb", 8, 1, RO_RESIDENT, 0), ("rate12_swb", 12, 1, RO_RESIDENT, 0),
+                                      (f"rate{args.rate}_swb_m_streamed", args.rate, 1, 0, 0),
+                                      ("uncompressed_swb_m_streamed", 0, 1, 0, 0),
+                                      ("uncompressed_classic_m_streamed", 0, 3, 0, 0),
+                                      # the simpler codec of the Sec. 7 (1) comparison
+                                      ("quant12_swb", 12, 1, RO_RESIDENT, 1),
+                                      ("quant16_swb", 16, 1, RO_RESIDENT, 1),
+                                      ("quant20_swb", 20, 1, RO_RESIDENT, 1)):
+        st, pin = open_ctx(P, torch, rate, wb, inputs, ro, codec)
+        snap_u = st.snapshot_stores()
+        timed_calls(torch, st, 1, snap_u)
+        k = 2
+        cms = timed_calls(torch, st, k, snap_u)
+        compare[name] = {"value": interior_points() * STEPS_PER_CALL * k / (cms / 1e3) / 1e9,
+                         "workspace_bytes": st.plan.workspace_bytes}
+        st.close()
+        del st, pin, snap_u
+        torch.cuda.empty_cache()
+        if rate and wb == 1 and ro == RO_RESIDENT:  # accuracy of each codec and rate
+            compare[name]["rel_l2_vs_uncompressed_fp32"] = check_accuracy(
+                P, torch, dev, rate, inputs, codec, ref)["rel_l2_vs_uncompressed_fp32"]
+    del ref
+    compare["codec_kernels"] = codec_kernel_rates(P, torch, dev, args.rate, float(peaks["hbm_gbs"]))
+    # the same workload as a batch of one, its 100-step call replayed as one CUDA graph
+    m, w, src, z = inputs
+    b = P.OutOfCoreBatch([wave_desc(P, args.rate)])
+    bp = b.problems[0]
+    pin = {}
+    for name, arr in (("z", z), ("m", m)):
+        t = torch.empty(arr.shape, dtype=torch.float32, pin_memory=True)
+        t.numpy()[...] = arr
+        pin[name] = t
+    bp.compress(P.OOCS_FIELD_U, pin["z"])
+    bp.compress(P.OOCS_FIELD_U_PREV, pin["z"])
+    bp.compress(P.OOCS_FIELD_M, pin["m"])
+    bp.set_source(src[0], src[1], src[2], w)
+    b.synchronize(600.0)
+    snap_g = bp.snapshot_stores()
+    b.capture(STEPS_PER_CALL)
+    gms = []
+    for i in range(3):
+        bp.restore_stores(snap_g, 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.streams[0])
+        b.launch()
+        e1.record(b.streams[0])
+        b.synchronize(600.0)
+        e1.synchronize()
+        if i:
+            gms.append(e0.elapsed_time(e1))
+    compare[f"rate{args.rate}_swb_graph_replay"] = {
+        "value": interior_points() * STEPS_PER_CALL * len(gms) / (sum(gms) / 1e3) / 1e9,
+        "note": "the 100-step call captured once (oocs_batch_capture) and replayed"}
+    b.close()
+    del b, bp, pin, snap_g
+    torch.cuda.empty_cache()
+    compare["speedup_compressed_vs_uncompressed"] = value / world / compare["uncompressed_swb"]["value"]
+    compare["speedup_compressed_vs_uncompressed_m_streamed"] = \
+        compare[f"rate{args.rate}_swb_m_streamed"]["value"] / compare["uncompressed_swb_m_streamed"]["value"]
+    # the paper's memory comparison (Sec. 6.2): compressed SWB against
+    # uncompressed classic, both streaming m as the paper does
+    compare["memory_reduction_vs_uncompressed_classic"] = \
+        1.0 - compare[f"rate{args.rate}_swb_m_streamed"]["workspace_bytes"] \
+        / compare["uncompressed_classic_m_streamed"]["workspace_bytes"]
+    compare["paper_v100"] = {"speedup": 1.1, "memory_reduction": 0.330,
+                             "source": "Sec. 6.1 and Sec. 6.2 (V100-PCIe, FP64, context only)"}
+    return compare
 
 
 def run_true_out_of_core(P, torch, dev):
