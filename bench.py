@@ -49,8 +49,8 @@ WAVE_BYTES_PER_POINT = 16  # read u, u_prev, m; write u_next (FP32)
 WORKLOAD = "wave25_512cubed_100steps_8slabs_k4_rate16_swb_m_resident"
 # DRAM bytes (read + write) per updated point of the wave step kernel from one ncu
 # capture of a 512x512x80 launch, the window size of the sweep's balanced step
-# launches (profiles/k_star_step_and_codec_512x512x192_512x512x80.md); scaled
-# to a launch by its points.  Set to None whenever the kernel changes.
+# launches; scaled to a launch by its points.  Set to None whenever the kernel
+# changes.
 STEP_TRAFFIC_B_PER_POINT = 15.78
 
 

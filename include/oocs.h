@@ -20,8 +20,9 @@
  *    any raw host arrays.  The library allocates only CUDA events and small
  *    host metadata, and frees only what it allocated.
  *  - Every call returns an oocs_status and never aborts, throws or traps.
- *    OOCS_ERR_CUDA and OOCS_ERR_TIMEOUT are sticky on a context until
- *    oocs_destroy; the text of the last error is in oocs_last_error().
+ *    OOCS_ERR_CUDA, OOCS_ERR_TIMEOUT and OOCS_ERR_NONFINITE are sticky on a
+ *    context until oocs_destroy; the text of the last error is in
+ *    oocs_last_error().
  *  - Calls that enqueue GPU work are asynchronous with respect to the host;
  *    completion and device-side errors surface in oocs_synchronize().
  *  - A context is used by one host thread at a time.
@@ -44,7 +45,8 @@ typedef enum {
     OOCS_ERR_CUDA = 4,         /* a CUDA call failed (sticky)                             */
     OOCS_ERR_TIMEOUT = 5,      /* oocs_synchronize ran out of time (sticky)               */
     OOCS_ERR_STATE = 6,        /* call not valid in the context's current state           */
-    OOCS_ERR_UNSUPPORTED = 7   /* valid request this build does not implement             */
+    OOCS_ERR_UNSUPPORTED = 7,  /* valid request this build does not implement             */
+    OOCS_ERR_NONFINITE = 8     /* the codec was handed an Inf or NaN (sticky); see below  */
 } oocs_status;
 
 /* Time schemes (Sec. 6 uses a 25-point acoustic wave code).
@@ -270,10 +272,37 @@ oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps);
  * GPU) stay usable.  For tests of the error path.                          */
 oocs_status oocs_selftest_stuck_wait(oocs_ctx *ctx);
 
+/* Host-side fault injection, for tests of the error path (no GPU fault is
+ * involved): after this call, the nth_call-th CUDA runtime call the context
+ * checks (counting from 1; enqueues of copies, kernels and events, event and
+ * stream queries) is reported as failed once it has been issued, exactly as
+ * if CUDA had returned an error: the entry point that made it returns
+ * OOCS_ERR_CUDA, sticky on the context ("injected failure" in
+ * oocs_last_error).  Work already enqueued still runs; destroy the context
+ * and create a new one to go on.  nth_call = 0 disarms.  Not in the paper:
+ * failure detection of the runtime around its Algorithm 1.                */
+oocs_status oocs_set_fault_injection(oocs_ctx *ctx, int64_t nth_call);
+
 /* Wait for all work of the context, at most timeout_ns nanoseconds
- * (0 = no limit).  OOCS_ERR_TIMEOUT if it is still running (sticky);
- * OOCS_ERR_CUDA on a device error.                                         */
+ * (0 = no limit).  OOCS_ERR_TIMEOUT if it is still running (sticky; the work
+ * goes on, and a later cudaStreamSynchronize of the streams waits for it);
+ * OOCS_ERR_CUDA on a device error or a bounded wait that ran out;
+ * OOCS_ERR_NONFINITE when the codec met an infinity or a NaN in a field it
+ * encoded (a run past the stability limit, or bad input).  The fixed-rate
+ * codec (Sec. 4.2) is defined for finite values: a 4x4x4 block holding a
+ * non-finite value is stored as an all-zero block, and the stores no longer
+ * describe the run.  Device-side errors are read from, and cleared in, the
+ * device's error word (see oocs_device_errors).                           */
 oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns);
+
+/* The device error word of the current device, for callers of the
+ * device-level entry points (oocs_encode_device, oocs_incore_run, ...), which
+ * have no context to report through: the OR of OOCS_DEVERR_* flags raised by
+ * kernels since it was last cleared.  Synchronises the device; clears the
+ * word if `clear` is non-zero.  The word is shared by every context and call
+ * on the device (oocs_synchronize also reads and clears it).              */
+enum { OOCS_DEVERR_WAIT_TIMEOUT = 1, OOCS_DEVERR_NONFINITE = 2 };
+oocs_status oocs_device_errors(uint32_t *flags, int32_t clear);
 
 oocs_status oocs_get_stats(const oocs_ctx *ctx, oocs_stats *out);
 
@@ -317,8 +346,9 @@ oocs_status oocs_incore_run(const oocs_desc *desc, float *u, float *u_prev, cons
  * maximum are rejected with OOCS_ERR_INVALID_ARG.  Allocates nothing: no
  * cudaMalloc, cudaFree or allocating library call.
  *  - The first call made with a device current looks up the array's device
- *    address (cudaGetSymbolAddress) and caches it; make that first call
- *    before any stream capture.
+ *    address (cudaGetSymbolAddress) and caches it per device and context; a
+ *    context created anew (after cudaDeviceReset) is looked up again.  Make
+ *    the first call on a device before any stream capture.
  *  - Every call shares the one array and it keeps the last call's contents;
  *    nothing in it needs to start at zero (each step overwrites all of it
  *    before reading it).  Calls that overlap on the GPU (other streams, other
@@ -389,7 +419,9 @@ oocs_status oocs_misfit_backward(const oocs_desc *desc, const float *m, const in
  * [nz][ny][nx] FP32 -> (nx/4)(ny/4)(nz/4) blocks of 8*rate bytes in layer
  * order (block (bx,by,bz) at ((bz*(ny/4)+by)*(nx/4)+bx)).  decode: inverse.
  * codec OOCS_CODEC_TRANSFORM with rate in [1, 32] or OOCS_CODEC_QUANT with
- * rate in [2, 32]; dims multiples of 4; pointers 16-byte aligned.          */
+ * rate in [2, 32]; dims multiples of 4; pointers 16-byte aligned.  A block
+ * holding an Inf or NaN is encoded as all zeros and raises
+ * OOCS_DEVERR_NONFINITE in the device error word (oocs_device_errors).     */
 oocs_status oocs_encode_device(const float *field, int64_t nx, int64_t ny, int64_t nz,
                                int32_t rate, int32_t codec, void *blocks, void *stream);
 oocs_status oocs_decode_device(const void *blocks, int64_t nx, int64_t ny, int64_t nz,

@@ -90,15 +90,19 @@ def _declare(L):
     L.oracle_decode_planes.argtypes = [_u32p, _i32, _i32, _u32p]
     L.oracle_decode_planes.restype = _i32
     L.oracle_encode_block.argtypes = [_fp, _i32, _u32p]
+    L.oracle_encode_block.restype = _i32
     L.oracle_decode_block.argtypes = [_u32p, _i32, _fp]
     L.oracle_decode_block.restype = _i32
     L.oracle_encode_field.argtypes = [_fp, _i64, _i64, _i64, _i32, _u32p]
+    L.oracle_encode_field.restype = _i64
     L.oracle_decode_field.argtypes = [_u32p, _i64, _i64, _i64, _i32, _fp, _i8p]
     L.oracle_bq_header.argtypes = [_fp]
     L.oracle_bq_header.restype = _i32
     L.oracle_bq_encode_block.argtypes = [_fp, _i32, _u32p]
+    L.oracle_bq_encode_block.restype = _i32
     L.oracle_bq_decode_block.argtypes = [_u32p, _i32, _fp]
     L.oracle_bq_encode_field.argtypes = [_fp, _i64, _i64, _i64, _i32, _u32p]
+    L.oracle_bq_encode_field.restype = _i64
     L.oracle_bq_decode_field.argtypes = [_u32p, _i64, _i64, _i64, _i32, _fp]
 
 
@@ -306,11 +310,13 @@ def decode_planes(words, budget):
     return u, int(low)
 
 
-def encode_block(v64, rate):
+def encode_block(v64, rate, with_flag=False):
+    """Words of one block; with_flag: also whether it held an Inf or NaN
+    (such a block is coded as all zeros)."""
     v = np.ascontiguousarray(v64, dtype=np.float32).reshape(64)
     words = np.zeros(2 * rate, np.uint32)
-    lib().oracle_encode_block(_p(v, _fp), int(rate), _p(words, _u32p))
-    return words
+    bad = lib().oracle_encode_block(_p(v, _fp), int(rate), _p(words, _u32p))
+    return (words, bool(bad)) if with_flag else words
 
 
 def decode_block(words, rate):
@@ -320,18 +326,19 @@ def decode_block(words, rate):
     return v, int(low)
 
 
-def encode_field(f, rate):
+def encode_field(f, rate, with_nonfinite=False):
     """Compress an [nz][ny][nx] FP32 field (multiples of 4) into uint32 words.
 
     Block (bx, by, bz) occupies words [(((bz*(ny/4)+by)*(nx/4)+bx)*2*rate, +2*rate).
+    with_nonfinite: also return how many blocks held an Inf or NaN.
     """
     f = np.ascontiguousarray(f, dtype=np.float32)
     nz, ny, nx = f.shape
     assert nx % 4 == 0 and ny % 4 == 0 and nz % 4 == 0
     nb = (nx // 4) * (ny // 4) * (nz // 4)
     out = np.zeros(nb * 2 * rate, np.uint32)
-    lib().oracle_encode_field(_p(f, _fp), nx, ny, nz, int(rate), _p(out, _u32p))
-    return out
+    bad = lib().oracle_encode_field(_p(f, _fp), nx, ny, nz, int(rate), _p(out, _u32p))
+    return (out, int(bad)) if with_nonfinite else out
 
 
 def decode_field(words, shape, rate, with_planes=False):
@@ -354,11 +361,11 @@ def bq_header(v64) -> int:
     return int(lib().oracle_bq_header(_p(v, _fp)))
 
 
-def bq_encode_block(v64, rate):
+def bq_encode_block(v64, rate, with_flag=False):
     v = np.ascontiguousarray(v64, dtype=np.float32).reshape(64)
     words = np.zeros(2 * rate, np.uint32)
-    lib().oracle_bq_encode_block(_p(v, _fp), int(rate), _p(words, _u32p))
-    return words
+    bad = lib().oracle_bq_encode_block(_p(v, _fp), int(rate), _p(words, _u32p))
+    return (words, bool(bad)) if with_flag else words
 
 
 def bq_decode_block(words, rate):
@@ -368,15 +375,15 @@ def bq_decode_block(words, rate):
     return v
 
 
-def bq_encode_field(f, rate):
+def bq_encode_field(f, rate, with_nonfinite=False):
     """Block-quantise an [nz][ny][nx] FP32 field; same block layout as encode_field."""
     f = np.ascontiguousarray(f, dtype=np.float32)
     nz, ny, nx = f.shape
     assert nx % 4 == 0 and ny % 4 == 0 and nz % 4 == 0 and 2 <= rate <= 32
     nb = (nx // 4) * (ny // 4) * (nz // 4)
     out = np.zeros(nb * 2 * rate, np.uint32)
-    lib().oracle_bq_encode_field(_p(f, _fp), nx, ny, nz, int(rate), _p(out, _u32p))
-    return out
+    bad = lib().oracle_bq_encode_field(_p(f, _fp), nx, ny, nz, int(rate), _p(out, _u32p))
+    return (out, int(bad)) if with_nonfinite else out
 
 
 def bq_decode_field(words, shape, rate):

@@ -413,18 +413,33 @@ int oracle_decode_planes(const uint32_t *words, int bitpos, int budget, uint32_t
     return lowest_complete;
 }
 
+/* 1 if any of the 64 values is an infinity or a NaN.  The codec is defined
+ * for finite values only; such a block is written as an all-zero block and
+ * the encoder reports it (a reading of this project: the paper's codec input
+ * is a simulation field, which is finite unless the run has blown up).    */
+static int block_nonfinite(const float *v)
+{
+    for (int i = 0; i < 64; i++)
+        if (!isfinite(v[i]))
+            return 1;
+    return 0;
+}
+
 /* Encode one block of 64 floats (index i + 4j + 16k) at `rate` bits/value
- * into words[0 .. 2*rate): exactly 64*rate bits, zero padded.            */
-void oracle_encode_block(const float *v, int rate, uint32_t *words)
+ * into words[0 .. 2*rate): exactly 64*rate bits, zero padded.  Returns 0, or
+ * 1 for a block holding a non-finite value (then coded as all zeros).     */
+int oracle_encode_block(const float *v, int rate, uint32_t *words)
 {
     int nwords = 2 * rate, maxbits = 64 * rate;
     memset(words, 0, (size_t)nwords * sizeof(uint32_t));
+    if (block_nonfinite(v))
+        return 1;
     int hdr = oracle_block_header(v);
     for (int b = 0; b < 8; b++)
         if ((hdr >> b) & 1)
             words[0] |= 1u << b;
     if (hdr == 0)
-        return;
+        return 0;
     int emax = hdr - 127;
     int32_t q[64];
     oracle_quantize(v, emax, q);
@@ -435,6 +450,7 @@ void oracle_encode_block(const float *v, int rate, uint32_t *words)
     for (int n = 0; n < 64; n++)
         u[n] = oracle_to_negabinary(q[perm[n]]);
     oracle_encode_planes(u, maxbits - 8, words, 8);
+    return 0;
 }
 
 /* Decode one block; returns the lowest completely decoded plane (32 for a
@@ -485,18 +501,20 @@ static void scatter(float *f, int64_t nx, int64_t ny, int64_t bx, int64_t by, in
                 f[IDX(4 * bx + i, 4 * by + j, 4 * bz + k)] = v[i + 4 * j + 16 * k];
 }
 
-void oracle_encode_field(const float *f, int64_t nx, int64_t ny, int64_t nz, int rate,
-                         uint32_t *out)
+/* Returns the number of blocks that held a non-finite value. */
+int64_t oracle_encode_field(const float *f, int64_t nx, int64_t ny, int64_t nz, int rate,
+                            uint32_t *out)
 {
-    int64_t bnx = nx / 4, bny = ny / 4, bnz = nz / 4, b;
+    int64_t bnx = nx / 4, bny = ny / 4, bnz = nz / 4, b, bad = 0;
     int64_t nb = bnx * bny * bnz;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) reduction(+ : bad)
     for (b = 0; b < nb; b++) {
         int64_t bx = b % bnx, by = (b / bnx) % bny, bz = b / (bnx * bny);
         float v[64];
         gather(f, nx, ny, bx, by, bz, v);
-        oracle_encode_block(v, rate, out + b * 2 * rate);
+        bad += oracle_encode_block(v, rate, out + b * 2 * rate);
     }
+    return bad;
 }
 
 void oracle_decode_field(const uint32_t *in, int64_t nx, int64_t ny, int64_t nz, int rate,
@@ -667,16 +685,20 @@ int oracle_bq_header(const float *v)
     return e + 127;
 }
 
-void oracle_bq_encode_block(const float *v, int rate, uint32_t *words)
+/* Returns 0, or 1 for a block holding a non-finite value, which is written
+ * as an all-zero block (the same rule as the transform codec).            */
+int oracle_bq_encode_block(const float *v, int rate, uint32_t *words)
 {
     const int q = rate - 1;
     const int64_t lim = ((int64_t)1 << (q - 1)) - 1;
     memset(words, 0, (size_t)(2 * rate) * sizeof(uint32_t));
+    if (block_nonfinite(v))
+        return 1;
     const int hdr = oracle_bq_header(v);
     for (int b = 0; b < 8; b++)
         bq_put_bit(words, b, (hdr >> b) & 1);
     if (hdr == 0)
-        return;
+        return 0;
     const int emax = hdr - 127;
     for (int j = 0; j < 64; j++) {
         /* v 2^(q-1-emax) is exact in double for every finite float */
@@ -690,6 +712,7 @@ void oracle_bq_encode_block(const float *v, int rate, uint32_t *words)
         for (int b = 0; b < q; b++)
             bq_put_bit(words, 8 + j * q + b, (unsigned)((u >> b) & 1u));
     }
+    return 0;
 }
 
 void oracle_bq_decode_block(const uint32_t *words, int rate, float *v)
@@ -715,17 +738,18 @@ void oracle_bq_decode_block(const uint32_t *words, int rate, float *v)
     }
 }
 
-void oracle_bq_encode_field(const float *f, int64_t nx, int64_t ny, int64_t nz, int rate, uint32_t *out)
+int64_t oracle_bq_encode_field(const float *f, int64_t nx, int64_t ny, int64_t nz, int rate, uint32_t *out)
 {
-    int64_t bnx = nx / 4, bny = ny / 4, bnz = nz / 4, b;
+    int64_t bnx = nx / 4, bny = ny / 4, bnz = nz / 4, b, bad = 0;
     int64_t nb = bnx * bny * bnz;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) reduction(+ : bad)
     for (b = 0; b < nb; b++) {
         int64_t bx = b % bnx, by = (b / bnx) % bny, bz = b / (bnx * bny);
         float v[64];
         gather(f, nx, ny, bx, by, bz, v);
-        oracle_bq_encode_block(v, rate, out + b * 2 * rate);
+        bad += oracle_bq_encode_block(v, rate, out + b * 2 * rate);
     }
+    return bad;
 }
 
 void oracle_bq_decode_field(const uint32_t *in, int64_t nx, int64_t ny, int64_t nz, int rate, float *f)

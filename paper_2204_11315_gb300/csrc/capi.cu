@@ -352,6 +352,10 @@ struct oocs_ctx {
     oocs_status sticky = OOCS_OK;
     std::string err = "no error";
 
+    // host-side fault injection (oocs_set_fault_injection): the inject_at-th
+    // CUDA call checked after arming is reported as failed
+    int64_t inject_at = 0, inject_seen = 0;
+
     // member of a batch (oocs_batch_create): the workspace, the three streams,
     // the Algorithm-1 events and the visit counter belong to the batch
     oocs_batch *batch = nullptr;
@@ -397,12 +401,19 @@ oocs_status fail(oocs_ctx *c, oocs_status s, const std::string &msg)
 {
     if (c) {
         c->err = msg;
-        if (s == OOCS_ERR_CUDA || s == OOCS_ERR_TIMEOUT)
+        if (s == OOCS_ERR_CUDA || s == OOCS_ERR_TIMEOUT || s == OOCS_ERR_NONFINITE)
             c->sticky = s;
     } else {
         g_last_error = msg;
     }
     return s;
+}
+
+// true when fault injection is armed on c and this checked call is the one
+// chosen to fail
+bool inject_now(oocs_ctx *c)
+{
+    return c && c->inject_at > 0 && ++c->inject_seen == c->inject_at;
 }
 
 #define CU(ctx, call)                                                                        \
@@ -411,6 +422,8 @@ oocs_status fail(oocs_ctx *c, oocs_status s, const std::string &msg)
         if (e_ != cudaSuccess)                                                               \
             return fail((ctx), OOCS_ERR_CUDA,                                                \
                         std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+        if (inject_now(ctx))                                                                 \
+            return fail((ctx), OOCS_ERR_CUDA, std::string(#call) + ": injected failure");    \
     } while (0)
 
 // in-field index -> context field id
@@ -1574,9 +1587,14 @@ oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns)
     }
     unsigned int code = 0;
     CU(ctx, read_device_error(&code, true));
-    if (code)
+    if (code & OOCS_DEVERR_WAIT_TIMEOUT)
         return fail(ctx, OOCS_ERR_CUDA, "a kernel's bounded wait ran out (device error " +
                                             std::to_string(code) + ")");
+    if (code & OOCS_DEVERR_NONFINITE)
+        return fail(ctx, OOCS_ERR_NONFINITE,
+                    "the codec met an infinity or a NaN: the blocks holding one were stored as zeros");
+    if (code)
+        return fail(ctx, OOCS_ERR_CUDA, "device error " + std::to_string(code));
     if (ctx->timing_pending) {
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, ctx->ev_t0, ctx->ev_t1) == cudaSuccess)
@@ -1584,6 +1602,29 @@ oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns)
         ctx->timing_pending = false;
     }
     collect_profile(ctx);
+    return OOCS_OK;
+}
+
+oocs_status oocs_set_fault_injection(oocs_ctx *ctx, int64_t nth_call)
+{
+    if (!ctx || nth_call < 0)
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "ctx is NULL or nth_call < 0");
+    ctx->inject_at = nth_call;
+    ctx->inject_seen = 0;
+    return OOCS_OK;
+}
+
+oocs_status oocs_device_errors(uint32_t *flags, int32_t clear)
+{
+    if (!flags)
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "flags is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    unsigned int code = 0;
+    if (e == cudaSuccess)
+        e = read_device_error(&code, clear != 0);
+    if (e != cudaSuccess)
+        return fail(nullptr, OOCS_ERR_CUDA, std::string("oocs_device_errors: ") + cudaGetErrorString(e));
+    *flags = code;
     return OOCS_OK;
 }
 

@@ -21,7 +21,8 @@
 // formed by two 32x32 bit-matrix transposes (no per-bit loop), and each plane
 // is emitted in closed form: the verbatim part is one masked word, and each
 // group-test hit is one "1, zeros, 1" code found with a count-trailing-zeros.
-// Inputs must be finite.
+// A block holding an infinity or a NaN is coded as an all-zero block and
+// reported to the caller (encode_block returns false).
 #pragma once
 #include <stdint.h>
 
@@ -274,9 +275,11 @@ struct BitReader {
 
 // ------------------------------------------------------------------- codec --
 
-// Encode one block.  sink(word_index, word) receives words 0 .. 2*rate-1 in order.
+// Encode one block.  sink(word_index, word) receives words 0 .. 2*rate-1 in
+// order.  Returns false for a block holding an infinity or a NaN, which is
+// written as an all-zero block (the codec is defined for finite values).
 template <class Sink>
-OOCS_FN void encode_block(const float (&v)[64], int rate, Sink &&sink)
+OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink)
 {
     const int nwords = 2 * rate;
     uint32_t mag = 0;
@@ -284,9 +287,9 @@ OOCS_FN void encode_block(const float (&v)[64], int rate, Sink &&sink)
     for (int i = 0; i < 64; ++i)
         mag = max(mag, f32_bits(v[i]) & 0x7FFFFFFFu);
     BitWriter<Sink> bw(sink, nwords);
-    if (mag == 0) {
+    if (mag == 0 || mag >= 0x7F800000u) {
         bw.finish();
-        return;
+        return mag == 0;
     }
     // emax = max(biased - 126, -95); header = emax + 127
     const int hdr = max((int)(mag >> 23), 31) + 1;
@@ -305,7 +308,7 @@ OOCS_FN void encode_block(const float (&v)[64], int rate, Sink &&sink)
         // zero: every plane is one group-test 0, which the zero padding writes
         bw.put((uint32_t)hdr, 8);
         bw.finish();
-        return;
+        return true;
     }
     xform_fwd(q);
 
@@ -353,6 +356,7 @@ OOCS_FN void encode_block(const float (&v)[64], int rate, Sink &&sink)
         }
     }
     bw.finish();
+    return true;
 }
 
 // Decode one block.  src(word_index) returns word i of the block (0 past the end).

@@ -1,10 +1,10 @@
 // kernels.cu -- sm_103a kernels: star-stencil time step and the block codec.
 //
 // Stencil step (Sec. 3.1, Sec. 6 25-point acoustic code): a 2.5D z-march.  A
-// CTA owns a 32 x 16 tile of the x-y plane and walks its share of the z range.
-// The u planes (with their x-y halo) arrive by TMA into a shared-memory ring
-// several planes ahead of use; each thread keeps u(z-R .. z+R) of its four
-// points in a register queue.  Nothing here is a dense contraction, so the
+// CTA owns 64 x 16 tiles of the x-y plane and walks its share of their z
+// range.  The u planes (with their x-y halo) arrive by TMA into a
+// shared-memory ring several planes ahead of use; each consumer thread keeps
+// u(z-R .. z+R) of its 2 x 4 points in a register queue.  Nothing here is a dense contraction, so the
 // kernel is HBM-bound and uses no tensor cores.
 //
 // Codec (Sec. 4.2): one thread per 4x4x4 block; 16 float4 loads per block
@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 #include <utility>
 
@@ -525,21 +526,82 @@ static cudaError_t make_plane_map(CUtensorMap *m, const float *base, int64_t nx,
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Per-device launch facts, looked up once per device ordinal (a process may
+// drive several GPUs, from several host threads): the SM count, and for each
+// step-kernel instance whether its dynamic shared-memory opt-in was applied on
+// that device (cudaFuncSetAttribute acts on the current device only) and how
+// many of its CTAs fit on an SM.
+constexpr int kMaxDevices = 64;
+constexpr int kStepInstances = 8;  // (radius, scheme) instances of k_star_step
+
 struct DevInfo {
     int sms = 0;
+    int resident[kStepInstances] = {};  // 0: not yet opted in on this device
 };
 
-static const DevInfo &dev_info()
+static std::mutex g_dev_mu;
+static DevInfo g_dev[kMaxDevices];
+
+static cudaError_t current_device(int &dev)
 {
-    static DevInfo info;
-    static int dev_cached = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && (dev < 0 || dev >= kMaxDevices))
+        e = cudaErrorInvalidDevice;
+    return e;
+}
+
+// SM count of the current device (0 if it cannot be read).
+static int device_sms()
+{
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev != dev_cached) {
-        cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev);
-        dev_cached = dev;
+    if (current_device(dev) != cudaSuccess)
+        return 0;
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    DevInfo &info = g_dev[dev];
+    if (info.sms == 0 && cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        info.sms = 0;
+    return info.sms;
+}
+
+template <int R, int SCHEME>
+constexpr int step_instance() { return (R == 4 ? 4 : 0) + SCHEME; }
+
+// Applies the step kernel's shared-memory opt-in on the current device (once
+// per device) and returns its CTAs per SM and the device's SM count.
+template <int R, int SCHEME>
+static cudaError_t step_residency(int &resident, int &sms)
+{
+    using C = StepCfg<R, centre_fields<SCHEME>()>;
+    static_assert(step_instance<R, SCHEME>() < kStepInstances, "instance table too small");
+    int dev = 0;
+    cudaError_t e = current_device(dev);
+    if (e != cudaSuccess)
+        return e;
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    DevInfo &info = g_dev[dev];
+    if (info.sms == 0) {
+        e = cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess)
+            return e;
     }
-    return info;
+    int &res = info.resident[step_instance<R, SCHEME>()];
+    if (res == 0) {
+        const size_t smem = C::smem_bytes();
+        auto kern = k_star_step<R, SCHEME>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kStepThreads, smem);
+        if (e != cudaSuccess)
+            return e;
+        if (n < 1)
+            return cudaErrorInvalidConfiguration;
+        res = n;
+    }
+    resident = res;
+    sms = info.sms;
+    return cudaSuccess;
 }
 
 template <int R, int SCHEME>
@@ -548,16 +610,11 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
     using C = StepCfg<R, centre_fields<SCHEME>()>;
     const size_t smem = C::smem_bytes();
     auto kern = k_star_step<R, SCHEME>;
-    static int resident = 0;  // CTAs per SM (same on every GB300)
-    if (!resident) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int resident = 0, sms = 0;
+    {
+        cudaError_t e = step_residency<R, SCHEME>(resident, sms);
         if (e != cudaSuccess)
             return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, kStepThreads, smem);
-        if (e != cudaSuccess)
-            return e;
-        if (resident < 1)
-            return cudaErrorInvalidConfiguration;
     }
     constexpr int NCF = centre_fields<SCHEME>();
     CUtensorMap mc, mp, mm, m2;
@@ -579,7 +636,7 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
     a.ntiles = tiles;
     // z chunks: keep >= 12 planes per CTA and choose the count whose last wave
     // of CTAs (sms x resident per wave) is fullest
-    const int slots = dev_info().sms * resident;
+    const int slots = sms * resident;
     int best = 1;
     double best_eff = 0.0;
     const int max_chunks = std::max(1, nplanes / 12);
@@ -672,7 +729,7 @@ cudaError_t launch_product(float *out, const float *a, const float *b, int64_t n
     if (n <= 0)
         return cudaSuccess;
     const int64_t n4 = n / 4;
-    const unsigned grid = (unsigned)std::min<int64_t>((n4 + 255) / 256, (int64_t)dev_info().sms * 8);
+    const unsigned grid = (unsigned)std::min<int64_t>((n4 + 255) / 256, (int64_t)std::max(device_sms(), 1) * 8);
     return launch_pdl(k_product, dim3(grid), dim3(256), 0, s, out, a, b, n4);
 }
 
@@ -776,10 +833,13 @@ __global__ void __launch_bounds__(kCodecThreads, 6)
                 v[16 * k + 4 * j + 3] = f.w;
             }
         uint32_t *row = sw + threadIdx.x * stride;
+        bool finite;
         if constexpr (KIND == kCodecQuant)
-            bq_encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
+            finite = bq_encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
         else
-            encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
+            finite = encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
+        if (!finite)
+            atomicOr(&g_device_error, kErrNonFinite);
     }
     __syncthreads();
     // each warp copies whole blocks out, its lanes over the block's words

@@ -11,7 +11,8 @@
 // The array lives in every GPU that loads this library, until the process
 // exits.  Host code must not pass the array's name to a kernel (on the host it
 // is only a stand-in for the device symbol); the device address is looked up
-// once per device with cudaGetSymbolAddress and passed on.
+// with cudaGetSymbolAddress once per device and context, and passed on.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,6 +29,7 @@ static __device__ __align__(256) float g_noalloc_scratch[OOCS_NOALLOC_MAX_VALUES
 
 struct DeviceScratch {
     int device;
+    CUcontext ctx;  // the context the address belongs to
     float *ptr;
 };
 
@@ -35,8 +37,28 @@ std::mutex g_mu;
 DeviceScratch g_known[256];
 int g_nknown = 0;
 
-// Device address of the scratch array on the current device; looked up on the
-// first call made with that device current, then cached.
+// cuCtxGetCurrent, taken from the driver through the runtime (no link to libcuda)
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+
+CtxGetCurrentFn ctx_get_current()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    });
+    return fn;
+}
+
+// Device address of the scratch array in the current device's current
+// context; looked up on the first call made in that (device, context) pair,
+// then cached.  The context is part of the key because cudaDeviceReset ends
+// the primary context: the runtime then loads this module again in a new one,
+// where the array may have another address.
 oocs_status scratch_on_current_device(float **out)
 {
     int dev = -1;
@@ -45,21 +67,40 @@ oocs_status scratch_on_current_device(float **out)
         oocs::set_last_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
         return OOCS_ERR_CUDA;
     }
+    CtxGetCurrentFn get = ctx_get_current();
+    if (!get) {
+        oocs::set_last_error("cuCtxGetCurrent is not available from the driver");
+        return OOCS_ERR_CUDA;
+    }
+    CUcontext ctx = nullptr;  // null before the runtime has made the context current
+    if (get(&ctx) != CUDA_SUCCESS)
+        ctx = nullptr;
     std::lock_guard<std::mutex> lock(g_mu);
-    for (int i = 0; i < g_nknown; ++i)
-        if (g_known[i].device == dev) {
+    for (int i = 0; i < g_nknown && ctx; ++i)
+        if (g_known[i].device == dev && g_known[i].ctx == ctx) {
             *out = g_known[i].ptr;
             return OOCS_OK;
         }
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // also makes the primary context current
     if (e != cudaSuccess || !p) {
         oocs::set_last_error(std::string("cudaGetSymbolAddress(no-allocation scratch): ") +
                              cudaGetErrorString(e));
         return OOCS_ERR_CUDA;
     }
-    if (g_nknown < 256)
-        g_known[g_nknown++] = {dev, static_cast<float *>(p)};
+    if (get(&ctx) != CUDA_SUCCESS || !ctx) {
+        oocs::set_last_error("cuCtxGetCurrent: no current context for the no-allocation scratch");
+        return OOCS_ERR_CUDA;
+    }
+    // a device seen before with another context: replace its entry
+    int slot = -1;
+    for (int i = 0; i < g_nknown; ++i)
+        if (g_known[i].device == dev)
+            slot = i;
+    if (slot < 0 && g_nknown < 256)
+        slot = g_nknown++;
+    if (slot >= 0)
+        g_known[slot] = {dev, ctx, static_cast<float *>(p)};
     *out = static_cast<float *>(p);
     return OOCS_OK;
 }

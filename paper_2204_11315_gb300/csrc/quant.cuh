@@ -14,7 +14,8 @@
 //
 // Decoding returns RN(RN(n) 2^(emax-q+1)).  No transform, no bit planes: a
 // value costs a few integer operations, so the kernels move bytes rather than
-// issue instructions.  Inputs must be finite; rate in [2, 32].
+// issue instructions.  Rate in [2, 32]; a block with an infinity or a NaN
+// is written as an all-zero block and reported (bq_encode_block returns false).
 //
 // Exact scaling in FP32: 2^s with |s| up to 156 is not a float, so it is
 // applied as two factors 2^(s/2) and 2^(s - s/2), each a normal float.
@@ -41,8 +42,10 @@ OOCS_FN float scale2(float v, int s)
 }
 
 // Emit(i, word) receives the 2*rate words in order i = 0 .. 2*rate-1.
+// Returns false for a block holding an infinity or a NaN, which is written as
+// an all-zero block (the same rule as the transform codec).
 template <class Emit>
-OOCS_FN void bq_encode_block(const float (&v)[64], int rate, Emit &&emit)
+OOCS_FN bool bq_encode_block(const float (&v)[64], int rate, Emit &&emit)
 {
     uint32_t mbits = 0;
 #pragma unroll
@@ -51,11 +54,11 @@ OOCS_FN void bq_encode_block(const float (&v)[64], int rate, Emit &&emit)
         mbits = a > mbits ? a : mbits;
     }
     const int nw = 2 * rate;
-    if (mbits == 0) {
+    if (mbits == 0 || mbits >= 0x7f800000u) {
 #pragma unroll 1
         for (int i = 0; i < nw; ++i)
             emit(i, 0u);
-        return;
+        return mbits == 0;
     }
     // biased exponent E of max|v|: frexp exponent E - 126 (normal), clamped to -126
     const int be = (int)(mbits >> 23);
@@ -84,6 +87,7 @@ OOCS_FN void bq_encode_block(const float (&v)[64], int rate, Emit &&emit)
 #pragma unroll 1
     for (; wi < nw; ++wi)
         emit(wi, 0u);
+    return true;
 }
 
 // Read(i) returns word i (i < 2*rate).

@@ -11,11 +11,14 @@
 
 namespace oocs {
 
-// device error word: 0 = fine, else the code of the first failure seen
+// device error word: 0 = fine, else the OR of the flags of the failures seen
 // (this header is included by one translation unit, which owns the word)
 __device__ unsigned int g_device_error = 0u;
 
-enum : unsigned int { kErrWaitTimeout = 1u };
+enum : unsigned int {
+    kErrWaitTimeout = 1u,  // a bounded wait ran out (OOCS_DEVERR_WAIT_TIMEOUT)
+    kErrNonFinite = 2u,    // the encoder met an infinity or a NaN (OOCS_DEVERR_NONFINITE)
+};
 
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 
@@ -77,7 +80,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
         if (mbar_try_wait(bar, parity))
             return true;
         if (global_ns() - t0 > kWaitLimitNs) {
-            atomicCAS(&g_device_error, 0u, kErrWaitTimeout);
+            atomicOr(&g_device_error, kErrWaitTimeout);
             return false;
         }
     }

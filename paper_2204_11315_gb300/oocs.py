@@ -21,7 +21,9 @@ from . import build as _build
 OOCS_OK = 0
 STATUS_NAMES = {0: "OOCS_OK", 1: "OOCS_ERR_INVALID_ARG", 2: "OOCS_ERR_BUDGET",
                 3: "OOCS_ERR_HOST_ALLOC", 4: "OOCS_ERR_CUDA", 5: "OOCS_ERR_TIMEOUT",
-                6: "OOCS_ERR_STATE", 7: "OOCS_ERR_UNSUPPORTED"}
+                6: "OOCS_ERR_STATE", 7: "OOCS_ERR_UNSUPPORTED", 8: "OOCS_ERR_NONFINITE"}
+OOCS_ERR_TIMEOUT, OOCS_ERR_NONFINITE = 5, 8
+OOCS_DEVERR_WAIT_TIMEOUT, OOCS_DEVERR_NONFINITE = 1, 2
 OOCS_HEAT, OOCS_WAVE, OOCS_WAVE_ADJOINT = 0, 1, 2
 OOCS_CODEC_TRANSFORM, OOCS_CODEC_QUANT = 0, 1
 OOCS_FIELD_U, OOCS_FIELD_U_PREV, OOCS_FIELD_M = 0, 1, 2
@@ -152,6 +154,8 @@ SIGNATURES = {
     "oocs_set_receiver": (_i32, [_vp, _i64, _vp, _i64]),
     "oocs_set_state_record": (_i32, [_vp, ctypes.POINTER(_vp), _i64, _i64]),
     "oocs_selftest_stuck_wait": (_i32, [_vp]),
+    "oocs_device_errors": (_i32, [ctypes.POINTER(ctypes.c_uint32), _i32]),
+    "oocs_set_fault_injection": (_i32, [_vp, _i64]),
     "oocs_compress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
     "oocs_decompress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
     "oocs_host_alloc": (_i32, [_u64, ctypes.POINTER(_vp)]),
@@ -426,6 +430,17 @@ def oocs_set_receiver(ctx, zr, planes_ptr, nplanes):
 
 def oocs_selftest_stuck_wait(ctx):
     _check(lib().oocs_selftest_stuck_wait(_vp(ctx)), ctx)
+
+
+def oocs_set_fault_injection(ctx, nth_call):
+    _check(lib().oocs_set_fault_injection(_vp(ctx), int(nth_call)), ctx)
+
+
+def oocs_device_errors(clear=True) -> int:
+    """OOCS_DEVERR_* flags of the current device's error word (synchronises the device)."""
+    f = ctypes.c_uint32()
+    _check(lib().oocs_device_errors(ctypes.byref(f), 1 if clear else 0))
+    return int(f.value)
 
 
 def oocs_set_state_record(ctx, store_ptrs, t0=0):

@@ -2,7 +2,7 @@
 
 FP32 GPU arithmetic against FP64: relative L2 within 1e-6 (heat) and 1e-5
 (wave), the uncompressed bars.  Grids with x-y sizes that are not multiples of
-the 32 x 16 CTA tile exercise the ragged tail.
+the 64 x 16 CTA tile exercise the ragged tail.
 """
 import math
 

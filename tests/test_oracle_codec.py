@@ -226,3 +226,30 @@ def test_block_layout_in_field(orc):
         blk = f[4 * bz:4 * bz + 4, 4 * by:4 * by + 4, 4 * bx:4 * bx + 4].reshape(64)
         off = ((bz * 3 + by) * 4 + bx) * 2 * rate
         assert np.array_equal(words[off:off + 2 * rate], orc.encode_block(blk, rate))
+
+
+@pytest.mark.parametrize("bad", [np.inf, -np.inf, np.nan])
+def test_nonfinite_block_is_stored_as_zeros_and_reported(orc, bad):
+    """The codec is defined for finite values; a block holding an Inf or a NaN
+    is written as an all-zero block and reported, by both codecs, and the other
+    blocks of a field are coded as if it were not there."""
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(64).astype(np.float32)
+    clean = orc.encode_block(v, 16)
+    v[37] = bad
+    for enc in (orc.encode_block, orc.bq_encode_block):
+        words, flagged = enc(v, 16, with_flag=True)
+        assert flagged and not words.any()
+    assert not orc.encode_block(np.ones(64, np.float32), 16, with_flag=True)[1]
+    f = rng.standard_normal((8, 8, 8)).astype(np.float32)
+    ref = orc.encode_field(f, 12).reshape(8, 24)
+    f[5, 1, 6] = bad  # block (bx, by, bz) = (1, 0, 1): index 5
+    for enc in (orc.encode_field, orc.bq_encode_field):
+        got, n = enc(f, 12, with_nonfinite=True)
+        assert n == 1
+        got = got.reshape(8, 24)
+        assert not got[5].any()
+    got = orc.encode_field(f, 12).reshape(8, 24)
+    keep = [b for b in range(8) if b != 5]
+    assert np.array_equal(got[keep], ref[keep])
+    assert clean.any()
