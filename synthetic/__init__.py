@@ -189,13 +189,26 @@ def blocks_field(shape, seed: int, kind: str) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
-# Accuracy bar of each workload (relative L2 error against the FP64 oracle),
-# fixed before any timed run.  Uncompressed FP32 runs: 1e-6 (heat), 1e-5
-# (wave).  Compressed: per codec rate in bits/value.
+# Accuracy bars of each workload against the FP64 oracle, fixed before any
+# timed run.
+#
+# Relative L2 error ||got - ref|| / ||ref||: uncompressed FP32 runs 1e-6
+# (heat), 1e-5 (wave); compressed, per codec rate in bits/value.
+#
+# Max-abs error, point by point, against the field's peak:
+# max |got - ref| <= bar * max |ref|, with each bar ten times the rel-L2 bar of
+# the same run.  An error confined to a few points (a wrong halo plane at a
+# slab seam, a source or receiver in the wrong slab) is of the order of the
+# field itself there and fails it, while it can pass a global L2 norm; spread
+# codec or rounding error stays well inside it.  Single kernels (one adjoint or
+# gradient step in FP32): 1e-6 and 1e-5.
 # ----------------------------------------------------------------------------
 
 TOL_UNCOMPRESSED = {"heat": 1e-6, "wave": 1e-5}
 TOL_COMPRESSED = {16: 1e-4, 12: 2e-3, 8: 3e-2}
+TOL_MAXABS_UNCOMPRESSED = {"heat": 1e-5, "wave": 1e-4}
+TOL_MAXABS_COMPRESSED = {16: 1e-3, 12: 2e-2, 8: 3e-1}
+TOL_KERNEL, TOL_MAXABS_KERNEL = 1e-6, 1e-5
 
 
 # ----------------------------------------------------------------------------

@@ -74,3 +74,35 @@ def rel_l2(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def max_abs_rel(a, b):
+    """max |a - b| over max |b|: the largest pointwise error against the field's peak."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def assert_parity(got, ref, l2_bar, maxabs_bar, what=""):
+    """Relative L2 error within l2_bar and, element by element,
+    |got - ref| <= maxabs_bar * max |ref| (the worst point is named on failure)."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    assert got.shape == ref.shape, (got.shape, ref.shape)
+    e2 = rel_l2(got, ref)
+    peak = float(np.max(np.abs(ref)))
+    err = np.abs(got - ref)
+    worst = np.unravel_index(int(np.argmax(err)), err.shape)
+    ok = err <= maxabs_bar * peak
+    assert e2 <= l2_bar and bool(np.all(ok)), (
+        f"{what}: rel-L2 {e2:.3e} (bar {l2_bar:.1e}); max-abs {err[worst]:.3e} = "
+        f"{err[worst] / peak:.3e} of the peak {peak:.3e} at {tuple(int(i) for i in worst)} "
+        f"(bar {maxabs_bar:.1e}); {int(np.size(ok) - np.count_nonzero(ok))} points over")
+
+
+def assert_uncompressed(got, ref, scheme, what=""):
+    assert_parity(got, ref, synthetic.TOL_UNCOMPRESSED[scheme], synthetic.TOL_MAXABS_UNCOMPRESSED[scheme], what)
+
+
+def assert_compressed(got, ref, rate, what=""):
+    assert_parity(got, ref, synthetic.TOL_COMPRESSED[rate], synthetic.TOL_MAXABS_COMPRESSED[rate], what)

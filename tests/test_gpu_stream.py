@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import synthetic
-from gpu_util import heat_desc, incore, rel_l2, streamed, wave_desc
+from gpu_util import assert_compressed, heat_desc, incore, streamed, wave_desc
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +56,7 @@ def test_heat_compressed_within_tolerance(P, orc, rate):
     desc = heat_desc(P, u0.shape, rate=rate, k=1, T=32)
     got, _, stores, stats, plan = streamed(P, desc, u0, 10)
     ref = orc.heat_run(u0, synthetic.heat_star_coef(0.1), 10)
-    assert rel_l2(got, ref) <= synthetic.TOL_COMPRESSED[rate]
+    assert_compressed(got, ref, rate, f"heat rate {rate}")
     # fixed rate: exactly rate bits per value in the store and over the link
     assert plan.host_store_bytes == u0.size * rate // 8
     assert stats["h2d_bytes"] == 10 * plan.host_store_bytes
@@ -127,8 +127,8 @@ def test_wave_compressed_within_tolerance(P, orc, rate):
     gu, gup, _, _, _ = streamed(P, desc, z, steps, up0=z, m=m, src=src, w=w)
     ru, rup = orc.wave_run(z, z, m, synthetic.wave_star_coef(), steps,
                            src=synthetic.centre(shape), w=w)
-    assert rel_l2(gu, ru) <= synthetic.TOL_COMPRESSED[rate]
-    assert rel_l2(gup, rup) <= synthetic.TOL_COMPRESSED[rate]
+    assert_compressed(gu, ru, rate, f"wave u rate {rate}")
+    assert_compressed(gup, rup, rate, f"wave u_prev rate {rate}")
 
 
 @pytest.mark.parametrize("rate,wb", [(0, 1), (16, 1), (12, 3)])
@@ -212,5 +212,5 @@ def test_wave_benchmark_plan_within_tolerance_of_oracle(P, orc):
     gu, gup, _, stats, plan = streamed(P, desc, z, steps, up0=z, m=m, src=src, w=w)
     assert plan.num_slabs == 8 and plan.readonly_resident == 1 and plan.workspace_bytes <= 4 << 30
     ru, rup = orc.wave_run(z, z, m, synthetic.wave_star_coef(), steps, src=synthetic.centre(shape), w=w)
-    assert rel_l2(gu, ru) <= synthetic.TOL_COMPRESSED[16]
-    assert rel_l2(gup, rup) <= synthetic.TOL_COMPRESSED[16]
+    assert_compressed(gu, ru, 16, "512^3 wave u")
+    assert_compressed(gup, rup, 16, "512^3 wave u_prev")

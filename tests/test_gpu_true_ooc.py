@@ -7,7 +7,8 @@ Full-size parity on sampled outputs: after n steps a point depends only on the
 initial values within distance n, so the FP64 oracle run on the (2n+1)^3 cube
 around a sample (its faces held, which the centre cannot see within n steps)
 gives that point's exact value; 8 seeded samples are compared with the
-decompressed GPU values within the rate-16 bar.
+decompressed GPU values: each within the rate-16 max-abs bar, and all eight
+within the rate-16 rel-L2 bar.
 """
 import numpy as np
 import pytest
@@ -65,7 +66,14 @@ def test_true_out_of_core_heat_sampled_against_oracle(orc):
         st.close()
         host.close()
         torch.cuda.empty_cache()
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
     assert rel_l2(got, ref) <= synthetic.TOL_COMPRESSED[16]
+    # each sample on its own: |got - ref| within the rate-16 max-abs bar of the
+    # largest sampled value (at most the field's peak, so no looser than the
+    # bar against the peak)
+    bound = synthetic.TOL_MAXABS_COMPRESSED[16] * float(np.max(np.abs(ref)))
+    for i, (g, r) in enumerate(zip(got, ref)):
+        assert abs(g - r) <= bound, (i, samples[i], g, r, bound)
 
 
 def test_cube_reading_is_exact(orc):

@@ -89,3 +89,53 @@ def test_noalloc_rejects_grids_above_the_maximum(P):
     P.oocs_incore_run_noalloc(ok, u.data_ptr(), 0, 0, 1,
                               stream=torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
+
+
+def test_noalloc_and_incore_from_two_host_threads(P):
+    """oocs_incore_run and oocs_incore_run_noalloc called at the same time from
+    two host threads, each on its own stream: the per-device caches (the step
+    kernel's shared-memory opt-in, the scratch address) are taken under their
+    locks, only the no-allocation call uses the library's array, and both
+    results equal the same runs made one after the other."""
+    import threading
+    torch = torch_cuda()
+    u0 = synthetic.heat_initial(128)
+    d_heat = heat_desc(P, u0.shape)
+    ref = _run(P, d_heat, u0, 10, noalloc=False)
+    shape = (96, 80, 112)
+    m = synthetic.wave_model(shape)
+    z = np.zeros(shape, np.float32)
+    d_wave = wave_desc(P, shape)
+    ref_w = _run(P, d_wave, z + 1e-3, 6, noalloc=False, up0=z, m=m)
+
+    results, errors = {}, []
+
+    def worker(name, desc, fields, nsteps, noalloc):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                dev = [torch.from_numpy(np.ascontiguousarray(f, np.float32)).cuda() for f in fields]
+                wave = desc.scheme == P.OOCS_WAVE
+                ptrs = [dev[0].data_ptr(), dev[1].data_ptr() if wave else 0, dev[2].data_ptr() if wave else 0]
+                for _ in range(3):
+                    for t, f in zip(dev, fields):
+                        t.copy_(torch.from_numpy(np.ascontiguousarray(f, np.float32)))
+                    if noalloc:
+                        P.oocs_incore_run_noalloc(desc, *ptrs, nsteps, stream=s.cuda_stream)
+                    else:
+                        scratch = torch.empty_like(dev[0])
+                        P.oocs_incore_run(desc, *ptrs, scratch.data_ptr(), nsteps, stream=s.cuda_stream)
+                s.synchronize()
+                results[name] = tuple(t.cpu().numpy() for t in dev[:2 if wave else 1])
+        except Exception as e:  # reported by the main thread
+            errors.append(e)
+
+    th = [threading.Thread(target=worker, args=("heat_noalloc", d_heat, [u0], 10, True)),
+          threading.Thread(target=worker, args=("wave_incore", d_wave, [z + 1e-3, z, m], 6, False))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
+    assert _same(results["heat_noalloc"], ref)
+    assert _same(results["wave_incore"], ref_w)
