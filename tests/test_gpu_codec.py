@@ -99,3 +99,26 @@ def test_argument_errors(P):
         P.oocs_encode_device(buf.data_ptr(), 4, 4, 4, 33, buf.data_ptr())
     with pytest.raises(P.OOCSError):
         P.oocs_decode_device(buf.data_ptr() + 4, 4, 4, 4, 8, buf.data_ptr())
+
+
+@pytest.mark.parametrize("rate", [16, 8, 1])
+def test_worked_block_on_the_gpu(P, rate):
+    """The block worked by hand in tests/golden/xform_block_rate16.txt, encoded
+    by the GPU kernel: exactly the hand-derived words (and decoded back exactly
+    where the whole stream fits)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "xform_block_rate16.txt")
+    rows = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            key, *vals = line.split()
+            rows[key] = vals
+    f, g, h = ([int(x) for x in rows[k]] for k in ("f", "g", "h"))
+    blk = np.array([[[f[i] * g[j] * h[k] / 64.0 for i in range(4)] for j in range(4)] for k in range(4)],
+                   np.float32)
+    bits = "".join(rows["bits"]).ljust(64 * rate, "0")[:64 * rate]
+    want = np.array([int(bits[32 * i:32 * i + 32][::-1], 2) for i in range(2 * rate)], np.uint32)
+    got = gpu_encode(P, blk, rate)
+    assert np.array_equal(got, want)
+    if rate >= 8:
+        assert np.array_equal(gpu_decode(P, want, blk.shape, rate), blk)

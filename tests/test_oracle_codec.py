@@ -8,6 +8,7 @@ digit expansions, lossless and embedded (prefix) bit-plane coding, and a
 per-block error bound derived from the stages.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -253,3 +254,77 @@ def test_nonfinite_block_is_stored_as_zeros_and_reported(orc, bad):
     keep = [b for b in range(8) if b != 5]
     assert np.array_equal(got[keep], ref[keep])
     assert clean.any()
+
+
+# ---------------------------------------------------------------------------
+# A block worked by hand (tests/golden/xform_block_rate16.txt): pins every
+# stage, the sequency tie-break and the group-test rule of the bitstream
+# ---------------------------------------------------------------------------
+
+XGOLDEN = os.path.join(os.path.dirname(__file__), "golden", "xform_block_rate16.txt")
+
+
+def _xgolden():
+    rows = {}
+    for line in open(XGOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        key, *vals = line.split()
+        rows[key] = vals
+    return rows
+
+
+def _xgolden_block(g):
+    f, gg, h = ([int(x) for x in g[k]] for k in ("f", "g", "h"))
+    v = np.zeros(64, np.float32)
+    for k in range(4):
+        for j in range(4):
+            for i in range(4):
+                v[i + 4 * j + 16 * k] = f[i] * gg[j] * h[k] / 64.0
+    return v, f, gg, h
+
+
+def test_worked_transform_block_stages(orc):
+    g = _xgolden()
+    v, f, gg, h = _xgolden_block(g)
+    assert orc.block_header(v) == int(g["header"][0])
+    emax = int(g["header"][0]) - 127
+    q = orc.quantize(v, emax)
+    assert [int(x) for x in q] == [f[i % 4] * gg[(i // 4) % 4] * h[i // 16] * 2 ** 22 for i in range(64)]
+    c = orc.fwd_xform(q)
+    want = np.zeros(64, np.int64)
+    for item in g["coef"]:
+        idx, val = item.split(":")
+        want[int(idx)] = int(val)
+    assert np.array_equal(np.asarray(c, np.int64), want)
+    order = [int(x) for x in g["order"]]
+    assert sorted(order) == list(range(64))
+    assert list(orc.sequency_order()) == order
+    nb = np.zeros(64, np.uint32)
+    for item in g["negabinary"]:
+        pos, val = item.split(":")
+        nb[int(pos)] = int(val, 16)
+    assert np.array_equal(np.array([orc.to_negabinary(int(c[order[n]])) for n in range(64)], np.uint32), nb)
+
+
+def _pack_bits(bitstring, nwords):
+    bits = bitstring.ljust(32 * nwords, "0")[:32 * nwords]
+    return np.array([int(bits[32 * i:32 * i + 32][::-1], 2) for i in range(nwords)], np.uint32)
+
+
+@pytest.mark.parametrize("rate", [16, 8, 1])
+def test_worked_transform_block_bitstream(orc, rate):
+    """The header bits (LSB first), the five empty planes, planes 26 and 25
+    with their group tests, the verbatim planes 24 and 23, then zeros; cut at
+    exactly 64 rate bits."""
+    g = _xgolden()
+    v, _, _, _ = _xgolden_block(g)
+    bitstring = "".join(g["bits"])
+    assert bitstring[:8] == format(int(g["header"][0]), "08b")[::-1]
+    assert len(bitstring) == 8 + 5 + 7 + 24 + 22 + 22
+    want = _pack_bits(bitstring, 2 * rate)
+    assert np.array_equal(want[:3], np.array([int(w, 16) for w in g["words"]], np.uint32)[:2 * rate])
+    assert np.array_equal(orc.encode_block(v, rate), want)
+    if rate >= 8:  # everything significant fits: lossless
+        back, low = orc.decode_block(want, rate)
+        assert np.array_equal(back, v)
