@@ -226,11 +226,18 @@ oocs_status oocs_set_state_record(oocs_ctx *ctx, void *const *stores, int64_t t0
 /* Fill the bound store of `field` from a raw FP32 host array of nx*ny*nz
  * values (initial compression of the chunks, Algorithm 1 input (1)): copies
  * go through the workspace and the codec kernels, using streams[0..1].
- * Asynchronous: `src` must stay valid until oocs_synchronize.              */
+ * Asynchronous: `src` must stay valid until oocs_synchronize.
+ * In place: the store may be the first host_store_bytes of `src` itself (the
+ * compressed layers of planes [z0, z1) never lie above the raw planes
+ * [z0, z1), and the chunks are ordered so that nothing is overwritten before
+ * it is read), so a field that fills most of host memory needs no second
+ * array.  Any other overlap of the store and `src` is OOCS_ERR_INVALID_ARG. */
 oocs_status oocs_compress(oocs_ctx *ctx, int32_t field, const float *src);
 
 /* Inverse of oocs_compress: decode the bound store of `field` into the raw
- * FP32 host array `dst` of nx*ny*nz values.  Asynchronous.                 */
+ * FP32 host array `dst` of nx*ny*nz values.  Asynchronous.  In place as for
+ * oocs_compress: the store may start at `dst` (the array then holds the
+ * decoded field, the store is consumed).                                   */
 oocs_status oocs_decompress(oocs_ctx *ctx, int32_t field, float *dst);
 
 /* Planes [z0, z0 + nplanes) (whole 4-plane layers) of `field` between a

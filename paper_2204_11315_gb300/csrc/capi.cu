@@ -327,6 +327,7 @@ struct oocs_ctx {
     int64_t srec_t0 = 0;
 
     cudaEvent_t ev_decoded[3] = {}, ev_h2d[3] = {}, ev_wrel[3] = {}, ev_join[3] = {};
+    cudaEvent_t ev_codec[2] = {};  // oocs_compress / oocs_decompress: a chunk's raw copy has run
     std::vector<cudaEvent_t> ev_d2h;
     std::vector<char> d2h_recorded;
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
@@ -1172,6 +1173,8 @@ oocs_status oocs_create(const oocs_desc *desc, void *workspace, uint64_t workspa
     }
     for (int i = 0; i < nd2h && e == cudaSuccess; ++i)
         e = mk(&c->ev_d2h[i]);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = mk(&c->ev_codec[i]);
     if (e == cudaSuccess)
         e = cudaEventCreate(&c->ev_t0);
     if (e == cudaSuccess)
@@ -1278,10 +1281,22 @@ static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, f
         return fail(ctx, OOCS_ERR_STATE, "field is not bound");
     if (enc ? !src : !dst)
         return fail(ctx, OOCS_ERR_INVALID_ARG, "raw host array is NULL");
-    if (enc && field == OOCS_FIELD_M)
-        ctx->ro_dirty = true;
     const oocs_desc &d = ctx->d;
     const uint64_t plane_bytes = (uint64_t)d.nx * d.ny * 4;
+    // the store may share memory with the raw array only in place: starting at
+    // its first byte (the compressed layers of planes [z0, z1) then lie at or
+    // below the raw planes [z0, z1), see the chunk order below)
+    {
+        const uintptr_t r0 = reinterpret_cast<uintptr_t>(enc ? (const void *)src : (const void *)dst);
+        const uintptr_t r1 = r0 + (uintptr_t)d.nz * plane_bytes;
+        const uintptr_t s0 = reinterpret_cast<uintptr_t>(ctx->store[field]);
+        const uintptr_t s1 = s0 + (uintptr_t)ctx->p.host_store_bytes;
+        if (s0 < r1 && r0 < s1 && s0 != r0)
+            return fail(ctx, OOCS_ERR_INVALID_ARG,
+                        "the store overlaps the raw array without starting at its address (only in place is allowed)");
+    }
+    if (enc && field == OOCS_FIELD_M)
+        ctx->ro_dirty = true;
     // a resident M is decoded from each chunk's blocks while they are on the
     // device (the values the store decodes to), so no step has to upload it
     const bool ro_keep = enc && field == OOCS_FIELD_M && ctx->v.ro_res && d.rate_bits > 0;
@@ -1297,10 +1312,17 @@ static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, f
         return join_streams(ctx);
     }
     // chunks of T planes through working buffer 0's first two buffers and
-    // out slots 0 / 1 of field 0, alternating between streams 0 and 1
+    // out slots 0 / 1 of field 0, alternating between streams 0 and 1.
+    // Compression walks the chunks upwards in z, decompression downwards, and
+    // a chunk's device->host copy waits until the previous chunk (on the other
+    // stream) has read its host bytes: then a store that lives in place in the
+    // raw array (compressed layers of planes [z0, z1) at or below the raw
+    // planes [z0, z1)) is never overwritten before it is read, and never
+    // overwrites raw planes still to be read.
     const int64_t T = ctx->v.T;
-    int64_t chunk = 0;
-    for (int64_t z0 = 0; z0 < d.nz; z0 += T, ++chunk) {
+    const int64_t nchunks = ceil_div(d.nz, T);
+    for (int64_t chunk = 0; chunk < nchunks; ++chunk) {
+        const int64_t z0 = (enc ? chunk : nchunks - 1 - chunk) * T;
         const int64_t z1 = std::min<int64_t>(z0 + T, d.nz);
         const int i = (int)(chunk & 1);
         cudaStream_t st = ctx->st[i];
@@ -1311,14 +1333,20 @@ static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, f
         if (enc) {
             CU(ctx, cudaMemcpyAsync(raw, src + z0 * d.nx * d.ny, (z1 - z0) * plane_bytes,
                                     cudaMemcpyHostToDevice, st));
+            CU(ctx, cudaEventRecord(ctx->ev_codec[i], st));
             CU(ctx, launch_encode_layers(raw, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, d.codec, blk, st));
+            if (chunk > 0)
+                CU(ctx, cudaStreamWaitEvent(st, ctx->ev_codec[i ^ 1], 0));
             CU(ctx, cudaMemcpyAsync(host_blk, blk, cbytes, cudaMemcpyDeviceToHost, st));
             if (ro_keep)
                 CU(ctx, launch_decode_layers(blk, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, d.codec,
                                              ctx->ro_m() + z0 * d.nx * d.ny, st));
         } else {
             CU(ctx, cudaMemcpyAsync(blk, host_blk, cbytes, cudaMemcpyHostToDevice, st));
+            CU(ctx, cudaEventRecord(ctx->ev_codec[i], st));
             CU(ctx, launch_decode_layers(blk, d.nx, d.ny, (z1 - z0) / 4, d.rate_bits, d.codec, raw, st));
+            if (chunk > 0)
+                CU(ctx, cudaStreamWaitEvent(st, ctx->ev_codec[i ^ 1], 0));
             CU(ctx, cudaMemcpyAsync(dst + z0 * d.nx * d.ny, raw, (z1 - z0) * plane_bytes,
                                     cudaMemcpyDeviceToHost, st));
         }
@@ -1722,6 +1750,8 @@ static void destroy_ctx(oocs_ctx *ctx)
         }
     for (auto &e : ctx->ev_d2h)
         kill(e);
+    kill(ctx->ev_codec[0]);
+    kill(ctx->ev_codec[1]);
     for (auto &e : ctx->ev_pool)
         kill(e);
     kill(ctx->ev_t0);
@@ -1982,6 +2012,8 @@ oocs_status batch_build(oocs_batch *b, const std::vector<oocs_desc> &d, const st
         cudaError_t e = cudaSuccess;
         for (int k = 0; k < c->v.S && e == cudaSuccess; ++k)
             e = cudaEventCreateWithFlags(&c->ev_d2h[k], cudaEventDisableTiming);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&c->ev_codec[k], cudaEventDisableTiming);
         if (e == cudaSuccess)
             e = cudaEventCreate(&c->ev_t0);
         if (e == cudaSuccess)

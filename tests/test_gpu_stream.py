@@ -214,3 +214,42 @@ def test_wave_benchmark_plan_within_tolerance_of_oracle(P, orc):
     ru, rup = orc.wave_run(z, z, m, synthetic.wave_star_coef(), steps, src=synthetic.centre(shape), w=w)
     assert_compressed(gu, ru, 16, "512^3 wave u")
     assert_compressed(gup, rup, 16, "512^3 wave u_prev")
+
+
+@pytest.mark.parametrize("rate", [16, 8, 32])
+def test_compress_and_decompress_in_place(P, orc, rate):
+    """The store living in the first bytes of the raw FP32 array itself (a field
+    that fills host memory needs no second array): oocs_compress writes the
+    oracle codec's bytes, the sweep runs on them, and oocs_decompress returns
+    the same values as with separate arrays, over eight chunks on two streams."""
+    import torch
+    u0 = synthetic.heat_initial(128)
+    desc = heat_desc(P, u0.shape, rate=rate, k=2, T=16)
+    ref, _, ref_stores, _, _ = streamed(P, desc, u0, 6)
+    buf = torch.empty(u0.size * 4, dtype=torch.uint8, pin_memory=True)
+    raw = buf.view(torch.float32).reshape(u0.shape)
+    raw.numpy()[...] = u0
+    st = P.OutOfCoreStencil(desc, stores=[buf])
+    try:
+        assert st.stores[0].data_ptr() == raw.data_ptr()
+        st.compress(P.OOCS_FIELD_U, raw)
+        st.synchronize(60.0)
+        assert np.array_equal(buf[:st.plan.host_store_bytes].numpy().view(np.uint32), orc.encode_field(u0, rate))
+        st.step(6)
+        st.synchronize(60.0)
+        assert np.array_equal(buf[:st.plan.host_store_bytes].numpy(), ref_stores[0])
+        st.decompress(P.OOCS_FIELD_U, raw)
+        st.synchronize(60.0)
+        assert np.array_equal(raw.numpy().view(np.uint32), ref.view(np.uint32))
+    finally:
+        st.close()
+    if rate == 32:  # the store is the whole array: no room for an offset store
+        return
+    # an overlap that does not start at the array's address is refused
+    st = P.OutOfCoreStencil(desc, stores=[buf[4096:]])
+    try:
+        with pytest.raises(P.OOCSError) as e:
+            st.compress(P.OOCS_FIELD_U, raw)
+        assert e.value.status == 1 and "in place" in str(e.value)
+    finally:
+        st.close()
