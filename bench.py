@@ -1,30 +1,37 @@
 #!/usr/bin/env python
 """Benchmark of the compressed out-of-core stencil sweep on one GB300 per rank.
 
-Workload (the metric's configuration): 25-point 8th-order acoustic wave
-(leapfrog), FP32, 512^3 grid, dx = 10 m, dt = 0.8 ms, seeded 8-layer velocity
-model 1500-4500 m/s with +-5 % noise, 15 Hz Ricker source at the centre,
-device budget 4 GiB, 8 z-slabs of 64 planes, temporal blocking depth k = 4,
-fixed-rate codec at 16 bits/value, single working buffer (Sec. 5).  The
-read-only model m is kept on the device (decoded once from its rate-16 store,
-inside the budget), so u and u_prev stream; ``compare`` also times the
-paper's dataflow, which streams m with every slab visit.
+Headline workload (the largest configuration that runs on one GPU, out of
+core): 7-point heat (Jacobi) stencil, FP32, 2560 x 2560 x 5120 grid (one field
+of 134 GB), seeded U[0,1) field, alpha = 0.1, 20 time steps in 5 sweeps of
+temporal depth k = 4 over 42 z-slabs, a 16 GiB device budget, the fixed-rate
+codec at 16 bits/value, one working buffer (Sec. 5).  The field's compressed
+store (67 GB) is pinned host memory: the first half of the 134 GB raw FP32
+array that the e2e leg reads and writes in place.
 
-One bench step = one oocs_step(100) from rest (the host stores are reset to
-the compressed initial state and the time index to 0 before each, untimed):
-100 time steps = 25 sweeps over the 8 slabs, every slab's u and u_prev
-streamed host->GPU, decoded, advanced 4 steps, encoded and streamed back.  ``value`` = interior point-updates / s (Gpoint-updates/s) with
-the fields already in the compressed host store (pinned host memory: where
-the method keeps them); ``e2e`` adds the conversion from and to raw FP32 host
-arrays through oocs_compress / oocs_decompress.
+One bench step = one oocs_step(20) from the seeded initial state (the store is
+refilled before each, untimed: planes drawn on the GPU and compressed by
+oocs_compress_device).  ``value`` = interior point-updates/s with the field in
+its compressed host store, where the method keeps it (the device holds only
+the 16 GiB working set: every slab crosses the host link twice per sweep);
+``e2e`` = the same 20 steps from and to the raw FP32 host array,
+oocs_compress (in place) + oocs_step(20) + oocs_decompress (in place), every
+byte of which crosses the host link inside the timed region.
+
+Further sections (one GPU only): the uncompressed streaming of the same grid,
+accuracy against the FP64 oracle on seeded dependency cubes (the same oracle
+run is the CPU baseline), the 512^3 acoustic wave workload (model resident and
+streamed, the previous headline), the adjoint, the batched workload and the
+codec comparison.
 
 --impl reference times the CPU oracle (FP64, OpenMP on the host cores) on a
-bounded sample of the same workload.  Multi-GPU: independent replicas, one per
-rank (the method is single-GPU; no collective on the data path).
+bounded sample of the headline workload.  Multi-GPU: independent replicas, one
+per rank (the method is single-GPU; no collective on the data path).
 """
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import subprocess
@@ -38,6 +45,24 @@ if ROOT not in sys.path:
 
 METRIC = "out-of-core Gpoint-updates/s at stated max error; % of HBM/host-link roofline"
 UNIT = "Gpoint-updates/s"
+
+# ---- headline: the true out-of-core heat workload
+OOC_SHAPE = (5120, 2560, 2560)          # (nz, ny, nx)
+OOC_STEPS, OOC_K, OOC_BUDGET, OOC_SEED, OOC_RATE, OOC_ALPHA = 20, 4, 16 << 30, 31, 16, 0.1
+HEAT_BYTES_PER_POINT = 8                # read u, write u' (FP32)
+WORKLOAD = "heat7_2560x2560x5120_20steps_k4_rate16_budget16GiB_swb"
+# DRAM bytes (read + write) per window point of the heat step kernel from one
+# ncu capture of a 2560 x 2560 launch; scaled to a launch by its points.  None
+# until measured, and set to None whenever the kernel changes.
+HEAT_STEP_TRAFFIC_B_PER_POINT = None
+# FP64 oracle on dependency cubes: a point after 20 heat steps depends only on
+# the initial values within 20 planes, so the oracle on a cube of side
+# CUBE_IN + 2 CUBE_HALO gives exact values on its central CUBE_IN^3 points
+CUBE_IN, CUBE_HALO = 96, OOC_STEPS
+CUBES_BASELINE = 32                     # the CPU baseline and accuracy sample
+CUBES_PER_REF_STEP = 3                  # one step of the reference arm
+
+# ---- secondary: the 512^3 acoustic wave workload
 N = 512
 STEPS_PER_CALL = 100
 K_DEPTH = 4
@@ -46,7 +71,7 @@ BUDGET = 4 << 30
 RATE = 16
 RO_RESIDENT = 1  # keep m on the device (oocs_desc.readonly_resident)
 WAVE_BYTES_PER_POINT = 16  # read u, u_prev, m; write u_next (FP32)
-WORKLOAD = "wave25_512cubed_100steps_8slabs_k4_rate16_swb_m_resident"
+WAVE_WORKLOAD = "wave25_512cubed_100steps_8slabs_k4_rate16_swb_m_resident"
 # DRAM bytes (read + write) per updated point of the wave step kernel from one ncu
 # capture of a 512x512x80 launch, the window size of the sweep's balanced step
 # launches; scaled to a launch by its points.  Set to None whenever the kernel
@@ -60,19 +85,225 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--rate", type=int, default=RATE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-uncompressed", action="store_true")
+    ap.add_argument("--no-wave512", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--no-true-ooc", action="store_true")
-    ap.add_argument("--profile-run", choices=["sweep", "kernels"], default=None,
+    ap.add_argument("--planes", type=int, default=0,
+                    help="nz of the headline grid (default: 5120, fewer if host memory is short)")
+    ap.add_argument("--profile-run", choices=["ooc", "sweep", "kernels"], default=None,
                     help="run only the region to capture under ncu --profile-from-start off: "
-                         "'sweep' = one oocs_step(100) of the workload; 'kernels' = one launch each "
-                         "of the wave step, encode and decode kernels on a 512x512x192 grid, then "
-                         "one wave step on a 512x512x80 grid")
+                         "'ooc' = one oocs_step(20) of the headline workload; 'sweep' = one "
+                         "oocs_step(100) of the 512^3 wave workload; 'kernels' = one launch each of "
+                         "the step kernels (heat, wave, adjoint, gradient) and the codec kernels")
     return ap.parse_args()
 
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms; with mark()ed
+    host-time windows, only the samples taken inside a timed call count."""
+
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+        self.windows = []
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def mark(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        parsed = []
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                parsed.append((ts, float(r[2]), float(r[3]), float(r[4]),
+                               [nm for nm, v in zip(names, r[6:10]) if v.lower() == "active"]))
+            except ValueError:
+                continue
+        inside = [p for p in parsed if any(a <= p[0] <= b for a, b in self.windows)]
+        use = inside if inside else parsed
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(p[1] for p in use)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(p[2] for p in use),
+                "reasons": sorted({nm for p in use for nm in p[4]}), "samples": len(use),
+                "samples_in_timed_calls": bool(inside), "power_w_max": max(p[3] for p in use)}
+
+
+def host_mem_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def ooc_planes(args, world):
+    """nz of the headline grid on this rank: 5120, or fewer (a multiple of 64)
+    when the host cannot hold one raw FP32 array per rank."""
+    nz, ny, nx = OOC_SHAPE
+    if args.planes:
+        return args.planes
+    avail = host_mem_available()
+    if avail is None:
+        return nz
+    fit = int(0.9 * avail / world / (ny * nx * 4)) // 64 * 64
+    return max(min(nz, fit), 256)
+
+
+def ooc_desc(P, rate, nz):
+    import synthetic
+    return P.make_desc(OOC_SHAPE[2], OOC_SHAPE[1], nz, P.OOCS_HEAT, synthetic.heat_star_coef(OOC_ALPHA),
+                       OOC_BUDGET, rate_bits=rate, temporal_depth=OOC_K)
+
+
+def ooc_interior(nz):
+    return (OOC_SHAPE[2] - 2) * (OOC_SHAPE[1] - 2) * (nz - 2)
+
+
+def fill_store(P, torch, st, shape, chunk=64):
+    """The seeded U[0,1) field into the context's store: planes drawn on the
+    GPU on the context's stream 0 and coded into their store layers by
+    oocs_compress_device (a copy at rate 0).  Returns seconds."""
+    import synthetic
+    t0 = time.time()
+    with torch.cuda.stream(st.streams[0]):
+        for z0 in range(0, shape[0], chunk):
+            z1 = min(z0 + chunk, shape[0])
+            f = synthetic.uniform_field_planes_torch(shape, OOC_SEED, z0, z1, device=st.device)
+            P.oocs_compress_device(st.ctx, P.OOCS_FIELD_U, f.data_ptr(), z0, z1 - z0)
+            del f
+    st.synchronize(600.0)
+    return time.time() - t0
+
+
+def fill_raw(torch, raw, shape, dev, chunk=64):
+    """The seeded U[0,1) field into a pinned FP32 host array (drawn on the GPU)."""
+    import synthetic
+    for z0 in range(0, shape[0], chunk):
+        z1 = min(z0 + chunk, shape[0])
+        raw[z0:z1].copy_(synthetic.uniform_field_planes_torch(shape, OOC_SEED, z0, z1, device=dev))
+    torch.cuda.synchronize(dev)
+
+
+def timed_call(torch, st, steps, clocks=None):
+    """One oocs_step(steps) bracketed by CUDA events on stream 0 (the context
+    joins its three streams into stream 0 at the start and end of every call)."""
+    s0 = st.streams[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0 = time.time()
+    e0.record(s0)
+    st.step(steps)
+    e1.record(s0)
+    st.synchronize(3600.0)
+    e1.synchronize()
+    if clocks is not None:
+        clocks.mark(h0, time.time())
+    return e0.elapsed_time(e1)
+
+
+def cube_origins(shape, n, seed=32):
+    """n seeded cube centres' corners (z, y, x), multiples of 4, each cube of
+    side CUBE_IN + 2 CUBE_HALO inside the grid, clear of the zero shell."""
+    import synthetic
+    u = synthetic.uniform01(seed, 3 * n).reshape(n, 3)
+    out = []
+    for i in range(n):
+        c = []
+        for a in range(3):
+            lo, hi = CUBE_HALO + 4, shape[a] - CUBE_IN - CUBE_HALO - 4
+            c.append(int(lo + u[i, a] * (hi - lo)) // 4 * 4)
+        out.append(tuple(c))
+    return out
+
+
+def oracle_cube(shape, origin, rate):
+    """The FP64 oracle on one dependency cube of the headline workload: the
+    initial values of a cube of side CUBE_IN + 2 CUBE_HALO, 20 heat steps in 5
+    passes of 4, each pass followed by the reference codec's round trip of
+    the cube at `rate` (the work of one sweep's compression, timed; its result
+    is not fed back, so the stepping stays the exact FP64 reference).  Returns
+    (seconds, exact values on the central CUBE_IN^3 points)."""
+    import numpy as np
+
+    import oracle
+    import synthetic
+    z0, y0, x0 = origin
+    side = CUBE_IN + 2 * CUBE_HALO
+    cube = synthetic.uniform_field_box(shape, OOC_SEED, z0 - CUBE_HALO, y0 - CUBE_HALO, x0 - CUBE_HALO, side)
+    coef = synthetic.heat_star_coef(OOC_ALPHA)
+    t = time.perf_counter()
+    u = cube
+    for _ in range(OOC_STEPS // OOC_K):
+        u = oracle.heat_run(u, coef, OOC_K)
+        oracle.decode_field(oracle.encode_field(u.astype(np.float32), rate), u.shape, rate)
+    dt = time.perf_counter() - t
+    c = slice(CUBE_HALO, CUBE_HALO + CUBE_IN)
+    return dt, u[c, c, c]
+
+
+def oracle_cubes(shape, origins, rate):
+    """Times the oracle over the cubes; returns (seconds, refs, cores)."""
+    import oracle
+    tot, refs = 0.0, []
+    for o in origins:
+        dt, ref = oracle_cube(shape, o, rate)
+        tot += dt
+        refs.append(ref)
+    return tot, refs, oracle.threads()
+
+
+def base_line(args, world, nz):
+    return {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic",
+            "config": {"workload": WORKLOAD if nz == OOC_SHAPE[0] else f"{WORKLOAD}_nz{nz}",
+                       "grid": [OOC_SHAPE[2], OOC_SHAPE[1], nz], "stencil": "7-point star, r=1 (heat, alpha 0.1)",
+                       "time_steps_per_step": OOC_STEPS, "temporal_depth": OOC_K, "rate_bits": OOC_RATE,
+                       "working_buffers": 1, "device_budget_bytes": OOC_BUDGET,
+                       "field_bytes_fp32": OOC_SHAPE[2] * OOC_SHAPE[1] * nz * 4,
+                       "host_store": "pinned host memory, in place in the raw FP32 array",
+                       "l2": "inputs larger than L2 (the field is 134 GB; one slab window 3.5 GB)",
+                       "parallelism": f"replicas{world}"}}
+
+
+# ------------------------------------------------------------ helpers --
 
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
@@ -122,63 +353,6 @@ def interior_points(n=N, r=4):
     return (n - 2 * r) ** 3
 
 
-class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
-
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
-        self.proc = None
-        self.file = None
-
-    def start(self):
-        try:
-            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=self.file, stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
-            self.proc = None
-
-    def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.file.flush()
-        self.file.seek(0)
-        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
-        self.file.close()
-        os.unlink(self.file.name)
-        sm, smax, reasons, power = [], [], set(), []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            r = [x.strip() for x in r]
-            if len(r) < 9:
-                continue
-            try:
-                sm.append(float(r[1]))
-                smax.append(float(r[2]))
-                power.append(float(r[3]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, r[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        srt = sorted(sm)
-        return {"sm_mhz": srt[len(srt) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm), "power_w_max": max(power) if power else None}
-
-
 def link_bandwidth(torch, dev):
     """Pinned host <-> device copy bandwidth (GB/s, best of 5, 1 GiB), each way and both at once."""
     n = 1 << 30
@@ -214,6 +388,322 @@ def link_bandwidth(torch, dev):
     del h1, h2, d1, d2
     return {"h2d_GBs": n / t_h2d / 1e9, "d2h_GBs": n / t_d2h / 1e9,
             "bidir_GBs": 2 * n / t_both / 1e9}
+
+
+
+
+# ----------------------------------------------------------------- ours --
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2204_11315_gb300 as P
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    P.lib()
+    peaks, peak_src = measured_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    link = link_bandwidth(torch, dev)
+    nz = ooc_planes(args, world)
+    shape = (nz, OOC_SHAPE[1], OOC_SHAPE[2])
+    ny, nx = shape[1], shape[2]
+    n_all = nx * ny * nz
+    raw_bytes = n_all * 4
+
+    # the raw FP32 array; the rate-16 store lives in its first half (in place)
+    t0 = time.time()
+    host = P.HostBuffer(raw_bytes)
+    t_pin = time.time() - t0
+    desc16 = ooc_desc(P, OOC_RATE, nz)
+    st = P.OutOfCoreStencil(desc16, stores=[host.tensor()])
+    plan = st.plan
+    t_fill = fill_store(P, torch, st, shape)
+    # live timing of the dominant kernel class only (two event records per visit)
+    st.set_profiling(P.OOCS_PROF_STEP)
+    for _ in range(args.warmup):
+        fill_store(P, torch, st, shape)
+        timed_call(torch, st, OOC_STEPS)
+    before = st.stats()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = 0.0
+    for _ in range(args.steps):
+        fill_store(P, torch, st, shape)  # untimed: the same seeded initial state every step
+        ms += timed_call(torch, st, OOC_STEPS, clocks)
+    clk = clocks.stop()
+    after = st.stats()
+    ms = max_over_ranks(torch, ms, dev)
+    value = replica_throughput(ooc_interior(nz) * OOC_STEPS * args.steps, world, ms)
+    d = {k: after[k] - before[k] for k in ("h2d_bytes", "d2h_bytes", "kernel_launches", "slabs_done",
+                                            "passes_done")}
+    cls = {c: {k: after[c][k] - before[c][k] for k in ("launches", "units", "device_ms")}
+           for c in ("load", "step", "store")}
+    step_bytes = cls["step"]["units"] * HEAT_BYTES_PER_POINT
+    step_gbs = step_bytes / (cls["step"]["device_ms"] / 1e3) / 1e9 if cls["step"]["device_ms"] else None
+    nl = max(cls["step"]["launches"], 1)
+    roofline = {"bound": "hbm", "kernel": "k_star_step<1,heat>", "achieved": step_gbs, "peak": hbm_peak,
+                "unit": "GB/s", "frac": (step_gbs / hbm_peak) if step_gbs else None,
+                "traffic": (HEAT_STEP_TRAFFIC_B_PER_POINT * cls["step"]["units"] / nl
+                            if HEAT_STEP_TRAFFIC_B_PER_POINT else None),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on a "
+                                  "2560x2560 window, scaled by points per launch",
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+                "algorithmic_bytes_per_launch": step_bytes / nl,
+                "avg_launch_ms": cls["step"]["device_ms"] / nl,
+                "note": "the k launches of a visit are timed as one group on the visit's stream; "
+                        "8 B per window point per step (read u, write u')"}
+    # per-class device time from one extra call with every class timed (not in `value`)
+    fill_store(P, torch, st, shape)
+    st.set_profiling(P.OOCS_PROF_LOAD | P.OOCS_PROF_STEP | P.OOCS_PROF_STORE)
+    b2 = st.stats()
+    timed_call(torch, st, OOC_STEPS)
+    a2 = st.stats()
+    st.set_profiling(0)
+    kernels = {}
+    for c in ("load", "step", "store"):
+        k = {q: a2[c][q] - b2[c][q] for q in ("launches", "units", "device_ms")}
+        k["avg_ms"] = k["device_ms"] / max(k["launches"], 1)
+        kernels[c] = k
+    kernels["note"] = "one extra oocs_step(20) with all classes event-timed; ms per call"
+    # binding roofline of the whole sweep: algorithmic HBM bytes against the
+    # host link measured in this run.  Per sweep and grid value: H2D write (c),
+    # decode read (c) + FP32 write (4), step k reads/writes (8 B per point-step),
+    # encode FP32 read (4) + write (c), D2H read (c); c = rate / 8.
+    c_bytes = OOC_RATE / 8.0
+    passes = d["passes_done"]
+    hbm_alg = OOC_STEPS * args.steps * ooc_interior(nz) * HEAT_BYTES_PER_POINT \
+        + passes * n_all * (2 * c_bytes + 4) * 2
+    t_hbm = hbm_alg / (hbm_peak * 1e9)
+    t_h2d = d["h2d_bytes"] / (link["h2d_GBs"] * 1e9)
+    t_d2h = d["d2h_bytes"] / (link["d2h_GBs"] * 1e9)
+    t_bi = (d["h2d_bytes"] + d["d2h_bytes"]) / (link["bidir_GBs"] * 1e9)
+    t_roof = max(t_hbm, t_h2d, t_d2h, t_bi)
+    chain_ms = sum(kernels[c]["device_ms"] for c in ("load", "step", "store"))
+    sweep_roofline = {"bound": ["hbm", "h2d", "d2h", "bidir"][[t_hbm, t_h2d, t_d2h, t_bi].index(t_roof)],
+                      "t_roof_ms_per_step": t_roof * 1e3 / args.steps, "t_measured_ms_per_step": ms / args.steps,
+                      "frac": t_roof / (ms / 1e3),
+                      "t_hbm_ms": t_hbm * 1e3 / args.steps, "t_h2d_ms": t_h2d * 1e3 / args.steps,
+                      "t_d2h_ms": t_d2h * 1e3 / args.steps, "t_bidir_ms": t_bi * 1e3 / args.steps,
+                      "hbm_algorithmic_bytes_per_step": hbm_alg / args.steps,
+                      "h2d_bytes_per_step": d["h2d_bytes"] / args.steps,
+                      "d2h_bytes_per_step": d["d2h_bytes"] / args.steps, "link": link,
+                      "kernel_chain_ms_per_step": chain_ms,
+                      "measured_binding": "kernel chain" if chain_ms > t_roof * 1e3 / args.steps else "host link"}
+
+    # ---- accuracy: the rate-16 result after 20 steps (the store holds it)
+    # on the central CUBE_IN^3 points of seeded cubes, compared later with the
+    # FP64 oracle on the same cubes
+    single = world == 1
+    origins = cube_origins(shape, CUBES_BASELINE)
+    got_cubes = []
+    if rank == 0 and not args.no_cpu_baseline:
+        buf = torch.empty((CUBE_IN, ny, nx), dtype=torch.float32, device=dev)
+        for (z0, y0, x0) in origins:
+            P.oocs_decompress_device(st.ctx, P.OOCS_FIELD_U, buf.data_ptr(), z0, CUBE_IN)
+            st.synchronize(600.0)
+            got_cubes.append(buf[:, y0:y0 + CUBE_IN, x0:x0 + CUBE_IN].cpu().numpy().astype(np.float64))
+        del buf
+
+    # ---- e2e: the raw FP32 host array in, the result back in it; the store
+    # is the array's first half (in place), so the host needs one array
+    raw = host.tensor().view(torch.float32).reshape(shape)
+    fill_raw(torch, raw, shape, dev)
+    e2e_ms = []
+    e2e_b = st.stats()
+    for i in range(3):
+        s0 = st.streams[0]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s0)
+        st.compress(P.OOCS_FIELD_U, raw)
+        st.step(OOC_STEPS)
+        st.decompress(P.OOCS_FIELD_U, raw)
+        e1.record(s0)
+        st.synchronize(3600.0)
+        e1.synchronize()
+        if i > 0:  # the first is a warm-up; each continues from the previous result
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_a = st.stats()
+    calls = 3
+    e2e_step_ms = float(np.median(e2e_ms))
+    step_h2d = (e2e_a["h2d_bytes"] - e2e_b["h2d_bytes"]) / calls
+    step_d2h = (e2e_a["d2h_bytes"] - e2e_b["d2h_bytes"]) / calls
+    e2e = {"value": ooc_interior(nz) * OOC_STEPS * world / (e2e_step_ms / 1e3) / 1e9,
+           "unit": UNIT, "ms_per_step": e2e_step_ms,
+           "h2d_bytes_per_step": int(raw_bytes + step_h2d + plan.host_store_bytes),
+           "d2h_bytes_per_step": int(plan.host_store_bytes + step_d2h + raw_bytes),
+           "note": "oocs_compress(u from the pinned FP32 array, store in place) + oocs_step(20) + "
+                   "oocs_decompress(u into the same array), CUDA events on stream 0; each step "
+                   "continues from the previous result"}
+    st.close()
+    del st, raw
+    torch.cuda.empty_cache()
+
+    # ---- the same grid streamed uncompressed (the store is the raw array)
+    uncompressed = None
+    if single and not args.no_uncompressed:
+        def run_uncompressed():
+            st0 = P.OutOfCoreStencil(ooc_desc(P, 0, nz), stores=[host.tensor()])
+            try:
+                fill_store(P, torch, st0, shape)
+                timed_call(torch, st0, OOC_STEPS)
+                ms0 = []
+                for _ in range(2):
+                    fill_store(P, torch, st0, shape)
+                    ms0.append(timed_call(torch, st0, OOC_STEPS))
+                s0 = st0.stats()
+                v0 = ooc_interior(nz) * OOC_STEPS / (float(np.mean(ms0)) / 1e3) / 1e9
+                return {"value": v0, "ms_per_step": float(np.mean(ms0)), "slabs": st0.plan.num_slabs,
+                        "slab_planes": st0.plan.slab_planes, "workspace_bytes": st0.plan.workspace_bytes,
+                        "host_store_bytes": st0.plan.host_store_bytes,
+                        "h2d_bytes_per_step": s0["h2d_bytes"] / 3, "d2h_bytes_per_step": s0["d2h_bytes"] / 3,
+                        "speedup_compressed_vs_uncompressed": value / world / v0}
+            finally:
+                st0.close()
+                torch.cuda.empty_cache()
+        uncompressed = guarded(run_uncompressed)
+    host.close()
+    del host
+
+    line = base_line(args, world, nz)
+    line.update({"value": value, "ms_per_step": ms / args.steps, "dtype": "f32",
+                 "gpu_launches": int(d["kernel_launches"]), "e2e": e2e, "roofline": roofline,
+                 "sweep_roofline": sweep_roofline, "clocks": clk, "kernels": kernels,
+                 "plan": {"slabs": plan.num_slabs, "slab_planes": plan.slab_planes,
+                          "halo_planes": plan.halo_planes, "window_planes": plan.window_planes,
+                          "workspace_bytes": plan.workspace_bytes, "host_store_bytes": plan.host_store_bytes},
+                 "host": {"pin_seconds": t_pin, "fill_seconds": t_fill},
+                 "uncompressed": uncompressed})
+
+    # ---- FP64 oracle on the dependency cubes: the CPU baseline and the
+    # accuracy of the rate-16 result
+    if rank == 0 and not args.no_cpu_baseline:
+        secs, refs, cores = oracle_cubes(shape, origins, OOC_RATE)
+        useful = len(origins) * CUBE_IN ** 3 * OOC_STEPS
+        line["cpu_baseline"] = {"value": useful / secs / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "seconds": secs,
+                                "sample": f"{len(origins)} seeded cubes of {CUBE_IN + 2 * CUBE_HALO}^3 values "
+                                          f"of the workload's field: 20 FP64 heat steps in 5 passes, each "
+                                          f"pass followed by the reference codec round trip at rate "
+                                          f"{OOC_RATE}; counts the {CUBE_IN}^3 central points per cube"}
+        got = np.concatenate([g.ravel() for g in got_cubes])
+        ref = np.concatenate([r.ravel() for r in refs])
+        import synthetic
+        err = np.abs(got - ref)
+        peak = float(np.max(np.abs(ref)))
+        rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        line["accuracy"] = {"vs": "FP64 oracle on the central points of the dependency cubes",
+                            "points": int(got.size), "rel_l2": rel, "max_abs": float(err.max()),
+                            "max_abs_rel_peak": float(err.max()) / peak,
+                            "stated_rel_l2": synthetic.TOL_COMPRESSED[OOC_RATE],
+                            "stated_max_abs_rel_peak": synthetic.TOL_MAXABS_COMPRESSED[OOC_RATE],
+                            "within": bool(rel <= synthetic.TOL_COMPRESSED[OOC_RATE]
+                                           and float(err.max()) / peak <= synthetic.TOL_MAXABS_COMPRESSED[OOC_RATE])}
+
+    # The sections below characterise the method on one GPU; replicas under
+    # torchrun (N > 1) report the headline only.
+    if single:
+        if not args.no_wave512:
+            line["wave512"] = guarded(run_wave512, P, torch, dev, args, peaks, peak_src, link)
+        if not args.no_adjoint:
+            line["adjoint"] = guarded(run_adjoint, P, torch, dev, hbm_peak)
+        if not args.no_batch:
+            line["batched"] = guarded(run_batched, P, torch, dev)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------- the 512^3 wave workload --
+
+def run_wave512(P, torch, dev, args, peaks, peak_src, link, calls=3):
+    """The 512^3 acoustic wave workload (25-point star, leapfrog, 100 steps,
+    8 slabs, k = 4, rate 16, 4 GiB): oocs_step(100) from rest, m kept on the
+    device and m streamed with every visit as in the paper; e2e from raw FP32
+    host arrays; the live bandwidth of its step kernel; the comparison of
+    codecs, rates and buffer schemes."""
+    import numpy as np
+    hbm_peak = float(peaks["hbm_gbs"])
+    inputs = make_inputs((calls + 4) * STEPS_PER_CALL)
+    out = {"workload": WAVE_WORKLOAD, "unit": UNIT, "grid": [N, N, N], "time_steps_per_call": STEPS_PER_CALL,
+           "slabs": N // SLAB, "slab_planes": SLAB, "temporal_depth": K_DEPTH, "rate_bits": RATE,
+           "device_budget_bytes": BUDGET}
+    for ro, key in ((1, "m_resident"), (0, "m_streamed")):
+        st, pin = open_ctx(P, torch, RATE, 1, inputs, ro)
+        snap = st.snapshot_stores()
+        st.set_profiling(P.OOCS_PROF_STEP)
+        timed_calls(torch, st, 2, snap)
+        before = st.stats()
+        ms = timed_calls(torch, st, calls, snap)
+        after = st.stats()
+        r = {"value": interior_points() * STEPS_PER_CALL * calls / (ms / 1e3) / 1e9, "ms_per_call": ms / calls,
+             "workspace_bytes": st.plan.workspace_bytes}
+        if ro:
+            cls = {k: after["step"][k] - before["step"][k] for k in ("launches", "units", "device_ms")}
+            gbs = cls["units"] * WAVE_BYTES_PER_POINT / (cls["device_ms"] / 1e3) / 1e9
+            nl = max(cls["launches"], 1)
+            r["roofline"] = {"bound": "hbm", "kernel": "k_star_step<4,wave>", "achieved": gbs, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": gbs / hbm_peak,
+                             "traffic": (STEP_TRAFFIC_B_PER_POINT * cls["units"] / nl
+                                         if STEP_TRAFFIC_B_PER_POINT else None),
+                             "algorithmic_bytes_per_launch": cls["units"] * WAVE_BYTES_PER_POINT / nl,
+                             "avg_launch_ms": cls["device_ms"] / nl, "peak_source": peak_src}
+            dh = after["h2d_bytes"] - before["h2d_bytes"]
+            dd = after["d2h_bytes"] - before["d2h_bytes"]
+            t_link = max(dh / (link["h2d_GBs"] * 1e9), dd / (link["d2h_GBs"] * 1e9),
+                         (dh + dd) / (link["bidir_GBs"] * 1e9))
+            # per-class chain of one more call
+            st.set_profiling(P.OOCS_PROF_LOAD | P.OOCS_PROF_STEP | P.OOCS_PROF_STORE)
+            b2 = st.stats()
+            timed_calls(torch, st, 1, snap)
+            a2 = st.stats()
+            chain = {c: a2[c]["device_ms"] - b2[c]["device_ms"] for c in ("load", "step", "store")}
+            r["kernels_ms_per_call"] = chain
+            r["sweep_roofline"] = {"bound": "bidir", "t_link_ms_per_call": t_link * 1e3 / calls,
+                                   "frac": t_link / (ms / 1e3), "kernel_chain_ms_per_call": sum(chain.values()),
+                                   "measured_binding": "kernel chain" if sum(chain.values()) > t_link * 1e3 / calls
+                                   else "host link"}
+            # e2e: raw FP32 host arrays in, result back in host memory
+            res_host = st.pinned_field()
+            e2e_ms = []
+            for i in range(3):
+                s0 = st.streams[0]
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                st.set_time(0)
+                e0.record(s0)
+                st.compress(P.OOCS_FIELD_U, pin["z"])
+                st.compress(P.OOCS_FIELD_U_PREV, pin["z"])
+                st.compress(P.OOCS_FIELD_M, pin["m"])
+                st.step(STEPS_PER_CALL)
+                st.decompress(P.OOCS_FIELD_U, res_host)
+                e1.record(s0)
+                st.synchronize(600.0)
+                e1.synchronize()
+                if i:
+                    e2e_ms.append(e0.elapsed_time(e1))
+            r["e2e"] = {"value": interior_points() * STEPS_PER_CALL / (float(np.median(e2e_ms)) / 1e3) / 1e9,
+                        "ms_per_call": float(np.median(e2e_ms)),
+                        "note": "oocs_compress(u, u_prev, m from pinned FP32) + oocs_step(100) + "
+                                "oocs_decompress(u to pinned FP32)"}
+        st.set_profiling(0)
+        st.close()
+        del st, pin, snap
+        torch.cuda.empty_cache()
+        out[key] = r
+    out["value"] = out["m_resident"]["value"]
+    out["accuracy"] = check_accuracy(P, torch, dev, RATE, inputs)
+    if not args.no_compare:
+        out["compare"] = guarded(run_compare, P, torch, dev, args, inputs, peaks, out["value"], 1)
+    return out
 
 
 def make_inputs(total_steps):
@@ -272,227 +762,159 @@ def timed_calls(torch, st, k, snap, calls=STEPS_PER_CALL):
     return total
 
 
-SAMPLE_PLANES = 128
-
-
-def cpu_oracle_sample(inputs, rate=RATE, planes=SAMPLE_PLANES):
-    """One slab-sized sample of the workload on the CPU oracle: 4 FP64 leapfrog
-    steps (one sweep's depth) on a 512 x 512 x `planes` sub-grid of the model
-    (Dirichlet shell included) plus the reference codec round trip of u,
-    u_prev and m at `rate`.  Returns (seconds, interior points updated, threads)."""
+def check_accuracy(P, torch, dev, rate, inputs, codec=0, ref=None):
+    """Compressed run of the workload (100 steps from rest) against the
+    uncompressed in-core GPU run of the same FP32 arithmetic (which the tests
+    hold within 1e-5 of the FP64 oracle); `ref` reuses that run."""
     import numpy as np
 
-    import oracle
     import synthetic
-    m, w, src, z = inputs
-    z0 = (N - planes) // 2
-    mm = np.ascontiguousarray(m[z0:z0 + planes])
-    shape = mm.shape
-    rng = np.random.default_rng(0)
-    u = np.zeros(shape, np.float64)
-    up = np.zeros(shape, np.float64)
-    u[4:-4, 4:-4, 4:-4] = rng.standard_normal((planes - 8, N - 8, N - 8)) * 1e-3
-    t = time.perf_counter()
-    u, up = oracle.wave_run(u, up, mm, synthetic.wave_star_coef(), K_DEPTH,
-                            src=(planes // 2, src[1], src[0]), w=w)
-    for f in (u, up, mm):
-        oracle.decode_field(oracle.encode_field(np.asarray(f, np.float32), rate), shape, rate)
-    dt = time.perf_counter() - t
-    return dt, (planes - 8) * (N - 8) ** 2 * K_DEPTH, oracle.threads()
-
-
-def base_line(args, world):
-    peaks, _ = measured_peaks()
-    return {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [N, N, N], "stencil": "25-point star, r=4",
-                       "time_steps_per_step": STEPS_PER_CALL, "slabs": N // SLAB,
-                       "slab_planes": SLAB, "temporal_depth": K_DEPTH, "rate_bits": args.rate,
-                       "working_buffers": 1, "device_budget_bytes": BUDGET,
-                       "model_m": "device-resident (decoded once from its store)" if RO_RESIDENT
-                       else "streamed with every slab visit",
-                       "l2": "inputs larger than L2 (one 512^3 FP32 field = 537 MB)",
-                       "parallelism": f"replicas{world}"}}
-
-
-# ----------------------------------------------------------------- ours --
-
-def run_ours(args):
-    import numpy as np
-    import torch
-
-    import paper_2204_11315_gb300 as P
-    rank, world, local = dist_env()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    P.lib()
-    peaks, peak_src = measured_peaks()
-    total_steps = (args.warmup + args.steps + 2) * STEPS_PER_CALL
-    inputs = make_inputs(total_steps)
-    link = link_bandwidth(torch, dev)
-
-    # ---- main timed region: oocs_step from the compressed host store
-    st, pin = open_ctx(P, torch, args.rate, 1, inputs)
-    snap = st.snapshot_stores()
-    # live timing of the dominant kernel class only (two event records per
-    # step-kernel launch); the warm-up creates the event pool
-    st.set_profiling(P.OOCS_PROF_STEP)
-    timed_calls(torch, st, args.warmup, snap)
-    before = st.stats()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms = timed_calls(torch, st, args.steps, snap)
-    clk = clocks.stop()
-    after = st.stats()
-    ms = max_over_ranks(torch, ms, dev)
-    value = replica_throughput(interior_points() * STEPS_PER_CALL * args.steps, world, ms)
-
-    d = {k: after[k] - before[k] for k in ("h2d_bytes", "d2h_bytes", "kernel_launches",
-                                            "slabs_done", "passes_done")}
-    cls = {c: {k: after[c][k] - before[c][k] for k in ("launches", "units", "device_ms")}
-           for c in ("load", "step", "store")}
-    hbm_peak = float(peaks["hbm_gbs"])
-    step_bytes = cls["step"]["units"] * WAVE_BYTES_PER_POINT
-    step_gbs = step_bytes / (cls["step"]["device_ms"] / 1e3) / 1e9 if cls["step"]["device_ms"] else None
-    roofline = {"bound": "hbm", "kernel": "k_star_step<4,wave>",
-                "achieved": step_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": (step_gbs / hbm_peak) if step_gbs else None,
-                "traffic": (STEP_TRAFFIC_B_PER_POINT * cls["step"]["units"] / max(cls["step"]["launches"], 1)
-                            if STEP_TRAFFIC_B_PER_POINT else None),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 512x512x80 "
-                                  "launch, scaled by points per launch",
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                "algorithmic_bytes_per_launch": step_bytes / max(cls["step"]["launches"], 1),
-                "avg_launch_ms": cls["step"]["device_ms"] / max(cls["step"]["launches"], 1)}
-    # binding roofline of the whole sweep: HBM algorithmic bytes vs host link.
-    # Per sweep and grid value of a streamed field: in = H2D write (c) + decode
-    # read (c) + write (4); out = encode read (4) + write (c) + D2H read (c);
-    # c = 4 uncompressed (the decode / encode are copies).
-    n_all = N ** 3
-    c_bytes = args.rate / 8.0 if args.rate else 4.0
-    passes = d["passes_done"]
-    f_in = st.plan.fields_in
-    hbm_alg = STEPS_PER_CALL * args.steps * interior_points() * WAVE_BYTES_PER_POINT \
-        + passes * n_all * (f_in * (2 * c_bytes + 4) + 2 * (4 + 2 * c_bytes))
-    t_hbm = hbm_alg / (hbm_peak * 1e9)
-    t_h2d = d["h2d_bytes"] / (link["h2d_GBs"] * 1e9)
-    t_d2h = d["d2h_bytes"] / (link["d2h_GBs"] * 1e9)
-    t_bi = (d["h2d_bytes"] + d["d2h_bytes"]) / (link["bidir_GBs"] * 1e9)
-    t_roof = max(t_hbm, t_h2d, t_d2h, t_bi)
-    sweep_roofline = {"t_roof_ms": t_roof * 1e3, "t_measured_ms": ms / world if world else ms,
-                      "frac": t_roof / (ms / 1e3),
-                      "binding": ["hbm", "h2d", "d2h", "bidir"][[t_hbm, t_h2d, t_d2h, t_bi].index(t_roof)],
-                      "t_hbm_ms": t_hbm * 1e3, "t_h2d_ms": t_h2d * 1e3, "t_d2h_ms": t_d2h * 1e3,
-                      "t_bidir_ms": t_bi * 1e3, "hbm_algorithmic_bytes": hbm_alg,
-                      "h2d_bytes": d["h2d_bytes"], "d2h_bytes": d["d2h_bytes"], "link": link}
-    # per-class device time from one extra call with every class timed (not in `value`)
-    st.set_profiling(P.OOCS_PROF_LOAD | P.OOCS_PROF_STEP | P.OOCS_PROF_STORE)
-    b2 = st.stats()
-    timed_calls(torch, st, 1, snap)
-    a2 = st.stats()
-    kernels = {}
-    for c in ("load", "step", "store"):
-        k = {q: a2[c][q] - b2[c][q] for q in ("launches", "units", "device_ms")}
-        k["avg_ms"] = k["device_ms"] / max(k["launches"], 1)
-        kernels[c] = k
-    kernels["note"] = "one extra oocs_step(100) with all classes event-timed; ms per call"
-    st.set_profiling(0)
-    # what binds the call as measured: the serial chain of kernels (one working
-    # buffer: the visits' kernels never overlap) or the host-link floor
-    chain_ms = sum(kernels[c]["device_ms"] for c in ("load", "step", "store"))
-    t_call = ms / world if world else ms
-    sweep_roofline["kernel_chain_ms_per_call"] = chain_ms
-    sweep_roofline["link_floor_ms_per_call"] = t_roof * 1e3 / args.steps
-    sweep_roofline["measured_binding"] = ("kernel chain" if chain_ms > t_roof * 1e3 / args.steps
-                                          else "host link")
-    sweep_roofline["ms_per_call"] = t_call / args.steps
-
-    # ---- e2e: raw FP32 host arrays in, result back in host memory
-    e2e_ms = []
-    res_host = st.pinned_field()
-    for i in range(max(2, min(args.steps, 3)) + 1):
-        s0 = st.streams[0]
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        st.set_time(0)
-        e0.record(s0)
-        st.compress(P.OOCS_FIELD_U, pin["z"])
-        st.compress(P.OOCS_FIELD_U_PREV, pin["z"])
-        st.compress(P.OOCS_FIELD_M, pin["m"])
-        st.step(STEPS_PER_CALL)
-        st.decompress(P.OOCS_FIELD_U, res_host)
-        e1.record(s0)
-        st.synchronize(600.0)
-        e1.synchronize()
-        if i > 0:  # first round is a warm-up
-            e2e_ms.append(e0.elapsed_time(e1))
-    e2e_step_ms = float(np.median(e2e_ms))
-    raw = n_all * 4
-    comp = n_all * args.rate // 8 if args.rate else raw
-    per_call_h2d = d["h2d_bytes"] / args.steps
-    per_call_d2h = d["d2h_bytes"] / args.steps
-    e2e = {"value": interior_points() * STEPS_PER_CALL * world / (e2e_step_ms / 1e3) / 1e9,
-           "unit": UNIT, "ms_per_step": e2e_step_ms,
-           "h2d_bytes_per_step": int(3 * raw + per_call_h2d + comp),
-           "d2h_bytes_per_step": int(3 * comp + per_call_d2h + raw),
-           "note": "oocs_compress(u, u_prev, m from pinned FP32) + oocs_step(100) + "
-                   "oocs_decompress(u to pinned FP32), CUDA events on stream 0"}
+    st, pin = open_ctx(P, torch, rate, 1, inputs, codec=codec)
+    st.step(STEPS_PER_CALL)
+    st.synchronize(600.0)
+    out = st.decompress(P.OOCS_FIELD_U)
+    st.synchronize(600.0)
+    got = out.numpy().astype(np.float64)
     st.close()
     del st, pin
     torch.cuda.empty_cache()
+    if ref is None:
+        ref = incore_reference(P, torch, dev, inputs)
+    rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    tol = synthetic.TOL_COMPRESSED.get(rate) if rate else synthetic.TOL_UNCOMPRESSED["wave"]
+    return {"rel_l2_vs_uncompressed_fp32": rel, "max_abs": float(np.max(np.abs(got - ref))),
+            "max_ref": float(np.max(np.abs(ref))), "stated_max_rel_l2": tol,
+            "within": bool(tol is not None and rel <= tol)}
 
-    # The sections below characterise the method on one GPU; replicas under
-    # torchrun (N > 1) report the headline only (the true out-of-core run
-    # alone pins up to 134 GB of host memory per process).
-    single = world == 1
 
-    # ---- accuracy at the stated configuration: 100 steps from rest
-    accuracy = guarded(check_accuracy, P, torch, dev, args.rate, inputs) if single else None
+def incore_reference(P, torch, dev, inputs):
+    """The workload's 100 steps from rest, uncompressed and in core on the GPU (FP64 copy of u)."""
+    import numpy as np
+    m, w, src, z = inputs
+    u = torch.zeros((N, N, N), device=dev)
+    up = torch.zeros((N, N, N), device=dev)
+    mm = torch.from_numpy(m).to(dev)
+    sc = torch.empty_like(u)
+    srcv = (src[0], src[1], src[2])
+    P.oocs_incore_run(wave_desc(P, 0), u.data_ptr(), up.data_ptr(), mm.data_ptr(), sc.data_ptr(),
+                      STEPS_PER_CALL, 0, srcv, w, torch.cuda.current_stream(dev).cuda_stream)
+    ref = u.cpu().numpy().astype(np.float64)
+    del u, up, mm, sc
+    torch.cuda.empty_cache()
+    return ref
 
-    # ---- the adjoint workload (gradient of a receiver misfit)
-    adjoint = guarded(run_adjoint, P, torch, dev, float(peaks["hbm_gbs"])) \
-        if single and not args.no_adjoint else None
 
-    # ---- the batched workload (many independent problems, one pipeline)
-    batched = guarded(run_batched, P, torch, dev) if single and not args.no_batch else None
+def run_compare(P, torch, dev, args, inputs, peaks, value, world):
+    """Comparison on the same GPU (Fig. 9, Fig. 11 analogues): uncompressed
+    streaming, SWB and classic, other rates and the block quantiser with their
+    accuracy, the codec kernels alone, and the call replayed as a CUDA graph."""
+    compare = {}
+    ref = incore_reference(P, torch, dev, inputs)
+    for name, rate, wb, ro, codec in (("uncompressed_swb", 0, 1, RO_RESIDENT, 0),
+                                      ("uncompressed_classic", 0, 3, RO_RESIDENT, 0),
+                                      (f"rate{RATE}_classic", RATE, 3, RO_RESIDENT, 0),
+                                      ("rate8_swb", 8, 1, RO_RESIDENT, 0), ("rate12_swb", 12, 1, RO_RESIDENT, 0),
+                                      (f"rate{RATE}_swb_m_streamed", RATE, 1, 0, 0),
+                                      ("uncompressed_swb_m_streamed", 0, 1, 0, 0),
+                                      ("uncompressed_classic_m_streamed", 0, 3, 0, 0),
+                                      # the simpler codec of the Sec. 7 (1) comparison
+                                      ("quant12_swb", 12, 1, RO_RESIDENT, 1),
+                                      ("quant16_swb", 16, 1, RO_RESIDENT, 1),
+                                      ("quant20_swb", 20, 1, RO_RESIDENT, 1)):
+        st, pin = open_ctx(P, torch, rate, wb, inputs, ro, codec)
+        snap_u = st.snapshot_stores()
+        timed_calls(torch, st, 1, snap_u)
+        k = 2
+        cms = timed_calls(torch, st, k, snap_u)
+        compare[name] = {"value": interior_points() * STEPS_PER_CALL * k / (cms / 1e3) / 1e9,
+                         "workspace_bytes": st.plan.workspace_bytes}
+        st.close()
+        del st, pin, snap_u
+        torch.cuda.empty_cache()
+        if rate and wb == 1 and ro == RO_RESIDENT:  # accuracy of each codec and rate
+            compare[name]["rel_l2_vs_uncompressed_fp32"] = check_accuracy(
+                P, torch, dev, rate, inputs, codec, ref)["rel_l2_vs_uncompressed_fp32"]
+    del ref
+    compare["codec_kernels"] = codec_kernel_rates(P, torch, dev, RATE, float(peaks["hbm_gbs"]))
+    # the same workload as a batch of one, its 100-step call replayed as one CUDA graph
+    m, w, src, z = inputs
+    b = P.OutOfCoreBatch([wave_desc(P, RATE)])
+    bp = b.problems[0]
+    pin = {}
+    for name, arr in (("z", z), ("m", m)):
+        t = torch.empty(arr.shape, dtype=torch.float32, pin_memory=True)
+        t.numpy()[...] = arr
+        pin[name] = t
+    bp.compress(P.OOCS_FIELD_U, pin["z"])
+    bp.compress(P.OOCS_FIELD_U_PREV, pin["z"])
+    bp.compress(P.OOCS_FIELD_M, pin["m"])
+    bp.set_source(src[0], src[1], src[2], w)
+    b.synchronize(600.0)
+    snap_g = bp.snapshot_stores()
+    b.capture(STEPS_PER_CALL)
+    gms = []
+    for i in range(3):
+        bp.restore_stores(snap_g, 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.streams[0])
+        b.launch()
+        e1.record(b.streams[0])
+        b.synchronize(600.0)
+        e1.synchronize()
+        if i:
+            gms.append(e0.elapsed_time(e1))
+    compare[f"rate{RATE}_swb_graph_replay"] = {
+        "value": interior_points() * STEPS_PER_CALL * len(gms) / (sum(gms) / 1e3) / 1e9,
+        "note": "the 100-step call captured once (oocs_batch_capture) and replayed"}
+    b.close()
+    del b, bp, pin, snap_g
+    torch.cuda.empty_cache()
+    compare["speedup_compressed_vs_uncompressed"] = value / world / compare["uncompressed_swb"]["value"]
+    compare["speedup_compressed_vs_uncompressed_m_streamed"] = \
+        compare[f"rate{RATE}_swb_m_streamed"]["value"] / compare["uncompressed_swb_m_streamed"]["value"]
+    # the paper's memory comparison (Sec. 6.2): compressed SWB against
+    # uncompressed classic, both streaming m as the paper does
+    compare["memory_reduction_vs_uncompressed_classic"] = \
+        1.0 - compare[f"rate{RATE}_swb_m_streamed"]["workspace_bytes"] \
+        / compare["uncompressed_classic_m_streamed"]["workspace_bytes"]
+    compare["paper_v100"] = {"speedup": 1.1, "memory_reduction": 0.330,
+                             "source": "Sec. 6.1 and Sec. 6.2 (V100-PCIe, FP64, context only)"}
+    return compare
 
-    # ---- a grid larger than the device budget by far (two 134 GB arrays)
-    true_ooc = guarded(run_true_out_of_core, P, torch, dev) if single and not args.no_true_ooc else None
 
-    # ---- comparison: uncompressed streaming, SWB and classic (Fig. 9, Fig. 11 analogues)
-    compare = guarded(run_compare, P, torch, dev, args, inputs, peaks, value, world) \
-        if single and not args.no_compare else None
-
-    line = base_line(args, world)
-    line.update({"value": value, "ms_per_step": ms / args.steps, "dtype": "f32",
-                 "gpu_launches": int(d["kernel_launches"]), "e2e": e2e, "roofline": roofline,
-                 "clocks": clk, "sweep_roofline": sweep_roofline, "kernels": kernels,
-                 "accuracy": accuracy, "compare": compare, "adjoint": adjoint, "batched": batched,
-                 "true_out_of_core": true_ooc,
-                 "workspace_bytes": P.oocs_query(wave_desc(P, args.rate)).workspace_bytes})
-    if rank == 0 and not args.no_cpu_baseline:
-        tot, pts_cpu = 0.0, 0
-        for _ in range(3):
-            dt, npts, cores = cpu_oracle_sample(inputs, args.rate)
-            tot += dt
-            pts_cpu += npts
-        line["cpu_baseline"] = {"value": pts_cpu / tot / 1e9, "unit": UNIT, "cores": cores,
-                                "kind": "oracle", "seconds": tot,
-                                "sample": f"3 x (4 FP64 leapfrog steps on a 512x512x{SAMPLE_PLANES} "
-                                          "sub-grid of the model + reference codec round trip of u, "
-                                          f"u_prev, m at rate {args.rate})"}
-    if world > 1:
-        torch.distributed.barrier()
-        torch.distributed.destroy_process_group()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+def codec_kernel_rates(P, torch, dev, rate, hbm_peak, reps=10):
+    """Live rates of the codec kernels alone: encode and decode of a 512 x 512
+    x 192 field (201 MB FP32, above the 129 MB L2) at `rate`, each codec,
+    CUDA events over `reps` launches after a warm-up.  Algorithmic bytes per
+    value: 4 (FP32) + rate/8 (compressed)."""
+    nz = 192
+    noise = torch.randn((nz, N, N), device=dev) * 1e-3
+    zero = torch.zeros_like(noise)  # the sweep's fields are mostly all-zero blocks (a point source from rest)
+    g = torch.empty_like(noise)
+    blocks = torch.empty(N * N * nz * rate // 32, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    vals = N * N * nz
+    out = {}
+    for name, codec, f in (("transform", 0, noise), ("quant", 1, noise), ("transform_zero_field", 0, zero)):
+        enc = lambda: P.oocs_encode_device(f.data_ptr(), N, N, nz, rate, blocks.data_ptr(), s, codec=codec)
+        dec = lambda: P.oocs_decode_device(blocks.data_ptr(), N, N, nz, rate, g.data_ptr(), s, codec=codec)
+        r = {}
+        for kind, fn in (("encode", enc), ("decode", dec)):
+            fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / reps
+            gbs = vals * (4 + rate / 8) / (ms / 1e3) / 1e9
+            r[kind] = {"avg_launch_ms": ms, "gvalues_per_s": vals / (ms / 1e3) / 1e9, "achieved_gbs": gbs,
+                       "frac_of_hbm": gbs / hbm_peak}
+        out[name] = r
+    del noise, zero, g, blocks
+    torch.cuda.empty_cache()
+    return {"grid": [N, N, nz], "rate": rate, "bytes_per_value": 4 + rate / 8, **out}
 
 
 BATCH_N, BATCH_STEPS, BATCH_BUDGET, BATCH_TOL = 64, 50, 8 << 30, 1e-4
@@ -601,166 +1023,6 @@ def run_batched(P, torch, dev):
                        "temporal_depths": depths}}
 
 
-OOC_SHAPE, OOC_STEPS, OOC_K, OOC_BUDGET, OOC_SEED = (5120, 2560, 2560), 20, 4, 16 << 30, 31
-
-
-def ooc_samples(shape, n=64, seed=32, margin=24):
-    """n seeded interior points (z, y, x) at least `margin` from every face."""
-    import synthetic
-    u = synthetic.uniform01(seed, 3 * n).reshape(n, 3)
-    return [tuple(int(margin + u[i, a] * (shape[a] - 2 * margin)) for a in range(3)) for i in range(n)]
-
-
-def run_compare(P, torch, dev, args, inputs, peaks, value, world):
-    """Comparison on the same GPU (Fig. 9, Fig. 11 analogues): uncompressed
-    streaming, SWB and classic, other rates and the block quantiser with their
-    accuracy, the codec kernels alone, and the call replayed as a CUDA graph."""
-    compare = {}
-    ref = incore_reference(P, torch, dev, inputs)
-    for name, rate, wb, ro, codec in (("uncompressed_swb", 0, 1, RO_RESIDENT, 0),
-                                      ("uncompressed_classic", 0, 3, RO_RESIDENT, 0),
-                                      (f"rate{args.rate}_classic", args.rate, 3, RO_RESIDENT, 0),
-                                      ("rate8_swb", 8, 1, RO_RESIDENT, 0), ("rate12_swb", 12, 1, RO_RESIDENT, 0),
-                                      (f"rate{args.rate}_swb_m_streamed", args.rate, 1, 0, 0),
-                                      ("uncompressed_swb_m_streamed", 0, 1, 0, 0),
-                                      ("uncompressed_classic_m_streamed", 0, 3, 0, 0),
-                                      # the simpler codec of the Sec. 7 (1) comparison
-                                      ("quant12_swb", 12, 1, RO_RESIDENT, 1),
-                                      ("quant16_swb", 16, 1, RO_RESIDENT, 1),
-                                      ("quant20_swb", 20, 1, RO_RESIDENT, 1)):
-        st, pin = open_ctx(P, torch, rate, wb, inputs, ro, codec)
-        snap_u = st.snapshot_stores()
-        timed_calls(torch, st, 1, snap_u)
-        k = 2
-        cms = timed_calls(torch, st, k, snap_u)
-        compare[name] = {"value": interior_points() * STEPS_PER_CALL * k / (cms / 1e3) / 1e9,
-                         "workspace_bytes": st.plan.workspace_bytes}
-        st.close()
-        del st, pin, snap_u
-        torch.cuda.empty_cache()
-        if rate and wb == 1 and ro == RO_RESIDENT:  # accuracy of each codec and rate
-            compare[name]["rel_l2_vs_uncompressed_fp32"] = check_accuracy(
-                P, torch, dev, rate, inputs, codec, ref)["rel_l2_vs_uncompressed_fp32"]
-    del ref
-    compare["codec_kernels"] = codec_kernel_rates(P, torch, dev, args.rate, float(peaks["hbm_gbs"]))
-    # the same workload as a batch of one, its 100-step call replayed as one CUDA graph
-    m, w, src, z = inputs
-    b = P.OutOfCoreBatch([wave_desc(P, args.rate)])
-    bp = b.problems[0]
-    pin = {}
-    for name, arr in (("z", z), ("m", m)):
-        t = torch.empty(arr.shape, dtype=torch.float32, pin_memory=True)
-        t.numpy()[...] = arr
-        pin[name] = t
-    bp.compress(P.OOCS_FIELD_U, pin["z"])
-    bp.compress(P.OOCS_FIELD_U_PREV, pin["z"])
-    bp.compress(P.OOCS_FIELD_M, pin["m"])
-    bp.set_source(src[0], src[1], src[2], w)
-    b.synchronize(600.0)
-    snap_g = bp.snapshot_stores()
-    b.capture(STEPS_PER_CALL)
-    gms = []
-    for i in range(3):
-        bp.restore_stores(snap_g, 0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(b.streams[0])
-        b.launch()
-        e1.record(b.streams[0])
-        b.synchronize(600.0)
-        e1.synchronize()
-        if i:
-            gms.append(e0.elapsed_time(e1))
-    compare[f"rate{args.rate}_swb_graph_replay"] = {
-        "value": interior_points() * STEPS_PER_CALL * len(gms) / (sum(gms) / 1e3) / 1e9,
-        "note": "the 100-step call captured once (oocs_batch_capture) and replayed"}
-    b.close()
-    del b, bp, pin, snap_g
-    torch.cuda.empty_cache()
-    compare["speedup_compressed_vs_uncompressed"] = value / world / compare["uncompressed_swb"]["value"]
-    compare["speedup_compressed_vs_uncompressed_m_streamed"] = \
-        compare[f"rate{args.rate}_swb_m_streamed"]["value"] / compare["uncompressed_swb_m_streamed"]["value"]
-    # the paper's memory comparison (Sec. 6.2): compressed SWB against
-    # uncompressed classic, both streaming m as the paper does
-    compare["memory_reduction_vs_uncompressed_classic"] = \
-        1.0 - compare[f"rate{args.rate}_swb_m_streamed"]["workspace_bytes"] \
-        / compare["uncompressed_classic_m_streamed"]["workspace_bytes"]
-    compare["paper_v100"] = {"speedup": 1.1, "memory_reduction": 0.330,
-                             "source": "Sec. 6.1 and Sec. 6.2 (V100-PCIe, FP64, context only)"}
-    return compare
-
-
-def run_true_out_of_core(P, torch, dev):
-    """7-point heat, FP32, 2560 x 2560 x 5120 (one field of 134 GB), seeded
-    U[0,1), 20 steps, k = 4, a 16 GiB device budget, rate 16 and uncompressed.
-    The host store is exact-size pinned memory (67 GB compressed, 134 GB raw),
-    filled from planes drawn on the GPU (oocs_compress_device); one
-    oocs_step(20) is timed per rate.  Accuracy: the rate-16 result against the
-    uncompressed streamed result (bit-exact to an in-core run by the tests) at
-    64 seeded points."""
-    import numpy as np
-
-    import synthetic
-    nz, ny, nx = OOC_SHAPE
-    plane = nx * ny
-    samples = ooc_samples(OOC_SHAPE)
-    out, values = {}, {}
-    for rate in (16, 0):
-        desc = P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), OOC_BUDGET, rate_bits=rate,
-                           temporal_depth=OOC_K)
-        plan = P.oocs_query(desc)
-        t0 = time.time()
-        host = P.HostBuffer(plan.host_store_bytes)
-        t_pin = time.time() - t0
-        st = P.OutOfCoreStencil(desc, stores=[host.tensor()])
-        try:
-            t0 = time.time()
-            chunk = 64
-            for z0 in range(0, nz, chunk):
-                z1 = min(z0 + chunk, nz)
-                f = synthetic.uniform_field_planes_torch(OOC_SHAPE, OOC_SEED, z0, z1, device=dev)
-                torch.cuda.synchronize(dev)  # drawn on torch's stream; the context reads on its own
-                P.oocs_compress_device(st.ctx, P.OOCS_FIELD_U, f.data_ptr(), z0, z1 - z0)
-                st.synchronize(600.0)
-                del f
-            t_fill = time.time() - t0
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st.streams[0])
-            st.step(OOC_STEPS)
-            e1.record(st.streams[0])
-            st.synchronize(3600.0)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1)
-            stats = st.stats()
-            buf = torch.empty((4, ny, nx), dtype=torch.float32, device=dev)
-            vals = []
-            for (z, y, x) in samples:
-                P.oocs_decompress_device(st.ctx, P.OOCS_FIELD_U, buf.data_ptr(), z // 4 * 4, 4)
-                st.synchronize(600.0)
-                vals.append(float(buf[z % 4, y, x]))
-            values[rate] = np.array(vals, np.float64)
-            pts = (nx - 2) * (ny - 2) * (nz - 2) * OOC_STEPS
-            out[f"rate{rate}"] = {"value": pts / (ms / 1e3) / 1e9, "unit": UNIT, "ms": ms,
-                                  "slabs": plan.num_slabs, "slab_planes": plan.slab_planes,
-                                  "workspace_bytes": plan.workspace_bytes,
-                                  "host_store_bytes": plan.host_store_bytes,
-                                  "h2d_bytes": stats["h2d_bytes"], "d2h_bytes": stats["d2h_bytes"],
-                                  "pin_seconds": t_pin, "fill_seconds": t_fill}
-        finally:
-            st.close()
-            host.close()
-            torch.cuda.empty_cache()
-    err = values[16] - values[0]
-    out["workload"] = "heat7_2560x2560x5120_20steps_k4_budget16GiB"
-    out["grid_bytes_fp32"] = nx * ny * nz * 4
-    out["note"] = ("out of core by the device budget (16 GiB); the field alone is 134 GB and the "
-                   "GB300 has 284 GB of HBM")
-    out["speedup_rate16_vs_uncompressed"] = out["rate0"]["ms"] / out["rate16"]["ms"]
-    out["accuracy_rate16_vs_uncompressed"] = {
-        "samples": len(samples), "rel_l2": float(np.linalg.norm(err) / np.linalg.norm(values[0])),
-        "max_abs": float(np.abs(err).max()), "stated_max_rel_l2": 1e-4}
-    return out
-
-
 ADJ_N, ADJ_STEPS, ADJ_EVERY, ADJ_RATE = 256, 400, 10, 16
 
 
@@ -859,111 +1121,43 @@ def run_adjoint(P, torch, dev, hbm_peak):
             "out_of_core": ooc}
 
 
-def codec_kernel_rates(P, torch, dev, rate, hbm_peak, reps=10):
-    """Live rates of the codec kernels alone: encode and decode of a 512 x 512
-    x 192 field (201 MB FP32, above the 129 MB L2) at `rate`, each codec,
-    CUDA events over `reps` launches after a warm-up.  Algorithmic bytes per
-    value: 4 (FP32) + rate/8 (compressed)."""
-    nz = 192
-    noise = torch.randn((nz, N, N), device=dev) * 1e-3
-    zero = torch.zeros_like(noise)  # the sweep's fields are mostly all-zero blocks (a point source from rest)
-    g = torch.empty_like(noise)
-    blocks = torch.empty(N * N * nz * rate // 32, dtype=torch.int32, device=dev)
-    s = torch.cuda.current_stream(dev).cuda_stream
-    vals = N * N * nz
-    out = {}
-    for name, codec, f in (("transform", 0, noise), ("quant", 1, noise), ("transform_zero_field", 0, zero)):
-        enc = lambda: P.oocs_encode_device(f.data_ptr(), N, N, nz, rate, blocks.data_ptr(), s, codec=codec)
-        dec = lambda: P.oocs_decode_device(blocks.data_ptr(), N, N, nz, rate, g.data_ptr(), s, codec=codec)
-        r = {}
-        for kind, fn in (("encode", enc), ("decode", dec)):
-            fn()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(reps):
-                fn()
-            e1.record()
-            torch.cuda.synchronize(dev)
-            ms = e0.elapsed_time(e1) / reps
-            gbs = vals * (4 + rate / 8) / (ms / 1e3) / 1e9
-            r[kind] = {"avg_launch_ms": ms, "gvalues_per_s": vals / (ms / 1e3) / 1e9, "achieved_gbs": gbs,
-                       "frac_of_hbm": gbs / hbm_peak}
-        out[name] = r
-    del noise, zero, g, blocks
-    torch.cuda.empty_cache()
-    return {"grid": [N, N, nz], "rate": rate, "bytes_per_value": 4 + rate / 8, **out}
-
-
-def check_accuracy(P, torch, dev, rate, inputs, codec=0, ref=None):
-    """Compressed run of the workload (100 steps from rest) against the
-    uncompressed in-core GPU run of the same FP32 arithmetic (which the tests
-    hold within 1e-5 of the FP64 oracle); `ref` reuses that run."""
-    import numpy as np
-
-    import synthetic
-    st, pin = open_ctx(P, torch, rate, 1, inputs, codec=codec)
-    st.step(STEPS_PER_CALL)
-    st.synchronize(600.0)
-    out = st.decompress(P.OOCS_FIELD_U)
-    st.synchronize(600.0)
-    got = out.numpy().astype(np.float64)
-    st.close()
-    del st, pin
-    torch.cuda.empty_cache()
-    if ref is None:
-        ref = incore_reference(P, torch, dev, inputs)
-    rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-    tol = synthetic.TOL_COMPRESSED.get(rate) if rate else synthetic.TOL_UNCOMPRESSED["wave"]
-    return {"rel_l2_vs_uncompressed_fp32": rel, "max_abs": float(np.max(np.abs(got - ref))),
-            "max_ref": float(np.max(np.abs(ref))), "stated_max_rel_l2": tol,
-            "within": bool(tol is not None and rel <= tol)}
-
-
-def incore_reference(P, torch, dev, inputs):
-    """The workload's 100 steps from rest, uncompressed and in core on the GPU (FP64 copy of u)."""
-    import numpy as np
-    m, w, src, z = inputs
-    u = torch.zeros((N, N, N), device=dev)
-    up = torch.zeros((N, N, N), device=dev)
-    mm = torch.from_numpy(m).to(dev)
-    sc = torch.empty_like(u)
-    srcv = (src[0], src[1], src[2])
-    P.oocs_incore_run(wave_desc(P, 0), u.data_ptr(), up.data_ptr(), mm.data_ptr(), sc.data_ptr(),
-                      STEPS_PER_CALL, 0, srcv, w, torch.cuda.current_stream(dev).cuda_stream)
-    ref = u.cpu().numpy().astype(np.float64)
-    del u, up, mm, sc
-    torch.cuda.empty_cache()
-    return ref
-
-
 # ------------------------------------------------------------ reference --
 
 def run_reference(args):
+    """The FP64 oracle on a bounded sample of the headline workload: each step
+    is CUBES_PER_REF_STEP dependency cubes (20 heat steps in 5 passes, each
+    pass followed by the reference codec's round trip at rate 16), counting
+    the central CUBE_IN^3 points of each cube."""
     rank, world, local = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
-    inputs = make_inputs(K_DEPTH * (args.warmup + args.steps + 1))
-    for _ in range(args.warmup):
-        cpu_oracle_sample(inputs, args.rate)
+    shape = OOC_SHAPE
+    origins = cube_origins(shape, CUBES_PER_REF_STEP * (args.warmup + args.steps), seed=33)
+    chunks = [origins[i:i + CUBES_PER_REF_STEP] for i in range(0, len(origins), CUBES_PER_REF_STEP)]
+    for c in chunks[:args.warmup]:
+        oracle_cubes(shape, c, OOC_RATE)
     times = []
-    for _ in range(args.steps):
-        dt, npts, cores = cpu_oracle_sample(inputs, args.rate)
+    cores = oracle.threads()
+    for c in chunks[args.warmup:]:
+        dt, _, cores = oracle_cubes(shape, c, OOC_RATE)
         times.append(dt)
     total = sum(times)
-    value = npts * len(times) / total / 1e9
-    line = base_line(args, world)
-    sample = (f"per step: 4 FP64 leapfrog steps on a 512x512x{SAMPLE_PLANES} sub-grid of the "
-              f"model + reference codec round trip of u, u_prev, m at rate {args.rate}")
+    value = CUBES_PER_REF_STEP * CUBE_IN ** 3 * OOC_STEPS * len(times) / total / 1e9
+    line = base_line(args, world, shape[0])
+    sample = (f"per step: {CUBES_PER_REF_STEP} seeded cubes of {CUBE_IN + 2 * CUBE_HALO}^3 values of the "
+              f"workload's field, 20 FP64 heat steps in 5 passes each followed by the reference codec round "
+              f"trip at rate {OOC_RATE}; counts the {CUBE_IN}^3 central points per cube")
     line.update({"impl": "reference", "value": value, "ms_per_step": total / len(times) * 1e3,
                  "dtype": "f64",
                  "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                                   "sample": sample},
-                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                         "d2h_bytes_per_step": 0}})
+                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
     print(json.dumps(line), flush=True)
 
+
+# --------------------------------------------------------------- ncu runs --
 
 def run_profile(args):
     """Workloads for ncu: the captured region is bracketed by cudaProfilerStart/Stop."""
@@ -974,9 +1168,27 @@ def run_profile(args):
     import synthetic
     dev = torch.device("cuda", 0)
     P.lib()
+    if args.profile_run == "ooc":
+        nz = args.planes or OOC_SHAPE[0]
+        shape = (nz, OOC_SHAPE[1], OOC_SHAPE[2])
+        desc = ooc_desc(P, OOC_RATE, nz)
+        plan = P.oocs_query(desc)
+        host = P.HostBuffer(plan.host_store_bytes)
+        st = P.OutOfCoreStencil(desc, stores=[host.tensor()])
+        fill_store(P, torch, st, shape)
+        timed_call(torch, st, OOC_STEPS)
+        fill_store(P, torch, st, shape)
+        torch.cuda.profiler.start()
+        st.step(OOC_STEPS)
+        st.synchronize(3600.0)
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_run": "ooc", "grid": [shape[2], shape[1], nz], "stats": st.stats()}))
+        st.close()
+        host.close()
+        return
     if args.profile_run == "sweep":
         inputs = make_inputs(3 * STEPS_PER_CALL)
-        st, pin = open_ctx(P, torch, args.rate, 1, inputs)
+        st, pin = open_ctx(P, torch, RATE, 1, inputs)
         snap = st.snapshot_stores()
         st.step(STEPS_PER_CALL)
         st.synchronize(600.0)
@@ -988,33 +1200,44 @@ def run_profile(args):
         print(json.dumps({"profile_run": "sweep", "stats": st.stats()}))
         st.close()
         return
+    # one launch of each kernel on grids above the 129 MB L2, in this order:
+    # heat step (2560 x 2560 x 32), wave step (512 x 512 x 192), encode and
+    # decode (512 x 512 x 192 noise, transform codec), wave step (512 x 512 x 80),
+    # quantiser encode and decode, adjoint step and gradient step (512 x 512 x 192)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    hz = 32
+    hshape = (hz, OOC_SHAPE[1], OOC_SHAPE[2])
+    hu = synthetic.uniform_field_planes_torch(hshape, OOC_SEED, 0, hz, device=dev)
+    hsc = torch.empty_like(hu)
+    dh = ooc_desc(P, 0, hz)
     nz = 192
     shape = (nz, N, N)
     m = torch.from_numpy(synthetic.wave_model(shape)).to(dev)
     u = torch.randn(shape, device=dev) * 1e-3
     up = torch.randn(shape, device=dev) * 1e-3
     sc = torch.empty_like(u)
-    blocks = torch.empty(N * N * nz * args.rate // 32, dtype=torch.int32, device=dev)
-    s = torch.cuda.current_stream(dev).cuda_stream
+    blocks = torch.empty(N * N * nz * RATE // 32, dtype=torch.int32, device=dev)
     d = P.make_desc(N, N, nz, P.OOCS_WAVE, synthetic.wave_star_coef(), BUDGET, rate_bits=0,
                     temporal_depth=K_DEPTH, slab_planes=SLAB)
-    # an 80-plane grid: the window size of the sweep's balanced step launches
     d80 = P.make_desc(N, N, 80, P.OOCS_WAVE, synthetic.wave_star_coef(), BUDGET, rate_bits=0,
                       temporal_depth=K_DEPTH, slab_planes=SLAB)
     u80, up80, sc80, m80 = (t[:80].clone() for t in (u, up, sc, m))
+    lam, mu, mo = torch.randn_like(u) * 1e-3, torch.randn_like(u) * 1e-3, torch.empty_like(u)
+    g = torch.zeros_like(u)
     torch.cuda.synchronize(dev)
     torch.cuda.profiler.start()
+    P.oocs_incore_run(dh, hu.data_ptr(), 0, 0, hsc.data_ptr(), 1, 0, None, None, s)
     P.oocs_incore_run(d, u.data_ptr(), up.data_ptr(), m.data_ptr(), sc.data_ptr(), 1, 0, None, None, s)
-    P.oocs_encode_device(u.data_ptr(), N, N, nz, args.rate, blocks.data_ptr(), s)
-    P.oocs_decode_device(blocks.data_ptr(), N, N, nz, args.rate, sc.data_ptr(), s)
-    P.oocs_incore_run(d80, u80.data_ptr(), up80.data_ptr(), m80.data_ptr(), sc80.data_ptr(), 1, 0, None, None,
-                      s)
-    # the block quantiser's kernels on the same field and rate
-    P.oocs_encode_device(u.data_ptr(), N, N, nz, args.rate, blocks.data_ptr(), s, codec=1)
-    P.oocs_decode_device(blocks.data_ptr(), N, N, nz, args.rate, sc.data_ptr(), s, codec=1)
+    P.oocs_encode_device(u.data_ptr(), N, N, nz, RATE, blocks.data_ptr(), s)
+    P.oocs_decode_device(blocks.data_ptr(), N, N, nz, RATE, sc.data_ptr(), s)
+    P.oocs_incore_run(d80, u80.data_ptr(), up80.data_ptr(), m80.data_ptr(), sc80.data_ptr(), 1, 0, None, None, s)
+    P.oocs_encode_device(u.data_ptr(), N, N, nz, RATE, blocks.data_ptr(), s, codec=1)
+    P.oocs_decode_device(blocks.data_ptr(), N, N, nz, RATE, sc.data_ptr(), s, codec=1)
+    P.oocs_adjoint_step(d, lam.data_ptr(), up.data_ptr(), mu.data_ptr(), mo.data_ptr(), m.data_ptr(), 0, -1, s)
+    P.oocs_gradient_accumulate(d, g.data_ptr(), lam.data_ptr(), u.data_ptr(), 0.5, (N // 2, N // 2, nz // 2), s)
     torch.cuda.synchronize(dev)
     torch.cuda.profiler.stop()
-    print(json.dumps({"profile_run": "kernels", "grid": [N, N, nz], "rate": args.rate,
+    print(json.dumps({"profile_run": "kernels", "rate": RATE,
                       "finite": bool(np.isfinite(sc.cpu().numpy()).all())}))
 
 

@@ -275,3 +275,22 @@ def uniform_field_planes_torch(shape, seed: int, z0: int, z1: int, device="cpu")
     f[:, :, 0] = 0.0
     f[:, :, -1] = 0.0
     return f
+
+
+def uniform_field_box(shape, seed: int, z0: int, y0: int, x0: int, n: int) -> np.ndarray:
+    """The n^3 box of uniform_field(shape, seed) starting at (z0, y0, x0), drawn
+    directly from the counter (no need to hold the field); the box must lie
+    inside the grid, and the field's zero shell (any index 0 or n-1) is kept."""
+    nz, ny, nx = shape
+    assert 0 <= z0 and z0 + n <= nz and 0 <= y0 and y0 + n <= ny and 0 <= x0 and x0 + n <= nx
+    z = np.arange(z0, z0 + n, dtype=np.uint64)[:, None, None]
+    y = np.arange(y0, y0 + n, dtype=np.uint64)[None, :, None]
+    x = np.arange(x0, x0 + n, dtype=np.uint64)[None, None, :]
+    key = _key(seed, 0)
+    with np.errstate(over="ignore"):
+        idx = (z * np.uint64(ny) + y) * np.uint64(nx) + x + key
+    bits = splitmix64(idx) >> np.uint64(40)
+    f = (bits.astype(np.float64) * (1.0 / 16777216.0)).astype(np.float32)
+    shell = ((z == 0) | (z == nz - 1)) | ((y == 0) | (y == ny - 1)) | ((x == 0) | (x == nx - 1))
+    f[np.broadcast_to(shell, f.shape)] = 0.0
+    return f

@@ -26,8 +26,8 @@ def _rank(rank, world, port, q):
         value = bench.replica_throughput(1e9, w, ms)
 
         class A:
-            steps, warmup, rate = 5, 3, 16
-        line = bench.base_line(A, w)
+            steps, warmup = 5, 3
+        line = bench.base_line(A, w, bench.OOC_SHAPE[0])
         q.put((r, w, local, ms, value, line["n_gpus"], line["config"]["parallelism"], line["scaling"]))
     finally:
         dist.destroy_process_group()
@@ -58,3 +58,36 @@ def test_one_process_needs_no_group():
     import bench
     assert bench.max_over_ranks(torch, 12.5, "cpu") == 12.5
     assert bench.replica_throughput(2e9, 1, 1000.0) == pytest.approx(2.0)
+
+
+def test_headline_planes_follow_host_memory():
+    """Each replica holds one raw FP32 array of its grid in pinned host memory:
+    the headline keeps nz = 5120 when the host holds it, else shrinks nz (a
+    multiple of 64) to what fits, per rank."""
+    import bench
+
+    class A:
+        planes = 0
+    plane = bench.OOC_SHAPE[1] * bench.OOC_SHAPE[2] * 4
+    real = bench.host_mem_available
+    try:
+        bench.host_mem_available = lambda: 199 * 10 ** 9
+        assert bench.ooc_planes(A, 1) == 5120
+        nz2 = bench.ooc_planes(A, 2)
+        assert nz2 % 64 == 0 and nz2 * plane <= 0.9 * 199e9 / 2 and nz2 < 5120
+        bench.host_mem_available = lambda: None
+        assert bench.ooc_planes(A, 8) == 5120
+    finally:
+        bench.host_mem_available = real
+    A.planes = 512
+    assert bench.ooc_planes(A, 1) == 512
+
+
+def test_cube_origins_are_block_aligned_and_inside():
+    import bench
+    shape = bench.OOC_SHAPE
+    side = bench.CUBE_IN + 2 * bench.CUBE_HALO
+    for o in bench.cube_origins(shape, 64):
+        for a in range(3):
+            assert o[a] % 4 == 0
+            assert o[a] - bench.CUBE_HALO >= 1 and o[a] - bench.CUBE_HALO + side <= shape[a] - 1

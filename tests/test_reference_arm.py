@@ -19,7 +19,7 @@ def test_reference_arm_line():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "Gpoint-updates/s"
     assert line["higher_is_better"] is True and line["dtype"] == "f64" and line["data"] == "synthetic"
-    assert line["config"]["workload"].startswith("wave25_512cubed")
+    assert line["config"]["workload"].startswith("heat7_2560x2560x5120")
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]

@@ -32,3 +32,11 @@ def test_batch_shapes_recipe():
     assert sides.min() >= 64 and sides.max() <= 384 and np.all(sides % 16 == 0)
     assert len(set(sides.tolist())) > 10  # uneven
     assert sh == synthetic.batch_shapes(64)  # seeded
+
+
+def test_uniform_field_box_is_a_window_of_the_field():
+    shape = (20, 24, 28)
+    full = synthetic.uniform_field(shape, 7)
+    for (z0, y0, x0, n) in ((0, 0, 0, 8), (5, 9, 13, 7), (12, 16, 20, 8)):
+        box = synthetic.uniform_field_box(shape, 7, z0, y0, x0, n)
+        assert np.array_equal(box, full[z0:z0 + n, y0:y0 + n, x0:x0 + n])
