@@ -939,7 +939,20 @@ def run_batched(P, torch, dev):
         else:
             descs.append(P.make_desc(nx, ny, nz, P.OOCS_WAVE, synthetic.wave_star_coef(), BATCH_BUDGET))
     cache = os.path.join(tempfile.gettempdir(), f"oocs_autotune_{os.getpid()}.json")
-    tuned, report = autotune.tune(descs, BATCH_TOL, BATCH_BUDGET, cache)
+    shapes = synthetic.batch_shapes(BATCH_N)
+
+    class ProblemData:
+        """Each problem's own seeded initial fields, drawn when the tuner asks."""
+
+        def __getitem__(self, i):
+            sc, shape = shapes[i]
+            if sc == "heat":
+                return {P.OOCS_FIELD_U: synthetic.uniform_field(shape, 100 + i)}
+            u0 = synthetic.wave_initial(shape, 200 + i)
+            return {P.OOCS_FIELD_U: u0, P.OOCS_FIELD_U_PREV: u0, P.OOCS_FIELD_M: synthetic.wave_model(shape)}
+
+    tuned, report = autotune.tune(descs, BATCH_TOL, BATCH_BUDGET, cache, data=ProblemData(),
+                                  err_steps=BATCH_STEPS)
     t_tune = time.time() - t0
     b = P.OutOfCoreBatch(tuned)
     for i, (bp, d) in enumerate(zip(b.problems, tuned)):
@@ -1005,6 +1018,7 @@ def run_batched(P, torch, dev):
               for d in tuned) * BATCH_STEPS
     gpts = lambda ms: pts / (ms / 1e3) / 1e9
     rates, slabs, depths = {}, {}, {}
+    errors = {r["class"]: r["errors"] for r in report["problems"]}
     for r in report["problems"]:
         rates[r["rate"]] = rates.get(r["rate"], 0) + 1
         slabs[r["slabs"]] = slabs.get(r["slabs"], 0) + 1
@@ -1020,7 +1034,9 @@ def run_batched(P, torch, dev):
             "sum_of_alone_workspaces": int(sum(ws_alone)), "kernel_launches_per_batch_step": launches_per_step,
             "tuning": {"seconds": t_tune, "classes": report["classes"],
                        "candidates_timed": report["candidates_timed"], "rates": rates, "slabs": slabs,
-                       "temporal_depths": depths}}
+                       "temporal_depths": depths, "measured_rate_errors_by_class": errors,
+                       "rate_rule": f"lowest rate with measured rel-L2 <= {autotune.ERROR_MARGIN} x tolerance "
+                                    f"after {BATCH_STEPS} steps at the shallowest depth"}}
 
 
 ADJ_N, ADJ_STEPS, ADJ_EVERY, ADJ_RATE = 256, 400, 10, 16

@@ -4,22 +4,27 @@ The knobs of the out-of-core sweep (Sec. 3.1 temporal blocking, Sec. 4.2
 fixed rate) trade redundant halo work, pipeline depth and link bytes against
 each other differently for every grid, so they are measured, not modelled:
 
-* rates: those whose error bar meets the requested tolerance (the bars the
-  test suite holds each rate to, rel-L2 against the FP64 oracle: 1e-4 at 16
-  bits/value, 2e-3 at 12, 3e-2 at 8; rate 0 is exact);
+* rate: measured on the problem's own seeded data.  The problem runs
+  `err_steps` time steps uncompressed and at each rate in {8, 12, 16} with the
+  shallowest temporal depth tried (the most codec round trips of any
+  candidate); the lowest rate whose relative L2 error against the
+  uncompressed run is within half the tolerance is taken (rate 0 when none
+  is);
 * slabs: S in {1, 2, 4} (T = nz / S rounded up to the 4-plane layer), kept
   only when T >= 2 h so region sharing holds and the plan fits the budget;
 * temporal depth: k in {2, 4, 8} for the 7-point heat stencil, {2, 4} for the
   25-point wave stencil.
 
-Each candidate runs `steps` time steps of the problem's own grid on seeded
-data through a fresh context (one warm-up call, one call timed with CUDA
-events) and the fastest is kept.  Problems are grouped into classes (scheme
-and the rounded cube root of the volume); one problem per class is timed and
-its (S, k, rate) is applied to the class.  Choices are cached in a JSON file
-keyed by class, budget and tolerance.  The tile shape of the step kernel is
-fixed (64 x 16, the layout of its TMA rings); its launch geometry is chosen
-per launch by the occupancy model in the library.
+Each (S, k) candidate at the chosen rate runs `steps` time steps of the
+problem's grid through a fresh context: one warm-up call, then the median of
+`reps` calls timed with CUDA events on stream 0 (every oocs_step joins its
+three streams into stream 0 at its end, so the event follows the last copy).
+Problems are grouped into classes (scheme and the rounded cube root of the
+volume); one problem per class is measured and its (S, k, rate) is applied to
+the class.  Choices are cached in a JSON file keyed by class, budget and
+tolerance.  The tile shape of the step kernel is fixed (64 x 16, the layout of
+its TMA rings); its launch geometry is chosen per launch by the occupancy
+model in the library.
 """
 from __future__ import annotations
 
@@ -31,15 +36,16 @@ import numpy as np
 
 from . import oocs as O
 
-RATE_REL_L2 = {0: 0.0, 16: 1e-4, 12: 2e-3, 8: 3e-2}
+RATES = (8, 12, 16)
+ERROR_MARGIN = 0.5  # a rate is taken when its measured error is within this share of the tolerance
 SLABS = (1, 2, 4)
 DEPTHS = {O.OOCS_HEAT: (2, 4, 8), O.OOCS_WAVE: (2, 4)}
 
 
-def rates_for(tol: float):
-    """Compressed rates whose error bar meets tol; uncompressed (0) when none does."""
-    r = [q for q in (8, 12, 16) if RATE_REL_L2[q] <= tol]
-    return r or [0]
+def rate_for(errors: dict, tol: float) -> int:
+    """The lowest rate whose measured error is within ERROR_MARGIN * tol; 0 when none is."""
+    ok = [r for r in sorted(errors) if r and errors[r] <= ERROR_MARGIN * tol]
+    return ok[0] if ok else 0
 
 
 def with_plan(desc, slabs: int, k: int, rate: int):
@@ -68,19 +74,23 @@ def class_key(desc, budget: int, tol: float) -> str:
 
 
 class _Probe:
-    """Seeded FP32 fields of one grid and host stores, pinned once and reused
-    by every candidate of the grid."""
+    """FP32 fields of one grid and host stores, pinned once and reused by every
+    candidate of the grid: the problem's own initial fields when given
+    (`data`: field id -> array), else seeded stand-ins of the same kind."""
 
-    def __init__(self, desc, seed: int = 0):
+    def __init__(self, desc, seed: int = 0, data=None):
         import torch
         shape = (int(desc.nz), int(desc.ny), int(desc.nx))
         rng = np.random.default_rng(seed)
         nf = 1 if desc.scheme == O.OOCS_HEAT else 3
+        self.shape = shape
         self.fields = {}
         for f in range(nf):
             t = torch.empty(shape, dtype=torch.float32, pin_memory=True)
             a = t.numpy()
-            if desc.scheme == O.OOCS_HEAT:
+            if data is not None and f in data:
+                a[...] = np.asarray(data[f], dtype=np.float32).reshape(shape)
+            elif desc.scheme == O.OOCS_HEAT:
                 a[...] = rng.random(shape, dtype=np.float32)
             elif f == O.OOCS_FIELD_M:
                 a[...] = 0.02 + 0.1 * rng.random(shape, dtype=np.float32)
@@ -91,8 +101,9 @@ class _Probe:
         self.stores = [torch.empty(raw, dtype=torch.uint8, pin_memory=True) for _ in range(nf)]
 
 
-def time_candidate(desc, steps: int, probe: _Probe | None = None) -> float:
-    """Milliseconds per time step of one oocs_step(steps) call on seeded data."""
+def time_candidate(desc, steps: int, probe: _Probe | None = None, reps: int = 3) -> float:
+    """Milliseconds per time step: the median of `reps` oocs_step(steps) calls
+    after one warm-up call, on the probe's data."""
     import torch
     probe = probe or _Probe(desc)
     st = O.OutOfCoreStencil(desc, stores=probe.stores)
@@ -102,55 +113,95 @@ def time_candidate(desc, steps: int, probe: _Probe | None = None) -> float:
         st.synchronize(600.0)
         st.step(steps)
         st.synchronize(600.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st.streams[0])
-        st.step(steps)
-        e1.record(st.streams[0])
-        st.synchronize(600.0)
-        e1.synchronize()
-        return e0.elapsed_time(e1) / steps
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st.streams[0])
+            st.step(steps)
+            e1.record(st.streams[0])  # oocs_step ends with a join of its streams into stream 0
+            st.synchronize(600.0)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / steps)
+        return float(np.median(times))
     finally:
         st.close()
 
 
-def tune_one(desc, tol: float, steps: int = 4):
-    """(best desc, ms per step, every candidate timed) for one problem."""
+def measure_rate_errors(desc, steps: int, probe: _Probe, rates=RATES) -> dict:
+    """Relative L2 error of u after `steps` time steps at each rate against the
+    uncompressed run of the same plan (one slab, the shallowest depth tried:
+    the most codec round trips of any candidate), on the probe's data."""
+    k = min(DEPTHS[desc.scheme])
+
+    def run(rate):
+        d = with_plan(desc, 1, k, rate)
+        if d is None:
+            return None
+        st = O.OutOfCoreStencil(d, stores=probe.stores)
+        try:
+            for f, t in probe.fields.items():
+                st.compress(f, t)
+            st.step(steps)
+            out = st.decompress(O.OOCS_FIELD_U)
+            st.synchronize(600.0)
+            return out.numpy().astype(np.float64)
+        finally:
+            st.close()
+
+    ref = run(0)
+    errs = {}
+    for r in rates:
+        got = run(r)
+        if ref is None or got is None:
+            continue
+        errs[r] = float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
+    return errs
+
+
+def tune_one(desc, tol: float, steps: int = 4, data=None, err_steps: int | None = None):
+    """(best desc, ms per step, every candidate timed, measured errors by rate)
+    for one problem."""
     tried = []
     best, best_ms = None, math.inf
-    probe = _Probe(desc)
-    for rate in rates_for(tol):
-        for slabs in SLABS:
-            for k in DEPTHS[desc.scheme]:
-                d = with_plan(desc, slabs, k, rate)
-                if d is None:
-                    continue
-                ms = time_candidate(d, max(steps, k), probe)
-                tried.append({"slabs": slabs, "k": k, "rate": rate, "ms_per_step": ms})
-                if ms < best_ms:
-                    best, best_ms = d, ms
-    return best, best_ms, tried
+    probe = _Probe(desc, data=data)
+    errors = measure_rate_errors(desc, err_steps or steps, probe)
+    rate = rate_for(errors, tol)
+    for slabs in SLABS:
+        for k in DEPTHS[desc.scheme]:
+            d = with_plan(desc, slabs, k, rate)
+            if d is None:
+                continue
+            ms = time_candidate(d, max(steps, k), probe)
+            tried.append({"slabs": slabs, "k": k, "rate": rate, "ms_per_step": ms})
+            if ms < best_ms:
+                best, best_ms = d, ms
+    return best, best_ms, tried, errors
 
 
-def tune(descs, tol: float, budget: int, cache_path: str | None = None, steps: int = 4):
-    """Tuned copies of descs (and a report).  The batch of the tuned descs is
-    kept within `budget` bytes of shared workspace by adding slabs to the
-    largest problems if needed."""
+def tune(descs, tol: float, budget: int, cache_path: str | None = None, steps: int = 4, data=None,
+         err_steps: int | None = None):
+    """Tuned copies of descs (and a report).  data: optional per-problem dict
+    (field id -> initial array) on which a class's rate error is measured;
+    err_steps: time steps of that measurement (default `steps`).  The batch of
+    the tuned descs is kept within `budget` bytes of shared workspace by adding
+    slabs to the largest problems if needed."""
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
             cache = json.load(f)
     out, report, timed = [], [], 0
-    for d in descs:
+    for i, d in enumerate(descs):
         d = O.oocs_desc.from_buffer_copy(d)
         d.device_budget = budget
         key = class_key(d, budget, tol)
         if key not in cache:
-            best, ms, tried = tune_one(d, tol, steps)
+            best, ms, tried, errors = tune_one(d, tol, steps, data[i] if data is not None else None, err_steps)
             timed += len(tried)
             if best is None:
                 raise O.OOCSError(2, f"no plan of {key} fits the budget")
             cache[key] = {"slabs": -(-int(d.nz) // int(best.slab_planes)), "k": int(best.temporal_depth),
-                          "rate": int(best.rate_bits), "ms_per_step": ms, "tried": tried}
+                          "rate": int(best.rate_bits), "ms_per_step": ms, "tried": tried,
+                          "errors": {str(r): e for r, e in errors.items()}}
         c = cache[key]
         t = with_plan(d, c["slabs"], c["k"], c["rate"])
         slabs = c["slabs"]
@@ -158,7 +209,8 @@ def tune(descs, tol: float, budget: int, cache_path: str | None = None, steps: i
             slabs *= 2
             t = with_plan(d, slabs, c["k"], c["rate"])
         out.append(t)
-        report.append({"class": key, "slabs": slabs, "k": c["k"], "rate": c["rate"]})
+        report.append({"class": key, "slabs": slabs, "k": c["k"], "rate": c["rate"],
+                       "errors": c.get("errors", {})})
     # shared workspace of the batch within the budget: split the largest windows
     while O.oocs_batch_query(out) > budget:
         i = max(range(len(out)), key=lambda j: int(out[j].nx) * int(out[j].ny) * int(out[j].slab_planes))

@@ -327,13 +327,20 @@ OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink)
     bw.put((uint32_t)hdr, 8);
     int left = 64 * rate - 8;
     int n = 0;  // leading coefficients already significant
-    for (int p = 31; p >= 0 && left > 0; --p) {
+    // planes 31 .. 0, unrolled so that every plane word has a constant index
+    // and the 64 words stay in registers
+    static_for<0, 32>([&](auto I) {
+        constexpr int p = 31 - decltype(I)::value;
+        if (left <= 0)
+            return;
         const uint64_t X = ((uint64_t)hi[p] << 32) | lo[p];
         const int t = min(n, left);
         bw.put64(X, t);  // verbatim bits of the significant coefficients
         left -= t;
-        if (t < n)
-            break;
+        if (t < n) {
+            left = 0;
+            return;
+        }
         while (n < 64 && left > 0) {
             const uint64_t rest = X >> n;
             if (rest == 0) {  // group test: nothing new in this plane
@@ -354,7 +361,7 @@ OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink)
             left -= len;
             n = f + 1;
         }
-    }
+    });
     bw.finish();
     return true;
 }
@@ -392,7 +399,11 @@ OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64])
     }
     int left = 64 * rate - 8;
     int n = 0;
-    for (int p = 31; p >= 0 && left > 0; --p) {
+    // planes 31 .. 0, unrolled (constant plane indices: the words stay in registers)
+    static_for<0, 32>([&](auto I) {
+        constexpr int p = 31 - decltype(I)::value;
+        if (left <= 0)
+            return;
         const int t = min(n, left);
         uint64_t X = br.get64(t);
         left -= t;
@@ -463,7 +474,7 @@ OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64])
         }
         lo[p] = (uint32_t)X;
         hi[p] = (uint32_t)(X >> 32);
-    }
+    });
     transpose32(lo);  // back to coefficient words
     transpose32(hi);
 

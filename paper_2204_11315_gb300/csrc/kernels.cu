@@ -879,8 +879,10 @@ OOCS_FN void store_block(const CodecSegments &sg, int g, int nx, int ny, int bx,
                             v[16 * k + 4 * j + 3]);
 }
 
+// the transform decoder holds the 64 plane words, the bit reader and the
+// token state at once: 5 CTAs per SM leave it 96 registers (no spills)
 template <int KIND>
-__global__ void __launch_bounds__(kCodecThreads, 6)
+__global__ void __launch_bounds__(kCodecThreads, KIND == kCodecTransform ? 5 : 6)
     k_decode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
     extern __shared__ uint32_t sw[];

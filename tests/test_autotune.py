@@ -26,12 +26,21 @@ def A(monkeypatch):
         return 1.0 * S + abs(int(desc.temporal_depth) - 4) * 0.1 + int(desc.rate_bits) * 0.01
 
     class NoProbe:
-        def __init__(self, desc, seed=0):
-            pass
+        def __init__(self, desc, seed=0, data=None):
+            self.data = data
+
+    errors = {8: 3e-3, 12: 2e-4, 16: 1e-5}
+
+    def fake_errors(desc, steps, probe, rates=A.RATES):
+        A.err_calls.append((int(desc.nz), steps, probe.data))
+        return {r: errors[r] for r in rates}
 
     monkeypatch.setattr(A, "time_candidate", fake_time)
+    monkeypatch.setattr(A, "measure_rate_errors", fake_errors)
     monkeypatch.setattr(A, "_Probe", NoProbe)
     A.calls = calls
+    A.err_calls = []
+    A.errors = errors
     return A
 
 
@@ -43,11 +52,22 @@ def _heat(P, nz, ny, nx, budget=8 << 30):
     return P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), budget)
 
 
-def test_rates_follow_the_tolerance(A):
-    assert A.rates_for(1e-4) == [16]
-    assert A.rates_for(2e-3) == [12, 16]
-    assert A.rates_for(0.05) == [8, 12, 16]
-    assert A.rates_for(1e-6) == [0]
+def test_rate_follows_the_measured_error(A):
+    e = {8: 3e-3, 12: 2e-4, 16: 1e-5}
+    assert A.rate_for(e, 1e-4) == 16        # 1e-5 <= 0.5e-4
+    assert A.rate_for(e, 2e-3) == 12        # 2e-4 <= 1e-3 < 3e-3
+    assert A.rate_for(e, 0.05) == 8
+    assert A.rate_for(e, 1e-6) == 0         # nothing close enough: uncompressed
+    assert A.rate_for({8: 0.0, 16: 0.0}, 1e-9) == 8
+
+
+def test_rate_error_is_measured_on_the_problem_data(P, A):
+    descs = [_heat(P, 96, 96, 96), _wave(P, 64, 64, 64)]
+    data = [{0: "heat field"}, {0: "u", 2: "m"}]
+    out, rep = A.tune(descs, 1e-4, 8 << 30, data=data, err_steps=50)
+    assert [c[2] for c in A.err_calls] == data and all(c[1] == 50 for c in A.err_calls)
+    assert [r["rate"] for r in rep["problems"]] == [16, 16]
+    assert rep["problems"][0]["errors"] == {"8": 3e-3, "12": 2e-4, "16": 1e-5}
 
 
 def test_candidate_plans_respect_region_sharing(P, A):
