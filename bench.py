@@ -93,11 +93,13 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--planes", type=int, default=0,
                     help="nz of the headline grid (default: 5120, fewer if host memory is short)")
-    ap.add_argument("--profile-run", choices=["ooc", "sweep", "kernels"], default=None,
+    ap.add_argument("--profile-run", choices=["ooc", "sweep", "kernels", "adjoint"], default=None,
                     help="run only the region to capture under ncu --profile-from-start off: "
                          "'ooc' = one oocs_step(20) of the headline workload; 'sweep' = one "
                          "oocs_step(100) of the 512^3 wave workload; 'kernels' = one launch each of "
-                         "the step kernels (heat, wave, adjoint, gradient) and the codec kernels")
+                         "the step kernels (heat, wave, adjoint, gradient) and the codec kernels; "
+                         "'adjoint' = the backward pass of an out-of-core misfit gradient (256^3, "
+                         "20 steps, 4 slabs), whose sweep also runs k_product")
     return ap.parse_args()
 
 
@@ -1201,6 +1203,26 @@ def run_profile(args):
         print(json.dumps({"profile_run": "ooc", "grid": [shape[2], shape[1], nz], "stats": st.stats()}))
         st.close()
         host.close()
+        return
+    if args.profile_run == "adjoint":
+        import paper_2204_11315_gb300.adjoint as A
+        n, steps = 256, 20
+        shape = (n, n, n)
+        v = torch.from_numpy(synthetic.layered_velocity(shape, seed=4).astype(np.float32)).to(dev)
+        prob = A.WaveProblem(shape=shape, dt=synthetic.WAVE_DT, dx=synthetic.WAVE_DX,
+                             coef=synthetic.wave_star_coef(), src_xyz=(n // 2, n // 2, 32),
+                             wavelet=synthetic.ricker(steps), zr=8, nsteps=steps, checkpoint_every=10, rate=16,
+                             device_budget=2 << 30, slab_planes=64)
+        d = A.receiver_data(v * 1.01, prob)
+        vt = v.clone().requires_grad_(True)
+        J = A.wave_misfit(vt, d, prob)
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.start()
+        J.backward()
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_run": "adjoint", "misfit": float(J.detach()),
+                          "grad_norm": float(vt.grad.norm())}))
         return
     if args.profile_run == "sweep":
         inputs = make_inputs(3 * STEPS_PER_CALL)
