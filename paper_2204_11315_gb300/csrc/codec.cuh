@@ -18,9 +18,12 @@
 // Decoding inverts them and returns RN(q) * 2^(emax-29).
 //
 // GPU design: one thread codes one block entirely in registers.  Bit planes are
-// formed by two 32x32 bit-matrix transposes (no per-bit loop), and each plane
-// is emitted in closed form: the verbatim part is one masked word, and each
-// group-test hit is one "1, zeros, 1" code found with a count-trailing-zeros.
+// formed by two 32x32 bit-matrix transposes (no per-bit loop), the plane loop
+// is unrolled (constant plane indices), and each plane is emitted in closed
+// form: the verbatim part is one masked word, and all of the plane's
+// group-test tokens are built as one string of at most 127 bits (a few
+// operations per newly significant coefficient) and written with one or two
+// puts.
 // A block holding an infinity or a NaN is coded as an all-zero block and
 // reported to the caller (encode_block returns false).
 #pragma once
@@ -341,26 +344,57 @@ OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink)
             left = 0;
             return;
         }
-        while (n < 64 && left > 0) {
-            const uint64_t rest = X >> n;
-            if (rest == 0) {  // group test: nothing new in this plane
-                bw.put(0u, 1);
-                --left;
-                break;
-            }
-            const int f = n + ctz64(rest);  // next significant coefficient
-            // group-test 1, zeros for n .. f-1, then a one (implied at f = 63)
-            const int len = (f < 63) ? (f - n + 2) : (64 - n);
-            const uint64_t code = (f < 63) ? ((1ull << (f - n + 1)) | 1ull) : 1ull;
-            if (len > left) {
-                bw.put64(code, left);
-                left = 0;
-                break;
-            }
-            bw.put64(code, len);
-            left -= len;
-            n = f + 1;
+        if (n == 64)  // every coefficient significant: the plane is all verbatim
+            return;
+        const uint64_t Y = X >> n;  // the bits of coefficients n .. 63
+        if (Y == 0) {  // group test 0: nothing new in this plane
+            bw.put(0u, 1);
+            --left;
+            return;
         }
+        // The plane's group-test tokens as one string.  With f_1 < .. < f_k
+        // the window positions of Y's ones, the tokens are a leading 1 (the
+        // first group test), then for each one its zeros and itself, followed
+        // by a 1 (the next group test) except after the last, which a 0 (the
+        // final group test) follows.  Window bit j therefore lands at
+        // j + 1 + (ones before j): the one of rank r (0-based) at f + r + 1
+        // and its group-test 1 at f + r + 2, i.e. the string is
+        // 1 | D << 1 | D << 2 with D = sum of 2^(f + r), cut after the last
+        // one (whose group-test 1 is dropped), then the final 0.  When the
+        // last one is coefficient 63 it is implied: neither it nor the final
+        // 0 is sent.  At most 127 bits: D is kept in two words.
+        uint64_t dlo = 0, dhi = 0, y = Y;
+        int k = 0;
+        do {
+            const int pos = ctz64(y) + k;
+            y &= y - 1;
+            if (pos < 64)
+                dlo |= 1ull << pos;
+            else
+                dhi |= 1ull << (pos - 64);
+            ++k;
+        } while (y);
+        const int fk = 63 - clz64(Y);        // window position of the last new one
+        const bool implied = n + fk == 63;
+        const int keep = fk + k + (implied ? 0 : 1);  // bits of the string before its tail
+        const int len = implied ? keep : keep + 1;    // + the final group-test 0
+        uint64_t tlo = 1ull | (dlo << 1) | (dlo << 2);
+        uint64_t thi = (dhi << 1) | (dlo >> 63) | (dhi << 2) | (dlo >> 62);
+        if (keep < 64) {
+            tlo &= (1ull << keep) - 1ull;
+            thi = 0;
+        } else if (keep < 128) {
+            thi &= (1ull << (keep - 64)) - 1ull;
+        }
+        const int w = min(len, left);  // the budget may cut the string
+        if (w > 64) {
+            bw.put64(tlo, 64);
+            bw.put64(thi, w - 64);
+        } else {
+            bw.put64(tlo, w);
+        }
+        left -= w;
+        n += fk + 1;
     });
     bw.finish();
     return true;

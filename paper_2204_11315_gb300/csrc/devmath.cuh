@@ -58,5 +58,7 @@ OOCS_FN float2 fma2_rn(float2 a, float2 b, float2 c)
 // index of the lowest set bit of a non-zero word
 OOCS_FN int ctz64(uint64_t x) { return __ffsll((long long)x) - 1; }
 OOCS_FN int ctz32(uint32_t x) { return __ffs((int)x) - 1; }
+// number of leading zero bits (64 for 0)
+OOCS_FN int clz64(uint64_t x) { return __clzll((long long)x); }
 // byte permute: result byte i = byte (s >> 4i) & 7 of the 8-byte value (y:x)
 OOCS_FN uint32_t prmt(uint32_t x, uint32_t y, uint32_t s) { return __byte_perm(x, y, s); }

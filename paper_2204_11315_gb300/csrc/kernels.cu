@@ -803,8 +803,10 @@ OOCS_FN uint32_t *segment_word(const CodecSegments &sg, int64_t blk, int rate, i
     return static_cast<uint32_t *>(sg.blocks[g]) + (blk - sg.first[g]) * (int64_t)(2 * rate) + wi;
 }
 
+// like the decoder, the transform encoder keeps its 64 plane words and the
+// plane's token string in registers: 5 CTAs per SM (96 registers, no spills)
 template <int KIND>
-__global__ void __launch_bounds__(kCodecThreads, 6)
+__global__ void __launch_bounds__(kCodecThreads, KIND == kCodecTransform ? 5 : 6)
     k_encode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
     extern __shared__ uint32_t sw[];
