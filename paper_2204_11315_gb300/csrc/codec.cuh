@@ -17,13 +17,13 @@
 // x, y, z; order by (i+j+k, i^2+j^2+k^2, index); negabinary; plane coding.
 // Decoding inverts them and returns RN(q) * 2^(emax-29).
 //
-// GPU design: one thread codes one block entirely in registers.  Bit planes are
-// formed by two 32x32 bit-matrix transposes (no per-bit loop), the plane loop
-// is unrolled (constant plane indices), and each plane is emitted in closed
-// form: the verbatim part is one masked word, and all of the plane's
-// group-test tokens are built as one string of at most 127 bits (a few
-// operations per newly significant coefficient) and written with one or two
-// puts.
+// GPU design: one thread codes one block.  Bit planes are formed by two 32x32
+// bit-matrix transposes in registers (no per-bit loop) and kept in the
+// thread's column of shared memory for the plane loop, and each plane is
+// emitted in closed form: the verbatim part is one masked word, and all of the
+// plane's group-test tokens are built as one string of at most 127 bits (a
+// few operations per newly significant coefficient) and written with one or
+// two puts.
 // A block holding an infinity or a NaN is coded as an all-zero block and
 // reported to the caller (encode_block returns false).
 #pragma once
@@ -176,6 +176,19 @@ OOCS_FN void transpose32(uint32_t (&a)[32])
 
 OOCS_FN uint64_t low_mask64(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
 
+// Where a thread keeps its block's 32 plane words (64 bits each) while the
+// plane loop walks them with a runtime index.  A rolled loop over register
+// arrays would put them in local memory anyway (and a loop unrolled 32 times
+// overflows the instruction cache), so the kernels give each thread a column
+// of shared memory: word p at base[p * stride] (stride = threads of the CTA,
+// so a warp's accesses fall in distinct banks).
+struct SharedPlanes {
+    uint64_t *base;
+    int stride;
+    OOCS_FN uint64_t get(int p) const { return base[p * stride]; }
+    OOCS_FN void set(int p, uint64_t w) { base[p * stride] = w; }
+};
+
 // ----------------------------------------------------------------- bit I/O --
 
 template <class Sink>
@@ -282,7 +295,7 @@ struct BitReader {
 // order.  Returns false for a block holding an infinity or a NaN, which is
 // written as an all-zero block (the codec is defined for finite values).
 template <class Sink>
-OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink)
+OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink, SharedPlanes planes)
 {
     const int nwords = 2 * rate;
     uint32_t mag = 0;
@@ -326,31 +339,27 @@ OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink)
     });
     transpose32(lo);  // lo[p] / hi[p]: plane p of coefficients 0..31 / 32..63
     transpose32(hi);
+#pragma unroll
+    for (int p = 0; p < 32; ++p)
+        planes.set(p, ((uint64_t)hi[p] << 32) | lo[p]);
 
     bw.put((uint32_t)hdr, 8);
     int left = 64 * rate - 8;
     int n = 0;  // leading coefficients already significant
-    // planes 31 .. 0, unrolled so that every plane word has a constant index
-    // and the 64 words stay in registers
-    static_for<0, 32>([&](auto I) {
-        constexpr int p = 31 - decltype(I)::value;
-        if (left <= 0)
-            return;
-        const uint64_t X = ((uint64_t)hi[p] << 32) | lo[p];
+    for (int p = 31; p >= 0 && left > 0; --p) {
+        const uint64_t X = planes.get(p);
         const int t = min(n, left);
         bw.put64(X, t);  // verbatim bits of the significant coefficients
         left -= t;
-        if (t < n) {
-            left = 0;
-            return;
-        }
+        if (t < n || left == 0)  // the budget ended inside (or right after) them
+            break;
         if (n == 64)  // every coefficient significant: the plane is all verbatim
-            return;
+            continue;
         const uint64_t Y = X >> n;  // the bits of coefficients n .. 63
         if (Y == 0) {  // group test 0: nothing new in this plane
             bw.put(0u, 1);
             --left;
-            return;
+            continue;
         }
         // The plane's group-test tokens as one string.  With f_1 < .. < f_k
         // the window positions of Y's ones, the tokens are a leading 1 (the
@@ -395,14 +404,14 @@ OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink)
         }
         left -= w;
         n += fk + 1;
-    });
+    }
     bw.finish();
     return true;
 }
 
 // Decode one block.  src(word_index) returns word i of the block (0 past the end).
 template <class Src>
-OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64])
+OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64], SharedPlanes planes)
 {
     const uint32_t w0 = src(0);
     const int hdr = (int)(w0 & 0xFFu);
@@ -425,19 +434,12 @@ OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64])
     BitReader<Src> br(src);
     br.skip(8);
 
-    uint32_t lo[32], hi[32];
 #pragma unroll
-    for (int p = 0; p < 32; ++p) {
-        lo[p] = 0u;
-        hi[p] = 0u;
-    }
+    for (int p = 0; p < 32; ++p)
+        planes.set(p, 0ull);
     int left = 64 * rate - 8;
     int n = 0;
-    // planes 31 .. 0, unrolled (constant plane indices: the words stay in registers)
-    static_for<0, 32>([&](auto I) {
-        constexpr int p = 31 - decltype(I)::value;
-        if (left <= 0)
-            return;
+    for (int p = 31; p >= 0 && left > 0; --p) {
         const int t = min(n, left);
         uint64_t X = br.get64(t);
         left -= t;
@@ -506,9 +508,15 @@ OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64])
                 }
             }
         }
+        planes.set(p, X);
+    }
+    uint32_t lo[32], hi[32];
+#pragma unroll
+    for (int p = 0; p < 32; ++p) {
+        const uint64_t X = planes.get(p);
         lo[p] = (uint32_t)X;
         hi[p] = (uint32_t)(X >> 32);
-    });
+    }
     transpose32(lo);  // back to coefficient words
     transpose32(hi);
 
