@@ -202,6 +202,10 @@ oocs_status validate_desc(const oocs_desc *d, std::string &err)
         err = "codec must be OOCS_CODEC_TRANSFORM (0) or OOCS_CODEC_QUANT (1)";
         return OOCS_ERR_INVALID_ARG;
     }
+    if (d->step_fusion != 0 && d->step_fusion != 1) {
+        err = "step_fusion must be 0 or 1";
+        return OOCS_ERR_INVALID_ARG;
+    }
     if (d->codec == OOCS_CODEC_QUANT && d->rate_bits == 1) {
         err = "the block quantiser needs rate_bits >= 2";
         return OOCS_ERR_INVALID_ARG;
@@ -819,7 +823,30 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             return r;
     }
     uint64_t step_units = 0;
+    // heat: pairs of steps in one fused launch (the middle step on chip)
+    const bool fuse = d.scheme == OOCS_HEAT && d.radius == 1 && d.step_fusion == 0;
+    uint64_t launches = 0;
     for (int j = 1; j <= k_eff; ++j) {
+        if (fuse && j + 1 <= k_eff) {
+            const int64_t lo1 = std::max<int64_t>(z0 - (int64_t)(k_eff - j) * v.r, 0);
+            const int64_t hi1 = std::min<int64_t>(z1 + (int64_t)(k_eff - j) * v.r, d.nz);
+            const int64_t lo = std::max<int64_t>(z0 - (int64_t)(k_eff - j - 1) * v.r, 0);
+            const int64_t hi = std::min<int64_t>(z1 + (int64_t)(k_eff - j - 1) * v.r, d.nz);
+            Ls.z_lo = lo - w0;
+            Ls.z_hi = hi - w0;
+            Ls.cur = c->wbuf(wb, cur);
+            Ls.out = c->wbuf(wb, oth);
+            if (c->trace)
+                trace_push(c, OOCS_OP_STEP, q, -1, (int64_t)g, {acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
+            else
+                CU(c, launch_heat_step2(Ls, st));
+            c->stats.kernel_launches++;
+            ++launches;
+            step_units += (uint64_t)(hi1 - lo1 + hi - lo) * d.nx * d.ny;
+            std::swap(cur, oth);
+            ++j;
+            continue;
+        }
         const int64_t lo = std::max<int64_t>(z0 - (int64_t)(k_eff - j) * v.r, 0);
         const int64_t hi = std::min<int64_t>(z1 + (int64_t)(k_eff - j) * v.r, d.nz);
         Ls.z_lo = lo - w0;
@@ -854,6 +881,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         else
             CU(c, launch_star_step(Ls, st));
         c->stats.kernel_launches++;
+        ++launches;
         step_units += (uint64_t)(hi - lo) * d.nx * d.ny;
         // the receiver plane lies in this slab's interior, which every step of
         // the visit computes: record u^(tstep+1) there
@@ -863,7 +891,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         std::swap(cur, oth);
     }
     {
-        oocs_status r = ks_steps.end(kClsStep, step_units, (uint64_t)k_eff);
+        oocs_status r = ks_steps.end(kClsStep, step_units, launches);
         if (r != OOCS_OK)
             return r;
     }

@@ -13,6 +13,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <mutex>
@@ -489,6 +490,183 @@ __global__ void __launch_bounds__(kStepThreads, 2)
     }
 }
 
+// Two heat steps in one z-march (kernel-level temporal blocking of the
+// 7-point stencil, Sec. 3.1 / Fig. 1b applied on chip): steps j and j+1 of a
+// visit read the step j-1 planes once and write the step j+1 planes once; the
+// step j planes live only in shared memory.  A CTA's output is a 64 x 16 tile
+// (as in k_star_step); it computes step j on the tile plus a one-point x-y
+// halo (66 x 18, the halo points recomputed by the neighbouring tiles too)
+// from step j-1 values on a two-point halo (72 x 20 TMA boxes).  Per output
+// plane z: step j plane z+1 is computed into a four-plane ring, the consumer
+// warps meet at a named barrier, and output plane z is computed from step j
+// planes z-1, z, z+1.  Every point goes through the same operations as in
+// k_star_step<1, kHeat> (shell and out-of-grid points copy their input), and
+// a step j value outside step j's trapezoid is never read by an interior
+// output point, so the result is bit-identical to two single steps.
+constexpr int kH2InW = kBoxW;            // 72: input row, x0 - 4 .. x0 + 67
+constexpr int kH2InH = kTY + 4;          // 20: input rows, y0 - 2 .. y0 + 17
+constexpr int kH2MidH = kTY + 2;         // 18: step j rows, y0 - 1 .. y0 + 16
+constexpr int kH2NS = 6;                 // input ring stages
+constexpr int kH2NM = 4;                 // step j ring planes
+constexpr uint32_t kH2InBytes = kH2InW * kH2InH * 4;
+constexpr int kH2InStage = ((kH2InBytes + 127) / 128 * 128) / 4;   // floats
+constexpr int kH2MidPlane = kH2InW * kH2MidH;                     // floats
+constexpr size_t kH2Smem = 128 + (size_t)kH2NS * kH2InStage * 4 + (size_t)kH2NM * kH2MidPlane * 4 + 2 * kH2NS * 8;
+
+__global__ void __launch_bounds__(kStepThreads, 3)
+    k_heat_step2(const __grid_constant__ CUtensorMap tm_in, const StepArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    float *ins = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float *mids = ins + kH2NS * kH2InStage;
+    uint64_t *full = reinterpret_cast<uint64_t *>(mids + kH2NM * kH2MidPlane);
+    uint64_t *empty = full + kH2NS;
+    const int tx = threadIdx.x, wid = threadIdx.y;
+    if (wid == 0 && tx == 0) {
+        for (int i = 0; i < kH2NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kConsumerWarps);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+    pdl_launch_dependents();
+    pdl_wait_prior_grid();
+
+    SegCursor cur;
+    cur.init(a);
+    StepSeg sg;
+    if (wid == kConsumerWarps) {
+        // ------------------------------------------------ producer warp --
+        if (tx != 0)
+            return;
+        bool good = true;
+        uint32_t n = 0;  // input planes issued so far
+        while (good && cur.next(a, sg)) {
+            for (int p = sg.zs - 2; p < sg.ze + 2; ++p) {
+                const uint32_t st = n % kH2NS, k = n / kH2NS;
+                if (k > 0 && !mbar_wait(&empty[st], (k - 1) & 1)) {
+                    good = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[st], kH2InBytes);
+                tma_load_3d(ins + st * kH2InStage, &tm_in, sg.x0 - 4, sg.y0 - 2, p, &full[st]);
+                ++n;
+            }
+        }
+        for (uint32_t i = n > (uint32_t)kH2NS ? n - kH2NS : 0; i < n; ++i)
+            mbar_wait(&full[i % kH2NS], (i / kH2NS) & 1);
+        return;
+    }
+
+    // --------------------------------------------------- consumer warps --
+    // A wait that runs out (kErrWaitTimeout) only stops the computing: every
+    // consumer warp still passes the same sequence of named barriers, so no
+    // warp is left waiting at one for a warp that gave up.
+    const int tid = wid * 32 + tx;
+    const StarCoef c = a.c;
+    uint32_t icn = 0;  // input planes consumed before this segment
+    uint32_t mcn = 0;  // step j planes computed before this segment
+    bool good = true;
+    auto grid_interior = [&](int x, int y, int gz) {
+        return x >= 1 && x < a.nx - 1 && y >= 1 && y < a.ny - 1 && gz >= 1 && gz < a.nz - 1;
+    };
+    while (cur.next(a, sg)) {
+        const int x0 = sg.x0, y0 = sg.y0, zs = sg.zs, ze = sg.ze;
+        const int pi0 = zs - 2;  // first input plane of the segment
+        auto in_slot = [&](int p) { return (icn + (uint32_t)(p - pi0)) % kH2NS; };
+        auto in_phase = [&](int p) { return ((icn + (uint32_t)(p - pi0)) / kH2NS) & 1; };
+        auto mid_plane = [&](int q) { return mids + ((mcn + (uint32_t)(q - (zs - 1))) % kH2NM) * kH2MidPlane; };
+        auto wait_in = [&](int p) {
+            if (good)
+                good = __all_sync(0xffffffffu, mbar_wait(&full[in_slot(p)], in_phase(p)));
+        };
+        auto release = [&](int p) {
+            __syncwarp();
+            if (tx == 0)
+                mbar_arrive(&empty[in_slot(p)]);
+        };
+        // the previous segment's output planes are done before its step j
+        // planes are overwritten
+        named_bar_sync(1, 32 * kConsumerWarps);
+        // step j plane q (window-relative) from input planes q-1, q, q+1:
+        // 18 rows x 66 columns, columns x0-1 .. x0+64 in pairs
+        auto mid_step = [&](int q) {
+            const float *Pm = ins + in_slot(q - 1) * kH2InStage;
+            const float *P0 = ins + in_slot(q) * kH2InStage;
+            const float *Pp = ins + in_slot(q + 1) * kH2InStage;
+            float *M = mid_plane(q);
+            const int gz = a.gz0 + q;
+            for (int i = tid; i < kH2MidH * 33; i += 32 * kConsumerWarps) {
+                const int row = i / 33, pair = i - row * 33;
+                const int y = y0 - 1 + row;
+                const int ib = (row + 1) * kH2InW;  // the row in the input box
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int col = 3 + 2 * pair + cc;
+                    const int x = x0 - 4 + col;
+                    const float u = P0[ib + col];
+                    float r = u;
+                    if (grid_interior(x, y, gz)) {
+                        float sd[2];
+                        sd[0] = 0.0f;
+                        sd[1] = nbr_sum(P0[ib + col - 1], P0[ib + col + 1], P0[ib - kH2InW + col],
+                                        P0[ib + kH2InW + col], Pm[ib + col], Pp[ib + col]);
+                        r = star_L<1>(c, u, sd);
+                    }
+                    M[row * kH2InW + col] = r;
+                }
+            }
+        };
+        // prologue: step j planes zs-1 and zs
+        for (int q = zs - 1; q <= zs; ++q) {
+            for (int p = q - 1; p <= q + 1; ++p)
+                wait_in(p);
+            if (good)
+                mid_step(q);
+            release(q - 1);
+        }
+        for (int z = zs; z < ze; ++z) {
+            wait_in(z + 2);
+            if (good)
+                mid_step(z + 1);
+            release(z);
+            named_bar_sync(1, 32 * kConsumerWarps);  // step j planes z-1 .. z+1 are complete
+            if (!good)
+                continue;
+            const float *Mm = mid_plane(z - 1), *M0 = mid_plane(z), *Mp = mid_plane(z + 1);
+            const int gz = a.gz0 + z;
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) {
+                const int y = y0 + kRPT * wid + r;
+                const int row = 1 + kRPT * wid + r;
+#pragma unroll
+                for (int cc = 0; cc < kVX; ++cc) {
+                    const int x = x0 + kVX * tx + cc;
+                    if (x >= a.nx || y >= a.ny)
+                        continue;
+                    const int col = 4 + kVX * tx + cc;
+                    const int o = row * kH2InW + col;
+                    const float u = M0[o];
+                    float res = u;
+                    if (grid_interior(x, y, gz)) {
+                        float sd[2];
+                        sd[0] = 0.0f;
+                        sd[1] = nbr_sum(M0[o - 1], M0[o + 1], M0[o - kH2InW], M0[o + kH2InW], Mm[o], Mp[o]);
+                        res = star_L<1>(c, u, sd);
+                    }
+                    a.out[(int64_t)z * a.plane + (int64_t)y * a.nx + x] = res;
+                }
+            }
+        }
+        // input planes ze and ze+1 only fed the last step j plane
+        release(ze);
+        release(ze + 1);
+        icn += (uint32_t)(ze - zs + 4);
+        mcn += (uint32_t)(ze - zs + 2);
+    }
+}
+
 // ---- host side: tensor maps and launch geometry
 
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -604,6 +782,43 @@ static cudaError_t step_residency(int &resident, int &sms)
     return cudaSuccess;
 }
 
+// Launch geometry of a z-march over window planes [a.z_lo, a.z_hi) of an
+// nx x ny grid of 64 x 16 tiles, with `slots` CTAs resident at once.
+// Chunked launch when some z chunking (>= 12 planes per CTA) fills the last
+// wave of CTAs to 90 %; otherwise (short windows on a plane whose tiles do not
+// fill the SMs evenly, e.g. 256 tiles on 304 slots) one wave of equal
+// tile-plane ranges.  Sets a.zchunk, a.tiles_y and a.ntiles.
+static dim3 step_grid(int64_t nx, int64_t ny, int slots, StepArgs &a)
+{
+    const int tiles_x = (int)((nx + kTX - 1) / kTX);
+    const int tiles_y = (int)((ny + kTY - 1) / kTY);
+    const int tiles = tiles_x * tiles_y;
+    const int nplanes = a.z_hi - a.z_lo;
+    a.tiles_y = tiles_y;
+    a.ntiles = tiles;
+    int best = 1;
+    double best_eff = 0.0;
+    const int max_chunks = std::max(1, nplanes / 12);
+    for (int nc = 1; nc <= max_chunks && nc <= 64; ++nc) {
+        const int zc = (nplanes + nc - 1) / nc;
+        const int real = (nplanes + zc - 1) / zc;
+        const long total = (long)tiles * real;
+        const long waves = (total + slots - 1) / slots;
+        const double eff = (double)total / (double)(waves * slots);
+        if (eff > best_eff + 0.02) {
+            best_eff = eff;
+            best = nc;
+        }
+    }
+    if (best_eff >= 0.9) {
+        a.zchunk = (nplanes + best - 1) / best;
+        return dim3(tiles_x, tiles_y, (nplanes + a.zchunk - 1) / a.zchunk);
+    }
+    a.zchunk = 0;
+    const int64_t total = (int64_t)tiles * nplanes;
+    return dim3((unsigned)std::min<int64_t>(slots, (total + 15) / 16), 1, 1);
+}
+
 template <int R, int SCHEME>
 static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s)
 {
@@ -628,42 +843,62 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
     if (e != cudaSuccess)
         return e;
 
-    const int tiles_x = (int)((L.nx + kTX - 1) / kTX);
-    const int tiles_y = (int)((L.ny + kTY - 1) / kTY);
-    const int tiles = tiles_x * tiles_y;
-    const int nplanes = a.z_hi - a.z_lo;
-    a.tiles_y = tiles_y;
-    a.ntiles = tiles;
-    // z chunks: keep >= 12 planes per CTA and choose the count whose last wave
-    // of CTAs (sms x resident per wave) is fullest
-    const int slots = sms * resident;
-    int best = 1;
-    double best_eff = 0.0;
-    const int max_chunks = std::max(1, nplanes / 12);
-    for (int nc = 1; nc <= max_chunks && nc <= 64; ++nc) {
-        const int zc = (nplanes + nc - 1) / nc;
-        const int real = (nplanes + zc - 1) / zc;
-        const long total = (long)tiles * real;
-        const long waves = (total + slots - 1) / slots;
-        const double eff = (double)total / (double)(waves * slots);
-        if (eff > best_eff + 0.02) {
-            best_eff = eff;
-            best = nc;
-        }
-    }
-    dim3 grid;
-    if (best_eff >= 0.9) {
-        a.zchunk = (nplanes + best - 1) / best;
-        grid = dim3(tiles_x, tiles_y, (nplanes + a.zchunk - 1) / a.zchunk);
-    } else {
-        // short windows on a plane whose tiles do not fill the SMs evenly
-        // (e.g. 256 tiles on 304 slots): one wave of equal tile-plane ranges
-        a.zchunk = 0;
-        const int64_t total = (int64_t)tiles * nplanes;
-        grid = dim3((unsigned)std::min<int64_t>(slots, (total + 15) / 16), 1, 1);
-    }
+    const dim3 grid = step_grid(L.nx, L.ny, sms * resident, a);
     dim3 block(32, kConsumerWarps + 1, 1);
     return launch_pdl(kern, grid, block, smem, s, mc, mp, mm, m2, a);
+}
+
+cudaError_t launch_heat_step2(const StepLaunch &L, cudaStream_t s)
+{
+    if (L.z_hi <= L.z_lo)
+        return cudaSuccess;
+    if (L.scheme != kHeat || L.radius != 1)
+        return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t e = current_device(dev);
+    if (e != cudaSuccess)
+        return e;
+    int resident = 0, sms = 0;
+    {
+        static int res_dev[kMaxDevices] = {};
+        std::lock_guard<std::mutex> lock(g_dev_mu);
+        DevInfo &info = g_dev[dev];
+        if (info.sms == 0 && (e = cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        if (res_dev[dev] == 0) {
+            e = cudaFuncSetAttribute(k_heat_step2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kH2Smem);
+            if (e != cudaSuccess)
+                return e;
+            int n = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_heat_step2, kStepThreads, kH2Smem);
+            if (e != cudaSuccess)
+                return e;
+            if (n < 1)
+                return cudaErrorInvalidConfiguration;
+            res_dev[dev] = n;
+        }
+        resident = res_dev[dev];
+        sms = info.sms;
+    }
+    CUtensorMap m;
+    e = make_plane_map(&m, L.cur, L.nx, L.ny, L.wp, kH2InW, kH2InH);
+    if (e != cudaSuccess)
+        return e;
+    StepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.out = L.out;
+    a.nx = (int)L.nx;
+    a.ny = (int)L.ny;
+    a.nz = (int)L.nz;
+    a.plane = L.nx * L.ny;
+    a.gz0 = (int)L.gz0;
+    a.z_lo = (int)L.z_lo;
+    a.z_hi = (int)L.z_hi;
+    for (int i = 0; i < 5; ++i)
+        a.c.c[i] = L.coef[i];
+    a.src_x = a.src_y = a.src_zw = -1;
+    const dim3 grid = step_grid(L.nx, L.ny, sms * resident, a);
+    return launch_pdl(k_heat_step2, grid, dim3(32, kConsumerWarps + 1, 1), kH2Smem, s, m, a);
 }
 
 cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)

@@ -48,6 +48,12 @@ struct StepLaunch {
 
 cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s);
 
+// Two heat steps (radius 1) in one launch: L describes the second of the two
+// (its planes [z_lo, z_hi), written to L.out from the step-before-last values
+// in L.cur; the middle step stays on chip).  Bit-identical to two
+// launch_star_step calls.
+cudaError_t launch_heat_step2(const StepLaunch &L, cudaStream_t s);
+
 // out = a * b elementwise (FP32, one rounding each); n a multiple of 4.
 cudaError_t launch_product(float *out, const float *a, const float *b, int64_t n, cudaStream_t s);
 

@@ -99,6 +99,12 @@ __device__ __forceinline__ void pdl_wait_prior_grid()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Barrier among `count` threads (whole warps) of the CTA on hardware barrier `id`.
+__device__ __forceinline__ void named_bar_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // 3D tiled TMA load of a box at (x, y, z) into shared memory, completing on `bar`.
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
                                             uint64_t *bar)

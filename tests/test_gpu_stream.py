@@ -253,3 +253,30 @@ def test_compress_and_decompress_in_place(P, orc, rate):
         assert e.value.status == 1 and "in place" in str(e.value)
     finally:
         st.close()
+
+
+@pytest.mark.parametrize("shape,T,k,rate", [((64, 200, 264), 24, 4, 0), ((64, 200, 264), 24, 4, 16),
+                                            ((96, 72, 136), 32, 3, 0), ((40, 36, 52), 64, 2, 16),
+                                            ((128, 128, 128), 32, 4, 12)])
+def test_heat_fused_step_pairs_bitexact(P, shape, T, k, rate):
+    """Heat steps fused in pairs (the middle step of each pair kept in shared
+    memory, temporal blocking on chip) give the same stores and field, bit for
+    bit, as one kernel per step: ragged tiles in x and y, windows clipped at
+    both faces, an odd depth (a pair and a single step), several slabs."""
+    u0 = synthetic.uniform_field(shape, 21)
+    ref = None
+    for fusion in (1, 0):
+        nz, ny, nx = shape
+        desc = P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), 8 << 30, rate_bits=rate,
+                           temporal_depth=k, slab_planes=T, step_fusion=fusion)
+        got, _, stores, stats, _ = streamed(P, desc, u0, 2 * k + 1)
+        if ref is None:
+            ref = (got, stores, stats)
+        else:
+            assert np.array_equal(got.view(np.uint32), ref[0].view(np.uint32))
+            assert np.array_equal(stores[0], ref[1][0])
+            assert stats["step"]["units"] == ref[2]["step"]["units"]
+            assert stats["kernel_launches"] < ref[2]["kernel_launches"]
+    if rate == 0:
+        inc = incore(P, heat_desc(P, shape, rate=0, k=k, T=T), u0, 2 * k + 1)
+        assert np.array_equal(ref[0].view(np.uint32), inc.view(np.uint32))
