@@ -165,6 +165,8 @@ typedef struct {
     oocs_kernel_stats load;      /* decode / copy of staged layers into the working buffer  */
     oocs_kernel_stats step;      /* stencil time steps                                       */
     oocs_kernel_stats store;     /* encode / copy of the slab interior out of it            */
+    oocs_kernel_stats h2d;       /* host->device copies of a visit (units: bytes)            */
+    oocs_kernel_stats d2h;       /* device->host copies of a visit (units: bytes)            */
 } oocs_stats;
 
 typedef struct oocs_ctx oocs_ctx;
@@ -318,11 +320,29 @@ oocs_status oocs_device_errors(uint32_t *flags, int32_t clear);
 
 oocs_status oocs_get_stats(const oocs_ctx *ctx, oocs_stats *out);
 
-/* Per-launch event timing of the kernels enqueued by oocs_step.  `classes` is
- * a bit mask: OOCS_PROF_LOAD | OOCS_PROF_STEP | OOCS_PROF_STORE; 0 = off.
- * Adds two event records per timed kernel on its own stream.               */
-enum { OOCS_PROF_LOAD = 1, OOCS_PROF_STEP = 2, OOCS_PROF_STORE = 4 };
+/* Per-launch event timing of the work enqueued by oocs_step.  `classes` is a
+ * bit mask of OOCS_PROF_LOAD | OOCS_PROF_STEP | OOCS_PROF_STORE (kernels) and
+ * OOCS_PROF_H2D | OOCS_PROF_D2H (a visit's copies); 0 = off.  Adds two event
+ * records per timed item on its own stream.                                */
+enum { OOCS_PROF_LOAD = 1, OOCS_PROF_STEP = 2, OOCS_PROF_STORE = 4, OOCS_PROF_H2D = 8, OOCS_PROF_D2H = 16 };
 oocs_status oocs_set_profiling(oocs_ctx *ctx, int32_t classes);
+
+/* The timeline of the profiled items collected at the last oocs_synchronize:
+ * per item its class (0 load, 1 step, 2 store, 3 h2d, 4 d2h), the stream
+ * (0..2) and slab visit (counted over the context's life) it ran on, and its
+ * start and end in milliseconds after the start of the last oocs_step call
+ * enqueued before that synchronize (items of earlier calls come out
+ * negative).  Copies min(count, capacity) entries; *count = entries kept.
+ * The Nsight-style view of a sweep (which copy or kernel waits on which), for
+ * the scheduling of Algorithm 1 (Fig. 8).                                  */
+typedef struct {
+    int32_t cls;
+    int32_t stream;
+    int64_t visit;
+    double start_ms, end_ms;
+} oocs_timeline_entry;
+oocs_status oocs_get_timeline(const oocs_ctx *ctx, oocs_timeline_entry *entries, int64_t capacity,
+                              int64_t *count);
 
 /* Text of the last error of ctx, or of the last failed context-free call in
  * this thread when ctx is NULL.  Never NULL; valid until the next call.    */

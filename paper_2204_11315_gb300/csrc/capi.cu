@@ -350,10 +350,12 @@ struct oocs_ctx {
     std::vector<cudaEvent_t> ev_pool;  // created on demand, reused after collection
     size_t ev_used = 0;
     struct Pending {
-        int cls;
+        int cls, stream;
+        int64_t visit;
         cudaEvent_t a, b;
     };
     std::vector<Pending> pending;
+    std::vector<oocs_timeline_entry> timeline;  // of the last collection
     oocs_status sticky = OOCS_OK;
     std::string err = "no error";
 
@@ -552,11 +554,17 @@ oocs_status sched_record(oocs_ctx *c, int si, int ev)
             return r_;               \
     } while (0)
 
-enum { kClsLoad = 0, kClsStep = 1, kClsStore = 2 };
+enum { kClsLoad = 0, kClsStep = 1, kClsStore = 2, kClsH2D = 3, kClsD2H = 4 };
 
 oocs_kernel_stats &cls_stats(oocs_ctx *c, int cls)
 {
-    return cls == kClsLoad ? c->stats.load : (cls == kClsStep ? c->stats.step : c->stats.store);
+    switch (cls) {
+    case kClsLoad: return c->stats.load;
+    case kClsStep: return c->stats.step;
+    case kClsStore: return c->stats.store;
+    case kClsH2D: return c->stats.h2d;
+    default: return c->stats.d2h;
+    }
 }
 
 oocs_status take_event(oocs_ctx *c, cudaEvent_t *e)
@@ -600,7 +608,10 @@ struct KernelScope {
         if (r != OOCS_OK)
             return r;
         CU(c, cudaEventRecord(b, s));
-        c->pending.push_back({cls, a, b});
+        int si = 0;
+        while (si < 2 && c->st[si] != s)
+            ++si;
+        c->pending.push_back({cls, si, (int64_t)c->g, a, b});
         return OOCS_OK;
     }
 };
@@ -608,10 +619,17 @@ struct KernelScope {
 // fold the durations of completed profiled launches into the stats
 void collect_profile(oocs_ctx *c)
 {
+    if (!c->pending.empty())
+        c->timeline.clear();
     for (const auto &p : c->pending) {
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
             cls_stats(c, p.cls).device_ms += ms;
+        float t0 = 0.0f, t1 = 0.0f;
+        if (cudaEventElapsedTime(&t0, c->ev_t0, p.a) == cudaSuccess &&
+            cudaEventElapsedTime(&t1, c->ev_t0, p.b) == cudaSuccess)
+            c->timeline.push_back({p.cls, p.stream, p.visit, (double)t0, (double)t1});
+        cudaGetLastError();
     }
     c->pending.clear();
     c->ev_used = 0;
@@ -728,6 +746,10 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
                 c->trace->back().access[c->trace->back().naccess++] = a[1 + f];
         }
     } else {
+        KernelScope ks;
+        oocs_status r = ks.begin(c, st, kClsH2D);
+        if (r != OOCS_OK)
+            return r;
         for (int f = 0; f < v.fin_stream; ++f) {
             const int id = in_field_id(c, f);
             const uint64_t bytes = (uint64_t)(n1 - n0) / 4 * v.layer_bytes;
@@ -736,6 +758,9 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
                                       bytes, cudaMemcpyHostToDevice, st));
             }
         }
+        r = ks.end(kClsH2D, (uint64_t)v.fin_stream * (uint64_t)(n1 - n0) / 4 * v.layer_bytes);
+        if (r != OOCS_OK)
+            return r;
     }
     c->stats.h2d_bytes += (uint64_t)v.fin_stream * (uint64_t)(n1 - n0) / 4 * v.layer_bytes;
     SCHED(sched_record(c, q, kEvH2D + q));
@@ -938,12 +963,25 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             c->trace->back().access[c->trace->back().naccess++] =
                 acc(OOCS_RES_HOST, c->host_base + 1, z0 / 4, z1 / 4, true);
     }
-    for (int f = 0; f < v.fout; ++f) {
-        const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
-        if (!c->trace)
-            CU(c, cudaMemcpyAsync(c->store[f] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, f),
-                                  bytes, cudaMemcpyDeviceToHost, st));
-        c->stats.d2h_bytes += bytes;
+    {
+        KernelScope ks;
+        if (!c->trace) {
+            oocs_status r = ks.begin(c, st, kClsD2H);
+            if (r != OOCS_OK)
+                return r;
+        }
+        for (int f = 0; f < v.fout; ++f) {
+            const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
+            if (!c->trace)
+                CU(c, cudaMemcpyAsync(c->store[f] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, f),
+                                      bytes, cudaMemcpyDeviceToHost, st));
+            c->stats.d2h_bytes += bytes;
+        }
+        if (!c->trace) {
+            oocs_status r = ks.end(kClsD2H, (uint64_t)v.fout * (uint64_t)(z1 - z0) / 4 * v.layer_bytes);
+            if (r != OOCS_OK)
+                return r;
+        }
     }
     // 8b. the same layers into the state record: out slot f holds u^(t+k-f);
     //     nothing in the pipeline reads the record, and the out slot is
@@ -1661,6 +1699,18 @@ oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns)
     return OOCS_OK;
 }
 
+oocs_status oocs_get_timeline(const oocs_ctx *ctx, oocs_timeline_entry *entries, int64_t capacity,
+                              int64_t *count)
+{
+    if (!ctx || !count || capacity < 0 || (capacity > 0 && !entries))
+        return fail(nullptr, OOCS_ERR_INVALID_ARG, "ctx and count are required, entries when capacity > 0");
+    const int64_t n = (int64_t)ctx->timeline.size();
+    for (int64_t i = 0; i < std::min(n, capacity); ++i)
+        entries[i] = ctx->timeline[i];
+    *count = n;
+    return OOCS_OK;
+}
+
 oocs_status oocs_set_fault_injection(oocs_ctx *ctx, int64_t nth_call)
 {
     if (!ctx || nth_call < 0)
@@ -1697,8 +1747,8 @@ oocs_status oocs_set_profiling(oocs_ctx *ctx, int32_t classes)
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
-    if (classes < 0 || classes > 7)
-        return fail(ctx, OOCS_ERR_INVALID_ARG, "profiling mask must be in [0, 7]");
+    if (classes < 0 || classes > 31)
+        return fail(ctx, OOCS_ERR_INVALID_ARG, "profiling mask must be in [0, 31]");
     ctx->prof = classes;
     return OOCS_OK;
 }
@@ -2161,9 +2211,9 @@ void add_stats(oocs_stats &a, const oocs_stats &d, int sign)
     f(a.steps_done, d.steps_done);
     f(a.passes_done, d.passes_done);
     f(a.slabs_done, d.slabs_done);
-    for (int k = 0; k < 3; ++k) {
-        oocs_kernel_stats &x = k == 0 ? a.load : k == 1 ? a.step : a.store;
-        const oocs_kernel_stats &y = k == 0 ? d.load : k == 1 ? d.step : d.store;
+    for (int k = 0; k < 5; ++k) {
+        oocs_kernel_stats &x = k == 0 ? a.load : k == 1 ? a.step : k == 2 ? a.store : k == 3 ? a.h2d : a.d2h;
+        const oocs_kernel_stats &y = k == 0 ? d.load : k == 1 ? d.step : k == 2 ? d.store : k == 3 ? d.h2d : d.d2h;
         f(x.launches, y.launches);
         f(x.units, y.units);
     }

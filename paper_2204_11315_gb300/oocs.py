@@ -76,7 +76,12 @@ class oocs_stats(ctypes.Structure):
                 ("passes_done", ctypes.c_uint64), ("slabs_done", ctypes.c_uint64),
                 ("workspace_bytes", ctypes.c_uint64), ("last_step_ms", ctypes.c_double),
                 ("load", oocs_kernel_stats), ("step", oocs_kernel_stats),
-                ("store", oocs_kernel_stats)]
+                ("store", oocs_kernel_stats), ("h2d", oocs_kernel_stats), ("d2h", oocs_kernel_stats)]
+
+
+class oocs_timeline_entry(ctypes.Structure):
+    _fields_ = [("cls", ctypes.c_int32), ("stream", ctypes.c_int32), ("visit", ctypes.c_int64),
+                ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double)]
 
     def as_dict(self):
         d = {}
@@ -156,6 +161,7 @@ SIGNATURES = {
     "oocs_selftest_stuck_wait": (_i32, [_vp]),
     "oocs_device_errors": (_i32, [ctypes.POINTER(ctypes.c_uint32), _i32]),
     "oocs_set_fault_injection": (_i32, [_vp, _i64]),
+    "oocs_get_timeline": (_i32, [_vp, ctypes.POINTER(oocs_timeline_entry), _i64, ctypes.POINTER(_i64)]),
     "oocs_compress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
     "oocs_decompress_device": (_i32, [_vp, _i32, _vp, _i64, _i64]),
     "oocs_host_alloc": (_i32, [_u64, ctypes.POINTER(_vp)]),
@@ -273,11 +279,11 @@ def oocs_get_stats(ctx: int) -> oocs_stats:
     return s
 
 
-OOCS_PROF_LOAD, OOCS_PROF_STEP, OOCS_PROF_STORE = 1, 2, 4
+OOCS_PROF_LOAD, OOCS_PROF_STEP, OOCS_PROF_STORE, OOCS_PROF_H2D, OOCS_PROF_D2H = 1, 2, 4, 8, 16
 
 
 def oocs_set_profiling(ctx: int, classes: int):
-    """classes: bit mask of OOCS_PROF_LOAD / _STEP / _STORE (0 = off)."""
+    """classes: bit mask of OOCS_PROF_LOAD / _STEP / _STORE / _H2D / _D2H (0 = off)."""
     _check(lib().oocs_set_profiling(ctx, int(classes)), ctx)
 
 
@@ -431,6 +437,19 @@ def oocs_set_receiver(ctx, zr, planes_ptr, nplanes):
 
 def oocs_selftest_stuck_wait(ctx):
     _check(lib().oocs_selftest_stuck_wait(_vp(ctx)), ctx)
+
+
+TIMELINE_CLASSES = ("load", "step", "store", "h2d", "d2h")
+
+
+def oocs_get_timeline(ctx):
+    """Profiled items of the last collection as dicts {cls, stream, visit, start_ms, end_ms}."""
+    n = _i64()
+    _check(lib().oocs_get_timeline(_vp(ctx), None, 0, ctypes.byref(n)), ctx)
+    arr = (oocs_timeline_entry * max(n.value, 1))()
+    _check(lib().oocs_get_timeline(_vp(ctx), arr, n.value, ctypes.byref(n)), ctx)
+    return [{"cls": TIMELINE_CLASSES[e.cls], "stream": e.stream, "visit": e.visit, "start_ms": e.start_ms,
+             "end_ms": e.end_ms} for e in arr[:n.value]]
 
 
 def oocs_set_fault_injection(ctx, nth_call):
