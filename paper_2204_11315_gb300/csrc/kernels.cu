@@ -496,22 +496,37 @@ __global__ void __launch_bounds__(kStepThreads, 2)
 // step j planes live only in shared memory.  A CTA's output is a 64 x 16 tile
 // (as in k_star_step); it computes step j on the tile plus a one-point x-y
 // halo (66 x 18, the halo points recomputed by the neighbouring tiles too)
-// from step j-1 values on a two-point halo (72 x 20 TMA boxes).  Per output
-// plane z: step j plane z+1 is computed into a four-plane ring, the consumer
-// warps meet at a named barrier, and output plane z is computed from step j
-// planes z-1, z, z+1.  Every point goes through the same operations as in
-// k_star_step<1, kHeat> (shell and out-of-grid points copy their input), and
-// a step j value outside step j's trapezoid is never read by an interior
-// output point, so the result is bit-identical to two single steps.
+// from step j-1 values on a two-point halo (72 x 20 TMA boxes).
+//
+// Consumer thread (tx, w) owns the 2 x 4 points x0 + 2 tx + {0, 1},
+// y0 + 4 w + {0..3} of both steps, keeps their step j-1 and step j values of
+// three consecutive planes in register queues (the z neighbours), and takes
+// x-y neighbours from shared memory; the 164 halo points of a step j plane
+// are split over the four warps.  Per output plane z: step j plane z+1 is
+// computed into a three-plane ring, the consumer warps meet at a named
+// barrier, and output plane z is computed.  Every point goes through the same
+// operations as in k_star_step<1, kHeat> (shell and out-of-grid points copy
+// their input), and a step j value outside step j's trapezoid is never read
+// by an interior output point, so the result is bit-identical to two single
+// steps.
 constexpr int kH2InW = kBoxW;            // 72: input row, x0 - 4 .. x0 + 67
 constexpr int kH2InH = kTY + 4;          // 20: input rows, y0 - 2 .. y0 + 17
 constexpr int kH2MidH = kTY + 2;         // 18: step j rows, y0 - 1 .. y0 + 16
 constexpr int kH2NS = 6;                 // input ring stages
-constexpr int kH2NM = 4;                 // step j ring planes
+constexpr int kH2NM = 3;                 // step j ring planes
 constexpr uint32_t kH2InBytes = kH2InW * kH2InH * 4;
 constexpr int kH2InStage = ((kH2InBytes + 127) / 128 * 128) / 4;   // floats
 constexpr int kH2MidPlane = kH2InW * kH2MidH;                     // floats
 constexpr size_t kH2Smem = 128 + (size_t)kH2NS * kH2InStage * 4 + (size_t)kH2NM * kH2MidPlane * 4 + 2 * kH2NS * 8;
+
+// one heat point: the step-kernel arithmetic (nbr_sum, star_L<1>)
+OOCS_FN float heat_point(const StarCoef &c, float u, float xm, float xp, float ym, float yp, float zm, float zp)
+{
+    float sd[2];
+    sd[0] = 0.0f;
+    sd[1] = nbr_sum(xm, xp, ym, yp, zm, zp);
+    return star_L<1>(c, u, sd);
+}
 
 __global__ void __launch_bounds__(kStepThreads, 3)
     k_heat_step2(const __grid_constant__ CUtensorMap tm_in, const StepArgs a)
@@ -563,19 +578,17 @@ __global__ void __launch_bounds__(kStepThreads, 3)
     // A wait that runs out (kErrWaitTimeout) only stops the computing: every
     // consumer warp still passes the same sequence of named barriers, so no
     // warp is left waiting at one for a warp that gave up.
-    const int tid = wid * 32 + tx;
     const StarCoef c = a.c;
     uint32_t icn = 0;  // input planes consumed before this segment
     uint32_t mcn = 0;  // step j planes computed before this segment
     bool good = true;
-    auto grid_interior = [&](int x, int y, int gz) {
-        return x >= 1 && x < a.nx - 1 && y >= 1 && y < a.ny - 1 && gz >= 1 && gz < a.nz - 1;
-    };
+    const int col0 = 4 + kVX * tx;  // the thread's first column (72-wide rows)
     while (cur.next(a, sg)) {
         const int x0 = sg.x0, y0 = sg.y0, zs = sg.zs, ze = sg.ze;
         const int pi0 = zs - 2;  // first input plane of the segment
         auto in_slot = [&](int p) { return (icn + (uint32_t)(p - pi0)) % kH2NS; };
         auto in_phase = [&](int p) { return ((icn + (uint32_t)(p - pi0)) / kH2NS) & 1; };
+        auto in_plane = [&](int p) { return ins + in_slot(p) * kH2InStage; };
         auto mid_plane = [&](int q) { return mids + ((mcn + (uint32_t)(q - (zs - 1))) % kH2NM) * kH2MidPlane; };
         auto wait_in = [&](int p) {
             if (good)
@@ -586,77 +599,140 @@ __global__ void __launch_bounds__(kStepThreads, 3)
             if (tx == 0)
                 mbar_arrive(&empty[in_slot(p)]);
         };
+        auto interior = [&](int x, int y, int gz) {
+            return x >= 1 && x < a.nx - 1 && y >= 1 && y < a.ny - 1 && gz >= 1 && gz < a.nz - 1;
+        };
+        const int x = x0 + kVX * tx;
+        const int wy0 = y0 + kRPT * wid;
+        // queues of the thread's own points: step j-1 (in) and step j (mid)
+        // values of planes p-1, p, p+1 around the plane being computed
+        float2 inq[kRPT][3], midq[kRPT][3];
+        auto load_in_own = [&](int p, float2 (&dst)[kRPT]) {
+            const float *P = in_plane(p);
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r)
+                dst[r] = *reinterpret_cast<const float2 *>(P + (2 + kRPT * wid + r) * kH2InW + col0);
+        };
+        // step j plane q: own points from the queue inq (planes q-1, q, q+1
+        // at slots 0..2), halo points from the ring; written to the mid ring
+        auto mid_step = [&](int q) {
+            const float *P0 = in_plane(q);
+            float *M = mid_plane(q);
+            const int gz = a.gz0 + q;
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) {
+                const int y = wy0 + r;
+                const int ir = 2 + kRPT * wid + r;  // input row
+                const float2 u = inq[r][1];
+                const float2 ym = (r > 0) ? inq[r > 0 ? r - 1 : 0][1]
+                                          : *reinterpret_cast<const float2 *>(P0 + (ir - 1) * kH2InW + col0);
+                const float2 yp = (r < kRPT - 1) ? inq[r < kRPT - 1 ? r + 1 : 0][1]
+                                                 : *reinterpret_cast<const float2 *>(P0 + (ir + 1) * kH2InW + col0);
+                const float xl = P0[ir * kH2InW + col0 - 1], xr = P0[ir * kH2InW + col0 + 2];
+                float2 m;
+                m.x = interior(x, y, gz) ? heat_point(c, u.x, xl, u.y, ym.x, yp.x, inq[r][0].x, inq[r][2].x) : u.x;
+                m.y = interior(x + 1, y, gz) ? heat_point(c, u.y, u.x, xr, ym.y, yp.y, inq[r][0].y, inq[r][2].y)
+                                             : u.y;
+                midq[r][2] = m;
+                *reinterpret_cast<float2 *>(M + (1 + kRPT * wid + r) * kH2InW + col0) = m;
+            }
+            // halo: warp 0 row y0-1, warp 3 row y0+16 (columns x0-1 .. x0+64),
+            // warp 1 column x0-1, warp 2 column x0+64 (rows y0 .. y0+15)
+            const float *Pm = in_plane(q - 1), *Pp = in_plane(q + 1);
+            auto halo = [&](int mrow, int col) {
+                const int ir = mrow + 1;
+                const int o = ir * kH2InW + col;
+                const float u = P0[o];
+                const int hx = x0 - 4 + col, hy = y0 - 1 + mrow;
+                M[mrow * kH2InW + col] =
+                    interior(hx, hy, gz) ? heat_point(c, u, P0[o - 1], P0[o + 1], P0[o - kH2InW], P0[o + kH2InW],
+                                                      Pm[o], Pp[o])
+                                         : u;
+            };
+            if (wid == 0 || wid == kConsumerWarps - 1) {
+                const int mrow = wid == 0 ? 0 : kH2MidH - 1;
+                halo(mrow, col0);
+                halo(mrow, col0 + 1);
+                if (tx < 2)
+                    halo(mrow, tx == 0 ? 3 : 4 + kTX);
+            } else if (tx < kTY) {
+                halo(1 + tx, wid == 1 ? 3 : 4 + kTX);
+            }
+        };
         // the previous segment's output planes are done before its step j
         // planes are overwritten
         named_bar_sync(1, 32 * kConsumerWarps);
-        // step j plane q (window-relative) from input planes q-1, q, q+1:
-        // 18 rows x 66 columns, columns x0-1 .. x0+64 in pairs
-        auto mid_step = [&](int q) {
-            const float *Pm = ins + in_slot(q - 1) * kH2InStage;
-            const float *P0 = ins + in_slot(q) * kH2InStage;
-            const float *Pp = ins + in_slot(q + 1) * kH2InStage;
-            float *M = mid_plane(q);
-            const int gz = a.gz0 + q;
-            for (int i = tid; i < kH2MidH * 33; i += 32 * kConsumerWarps) {
-                const int row = i / 33, pair = i - row * 33;
-                const int y = y0 - 1 + row;
-                const int ib = (row + 1) * kH2InW;  // the row in the input box
+        // prologue: input planes zs-2 .. zs+1 and step j planes zs-1, zs
+        for (int p = zs - 2; p <= zs + 1; ++p)
+            wait_in(p);
+        if (good) {
+            float2 t[kRPT];
+            load_in_own(zs - 2, t);
 #pragma unroll
-                for (int cc = 0; cc < 2; ++cc) {
-                    const int col = 3 + 2 * pair + cc;
-                    const int x = x0 - 4 + col;
-                    const float u = P0[ib + col];
-                    float r = u;
-                    if (grid_interior(x, y, gz)) {
-                        float sd[2];
-                        sd[0] = 0.0f;
-                        sd[1] = nbr_sum(P0[ib + col - 1], P0[ib + col + 1], P0[ib - kH2InW + col],
-                                        P0[ib + kH2InW + col], Pm[ib + col], Pp[ib + col]);
-                        r = star_L<1>(c, u, sd);
-                    }
-                    M[row * kH2InW + col] = r;
-                }
+            for (int r = 0; r < kRPT; ++r)
+                inq[r][0] = t[r];
+            load_in_own(zs - 1, t);
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r)
+                inq[r][1] = t[r];
+            load_in_own(zs, t);
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r)
+                inq[r][2] = t[r];
+            mid_step(zs - 1);
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) {
+                midq[r][1] = midq[r][2];
+                inq[r][0] = inq[r][1];
+                inq[r][1] = inq[r][2];
             }
-        };
-        // prologue: step j planes zs-1 and zs
-        for (int q = zs - 1; q <= zs; ++q) {
-            for (int p = q - 1; p <= q + 1; ++p)
-                wait_in(p);
-            if (good)
-                mid_step(q);
-            release(q - 1);
+            load_in_own(zs + 1, t);
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r)
+                inq[r][2] = t[r];
+            mid_step(zs);
         }
+        release(zs - 2);
+        release(zs - 1);
         for (int z = zs; z < ze; ++z) {
+            // queues: midq[.][1] = mid(z-1), midq[.][2] = mid(z); inq = in(z-1 .. z+1)
             wait_in(z + 2);
-            if (good)
-                mid_step(z + 1);
+            if (good) {
+                float2 t[kRPT];
+                load_in_own(z + 2, t);
+#pragma unroll
+                for (int r = 0; r < kRPT; ++r) {
+                    midq[r][0] = midq[r][1];
+                    midq[r][1] = midq[r][2];
+                    inq[r][0] = inq[r][1];
+                    inq[r][1] = inq[r][2];
+                    inq[r][2] = t[r];
+                }
+                mid_step(z + 1);  // midq[.][2] = mid(z+1)
+            }
             release(z);
             named_bar_sync(1, 32 * kConsumerWarps);  // step j planes z-1 .. z+1 are complete
             if (!good)
                 continue;
-            const float *Mm = mid_plane(z - 1), *M0 = mid_plane(z), *Mp = mid_plane(z + 1);
+            const float *M0 = mid_plane(z);
             const int gz = a.gz0 + z;
 #pragma unroll
             for (int r = 0; r < kRPT; ++r) {
-                const int y = y0 + kRPT * wid + r;
-                const int row = 1 + kRPT * wid + r;
-#pragma unroll
-                for (int cc = 0; cc < kVX; ++cc) {
-                    const int x = x0 + kVX * tx + cc;
-                    if (x >= a.nx || y >= a.ny)
-                        continue;
-                    const int col = 4 + kVX * tx + cc;
-                    const int o = row * kH2InW + col;
-                    const float u = M0[o];
-                    float res = u;
-                    if (grid_interior(x, y, gz)) {
-                        float sd[2];
-                        sd[0] = 0.0f;
-                        sd[1] = nbr_sum(M0[o - 1], M0[o + 1], M0[o - kH2InW], M0[o + kH2InW], Mm[o], Mp[o]);
-                        res = star_L<1>(c, u, sd);
-                    }
-                    a.out[(int64_t)z * a.plane + (int64_t)y * a.nx + x] = res;
-                }
+                const int y = wy0 + r;
+                if (x >= a.nx || y >= a.ny)
+                    continue;
+                const int mr = 1 + kRPT * wid + r;  // mid row
+                const float2 u = midq[r][1];
+                const float2 ym = (r > 0) ? midq[r > 0 ? r - 1 : 0][1]
+                                          : *reinterpret_cast<const float2 *>(M0 + (mr - 1) * kH2InW + col0);
+                const float2 yp = (r < kRPT - 1) ? midq[r < kRPT - 1 ? r + 1 : 0][1]
+                                                 : *reinterpret_cast<const float2 *>(M0 + (mr + 1) * kH2InW + col0);
+                const float xl = M0[mr * kH2InW + col0 - 1], xr = M0[mr * kH2InW + col0 + 2];
+                float2 o;
+                o.x = interior(x, y, gz) ? heat_point(c, u.x, xl, u.y, ym.x, yp.x, midq[r][0].x, midq[r][2].x) : u.x;
+                o.y = interior(x + 1, y, gz) ? heat_point(c, u.y, u.x, xr, ym.y, yp.y, midq[r][0].y, midq[r][2].y)
+                                             : u.y;
+                *reinterpret_cast<float2 *>(a.out + (int64_t)z * a.plane + (int64_t)y * a.nx + x) = o;
             }
         }
         // input planes ze and ze+1 only fed the last step j plane
