@@ -18,12 +18,13 @@
 // Decoding inverts them and returns RN(q) * 2^(emax-29).
 //
 // GPU design: one thread codes one block.  Bit planes are formed by two 32x32
-// bit-matrix transposes in registers (no per-bit loop) and kept in the
-// thread's column of shared memory for the plane loop, and each plane is
-// emitted in closed form: the verbatim part is one masked word, and all of the
-// plane's group-test tokens are built as one string of at most 127 bits (a
-// few operations per newly significant coefficient) and written with one or
-// two puts.
+// bit-matrix transposes (no per-bit loop); the plane loop stays rolled (its 64
+// words live in the thread's local memory: unrolling it 32 times overflowed
+// the instruction cache, and per-thread columns of shared memory cost the
+// decoder its L1), and each plane is emitted in closed form: the verbatim
+// part is one masked word, and all of the plane's group-test tokens are built
+// as one string of at most 127 bits (a few operations per newly significant
+// coefficient) and written with one or two puts.
 // A block holding an infinity or a NaN is coded as an all-zero block and
 // reported to the caller (encode_block returns false).
 #pragma once
@@ -176,19 +177,6 @@ OOCS_FN void transpose32(uint32_t (&a)[32])
 
 OOCS_FN uint64_t low_mask64(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
 
-// Where a thread keeps its block's 32 plane words (64 bits each) while the
-// plane loop walks them with a runtime index.  A rolled loop over register
-// arrays would put them in local memory anyway (and a loop unrolled 32 times
-// overflows the instruction cache), so the kernels give each thread a column
-// of shared memory: word p at base[p * stride] (stride = threads of the CTA,
-// so a warp's accesses fall in distinct banks).
-struct SharedPlanes {
-    uint64_t *base;
-    int stride;
-    OOCS_FN uint64_t get(int p) const { return base[p * stride]; }
-    OOCS_FN void set(int p, uint64_t w) { base[p * stride] = w; }
-};
-
 // ----------------------------------------------------------------- bit I/O --
 
 template <class Sink>
@@ -295,7 +283,7 @@ struct BitReader {
 // order.  Returns false for a block holding an infinity or a NaN, which is
 // written as an all-zero block (the codec is defined for finite values).
 template <class Sink>
-OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink, SharedPlanes planes)
+OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink)
 {
     const int nwords = 2 * rate;
     uint32_t mag = 0;
@@ -339,15 +327,12 @@ OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink, SharedPla
     });
     transpose32(lo);  // lo[p] / hi[p]: plane p of coefficients 0..31 / 32..63
     transpose32(hi);
-#pragma unroll
-    for (int p = 0; p < 32; ++p)
-        planes.set(p, ((uint64_t)hi[p] << 32) | lo[p]);
 
     bw.put((uint32_t)hdr, 8);
     int left = 64 * rate - 8;
     int n = 0;  // leading coefficients already significant
     for (int p = 31; p >= 0 && left > 0; --p) {
-        const uint64_t X = planes.get(p);
+        const uint64_t X = ((uint64_t)hi[p] << 32) | lo[p];
         const int t = min(n, left);
         bw.put64(X, t);  // verbatim bits of the significant coefficients
         left -= t;
@@ -411,7 +396,7 @@ OOCS_FN bool encode_block(const float (&v)[64], int rate, Sink &&sink, SharedPla
 
 // Decode one block.  src(word_index) returns word i of the block (0 past the end).
 template <class Src>
-OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64], SharedPlanes planes)
+OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64])
 {
     const uint32_t w0 = src(0);
     const int hdr = (int)(w0 & 0xFFu);
@@ -434,9 +419,12 @@ OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64], SharedPlanes plan
     BitReader<Src> br(src);
     br.skip(8);
 
+    uint32_t lo[32], hi[32];
 #pragma unroll
-    for (int p = 0; p < 32; ++p)
-        planes.set(p, 0ull);
+    for (int p = 0; p < 32; ++p) {
+        lo[p] = 0u;
+        hi[p] = 0u;
+    }
     int left = 64 * rate - 8;
     int n = 0;
     for (int p = 31; p >= 0 && left > 0; --p) {
@@ -508,12 +496,6 @@ OOCS_FN void decode_block(int rate, Src &&src, float (&v)[64], SharedPlanes plan
                 }
             }
         }
-        planes.set(p, X);
-    }
-    uint32_t lo[32], hi[32];
-#pragma unroll
-    for (int p = 0; p < 32; ++p) {
-        const uint64_t X = planes.get(p);
         lo[p] = (uint32_t)X;
         hi[p] = (uint32_t)(X >> 32);
     }

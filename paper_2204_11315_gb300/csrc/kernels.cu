@@ -1114,18 +1114,11 @@ OOCS_FN uint32_t *segment_word(const CodecSegments &sg, int64_t blk, int rate, i
     return static_cast<uint32_t *>(sg.blocks[g]) + (blk - sg.first[g]) * (int64_t)(2 * rate) + wi;
 }
 
-// Dynamic shared memory of the codec kernels: the encoder's rows of
-// compressed words (2 rate + 1 per thread), then, for the transform codec,
-// each thread's column of 32 plane words.
-__host__ __device__ inline int codec_rows_words(int rate) { return (kCodecThreads * (2 * rate + 1) + 1) & ~1; }
-
 template <int KIND>
-__global__ void __launch_bounds__(kCodecThreads, 4)
+__global__ void __launch_bounds__(kCodecThreads, 6)
     k_encode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
     extern __shared__ uint32_t sw[];
-    [[maybe_unused]] const SharedPlanes planes{reinterpret_cast<uint64_t *>(sw + codec_rows_words(rate)) + threadIdx.x,
-                                               kCodecThreads};
     pdl_launch_dependents();
     pdl_wait_prior_grid();
     const int nw = 2 * rate, stride = 2 * rate + 1;
@@ -1155,7 +1148,7 @@ __global__ void __launch_bounds__(kCodecThreads, 4)
         if constexpr (KIND == kCodecQuant)
             finite = bq_encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
         else
-            finite = encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; }, planes);
+            finite = encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
         if (!finite)
             atomicOr(&g_device_error, kErrNonFinite);
     }
@@ -1216,8 +1209,7 @@ __global__ void __launch_bounds__(kCodecThreads, 6)
         // each line brings the rest into L1
         const uint32_t *src = static_cast<const uint32_t *>(sg.blocks[g]) + (b - sg.first[g]) * (int64_t)nw;
         float v[64];
-        decode_block(rate, [&](int i) -> uint32_t { return i < nw ? __ldg(src + i) : 0u; }, v,
-                     SharedPlanes{reinterpret_cast<uint64_t *>(sw) + threadIdx.x, kCodecThreads});
+        decode_block(rate, [&](int i) -> uint32_t { return i < nw ? __ldg(src + i) : 0u; }, v);
         store_block(sg, g, nx, ny, bx, by, bl, v);
     } else {
         // quantiser: a warp with a coded block copies its 32 blocks' words to
@@ -1289,28 +1281,6 @@ __global__ void __launch_bounds__(kCodecThreads, 6)
     }
 }
 
-// The transform encoder's rows and plane columns exceed 48 KB at high rates:
-// apply the dynamic shared-memory opt-in (its maximum, 32 rows of 65 words
-// plus the columns) once per device.
-static cudaError_t codec_smem_optin(void (*kern)(const CodecSegments, int, int, int), size_t smem)
-{
-    static bool done[kMaxDevices] = {};
-    int dev = 0;
-    cudaError_t e = current_device(dev);
-    if (e != cudaSuccess)
-        return e;
-    std::lock_guard<std::mutex> lock(g_dev_mu);
-    if (!done[dev]) {
-        const size_t most = (size_t)codec_rows_words(32) * 4 + (size_t)kCodecThreads * 32 * 8;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
-        if (e != cudaSuccess)
-            return e;
-        done[dev] = true;
-    }
-    return smem <= (size_t)codec_rows_words(32) * 4 + (size_t)kCodecThreads * 32 * 8 ? cudaSuccess
-                                                                                         : cudaErrorInvalidValue;
-}
-
 static cudaError_t seal_segments(CodecSegments &sg, int64_t nx, int64_t ny, const int64_t *nlayers)
 {
     if (sg.nseg < 0 || sg.nseg > kMaxCodecSegments)
@@ -1340,13 +1310,10 @@ cudaError_t launch_encode_segments(CodecSegments sg, const int64_t *nlayers, int
     if (nb >= (int64_t)1 << 31)  // the kernels' block indices are 32-bit within a segment
         return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((nb + kCodecThreads - 1) / kCodecThreads));
+    const size_t smem = (size_t)kCodecThreads * (2 * rate + 1) * 4;
     if (kind == kCodecQuant)
-        return launch_pdl(k_encode_layers<kCodecQuant>, grid, dim3(kCodecThreads),
-                          (size_t)kCodecThreads * (2 * rate + 1) * 4, s, sg, (int)nx, (int)ny, rate);
-    const size_t smem = (size_t)codec_rows_words(rate) * 4 + (size_t)kCodecThreads * 32 * 8;
-    cudaError_t e2 = codec_smem_optin(k_encode_layers<kCodecTransform>, smem);
-    if (e2 != cudaSuccess)
-        return e2;
+        return launch_pdl(k_encode_layers<kCodecQuant>, grid, dim3(kCodecThreads), smem, s, sg, (int)nx, (int)ny,
+                          rate);
     return launch_pdl(k_encode_layers<kCodecTransform>, grid, dim3(kCodecThreads), smem, s, sg, (int)nx, (int)ny,
                       rate);
 }
@@ -1368,8 +1335,8 @@ cudaError_t launch_decode_segments(CodecSegments sg, const int64_t *nlayers, int
     if (kind == kCodecQuant)  // staging rows for the warps with coded blocks
         return launch_pdl(k_decode_layers<kCodecQuant>, grid, dim3(kCodecThreads),
                           (size_t)kCodecThreads * (2 * rate + 1) * 4, s, sg, (int)nx, (int)ny, rate);
-    return launch_pdl(k_decode_layers<kCodecTransform>, grid, dim3(kCodecThreads), (size_t)kCodecThreads * 32 * 8,
-                      s, sg, (int)nx, (int)ny, rate);
+    return launch_pdl(k_decode_layers<kCodecTransform>, grid, dim3(kCodecThreads), 0, s, sg, (int)nx, (int)ny,
+                      rate);
 }
 
 cudaError_t launch_encode_layers(const float *planes, int64_t nx, int64_t ny, int64_t nlayers,

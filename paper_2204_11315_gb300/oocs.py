@@ -78,17 +78,17 @@ class oocs_stats(ctypes.Structure):
                 ("load", oocs_kernel_stats), ("step", oocs_kernel_stats),
                 ("store", oocs_kernel_stats), ("h2d", oocs_kernel_stats), ("d2h", oocs_kernel_stats)]
 
-
-class oocs_timeline_entry(ctypes.Structure):
-    _fields_ = [("cls", ctypes.c_int32), ("stream", ctypes.c_int32), ("visit", ctypes.c_int64),
-                ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double)]
-
     def as_dict(self):
         d = {}
         for k, _ in self._fields_:
             v = getattr(self, k)
             d[k] = v.as_dict() if isinstance(v, oocs_kernel_stats) else v
         return d
+
+
+class oocs_timeline_entry(ctypes.Structure):
+    _fields_ = [("cls", ctypes.c_int32), ("stream", ctypes.c_int32), ("visit", ctypes.c_int64),
+                ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double)]
 
 
 class oocs_trace_access(ctypes.Structure):

@@ -144,3 +144,14 @@ def test_null_arguments(P):
     assert L.oocs_synchronize(None, 0) == 1
     assert L.oocs_destroy(None) == 0
     assert L.oocs_last_error(None)
+
+
+def test_stats_binding_layout(P):
+    """The stats record of the binding mirrors oocs_stats: nested per-class
+    counters for the kernels and the copies, as dicts."""
+    d = P.oocs.oocs_stats().as_dict()
+    for k in ("load", "step", "store", "h2d", "d2h"):
+        assert set(d[k]) == {"launches", "units", "device_ms"}
+    assert d["h2d_bytes"] == 0 and d["last_step_ms"] == 0.0
+    e = P.oocs.oocs_timeline_entry()
+    assert [f for f, _ in e._fields_] == ["cls", "stream", "visit", "start_ms", "end_ms"]
