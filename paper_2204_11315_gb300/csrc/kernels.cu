@@ -528,7 +528,7 @@ OOCS_FN float heat_point(const StarCoef &c, float u, float xm, float xp, float y
     return star_L<1>(c, u, sd);
 }
 
-__global__ void __launch_bounds__(kStepThreads, 3)
+__global__ void __launch_bounds__(kStepThreads, 4)
     k_heat_step2(const __grid_constant__ CUtensorMap tm_in, const StepArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -628,7 +628,12 @@ __global__ void __launch_bounds__(kStepThreads, 3)
                                           : *reinterpret_cast<const float2 *>(P0 + (ir - 1) * kH2InW + col0);
                 const float2 yp = (r < kRPT - 1) ? inq[r < kRPT - 1 ? r + 1 : 0][1]
                                                  : *reinterpret_cast<const float2 *>(P0 + (ir + 1) * kH2InW + col0);
-                const float xl = P0[ir * kH2InW + col0 - 1], xr = P0[ir * kH2InW + col0 + 2];
+                // x neighbours: the next lane's columns (loads only at the warp's edges)
+                float xl = __shfl_up_sync(0xffffffffu, u.y, 1), xr = __shfl_down_sync(0xffffffffu, u.x, 1);
+                if (tx == 0)
+                    xl = P0[ir * kH2InW + col0 - 1];
+                if (tx == 31)
+                    xr = P0[ir * kH2InW + col0 + 2];
                 float2 m;
                 m.x = interior(x, y, gz) ? heat_point(c, u.x, xl, u.y, ym.x, yp.x, inq[r][0].x, inq[r][2].x) : u.x;
                 m.y = interior(x + 1, y, gz) ? heat_point(c, u.y, u.x, xr, ym.y, yp.y, inq[r][0].y, inq[r][2].y)
@@ -650,9 +655,26 @@ __global__ void __launch_bounds__(kStepThreads, 3)
                                          : u;
             };
             if (wid == 0 || wid == kConsumerWarps - 1) {
+                // a halo row: the pair of columns of each lane as in mid_step's
+                // own points, then the two end columns
                 const int mrow = wid == 0 ? 0 : kH2MidH - 1;
-                halo(mrow, col0);
-                halo(mrow, col0 + 1);
+                const int ir = mrow + 1;
+                const int o = ir * kH2InW + col0;
+                const float2 u = *reinterpret_cast<const float2 *>(P0 + o);
+                const float2 ym = *reinterpret_cast<const float2 *>(P0 + o - kH2InW);
+                const float2 yp = *reinterpret_cast<const float2 *>(P0 + o + kH2InW);
+                const float2 zm = *reinterpret_cast<const float2 *>(Pm + o);
+                const float2 zp = *reinterpret_cast<const float2 *>(Pp + o);
+                float xl = __shfl_up_sync(0xffffffffu, u.y, 1), xr = __shfl_down_sync(0xffffffffu, u.x, 1);
+                if (tx == 0)
+                    xl = P0[o - 1];
+                if (tx == 31)
+                    xr = P0[o + 2];
+                const int hy = y0 - 1 + mrow;
+                float2 m;
+                m.x = interior(x, hy, gz) ? heat_point(c, u.x, xl, u.y, ym.x, yp.x, zm.x, zp.x) : u.x;
+                m.y = interior(x + 1, hy, gz) ? heat_point(c, u.y, u.x, xr, ym.y, yp.y, zm.y, zp.y) : u.y;
+                *reinterpret_cast<float2 *>(M + mrow * kH2InW + col0) = m;
                 if (tx < 2)
                     halo(mrow, tx == 0 ? 3 : 4 + kTX);
             } else if (tx < kTY) {
@@ -719,20 +741,23 @@ __global__ void __launch_bounds__(kStepThreads, 3)
 #pragma unroll
             for (int r = 0; r < kRPT; ++r) {
                 const int y = wy0 + r;
-                if (x >= a.nx || y >= a.ny)
-                    continue;
                 const int mr = 1 + kRPT * wid + r;  // mid row
                 const float2 u = midq[r][1];
                 const float2 ym = (r > 0) ? midq[r > 0 ? r - 1 : 0][1]
                                           : *reinterpret_cast<const float2 *>(M0 + (mr - 1) * kH2InW + col0);
                 const float2 yp = (r < kRPT - 1) ? midq[r < kRPT - 1 ? r + 1 : 0][1]
                                                  : *reinterpret_cast<const float2 *>(M0 + (mr + 1) * kH2InW + col0);
-                const float xl = M0[mr * kH2InW + col0 - 1], xr = M0[mr * kH2InW + col0 + 2];
+                float xl = __shfl_up_sync(0xffffffffu, u.y, 1), xr = __shfl_down_sync(0xffffffffu, u.x, 1);
+                if (tx == 0)
+                    xl = M0[mr * kH2InW + col0 - 1];
+                if (tx == 31)
+                    xr = M0[mr * kH2InW + col0 + 2];
                 float2 o;
                 o.x = interior(x, y, gz) ? heat_point(c, u.x, xl, u.y, ym.x, yp.x, midq[r][0].x, midq[r][2].x) : u.x;
                 o.y = interior(x + 1, y, gz) ? heat_point(c, u.y, u.x, xr, ym.y, yp.y, midq[r][0].y, midq[r][2].y)
                                              : u.y;
-                *reinterpret_cast<float2 *>(a.out + (int64_t)z * a.plane + (int64_t)y * a.nx + x) = o;
+                if (x < a.nx && y < a.ny)
+                    *reinterpret_cast<float2 *>(a.out + (int64_t)z * a.plane + (int64_t)y * a.nx + x) = o;
             }
         }
         // input planes ze and ze+1 only fed the last step j plane
@@ -860,11 +885,11 @@ static cudaError_t step_residency(int &resident, int &sms)
 
 // Launch geometry of a z-march over window planes [a.z_lo, a.z_hi) of an
 // nx x ny grid of 64 x 16 tiles, with `slots` CTAs resident at once.
-// Chunked launch when some z chunking (>= 12 planes per CTA) fills the last
+// Chunked launch when some z chunking (>= min_planes per CTA) fills the last
 // wave of CTAs to 90 %; otherwise (short windows on a plane whose tiles do not
 // fill the SMs evenly, e.g. 256 tiles on 304 slots) one wave of equal
 // tile-plane ranges.  Sets a.zchunk, a.tiles_y and a.ntiles.
-static dim3 step_grid(int64_t nx, int64_t ny, int slots, StepArgs &a)
+static dim3 step_grid(int64_t nx, int64_t ny, int slots, StepArgs &a, int min_planes = 12)
 {
     const int tiles_x = (int)((nx + kTX - 1) / kTX);
     const int tiles_y = (int)((ny + kTY - 1) / kTY);
@@ -874,7 +899,7 @@ static dim3 step_grid(int64_t nx, int64_t ny, int slots, StepArgs &a)
     a.ntiles = tiles;
     int best = 1;
     double best_eff = 0.0;
-    const int max_chunks = std::max(1, nplanes / 12);
+    const int max_chunks = std::max(1, nplanes / min_planes);
     for (int nc = 1; nc <= max_chunks && nc <= 64; ++nc) {
         const int zc = (nplanes + nc - 1) / nc;
         const int real = (nplanes + zc - 1) / zc;
@@ -973,7 +998,9 @@ cudaError_t launch_heat_step2(const StepLaunch &L, cudaStream_t s)
     for (int i = 0; i < 5; ++i)
         a.c.c[i] = L.coef[i];
     a.src_x = a.src_y = a.src_zw = -1;
-    const dim3 grid = step_grid(L.nx, L.ny, sms * resident, a);
+    // a segment re-reads a 4-plane z halo and recomputes two step j planes:
+    // keep z chunks long
+    const dim3 grid = step_grid(L.nx, L.ny, sms * resident, a, 48);
     return launch_pdl(k_heat_step2, grid, dim3(32, kConsumerWarps + 1, 1), kH2Smem, s, m, a);
 }
 
