@@ -331,6 +331,7 @@ struct oocs_ctx {
     int64_t srec_t0 = 0;
 
     cudaEvent_t ev_decoded[3] = {}, ev_h2d[3] = {}, ev_wrel[3] = {}, ev_join[3] = {};
+    cudaEvent_t ev_out[3] = {};    // out slot q copied back (streams by role)
     cudaEvent_t ev_codec[2] = {};  // oocs_compress / oocs_decompress: a chunk's raw copy has run
     std::vector<cudaEvent_t> ev_d2h;
     std::vector<char> d2h_recorded;
@@ -387,7 +388,7 @@ struct oocs_batch {
     std::vector<oocs_ctx *> ctx;
     char *ws = nullptr;
     cudaStream_t st[3] = {};
-    cudaEvent_t ev_decoded[3] = {}, ev_h2d[3] = {}, ev_wrel[3] = {}, ev_join[3] = {};
+    cudaEvent_t ev_decoded[3] = {}, ev_h2d[3] = {}, ev_wrel[3] = {}, ev_join[3] = {}, ev_out[3] = {};
     uint64_t g = 0;
     std::vector<oocs_trace_op> *trace = nullptr;
     // CUDA graph of one oocs_batch_step (oocs_batch_capture / oocs_batch_launch)
@@ -473,7 +474,7 @@ oocs_status check_ready(oocs_ctx *c)
 // ---- scheduling primitives: issued to CUDA, or recorded in trace mode
 
 enum : int { kEvDecoded = 100, kEvH2D = 200, kEvWrel = 300, kEvJoin = 400, kEvT0 = 500, kEvT1 = 501,
-             kEvD2H = 1000 };
+             kEvOut = 600, kEvD2H = 1000 };
 
 cudaEvent_t event_of(oocs_ctx *c, int id)
 {
@@ -487,6 +488,7 @@ cudaEvent_t event_of(oocs_ctx *c, int id)
     case 1: return c->ev_decoded[id % 100];
     case 2: return c->ev_h2d[id % 100];
     case 3: return c->ev_wrel[id % 100];
+    case 6: return c->ev_out[id % 100];
     default: return c->ev_join[id % 100];
     }
 }
@@ -716,8 +718,19 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     const uint64_t g = c->g;
     const int q = (int)(g % 3);
     const int qp = (int)((g + 2) % 3);  // slot of visit g-1
-    cudaStream_t st = c->st[q];
     const int wb = (d.working_buffers == OOCS_SWB) ? 0 : q;
+    // Streams by role with one working buffer: host->device copies on stream
+    // 0, kernels on stream 1, device->host copies on stream 2, ordered by the
+    // same events as Algorithm 1 (Fig. 8a).  With the round robin of the
+    // listing (visit g's copies and kernels all on stream g % 3) a visit's
+    // next copy waits in its stream behind the copy-back of the visit three
+    // before, and on GB300 kernels of one visit were then measured waiting
+    // for the copies of the next (every other visit idle ~7 ms of ~12).
+    // Classic mode (three working buffers) keeps the round robin, whose
+    // kernels of consecutive visits may overlap.
+    const bool roles = d.working_buffers == OOCS_SWB;
+    const int sh = roles ? 0 : q, sk = roles ? 1 : q, sd = roles ? 2 : q;
+    cudaStream_t st_h = c->st[sh], st_k = c->st[sk], st_d = c->st[sd];
 
     const int64_t z0 = (int64_t)s * v.T;
     const int64_t z1 = std::min<int64_t>(z0 + v.T, d.nz);
@@ -730,24 +743,24 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
 
     // 1. staging slot q is free once visit g-2 has read its borrowed overlap
     if (g >= 2)
-        SCHED(sched_wait(c, q, kEvDecoded + (int)((g - 2) % 3)));
+        SCHED(sched_wait(c, sh, kEvDecoded + (int)((g - 2) % 3)));
     // 2. host layers [n0, n1) were last written by slabs s and s+1 of the previous sweep
     for (int ss = s; ss <= s + 1 && ss < v.S; ++ss)
         if (c->d2h_recorded[ss])
-            SCHED(sched_wait(c, q, kEvD2H + c->d2h_base + ss));
+            SCHED(sched_wait(c, sh, kEvD2H + c->d2h_base + ss));
     // 3. H2D of the new layers of every streamed field
     if (c->trace) {
         if (n1 > n0) {
             oocs_trace_access a[4] = {acc(OOCS_RES_IN_SLOT, q, n0 / 4, n1 / 4, true)};
             for (int f = 0; f < v.fin_stream; ++f)
                 a[1 + f] = acc(OOCS_RES_HOST, c->host_base + in_field_id(c, f), n0 / 4, n1 / 4, false);
-            trace_push(c, OOCS_OP_H2D, q, -1, (int64_t)g, {a[0], a[1]});
+            trace_push(c, OOCS_OP_H2D, sh, -1, (int64_t)g, {a[0], a[1]});
             for (int f = 1; f < v.fin_stream; ++f)
                 c->trace->back().access[c->trace->back().naccess++] = a[1 + f];
         }
     } else {
         KernelScope ks;
-        oocs_status r = ks.begin(c, st, kClsH2D);
+        oocs_status r = ks.begin(c, st_h, kClsH2D);
         if (r != OOCS_OK)
             return r;
         for (int f = 0; f < v.fin_stream; ++f) {
@@ -755,7 +768,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             const uint64_t bytes = (uint64_t)(n1 - n0) / 4 * v.layer_bytes;
             if (bytes) {
                 CU(c, cudaMemcpyAsync(c->in_slot(q, f), c->store[id] + (uint64_t)(n0 / 4) * v.layer_bytes,
-                                      bytes, cudaMemcpyHostToDevice, st));
+                                      bytes, cudaMemcpyHostToDevice, st_h));
             }
         }
         r = ks.end(kClsH2D, (uint64_t)v.fin_stream * (uint64_t)(n1 - n0) / 4 * v.layer_bytes);
@@ -763,13 +776,16 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             return r;
     }
     c->stats.h2d_bytes += (uint64_t)v.fin_stream * (uint64_t)(n1 - n0) / 4 * v.layer_bytes;
-    SCHED(sched_record(c, q, kEvH2D + q));
-    // 4. working buffer released by visit g-1 (single working buffer); the
-    //    overlap borrowed from visit g-1's slot has landed
+    SCHED(sched_record(c, sh, kEvH2D + q));
+    // 4. the visit's own layers have landed (when copies have a stream of
+    //    their own); the working buffer is released by visit g-1 (single
+    //    working buffer); the overlap borrowed from visit g-1's slot has landed
+    if (roles)
+        SCHED(sched_wait(c, sk, kEvH2D + q));
     if (g >= 1 && d.working_buffers == OOCS_SWB)
-        SCHED(sched_wait(c, q, kEvWrel + (int)((g - 1) % 3)));
+        SCHED(sched_wait(c, sk, kEvWrel + (int)((g - 1) % 3)));
     if (s > 0)
-        SCHED(sched_wait(c, q, kEvH2D + qp));
+        SCHED(sched_wait(c, sk, kEvH2D + qp));
     // 5. load / decode the window at time t
     // slot of slab s-1 holds layers starting at its own n0
     const int64_t pz0 = (int64_t)(s - 1) * v.T;
@@ -777,12 +793,12 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     const int64_t plane_f = d.nx * d.ny;
     if (c->trace) {
         if (s > 0)
-            trace_push(c, OOCS_OP_LOAD, q, -1, (int64_t)g,
+            trace_push(c, OOCS_OP_LOAD, sk, -1, (int64_t)g,
                        {acc(OOCS_RES_IN_SLOT, qp, w0 / 4, n0 / 4, false),
                         acc(OOCS_RES_IN_SLOT, q, n0 / 4, n1 / 4, false),
                         acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
         else
-            trace_push(c, OOCS_OP_LOAD, q, -1, (int64_t)g,
+            trace_push(c, OOCS_OP_LOAD, sk, -1, (int64_t)g,
                        {acc(OOCS_RES_IN_SLOT, q, n0 / 4, n1 / 4, false),
                         acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
     } else if (d.rate_bits > 0) {
@@ -803,10 +819,10 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             }
         }
         KernelScope ks;
-        oocs_status r = ks.begin(c, st, kClsLoad);
+        oocs_status r = ks.begin(c, st_k, kClsLoad);
         if (r != OOCS_OK)
             return r;
-        CU(c, launch_decode_segments(sg, nl, d.nx, d.ny, d.rate_bits, d.codec, st));
+        CU(c, launch_decode_segments(sg, nl, d.nx, d.ny, d.rate_bits, d.codec, st_k));
         c->stats.kernel_launches++;
         r = ks.end(kClsLoad, (uint64_t)v.fin_stream * (w1 - w0) * plane_f);
         if (r != OOCS_OK)
@@ -815,16 +831,16 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         for (int f = 0; f < v.fin_stream; ++f) {
             float *dst = c->wbuf(wb, f);
             if (s > 0) {
-                oocs_status r = load_layers(c, c->in_slot(qp, f), pn0 / 4, w0 / 4, n0 / 4, dst, w0, st);
+                oocs_status r = load_layers(c, c->in_slot(qp, f), pn0 / 4, w0 / 4, n0 / 4, dst, w0, st_k);
                 if (r != OOCS_OK)
                     return r;
             }
-            oocs_status r = load_layers(c, c->in_slot(q, f), n0 / 4, n0 / 4, n1 / 4, dst, w0, st);
+            oocs_status r = load_layers(c, c->in_slot(q, f), n0 / 4, n0 / 4, n1 / 4, dst, w0, st_k);
             if (r != OOCS_OK)
                 return r;
         }
     }
-    SCHED(sched_record(c, q, kEvDecoded + q));
+    SCHED(sched_record(c, sk, kEvDecoded + q));
 
     // 6. k_eff steps over the shrinking trapezoid
     int cur = 0, oth = 1;
@@ -843,7 +859,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     // visit), so profiling does not sit between consecutive step kernels
     KernelScope ks_steps;
     {
-        oocs_status r = ks_steps.begin(c, st, kClsStep);
+        oocs_status r = ks_steps.begin(c, st_k, kClsStep);
         if (r != OOCS_OK)
             return r;
     }
@@ -862,9 +878,9 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             Ls.cur = c->wbuf(wb, cur);
             Ls.out = c->wbuf(wb, oth);
             if (c->trace)
-                trace_push(c, OOCS_OP_STEP, q, -1, (int64_t)g, {acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
+                trace_push(c, OOCS_OP_STEP, sk, -1, (int64_t)g, {acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
             else
-                CU(c, launch_heat_step2(Ls, st));
+                CU(c, launch_heat_step2(Ls, st_k));
             c->stats.kernel_launches++;
             ++launches;
             step_units += (uint64_t)(hi1 - lo1 + hi - lo) * d.nx * d.ny;
@@ -902,9 +918,9 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             Ls.w = c->w[tstep];
         }
         if (c->trace)
-            trace_push(c, OOCS_OP_STEP, q, -1, (int64_t)g, {acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
+            trace_push(c, OOCS_OP_STEP, sk, -1, (int64_t)g, {acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
         else
-            CU(c, launch_star_step(Ls, st));
+            CU(c, launch_star_step(Ls, st_k));
         c->stats.kernel_launches++;
         ++launches;
         step_units += (uint64_t)(hi - lo) * d.nx * d.ny;
@@ -912,7 +928,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         // the visit computes: record u^(tstep+1) there
         if (c->rec && c->rec_z >= z0 && c->rec_z < z1 && tstep < c->rec_n && !c->trace)
             CU(c, cudaMemcpyAsync(c->rec + tstep * plane_f, Ls.out + (c->rec_z - w0) * plane_f,
-                                  (size_t)plane_f * 4, cudaMemcpyDeviceToDevice, st));
+                                  (size_t)plane_f * 4, cudaMemcpyDeviceToDevice, st_k));
         std::swap(cur, oth);
     }
     {
@@ -920,9 +936,12 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         if (r != OOCS_OK)
             return r;
     }
-    // 7. interior [z0, z1) -> out slot(s): u^(t+k) and, for the wave, u^(t+k-1)
+    // 7. interior [z0, z1) -> out slot(s): u^(t+k) and, for the wave, u^(t+k-1);
+    //    the slot was copied back by visit g-3 (by role: on another stream)
+    if (roles && g >= 3)
+        SCHED(sched_wait(c, sk, kEvOut + q));
     if (c->trace) {
-        trace_push(c, OOCS_OP_STORE, q, -1, (int64_t)g,
+        trace_push(c, OOCS_OP_STORE, sk, -1, (int64_t)g,
                    {acc(OOCS_RES_WORK, wb, z0 / 4, z1 / 4, false), acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, true)});
     } else if (d.rate_bits > 0) {
         // one encode launch for both output fields
@@ -935,28 +954,31 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             nl[sg.nseg++] = (z1 - z0) / 4;
         }
         KernelScope ks;
-        oocs_status r = ks.begin(c, st, kClsStore);
+        oocs_status r = ks.begin(c, st_k, kClsStore);
         if (r != OOCS_OK)
             return r;
-        CU(c, launch_encode_segments(sg, nl, d.nx, d.ny, d.rate_bits, d.codec, st));
+        CU(c, launch_encode_segments(sg, nl, d.nx, d.ny, d.rate_bits, d.codec, st_k));
         c->stats.kernel_launches++;
         r = ks.end(kClsStore, (uint64_t)v.fout * (z1 - z0) * plane_f);
         if (r != OOCS_OK)
             return r;
     } else {
-        oocs_status r = store_layers(c, c->wbuf(wb, cur), w0, z0 / 4, z1 / 4, c->out_slot(q, 0), st);
+        oocs_status r = store_layers(c, c->wbuf(wb, cur), w0, z0 / 4, z1 / 4, c->out_slot(q, 0), st_k);
         if (r != OOCS_OK)
             return r;
         if (v.fout == 2) {
-            r = store_layers(c, c->wbuf(wb, oth), w0, z0 / 4, z1 / 4, c->out_slot(q, 1), st);
+            r = store_layers(c, c->wbuf(wb, oth), w0, z0 / 4, z1 / 4, c->out_slot(q, 1), st_k);
             if (r != OOCS_OK)
                 return r;
         }
     }
-    SCHED(sched_record(c, q, kEvWrel + q));
-    // 8. D2H into the host store, in place
+    SCHED(sched_record(c, sk, kEvWrel + q));
+    // 8. D2H into the host store, in place (after the encode, by role on
+    //    the copy-back stream)
+    if (roles)
+        SCHED(sched_wait(c, sd, kEvWrel + q));
     if (c->trace) {
-        trace_push(c, OOCS_OP_D2H, q, -1, (int64_t)g,
+        trace_push(c, OOCS_OP_D2H, sd, -1, (int64_t)g,
                    {acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, false),
                     acc(OOCS_RES_HOST, c->host_base, z0 / 4, z1 / 4, true)});
         if (v.fout == 2)
@@ -966,7 +988,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     {
         KernelScope ks;
         if (!c->trace) {
-            oocs_status r = ks.begin(c, st, kClsD2H);
+            oocs_status r = ks.begin(c, st_d, kClsD2H);
             if (r != OOCS_OK)
                 return r;
         }
@@ -974,7 +996,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
             if (!c->trace)
                 CU(c, cudaMemcpyAsync(c->store[f] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, f),
-                                      bytes, cudaMemcpyDeviceToHost, st));
+                                      bytes, cudaMemcpyDeviceToHost, st_d));
             c->stats.d2h_bytes += bytes;
         }
         if (!c->trace) {
@@ -993,10 +1015,12 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
         const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
         if (!c->trace)
             CU(c, cudaMemcpyAsync(c->srec[i] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, f), bytes,
-                                  cudaMemcpyDeviceToHost, st));
+                                  cudaMemcpyDeviceToHost, st_d));
         c->stats.d2h_bytes += bytes;
     }
-    SCHED(sched_record(c, q, kEvD2H + c->d2h_base + s));
+    SCHED(sched_record(c, sd, kEvD2H + c->d2h_base + s));
+    if (roles)
+        SCHED(sched_record(c, sd, kEvOut + q));
     c->d2h_recorded[s] = 1;
     c->g++;
     c->stats.slabs_done++;
@@ -1236,6 +1260,7 @@ oocs_status oocs_create(const oocs_desc *desc, void *workspace, uint64_t workspa
         if (e == cudaSuccess) e = mk(&c->ev_h2d[i]);
         if (e == cudaSuccess) e = mk(&c->ev_wrel[i]);
         if (e == cudaSuccess) e = mk(&c->ev_join[i]);
+        if (e == cudaSuccess) e = mk(&c->ev_out[i]);
     }
     for (int i = 0; i < nd2h && e == cudaSuccess; ++i)
         e = mk(&c->ev_d2h[i]);
@@ -1825,6 +1850,7 @@ static void destroy_ctx(oocs_ctx *ctx)
             kill(ctx->ev_h2d[i]);
             kill(ctx->ev_wrel[i]);
             kill(ctx->ev_join[i]);
+            kill(ctx->ev_out[i]);
         }
     for (auto &e : ctx->ev_d2h)
         kill(e);
@@ -2077,6 +2103,7 @@ oocs_status batch_build(oocs_batch *b, const std::vector<oocs_desc> &d, const st
             c->ev_h2d[k] = b->ev_h2d[k];
             c->ev_wrel[k] = b->ev_wrel[k];
             c->ev_join[k] = b->ev_join[k];
+            c->ev_out[k] = b->ev_out[k];
         }
         memset(&c->stats, 0, sizeof(c->stats));
         c->stats.workspace_bytes = L.total;
@@ -2124,6 +2151,7 @@ void batch_free(oocs_batch *b)
         kill(b->ev_h2d[i]);
         kill(b->ev_wrel[i]);
         kill(b->ev_join[i]);
+        kill(b->ev_out[i]);
     }
     delete b;
 }
@@ -2288,6 +2316,7 @@ oocs_status oocs_batch_create(const oocs_desc *descs, int32_t n, void *workspace
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_h2d[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_wrel[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out[i], cudaEventDisableTiming);
     }
     if (e != cudaSuccess) {
         batch_free(b);

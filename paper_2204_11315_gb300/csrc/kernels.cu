@@ -528,7 +528,7 @@ OOCS_FN float heat_point(const StarCoef &c, float u, float xm, float xp, float y
     return star_L<1>(c, u, sd);
 }
 
-__global__ void __launch_bounds__(kStepThreads, 4)
+__global__ void __launch_bounds__(kStepThreads, 3)
     k_heat_step2(const __grid_constant__ CUtensorMap tm_in, const StepArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -1000,7 +1000,7 @@ cudaError_t launch_heat_step2(const StepLaunch &L, cudaStream_t s)
     a.src_x = a.src_y = a.src_zw = -1;
     // a segment re-reads a 4-plane z halo and recomputes two step j planes:
     // keep z chunks long
-    const dim3 grid = step_grid(L.nx, L.ny, sms * resident, a, 48);
+    const dim3 grid = step_grid(L.nx, L.ny, sms * resident, a, 24);
     return launch_pdl(k_heat_step2, grid, dim3(32, kConsumerWarps + 1, 1), kH2Smem, s, m, a);
 }
 

@@ -346,3 +346,20 @@ def test_adjoint_steps_in_one_call(P, calls):
     if max(calls) > 1:
         assert len(cut) < len(trace)
         assert check(cut, swb=True) is not None
+
+
+def test_streams_by_role_with_one_working_buffer(P):
+    """One working buffer: host->device copies on stream 0, kernels on stream
+    1, device->host copies on stream 2 (classic mode keeps the round robin),
+    and dropping the wait that keeps an out slot until its copy-back has run
+    leaves a race the check reports."""
+    desc = _desc(P, "wave", (128, 72, 40), 16, 4, 32, 1)
+    trace = P.oocs_trace_schedule(desc, [12])
+    assert check(trace) is None
+    streams = {op: {o["stream"] for o in trace if o["op"] == op} for op in ("H2D", "LOAD", "STEP", "STORE", "D2H")}
+    assert streams == {"H2D": {0}, "LOAD": {1}, "STEP": {1}, "STORE": {1}, "D2H": {2}}
+    cut = [o for o in trace if not (o["op"] == "WAIT" and o["event"] in range(600, 603))]
+    assert len(cut) < len(trace)
+    assert "race" in check(cut)
+    classic = P.oocs_trace_schedule(_desc(P, "wave", (128, 72, 40), 16, 4, 32, 3), [12])
+    assert {o["stream"] for o in classic if o["op"] == "H2D"} == {0, 1, 2}
