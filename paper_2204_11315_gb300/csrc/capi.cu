@@ -1039,7 +1039,10 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k, const char *fwd,
     const oocs_desc &d = c->d;
     const uint64_t g = c->g;
     const int q = (int)(g % 3);
-    cudaStream_t st = c->st[q];
+    // streams by role, as in enqueue_slab: host->device copies on stream 0,
+    // kernels on stream 1, device->host copies on stream 2
+    const int sh = 0, sk = 1, sd = 2;
+    cudaStream_t st_h = c->st[sh], st_k = c->st[sk], st_d = c->st[sd];
     const int64_t z0 = (int64_t)s * v.T;
     const int64_t z1 = std::min<int64_t>(z0 + v.T, d.nz);
     const int64_t w0 = std::max<int64_t>(z0 - v.h, 0);
@@ -1053,7 +1056,7 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k, const char *fwd,
     const int par = (int)(k & 1);  // this step's set of per-slab D2H events
     // 1. staging slot q is free once visit g-2 has decoded it
     if (g >= 2)
-        SCHED(sched_wait(c, q, kEvDecoded + (int)((g - 2) % 3)));
+        SCHED(sched_wait(c, sh, kEvDecoded + (int)((g - 2) % 3)));
     // 2. the window of lam^k was written by the previous step (k+1) of this
     //    call over slabs s-1 .. s+1; waiting for those copies also orders this
     //    visit's later write of lam^(k-1) after the previous step's reads of
@@ -1061,10 +1064,10 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k, const char *fwd,
     if (chained)
         for (int ss = std::max(s - 1, 0); ss <= std::min(s + 1, v.S - 1); ++ss)
             if (c->d2h_recorded[(1 - par) * v.S + ss])
-                SCHED(sched_wait(c, q, kEvD2H + c->d2h_base + (1 - par) * v.S + ss));
+                SCHED(sched_wait(c, sh, kEvD2H + c->d2h_base + (1 - par) * v.S + ss));
     // 3. H2D of the windows of lam^k and u^(k-1) and the interior of lam^(k+1)
     if (c->trace) {
-        trace_push(c, OOCS_OP_H2D, q, -1, (int64_t)g,
+        trace_push(c, OOCS_OP_H2D, sh, -1, (int64_t)g,
                    {acc(OOCS_RES_IN_SLOT, q, w0 / 4, w1 / 4, true),
                     acc(OOCS_RES_HOST, c->host_base + c->store_id[OOCS_FIELD_LAM], l0[0], l1[0], false),
                     acc(OOCS_RES_HOST, c->host_base + c->store_id[OOCS_FIELD_LAM_PREV], l0[1], l1[1], false),
@@ -1073,21 +1076,24 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k, const char *fwd,
         const char *src[3] = {c->store[store_of[0]], c->store[store_of[1]], fwd};
         for (int f = 0; f < 3; ++f)
             CU(c, cudaMemcpyAsync(c->in_slot(q, f), src[f] + (uint64_t)l0[f] * v.layer_bytes,
-                                  (uint64_t)(l1[f] - l0[f]) * v.layer_bytes, cudaMemcpyHostToDevice, st));
+                                  (uint64_t)(l1[f] - l0[f]) * v.layer_bytes, cudaMemcpyHostToDevice, st_h));
     }
     for (int f = 0; f < 3; ++f)
         c->stats.h2d_bytes += (uint64_t)(l1[f] - l0[f]) * v.layer_bytes;
-    // 4. the working buffer is free once visit g-1 has encoded from it
+    SCHED(sched_record(c, sh, kEvH2D + q));
+    // 4. the visit's layers have landed; the working buffer is free once
+    //    visit g-1 has encoded from it (implied on the kernel stream)
+    SCHED(sched_wait(c, sk, kEvH2D + q));
     if (g >= 1)
-        SCHED(sched_wait(c, q, kEvWrel + (int)((g - 1) % 3)));
+        SCHED(sched_wait(c, sk, kEvWrel + (int)((g - 1) % 3)));
     // 5. decode lam^k, lam^(k+1) (interior planes, at their window positions), u^(k-1)
     float *dst[3] = {W0, W1 + (z0 - w0) * plane_f, W2};
     if (c->trace) {
-        trace_push(c, OOCS_OP_LOAD, q, -1, (int64_t)g,
+        trace_push(c, OOCS_OP_LOAD, sk, -1, (int64_t)g,
                    {acc(OOCS_RES_IN_SLOT, q, w0 / 4, w1 / 4, false), acc(OOCS_RES_WORK, 0, w0 / 4, w1 / 4, true)});
     } else {
         KernelScope ks;
-        oocs_status r = ks.begin(c, st, kClsLoad);
+        oocs_status r = ks.begin(c, st_k, kClsLoad);
         if (r != OOCS_OK)
             return r;
         if (d.rate_bits > 0) {
@@ -1098,18 +1104,18 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k, const char *fwd,
                 sg.planes[sg.nseg] = dst[f];
                 nl[sg.nseg++] = l1[f] - l0[f];
             }
-            CU(c, launch_decode_segments(sg, nl, d.nx, d.ny, d.rate_bits, d.codec, st));
+            CU(c, launch_decode_segments(sg, nl, d.nx, d.ny, d.rate_bits, d.codec, st_k));
             c->stats.kernel_launches++;
         } else {
             for (int f = 0; f < 3; ++f)
                 CU(c, cudaMemcpyAsync(dst[f], c->in_slot(q, f), (uint64_t)(l1[f] - l0[f]) * v.layer_bytes,
-                                      cudaMemcpyDeviceToDevice, st));
+                                      cudaMemcpyDeviceToDevice, st_k));
         }
         r = ks.end(kClsLoad, (uint64_t)(2 * (w1 - w0) + (z1 - z0)) * plane_f);
         if (r != OOCS_OK)
             return r;
     }
-    SCHED(sched_record(c, q, kEvDecoded + q));
+    SCHED(sched_record(c, sk, kEvDecoded + q));
     // 6. m lam^k over the window, the gradient term, the adjoint step
     StepLaunch G;
     memset(&G, 0, sizeof(G));
@@ -1150,41 +1156,46 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k, const char *fwd,
     }
     if (c->trace) {
         for (int i = 0; i < 3; ++i)
-            trace_push(c, OOCS_OP_STEP, q, -1, (int64_t)g, {acc(OOCS_RES_WORK, 0, w0 / 4, w1 / 4, true)});
+            trace_push(c, OOCS_OP_STEP, sk, -1, (int64_t)g, {acc(OOCS_RES_WORK, 0, w0 / 4, w1 / 4, true)});
     } else {
         KernelScope ks;
-        oocs_status r = ks.begin(c, st, kClsStep);
+        oocs_status r = ks.begin(c, st_k, kClsStep);
         if (r != OOCS_OK)
             return r;
-        CU(c, launch_product(W3, c->ro_m() + w0 * plane_f, W0, (w1 - w0) * plane_f, st));
-        CU(c, launch_star_step(G, st));
-        CU(c, launch_star_step(A, st));
+        CU(c, launch_product(W3, c->ro_m() + w0 * plane_f, W0, (w1 - w0) * plane_f, st_k));
+        CU(c, launch_star_step(G, st_k));
+        CU(c, launch_star_step(A, st_k));
         c->stats.kernel_launches += 3;
         r = ks.end(kClsStep, (uint64_t)(z1 - z0) * plane_f, 2);
         if (r != OOCS_OK)
             return r;
     }
-    // 7. encode lam^(k-1) on the interior into the out slot
+    // 7. encode lam^(k-1) on the interior into the out slot (copied back by
+    //    visit g-3 on the copy-back stream)
+    if (g >= 3)
+        SCHED(sched_wait(c, sk, kEvOut + q));
     if (c->trace) {
-        trace_push(c, OOCS_OP_STORE, q, -1, (int64_t)g,
+        trace_push(c, OOCS_OP_STORE, sk, -1, (int64_t)g,
                    {acc(OOCS_RES_WORK, 0, z0 / 4, z1 / 4, false), acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, true)});
     } else {
-        oocs_status r = store_layers(c, W1, w0, z0 / 4, z1 / 4, c->out_slot(q, 0), st);
+        oocs_status r = store_layers(c, W1, w0, z0 / 4, z1 / 4, c->out_slot(q, 0), st_k);
         if (r != OOCS_OK)
             return r;
     }
-    SCHED(sched_record(c, q, kEvWrel + q));
-    // 8. D2H over lam^(k+1)'s layers of the host store
+    SCHED(sched_record(c, sk, kEvWrel + q));
+    // 8. D2H over lam^(k+1)'s layers of the host store, after the encode
+    SCHED(sched_wait(c, sd, kEvWrel + q));
     const uint64_t bytes = (uint64_t)(z1 - z0) / 4 * v.layer_bytes;
     if (c->trace)
-        trace_push(c, OOCS_OP_D2H, q, -1, (int64_t)g,
+        trace_push(c, OOCS_OP_D2H, sd, -1, (int64_t)g,
                    {acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, false),
                     acc(OOCS_RES_HOST, c->host_base + c->store_id[OOCS_FIELD_LAM_PREV], z0 / 4, z1 / 4, true)});
     else
         CU(c, cudaMemcpyAsync(c->store[OOCS_FIELD_LAM_PREV] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, 0),
-                              bytes, cudaMemcpyDeviceToHost, st));
+                              bytes, cudaMemcpyDeviceToHost, st_d));
     c->stats.d2h_bytes += bytes;
-    SCHED(sched_record(c, q, kEvD2H + c->d2h_base + par * v.S + s));
+    SCHED(sched_record(c, sd, kEvD2H + c->d2h_base + par * v.S + s));
+    SCHED(sched_record(c, sd, kEvOut + q));
     c->d2h_recorded[par * v.S + s] = 1;
     c->g++;
     c->stats.slabs_done++;
