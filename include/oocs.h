@@ -115,11 +115,13 @@ typedef struct {
     int32_t codec;               /* rate_bits > 0: OOCS_CODEC_TRANSFORM (0, the paper's kind of
                                   * codec, Sec. 4.2; rate 1..32) or OOCS_CODEC_QUANT (1, a plain
                                   * block quantiser, the comparison of Sec. 7 (1); rate 2..32) */
-    int32_t step_fusion;         /* HEAT with radius 1: 0 = the k steps of a slab visit run as
-                                  * pairs of steps fused in one kernel (temporal blocking on
-                                  * chip: the middle step stays in shared memory), the odd one
-                                  * out alone; 1 = one kernel per step.  Bit-identical either
-                                  * way.  Ignored for WAVE.                                   */
+    int32_t step_fusion;         /* HEAT with radius 1: 0 = one kernel per step (default);
+                                  * 1 = the k steps of a slab visit run as pairs of steps
+                                  * fused in one kernel (temporal blocking on chip: the middle
+                                  * step stays in shared memory), the odd one out alone.
+                                  * Bit-identical either way; the fused pairs halve the step
+                                  * kernels' HBM traffic but measured slower on GB300.
+                                  * Ignored for WAVE.                                          */
 } oocs_desc;
 
 /* Resolved plan (Sec. 3.1 chunking and temporal blocking; Sec. 6.2 memory model). */

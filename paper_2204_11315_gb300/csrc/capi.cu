@@ -865,7 +865,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     }
     uint64_t step_units = 0;
     // heat: pairs of steps in one fused launch (the middle step on chip)
-    const bool fuse = d.scheme == OOCS_HEAT && d.radius == 1 && d.step_fusion == 0;
+    const bool fuse = d.scheme == OOCS_HEAT && d.radius == 1 && d.step_fusion == 1;
     uint64_t launches = 0;
     for (int j = 1; j <= k_eff; ++j) {
         if (fuse && j + 1 <= k_eff) {

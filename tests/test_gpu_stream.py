@@ -265,7 +265,7 @@ def test_heat_fused_step_pairs_bitexact(P, shape, T, k, rate):
     both faces, an odd depth (a pair and a single step), several slabs."""
     u0 = synthetic.uniform_field(shape, 21)
     ref = None
-    for fusion in (1, 0):
+    for fusion in (0, 1):
         nz, ny, nx = shape
         desc = P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), 8 << 30, rate_bits=rate,
                            temporal_depth=k, slab_planes=T, step_fusion=fusion)
