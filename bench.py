@@ -438,12 +438,14 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(local)
     clocks.start()
-    ms = 0.0
+    ms, call_ms = 0.0, []
     for _ in range(args.steps):
         fill_store(P, torch, st, shape)  # untimed: the same seeded initial state every step
-        ms += timed_call(torch, st, OOC_STEPS, clocks)
+        call_ms.append(timed_call(torch, st, OOC_STEPS, clocks))
+        ms += call_ms[-1]
     clk = clocks.stop()
     after = st.stats()
+    link_after = link_bandwidth(torch, dev)
     ms = max_over_ranks(torch, ms, dev)
     value = replica_throughput(ooc_interior(nz) * OOC_STEPS * args.steps, world, ms)
     d = {k: after[k] - before[k] for k in ("h2d_bytes", "d2h_bytes", "kernel_launches", "slabs_done",
@@ -464,19 +466,28 @@ def run_ours(args):
                 "avg_launch_ms": cls["step"]["device_ms"] / nl,
                 "note": "the k launches of a visit are timed as one group on the visit's stream; "
                         "8 B per window point per step (read u, write u')"}
-    # per-class device time from one extra call with every class timed (not in `value`)
+    # per-class device time from one extra call with every class timed (not in
+    # `value`): the kernel classes and the host<->device copies
     fill_store(P, torch, st, shape)
-    st.set_profiling(P.OOCS_PROF_LOAD | P.OOCS_PROF_STEP | P.OOCS_PROF_STORE)
+    st.set_profiling(P.OOCS_PROF_LOAD | P.OOCS_PROF_STEP | P.OOCS_PROF_STORE | P.OOCS_PROF_H2D | P.OOCS_PROF_D2H)
     b2 = st.stats()
-    timed_call(torch, st, OOC_STEPS)
+    profiled_ms = timed_call(torch, st, OOC_STEPS)
     a2 = st.stats()
     st.set_profiling(0)
-    kernels = {}
-    for c in ("load", "step", "store"):
+    kernels, copies = {}, {}
+    for c in ("load", "step", "store", "h2d", "d2h"):
         k = {q: a2[c][q] - b2[c][q] for q in ("launches", "units", "device_ms")}
         k["avg_ms"] = k["device_ms"] / max(k["launches"], 1)
-        kernels[c] = k
+        if c in ("h2d", "d2h"):
+            k["copies"], k["bytes"] = k.pop("launches"), k.pop("units")
+            k["GBs"] = k["bytes"] / (k["device_ms"] / 1e3) / 1e9 if k["device_ms"] else None
+            copies[c] = k
+        else:
+            kernels[c] = k
     kernels["note"] = "one extra oocs_step(20) with all classes event-timed; ms per call"
+    copies["call_ms"] = profiled_ms
+    copies["note"] = ("the same extra call: each visit's host->device / device->host copy timed by "
+                      "events on its stream; GBs = bytes / summed copy time")
     # binding roofline of the whole sweep: algorithmic HBM bytes against the
     # host link measured in this run.  Per sweep and grid value: H2D write (c),
     # decode read (c) + FP32 write (4), step k reads/writes (8 B per point-step),
@@ -499,8 +510,11 @@ def run_ours(args):
                       "hbm_algorithmic_bytes_per_step": hbm_alg / args.steps,
                       "h2d_bytes_per_step": d["h2d_bytes"] / args.steps,
                       "d2h_bytes_per_step": d["d2h_bytes"] / args.steps, "link": link,
+                      "link_after_timed_calls": link_after,
                       "kernel_chain_ms_per_step": chain_ms,
-                      "measured_binding": "kernel chain" if chain_ms > t_roof * 1e3 / args.steps else "host link"}
+                      "copies_in_profiled_call": copies,
+                      "measured_binding": max((chain_ms, "kernel chain"), (copies["h2d"]["device_ms"], "h2d copies"),
+                                              (copies["d2h"]["device_ms"], "d2h copies"))[1]}
 
     # ---- accuracy: the rate-16 result after 20 steps (the store holds it)
     # on the central CUBE_IN^3 points of seeded cubes, compared later with the
@@ -581,6 +595,7 @@ def run_ours(args):
 
     line = base_line(args, world, nz)
     line.update({"value": value, "ms_per_step": ms / args.steps, "dtype": "f32",
+                 "ms_per_call": {"min": min(call_ms), "median": float(np.median(call_ms)), "max": max(call_ms)},
                  "gpu_launches": int(d["kernel_launches"]), "e2e": e2e, "roofline": roofline,
                  "sweep_roofline": sweep_roofline, "clocks": clk, "kernels": kernels,
                  "plan": {"slabs": plan.num_slabs, "slab_planes": plan.slab_planes,

@@ -66,6 +66,21 @@ def with_plan(desc, slabs: int, k: int, rate: int):
     return d
 
 
+def member_plan(desc, slabs: int, k: int, rate: int):
+    """(desc, slabs, k) of the class's plan applied to one member of the class;
+    members differ in shape, so when the class's plan is invalid for this one
+    (too few planes per slab for region sharing, or a window over the budget)
+    the nearest valid plan is taken: fewer slabs first, then more, then the
+    next shallower depths.  (None, slabs, k) when none is valid."""
+    depths = [k] + [j for j in sorted(DEPTHS[desc.scheme], reverse=True) if j < k]
+    for kk in depths:
+        for s in [slabs] + list(range(slabs - 1, 0, -1)) + [slabs << j for j in range(1, 7)]:
+            t = with_plan(desc, s, kk, rate)
+            if t is not None:
+                return t, s, kk
+    return None, slabs, k
+
+
 def class_key(desc, budget: int, tol: float) -> str:
     vol = int(desc.nx) * int(desc.ny) * int(desc.nz)
     side = int(round(vol ** (1.0 / 3.0) / 32.0)) * 32
@@ -203,13 +218,11 @@ def tune(descs, tol: float, budget: int, cache_path: str | None = None, steps: i
                           "rate": int(best.rate_bits), "ms_per_step": ms, "tried": tried,
                           "errors": {str(r): e for r, e in errors.items()}}
         c = cache[key]
-        t = with_plan(d, c["slabs"], c["k"], c["rate"])
-        slabs = c["slabs"]
-        while t is None and slabs < 64:  # this member of the class needs more slabs
-            slabs *= 2
-            t = with_plan(d, slabs, c["k"], c["rate"])
+        t, slabs, k = member_plan(d, c["slabs"], c["k"], c["rate"])
+        if t is None:
+            raise O.OOCSError(2, f"no plan of class {key} fits problem {i}")
         out.append(t)
-        report.append({"class": key, "slabs": slabs, "k": c["k"], "rate": c["rate"],
+        report.append({"class": key, "slabs": slabs, "k": k, "rate": c["rate"],
                        "errors": c.get("errors", {})})
     # shared workspace of the batch within the budget: split the largest windows
     while O.oocs_batch_query(out) > budget:

@@ -108,3 +108,22 @@ def test_batch_is_fitted_into_the_budget(P, A):
     tight, rep = A.tune(descs, 1e-4, budget)
     assert P.oocs_batch_query(tight) <= budget
     assert P.oocs_query(tight[0]).num_slabs > 1
+
+
+def test_class_plan_adapts_to_a_thin_member(P, A, tmp_path):
+    """A class groups grids by volume, so its measured plan (here 4 slabs at
+    k = 4) can be invalid for a member with few planes: 64 x 192 x 192 has the
+    class's cube root, but 4 slabs of 16 planes break region sharing for the
+    25-point star (h = 16).  The member takes the nearest valid plan (fewer
+    slabs) instead of failing the whole batch."""
+    cache = tmp_path / "tune.json"
+    member = _wave(P, 64, 192, 192)
+    key = A.class_key(A.O.oocs_desc.from_buffer_copy(member), 8 << 30, 1e-4)
+    assert key == A.class_key(_wave(P, 128, 128, 144), 8 << 30, 1e-4)
+    cache.write_text(json.dumps({key: {"slabs": 4, "k": 4, "rate": 16, "ms_per_step": 1.0,
+                                       "tried": [], "errors": {}}}))
+    assert A.with_plan(member, 4, 4, 16) is None
+    out, rep = A.tune([member], 1e-4, 8 << 30, str(cache))
+    assert rep["candidates_timed"] == 0
+    assert (rep["problems"][0]["slabs"], rep["problems"][0]["k"]) == (2, 4)
+    assert P.oocs_query(out[0]).num_slabs == 2 and int(out[0].temporal_depth) == 4
