@@ -52,9 +52,9 @@ OOC_STEPS, OOC_K, OOC_BUDGET, OOC_SEED, OOC_RATE, OOC_ALPHA = 20, 4, 16 << 30, 3
 HEAT_BYTES_PER_POINT = 8                # read u, write u' (FP32)
 WORKLOAD = "heat7_2560x2560x5120_20steps_k4_rate16_budget16GiB_swb"
 # DRAM bytes (read + write) per window point of the heat step kernel from one
-# ncu capture of a 2560 x 2560 launch; scaled to a launch by its points.  None
-# until measured, and set to None whenever the kernel changes.
-HEAT_STEP_TRAFFIC_B_PER_POINT = None
+# ncu capture of a 2560 x 2560 x 32 launch (1635.3 MB for 209.7 M points);
+# scaled to a launch by its points.  Set to None whenever the kernel changes.
+HEAT_STEP_TRAFFIC_B_PER_POINT = 7.80
 # FP64 oracle on dependency cubes: a point after 20 heat steps depends only on
 # the initial values within 20 planes, so the oracle on a cube of side
 # CUBE_IN + 2 CUBE_HALO gives exact values on its central CUBE_IN^3 points
@@ -460,7 +460,7 @@ def run_ours(args):
                 "traffic": (HEAT_STEP_TRAFFIC_B_PER_POINT * cls["step"]["units"] / nl
                             if HEAT_STEP_TRAFFIC_B_PER_POINT else None),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on a "
-                                  "2560x2560 window, scaled by points per launch",
+                                  "2560x2560x32 slab (7.80 B per point), scaled by points per launch",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
                 "algorithmic_bytes_per_launch": step_bytes / nl,
                 "avg_launch_ms": cls["step"]["device_ms"] / nl,
