@@ -8,7 +8,8 @@
 // kernel is HBM-bound and uses no tensor cores.
 //
 // Codec (Sec. 4.2): one thread per 4x4x4 block; 16 float4 loads per block
-// (consecutive threads read consecutive blocks of a row: coalesced).
+// (consecutive threads read consecutive blocks of a row: coalesced); the
+// transform encoder's CTA first fills its doubling table in shared memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -1146,6 +1147,11 @@ __global__ void __launch_bounds__(kCodecThreads, 6)
     k_encode_layers(const CodecSegments sg, int nx, int ny, int rate)
 {
     extern __shared__ uint32_t sw[];
+    __shared__ uint32_t dbl[KIND == kCodecTransform ? 256 : 1];  // the transform encoder's doubling table
+    if constexpr (KIND == kCodecTransform) {
+        fill_doubling_table(dbl, threadIdx.x, kCodecThreads);
+        __syncthreads();
+    }
     pdl_launch_dependents();
     pdl_wait_prior_grid();
     const int nw = 2 * rate, stride = 2 * rate + 1;
@@ -1175,7 +1181,7 @@ __global__ void __launch_bounds__(kCodecThreads, 6)
         if constexpr (KIND == kCodecQuant)
             finite = bq_encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
         else
-            finite = encode_block(v, rate, [&](int i, uint32_t w) { row[i] = w; });
+            finite = encode_block(v, rate, dbl, [&](int i, uint32_t w) { row[i] = w; });
         if (!finite)
             atomicOr(&g_device_error, kErrNonFinite);
     }
