@@ -122,6 +122,11 @@ typedef struct {
                                   * Bit-identical either way; the fused pairs halve the step
                                   * kernels' HBM traffic but measured slower on GB300.
                                   * Ignored for WAVE.                                          */
+    int32_t step_tile;           /* x-y tile of the step kernel's z-march (Sec. 3.1 kernels):
+                                  * 0 = 64 x 16 points per CTA (four consumer warps, the
+                                  * default); 1 = 64 x 8 (two consumer warps: twice the
+                                  * tiles, for planes too small to fill the GPU).  Results
+                                  * are bit-identical; the autotuner searches it.            */
 } oocs_desc;
 
 /* Resolved plan (Sec. 3.1 chunking and temporal blocking; Sec. 6.2 memory model). */

@@ -13,18 +13,19 @@ each other differently for every grid, so they are measured, not modelled:
 * slabs: S in {1, 2, 4} (T = nz / S rounded up to the 4-plane layer), kept
   only when T >= 2 h so region sharing holds and the plan fits the budget;
 * temporal depth: k in {2, 4, 8} for the 7-point heat stencil, {2, 4} for the
-  25-point wave stencil.
+  25-point wave stencil;
+* the step kernel's x-y tile: 64 x 16 or 64 x 8 points per CTA
+  (`oocs_desc.step_tile`; smaller tiles give more CTAs on small planes).
 
-Each (S, k) candidate at the chosen rate runs `steps` time steps of the
+Each (S, k, tile) candidate at the chosen rate runs `steps` time steps of the
 problem's grid through a fresh context: one warm-up call, then the median of
 `reps` calls timed with CUDA events on stream 0 (every oocs_step joins its
 three streams into stream 0 at its end, so the event follows the last copy).
 Problems are grouped into classes (scheme and the rounded cube root of the
 volume); one problem per class is measured and its (S, k, rate) is applied to
 the class.  Choices are cached in a JSON file keyed by class, budget and
-tolerance.  The tile shape of the step kernel is fixed (64 x 16, the layout of
-its TMA rings); its launch geometry is chosen per launch by the occupancy
-model in the library.
+tolerance.  The launch geometry of each step (z chunks or balanced ranges)
+is chosen per launch by the occupancy model in the library.
 """
 from __future__ import annotations
 
@@ -40,6 +41,7 @@ RATES = (8, 12, 16)
 ERROR_MARGIN = 0.5  # a rate is taken when its measured error is within this share of the tolerance
 SLABS = (1, 2, 4)
 DEPTHS = {O.OOCS_HEAT: (2, 4, 8), O.OOCS_WAVE: (2, 4)}
+TILES = (0, 1)  # oocs_desc.step_tile: 64 x 16, 64 x 8
 
 
 def rate_for(errors: dict, tol: float) -> int:
@@ -48,8 +50,9 @@ def rate_for(errors: dict, tol: float) -> int:
     return ok[0] if ok else 0
 
 
-def with_plan(desc, slabs: int, k: int, rate: int):
-    """desc with S = slabs slabs (T rounded up to 4 planes), depth k, rate; None if invalid."""
+def with_plan(desc, slabs: int, k: int, rate: int, tile: int = 0):
+    """desc with S = slabs slabs (T rounded up to 4 planes), depth k, rate and
+    step tile; None if invalid."""
     d = O.oocs_desc.from_buffer_copy(desc)
     T = -(-int(d.nz) // slabs)
     T = -(-T // 4) * 4
@@ -59,6 +62,7 @@ def with_plan(desc, slabs: int, k: int, rate: int):
     d.slab_planes = min(T, int(d.nz))
     d.temporal_depth = k
     d.rate_bits = rate
+    d.step_tile = tile
     try:
         O.oocs_query(d)
     except O.OOCSError:
@@ -66,7 +70,7 @@ def with_plan(desc, slabs: int, k: int, rate: int):
     return d
 
 
-def member_plan(desc, slabs: int, k: int, rate: int):
+def member_plan(desc, slabs: int, k: int, rate: int, tile: int = 0):
     """(desc, slabs, k) of the class's plan applied to one member of the class;
     members differ in shape, so when the class's plan is invalid for this one
     (too few planes per slab for region sharing, or a window over the budget)
@@ -75,7 +79,7 @@ def member_plan(desc, slabs: int, k: int, rate: int):
     depths = [k] + [j for j in sorted(DEPTHS[desc.scheme], reverse=True) if j < k]
     for kk in depths:
         for s in [slabs] + list(range(slabs - 1, 0, -1)) + [slabs << j for j in range(1, 7)]:
-            t = with_plan(desc, s, kk, rate)
+            t = with_plan(desc, s, kk, rate, tile)
             if t is not None:
                 return t, s, kk
     return None, slabs, k
@@ -183,13 +187,14 @@ def tune_one(desc, tol: float, steps: int = 4, data=None, err_steps: int | None 
     rate = rate_for(errors, tol)
     for slabs in SLABS:
         for k in DEPTHS[desc.scheme]:
-            d = with_plan(desc, slabs, k, rate)
-            if d is None:
-                continue
-            ms = time_candidate(d, max(steps, k), probe)
-            tried.append({"slabs": slabs, "k": k, "rate": rate, "ms_per_step": ms})
-            if ms < best_ms:
-                best, best_ms = d, ms
+            for tile in TILES:
+                d = with_plan(desc, slabs, k, rate, tile)
+                if d is None:
+                    continue
+                ms = time_candidate(d, max(steps, k), probe)
+                tried.append({"slabs": slabs, "k": k, "rate": rate, "tile": tile, "ms_per_step": ms})
+                if ms < best_ms:
+                    best, best_ms = d, ms
     return best, best_ms, tried, errors
 
 
@@ -215,20 +220,21 @@ def tune(descs, tol: float, budget: int, cache_path: str | None = None, steps: i
             if best is None:
                 raise O.OOCSError(2, f"no plan of {key} fits the budget")
             cache[key] = {"slabs": -(-int(d.nz) // int(best.slab_planes)), "k": int(best.temporal_depth),
-                          "rate": int(best.rate_bits), "ms_per_step": ms, "tried": tried,
+                          "rate": int(best.rate_bits), "tile": int(best.step_tile), "ms_per_step": ms,
+                          "tried": tried,
                           "errors": {str(r): e for r, e in errors.items()}}
         c = cache[key]
-        t, slabs, k = member_plan(d, c["slabs"], c["k"], c["rate"])
+        t, slabs, k = member_plan(d, c["slabs"], c["k"], c["rate"], c.get("tile", 0))
         if t is None:
             raise O.OOCSError(2, f"no plan of class {key} fits problem {i}")
         out.append(t)
-        report.append({"class": key, "slabs": slabs, "k": k, "rate": c["rate"],
+        report.append({"class": key, "slabs": slabs, "k": k, "rate": c["rate"], "tile": c.get("tile", 0),
                        "errors": c.get("errors", {})})
     # shared workspace of the batch within the budget: split the largest windows
     while O.oocs_batch_query(out) > budget:
         i = max(range(len(out)), key=lambda j: int(out[j].nx) * int(out[j].ny) * int(out[j].slab_planes))
         slabs = 2 * -(-int(out[i].nz) // int(out[i].slab_planes))
-        t = with_plan(out[i], slabs, int(out[i].temporal_depth), int(out[i].rate_bits))
+        t = with_plan(out[i], slabs, int(out[i].temporal_depth), int(out[i].rate_bits), int(out[i].step_tile))
         if t is None:
             raise O.OOCSError(2, "the batch does not fit the budget")
         out[i] = t

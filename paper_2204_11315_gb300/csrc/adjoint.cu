@@ -101,6 +101,7 @@ StepLaunch grid_launch(const oocs_desc *d, int scheme)
     memset(&L, 0, sizeof(L));
     L.scheme = scheme;
     L.radius = 4;
+    L.tile = d->step_tile;
     L.nx = d->nx;
     L.ny = d->ny;
     L.nz = d->nz;

@@ -202,6 +202,10 @@ oocs_status validate_desc(const oocs_desc *d, std::string &err)
         err = "codec must be OOCS_CODEC_TRANSFORM (0) or OOCS_CODEC_QUANT (1)";
         return OOCS_ERR_INVALID_ARG;
     }
+    if (d->step_tile != 0 && d->step_tile != 1) {
+        err = "step_tile must be 0 or 1";
+        return OOCS_ERR_INVALID_ARG;
+    }
     if (d->step_fusion != 0 && d->step_fusion != 1) {
         err = "step_fusion must be 0 or 1";
         return OOCS_ERR_INVALID_ARG;
@@ -848,6 +852,7 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     memset(&Ls, 0, sizeof(Ls));
     Ls.scheme = d.scheme == OOCS_WAVE ? kWave : kHeat;
     Ls.radius = d.radius;
+    Ls.tile = d.step_tile;
     Ls.nx = d.nx;
     Ls.ny = d.ny;
     Ls.nz = d.nz;
@@ -1120,6 +1125,7 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k, const char *fwd,
     StepLaunch G;
     memset(&G, 0, sizeof(G));
     G.radius = 4;
+    G.tile = d.step_tile;
     G.nx = d.nx;
     G.ny = d.ny;
     G.nz = d.nz;
@@ -1906,6 +1912,7 @@ oocs_status oocs_incore_run(const oocs_desc *desc, float *u, float *u_prev, cons
     memset(&Ls, 0, sizeof(Ls));
     Ls.scheme = wave ? kWave : kHeat;
     Ls.radius = desc->radius;
+    Ls.tile = desc->step_tile;
     Ls.nx = desc->nx;
     Ls.ny = desc->ny;
     Ls.nz = desc->nz;

@@ -262,12 +262,12 @@ struct BitReader {
         win >>= n;
         nwin -= n;
     }
-    OOCS_FN uint32_t get(int n)  // n in [0, 32]
+    OOCS_FN uint32_t get(int n)  // n in [0, 32]; one refill check
     {
-        if (n == 0)
-            return 0;
-        uint32_t v = peek(n);
-        skip(n);
+        fill();
+        const uint32_t v = (uint32_t)(win & ((1ull << n) - 1ull));
+        win >>= n;
+        nwin -= n;
         return v;
     }
     OOCS_FN uint64_t get64(int n)  // n in [0, 64]

@@ -52,9 +52,13 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 constexpr int kVX = 2;                  // x-adjacent points per thread (float2)
 constexpr int kTX = 32 * kVX;           // tile width (x) = 64
 constexpr int kRPT = 4;                 // consecutive rows per thread
-constexpr int kConsumerWarps = 4;
-constexpr int kTY = kConsumerWarps * kRPT;         // tile height (y) = 16
+constexpr int kConsumerWarps = 4;              // default tile: 4 consumer warps, 64 x 16
+constexpr int kTY = kConsumerWarps * kRPT;         // default tile height (y) = 16
 constexpr int kStepThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
+// The step kernel also comes with CW = 2 consumer warps (64 x 8 tiles), a
+// choice of oocs_desc.step_tile that the autotuner searches.
+template <int CW>
+constexpr int tile_h() { return CW * kRPT; }
 constexpr int kBoxW = kTX + 8;          // u tile loaded from x0-4 (16-byte aligned) to x0+kTX+4
 
 // centre fields streamed beside the stencil field: wave (prev, m), adjoint
@@ -62,14 +66,15 @@ constexpr int kBoxW = kTX + 8;          // u tile loaded from x0-4 (16-byte alig
 template <int SCHEME>
 constexpr int centre_fields() { return SCHEME == kHeat ? 0 : SCHEME == kAdjoint ? 3 : 2; }
 
-template <int R, int NCF>
+template <int R, int NCF, int CW = kConsumerWarps>
 struct StepCfg {
-    static constexpr int H = kTY + 2 * R;                       // u tile rows
+    static constexpr int TY = tile_h<CW>();                     // tile rows
+    static constexpr int H = TY + 2 * R;                        // u tile rows
     static constexpr uint32_t kUBytes = H * kBoxW * 4;          // one TMA box of u
     static constexpr int kUStage = ((kUBytes + 127) / 128 * 128) / 4;  // floats per ring stage
     static constexpr int NSU = (2 * R + 2) > 6 ? (2 * R + 2) : 6;  // u ring stages (>= R+1 ahead)
     static constexpr int NSC = NCF == 3 ? 3 : 4;                // centre-field ring stages
-    static constexpr int kCStage = kTX * kTY;                   // floats per centre field and stage
+    static constexpr int kCStage = kTX * TY;                    // floats per centre field and stage
     static constexpr uint32_t kCBytes = kCStage * 4;
     static constexpr int Q = 2 * R + 1;                         // register queue length
     static constexpr size_t smem_bytes()
@@ -137,6 +142,7 @@ struct SegCursor {
             end = total * (blockIdx.x + 1) / gridDim.x;
         }
     }
+    template <int TY = kTY>
     OOCS_FN bool next(const StepArgs &a, StepSeg &s)
     {
         if (a.zchunk > 0) {
@@ -144,7 +150,7 @@ struct SegCursor {
                 return false;
             chunk_done = true;
             s.x0 = blockIdx.x * kTX;
-            s.y0 = blockIdx.y * kTY;
+            s.y0 = blockIdx.y * TY;
             s.zs = a.z_lo + blockIdx.z * a.zchunk;
             s.ze = min(s.zs + a.zchunk, a.z_hi);
             return s.zs < s.ze;
@@ -155,7 +161,7 @@ struct SegCursor {
         const int64_t t = pos / P;
         const int64_t e = min(end, (t + 1) * P);
         s.x0 = (int)(t / a.tiles_y) * kTX;
-        s.y0 = (int)(t % a.tiles_y) * kTY;
+        s.y0 = (int)(t % a.tiles_y) * TY;
         s.zs = a.z_lo + (int)(pos - t * P);
         s.ze = a.z_lo + (int)(e - t * P);
         pos = e;
@@ -181,14 +187,14 @@ struct SegCursor {
 //
 // kAdjoint and kGradient (the wave misfit's adjoint, see kernels.h) use the
 // same pipeline with three and two centre fields.
-template <int R, int SCHEME>
-__global__ void __launch_bounds__(kStepThreads, 2)
+template <int R, int SCHEME, int CW>
+__global__ void __launch_bounds__(32 * (CW + 1), CW == kConsumerWarps ? 2 : 3)
     k_star_step(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
                 const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_c2,
                 const StepArgs a)
 {
     constexpr int NCF = centre_fields<SCHEME>();
-    using C = StepCfg<R, NCF>;
+    using C = StepCfg<R, NCF, CW>;
     constexpr int Q = C::Q;
     constexpr bool kFastPath = R == 4;
     extern __shared__ unsigned char smem_raw[];
@@ -204,11 +210,11 @@ __global__ void __launch_bounds__(kStepThreads, 2)
     if (wid == 0 && tx == 0) {
         for (int i = 0; i < C::NSU; ++i) {
             mbar_init(&ufull[i], 1);
-            mbar_init(&uempty[i], kConsumerWarps);
+            mbar_init(&uempty[i], CW);
         }
         for (int i = 0; i < C::NSC; ++i) {
             mbar_init(&cfull[i], 1);
-            mbar_init(&cempty[i], kConsumerWarps);
+            mbar_init(&cempty[i], CW);
         }
         fence_barrier_init();
     }
@@ -222,13 +228,13 @@ __global__ void __launch_bounds__(kStepThreads, 2)
     cur.init(a);
     StepSeg sg;
 
-    if (wid == kConsumerWarps) {
+    if (wid == CW) {
         // ------------------------------------------------ producer warp --
         if (tx != 0)
             return;
         bool good = true;
         uint32_t un = 0, cn = 0;  // u planes / centre-field planes issued so far
-        while (good && cur.next(a, sg)) {
+        while (good && cur.template next<C::TY>(a, sg)) {
             // u planes in order (queue prologue first), the centre fields of
             // plane z alongside the u plane R ahead of it
             for (int p = sg.zs - R; p < sg.ze + R; ++p) {
@@ -276,7 +282,7 @@ __global__ void __launch_bounds__(kStepThreads, 2)
     auto urow = [&](int rel_row) { return (R + kRPT * wid + rel_row) * kBoxW + ucol; };
     uint32_t ucn = 0, ccn = 0;  // u planes / centre-field planes consumed before this segment
     bool good = true;
-    while (good && cur.next(a, sg)) {
+    while (good && cur.template next<C::TY>(a, sg)) {
         const int x0 = sg.x0, y0 = sg.y0, zs = sg.zs, ze = sg.ze;
         const int pu0 = zs - R;  // first u plane of the queue
         auto u_cnt = [&](int p) { return ucn + (uint32_t)(p - pu0); };
@@ -812,7 +818,7 @@ static cudaError_t make_plane_map(CUtensorMap *m, const float *base, int64_t nx,
 // that device (cudaFuncSetAttribute acts on the current device only) and how
 // many of its CTAs fit on an SM.
 constexpr int kMaxDevices = 64;
-constexpr int kStepInstances = 8;  // (radius, scheme) instances of k_star_step
+constexpr int kStepInstances = 16;  // (radius, scheme, tile) instances of k_star_step
 
 struct DevInfo {
     int sms = 0;
@@ -843,16 +849,16 @@ static int device_sms()
     return info.sms;
 }
 
-template <int R, int SCHEME>
-constexpr int step_instance() { return (R == 4 ? 4 : 0) + SCHEME; }
+template <int R, int SCHEME, int CW>
+constexpr int step_instance() { return (R == 4 ? 4 : 0) + SCHEME + (CW == kConsumerWarps ? 0 : 8); }
 
 // Applies the step kernel's shared-memory opt-in on the current device (once
 // per device) and returns its CTAs per SM and the device's SM count.
-template <int R, int SCHEME>
+template <int R, int SCHEME, int CW>
 static cudaError_t step_residency(int &resident, int &sms)
 {
-    using C = StepCfg<R, centre_fields<SCHEME>()>;
-    static_assert(step_instance<R, SCHEME>() < kStepInstances, "instance table too small");
+    using C = StepCfg<R, centre_fields<SCHEME>(), CW>;
+    static_assert(step_instance<R, SCHEME, CW>() < kStepInstances, "instance table too small");
     int dev = 0;
     cudaError_t e = current_device(dev);
     if (e != cudaSuccess)
@@ -864,15 +870,15 @@ static cudaError_t step_residency(int &resident, int &sms)
         if (e != cudaSuccess)
             return e;
     }
-    int &res = info.resident[step_instance<R, SCHEME>()];
+    int &res = info.resident[step_instance<R, SCHEME, CW>()];
     if (res == 0) {
         const size_t smem = C::smem_bytes();
-        auto kern = k_star_step<R, SCHEME>;
+        auto kern = k_star_step<R, SCHEME, CW>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
         int n = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kStepThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * (CW + 1), smem);
         if (e != cudaSuccess)
             return e;
         if (n < 1)
@@ -885,15 +891,15 @@ static cudaError_t step_residency(int &resident, int &sms)
 }
 
 // Launch geometry of a z-march over window planes [a.z_lo, a.z_hi) of an
-// nx x ny grid of 64 x 16 tiles, with `slots` CTAs resident at once.
+// nx x ny grid of 64 x ty tiles, with `slots` CTAs resident at once.
 // Chunked launch when some z chunking (>= min_planes per CTA) fills the last
 // wave of CTAs to 90 %; otherwise (short windows on a plane whose tiles do not
 // fill the SMs evenly, e.g. 256 tiles on 304 slots) one wave of equal
 // tile-plane ranges.  Sets a.zchunk, a.tiles_y and a.ntiles.
-static dim3 step_grid(int64_t nx, int64_t ny, int slots, StepArgs &a, int min_planes = 12)
+static dim3 step_grid(int64_t nx, int64_t ny, int slots, StepArgs &a, int min_planes = 12, int ty = kTY)
 {
     const int tiles_x = (int)((nx + kTX - 1) / kTX);
-    const int tiles_y = (int)((ny + kTY - 1) / kTY);
+    const int tiles_y = (int)((ny + ty - 1) / ty);
     const int tiles = tiles_x * tiles_y;
     const int nplanes = a.z_hi - a.z_lo;
     a.tiles_y = tiles_y;
@@ -921,15 +927,15 @@ static dim3 step_grid(int64_t nx, int64_t ny, int slots, StepArgs &a, int min_pl
     return dim3((unsigned)std::min<int64_t>(slots, (total + 15) / 16), 1, 1);
 }
 
-template <int R, int SCHEME>
+template <int R, int SCHEME, int CW = kConsumerWarps>
 static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s)
 {
-    using C = StepCfg<R, centre_fields<SCHEME>()>;
+    using C = StepCfg<R, centre_fields<SCHEME>(), CW>;
     const size_t smem = C::smem_bytes();
-    auto kern = k_star_step<R, SCHEME>;
+    auto kern = k_star_step<R, SCHEME, CW>;
     int resident = 0, sms = 0;
     {
-        cudaError_t e = step_residency<R, SCHEME>(resident, sms);
+        cudaError_t e = step_residency<R, SCHEME, CW>(resident, sms);
         if (e != cudaSuccess)
             return e;
     }
@@ -937,16 +943,16 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
     CUtensorMap mc, mp, mm, m2;
     cudaError_t e = make_plane_map(&mc, L.cur, L.nx, L.ny, L.wp, kBoxW, C::H);
     if (e == cudaSuccess)
-        e = make_plane_map(&mp, NCF >= 1 ? L.prev : L.cur, L.nx, L.ny, L.wp, kTX, kTY);
+        e = make_plane_map(&mp, NCF >= 1 ? L.prev : L.cur, L.nx, L.ny, L.wp, kTX, C::TY);
     if (e == cudaSuccess)
-        e = make_plane_map(&mm, NCF >= 2 ? L.m : L.cur, L.nx, L.ny, L.wp, kTX, kTY);
+        e = make_plane_map(&mm, NCF >= 2 ? L.m : L.cur, L.nx, L.ny, L.wp, kTX, C::TY);
     if (e == cudaSuccess)
-        e = make_plane_map(&m2, NCF >= 3 ? L.c2 : L.cur, L.nx, L.ny, L.wp, kTX, kTY);
+        e = make_plane_map(&m2, NCF >= 3 ? L.c2 : L.cur, L.nx, L.ny, L.wp, kTX, C::TY);
     if (e != cudaSuccess)
         return e;
 
-    const dim3 grid = step_grid(L.nx, L.ny, sms * resident, a);
-    dim3 block(32, kConsumerWarps + 1, 1);
+    const dim3 grid = step_grid(L.nx, L.ny, sms * resident, a, 12, C::TY);
+    dim3 block(32, CW + 1, 1);
     return launch_pdl(kern, grid, block, smem, s, mc, mp, mm, m2, a);
 }
 
@@ -1032,18 +1038,21 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
     a.t_dev = L.t_dev;
     a.t_rel = L.t_rel;
     a.nw = L.nw;
+    if (L.tile != 0 && L.tile != 1)
+        return cudaErrorInvalidValue;
+    const bool t8 = L.tile == 1;  // 64 x 8 tiles
     if (L.radius == 1 && L.scheme == kHeat)
-        return launch_step_t<1, kHeat>(L, a, s);
+        return t8 ? launch_step_t<1, kHeat, 2>(L, a, s) : launch_step_t<1, kHeat>(L, a, s);
     if (L.radius == 4 && L.scheme == kHeat)
-        return launch_step_t<4, kHeat>(L, a, s);
+        return t8 ? launch_step_t<4, kHeat, 2>(L, a, s) : launch_step_t<4, kHeat>(L, a, s);
     if (L.radius == 1 && L.scheme == kWave)
-        return launch_step_t<1, kWave>(L, a, s);
+        return t8 ? launch_step_t<1, kWave, 2>(L, a, s) : launch_step_t<1, kWave>(L, a, s);
     if (L.radius == 4 && L.scheme == kWave)
-        return launch_step_t<4, kWave>(L, a, s);
+        return t8 ? launch_step_t<4, kWave, 2>(L, a, s) : launch_step_t<4, kWave>(L, a, s);
     if (L.radius == 4 && L.scheme == kAdjoint && L.c2)
-        return launch_step_t<4, kAdjoint>(L, a, s);
+        return t8 ? launch_step_t<4, kAdjoint, 2>(L, a, s) : launch_step_t<4, kAdjoint>(L, a, s);
     if (L.radius == 4 && L.scheme == kGradient)
-        return launch_step_t<4, kGradient>(L, a, s);
+        return t8 ? launch_step_t<4, kGradient, 2>(L, a, s) : launch_step_t<4, kGradient>(L, a, s);
     return cudaErrorInvalidValue;
 }
 

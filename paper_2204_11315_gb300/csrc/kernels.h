@@ -44,6 +44,7 @@ struct StepLaunch {
     const int64_t *t_dev;
     int64_t t_rel;
     int64_t nw;
+    int tile;  // 0: 64 x 16 tiles (4 consumer warps); 1: 64 x 8 tiles (2)
 };
 
 cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s);

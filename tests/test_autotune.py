@@ -23,7 +23,9 @@ def A(monkeypatch):
         # cheaper with fewer slabs, k = 4 and lower rates
         S = -(-int(desc.nz) // int(desc.slab_planes))
         calls.append((int(desc.nz), S, int(desc.temporal_depth), int(desc.rate_bits)))
-        return 1.0 * S + abs(int(desc.temporal_depth) - 4) * 0.1 + int(desc.rate_bits) * 0.01
+        # the 64 x 8 tile costs A.tile8_cost more (negative: it is faster)
+        return (1.0 * S + abs(int(desc.temporal_depth) - 4) * 0.1 + int(desc.rate_bits) * 0.01
+                + A.tile8_cost * int(desc.step_tile))
 
     class NoProbe:
         def __init__(self, desc, seed=0, data=None):
@@ -39,6 +41,7 @@ def A(monkeypatch):
     monkeypatch.setattr(A, "measure_rate_errors", fake_errors)
     monkeypatch.setattr(A, "_Probe", NoProbe)
     A.calls = calls
+    A.tile8_cost = 0.05
     A.err_calls = []
     A.errors = errors
     return A
@@ -127,3 +130,25 @@ def test_class_plan_adapts_to_a_thin_member(P, A, tmp_path):
     assert rep["candidates_timed"] == 0
     assert (rep["problems"][0]["slabs"], rep["problems"][0]["k"]) == (2, 4)
     assert P.oocs_query(out[0]).num_slabs == 2 and int(out[0].temporal_depth) == 4
+
+
+def test_tile_is_searched_and_kept_per_class(P, A, tmp_path):
+    """Both step tiles are timed for every (slabs, k); the faster one is the
+    class's choice, cached and applied to every member, and a desc with it
+    is a valid plan of the library."""
+    cache = tmp_path / "tune.json"
+    descs = [_heat(P, 96, 96, 96), _heat(P, 96, 100, 92)]
+    out, rep = A.tune(descs, 2e-3, 8 << 30, str(cache))
+    assert all(int(d.step_tile) == 0 for d in out)
+    tried = json.loads(cache.read_text())[rep["problems"][0]["class"]]["tried"]
+    assert {t["tile"] for t in tried} == {0, 1}
+    assert len(tried) == 2 * len({(t["slabs"], t["k"]) for t in tried})
+    A.tile8_cost = -0.05
+    out8, rep8 = A.tune(descs, 2e-3, 8 << 30, str(tmp_path / "tune8.json"))
+    assert all(int(d.step_tile) == 1 for d in out8)
+    assert all(r["tile"] == 1 for r in rep8["problems"])
+    assert P.oocs_query(out8[0]).num_slabs >= 1
+    bad = A.with_plan(descs[0], 1, 4, 12, 1)
+    bad.step_tile = 2
+    with pytest.raises(P.OOCSError):
+        P.oocs_query(bad)
