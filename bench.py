@@ -1038,12 +1038,14 @@ def run_batched(P, torch, dev):
     pts = sum((int(d.nx) - 2 * d.radius) * (int(d.ny) - 2 * d.radius) * (int(d.nz) - 2 * d.radius)
               for d in tuned) * BATCH_STEPS
     gpts = lambda ms: pts / (ms / 1e3) / 1e9
-    rates, slabs, depths = {}, {}, {}
+    rates, slabs, depths, tiles = {}, {}, {}, {}
     errors = {r["class"]: r["errors"] for r in report["problems"]}
     for r in report["problems"]:
         rates[r["rate"]] = rates.get(r["rate"], 0) + 1
         slabs[r["slabs"]] = slabs.get(r["slabs"], 0) + 1
         depths[r["k"]] = depths.get(r["k"], 0) + 1
+        tl = "64x8" if r.get("tile", 0) == 1 else "64x16"
+        tiles[tl] = tiles.get(tl, 0) + 1
     return {"workload": f"{BATCH_N}_problems_heat_wave_sides64to384_{BATCH_STEPS}steps_budget8GiB_tol1e-4",
             "unit": UNIT, "value": gpts(ms_graph),
             "graph_replay": {"value": gpts(ms_graph), "ms": ms_graph},
@@ -1055,7 +1057,7 @@ def run_batched(P, torch, dev):
             "sum_of_alone_workspaces": int(sum(ws_alone)), "kernel_launches_per_batch_step": launches_per_step,
             "tuning": {"seconds": t_tune, "classes": report["classes"],
                        "candidates_timed": report["candidates_timed"], "rates": rates, "slabs": slabs,
-                       "temporal_depths": depths, "measured_rate_errors_by_class": errors,
+                       "temporal_depths": depths, "step_tiles": tiles, "measured_rate_errors_by_class": errors,
                        "rate_rule": f"lowest rate with measured rel-L2 <= {autotune.ERROR_MARGIN} x tolerance "
                                     f"after {BATCH_STEPS} steps at the shallowest depth"}}
 
