@@ -1078,10 +1078,20 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k, const char *fwd,
                     acc(OOCS_RES_HOST, c->host_base + c->store_id[OOCS_FIELD_LAM_PREV], l0[1], l1[1], false),
                     acc(OOCS_RES_HOST, c->host_base + 3, l0[2], l1[2], false)});
     } else {
+        KernelScope ks;
+        oocs_status r = ks.begin(c, st_h, kClsH2D);
+        if (r != OOCS_OK)
+            return r;
         const char *src[3] = {c->store[store_of[0]], c->store[store_of[1]], fwd};
-        for (int f = 0; f < 3; ++f)
+        uint64_t bytes = 0;
+        for (int f = 0; f < 3; ++f) {
             CU(c, cudaMemcpyAsync(c->in_slot(q, f), src[f] + (uint64_t)l0[f] * v.layer_bytes,
                                   (uint64_t)(l1[f] - l0[f]) * v.layer_bytes, cudaMemcpyHostToDevice, st_h));
+            bytes += (uint64_t)(l1[f] - l0[f]) * v.layer_bytes;
+        }
+        r = ks.end(kClsH2D, bytes);
+        if (r != OOCS_OK)
+            return r;
     }
     for (int f = 0; f < 3; ++f)
         c->stats.h2d_bytes += (uint64_t)(l1[f] - l0[f]) * v.layer_bytes;
@@ -1196,9 +1206,17 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k, const char *fwd,
         trace_push(c, OOCS_OP_D2H, sd, -1, (int64_t)g,
                    {acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, false),
                     acc(OOCS_RES_HOST, c->host_base + c->store_id[OOCS_FIELD_LAM_PREV], z0 / 4, z1 / 4, true)});
-    else
+    else {
+        KernelScope ks;
+        oocs_status r = ks.begin(c, st_d, kClsD2H);
+        if (r != OOCS_OK)
+            return r;
         CU(c, cudaMemcpyAsync(c->store[OOCS_FIELD_LAM_PREV] + (uint64_t)(z0 / 4) * v.layer_bytes, c->out_slot(q, 0),
                               bytes, cudaMemcpyDeviceToHost, st_d));
+        r = ks.end(kClsD2H, bytes);
+        if (r != OOCS_OK)
+            return r;
+    }
     c->stats.d2h_bytes += bytes;
     SCHED(sched_record(c, sd, kEvD2H + c->d2h_base + par * v.S + s));
     SCHED(sched_record(c, sd, kEvOut + q));
