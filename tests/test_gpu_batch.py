@@ -237,3 +237,48 @@ def test_batch_mixing_codecs_matches_problems_run_alone(P):
         ref, _ = _alone(P, d, fields, s, [8])
         for f in range(2 if d.scheme == P.OOCS_WAVE else 1):
             assert np.array_equal(got[i][f], ref[f]), (i, f)
+
+
+def test_batch_members_match_the_oracle(P, orc):
+    """One batch step of a mixed batch (heat at rate 16 and uncompressed, wave
+    at rate 16 and uncompressed with a resident model, each with a source),
+    every member checked against the FP64 oracle run of its own problem,
+    point by point and in rel-L2, within the bars of its rate."""
+    from gpu_util import assert_compressed, assert_uncompressed
+    torch_cuda()
+    steps = 12
+    probs = []
+    u = synthetic.uniform_field((64, 36, 44), 21)
+    probs.append((heat_desc(P, u.shape, rate=16, k=4, T=16), {0: u}, None, ("heat", u)))
+    u = synthetic.uniform_field((48, 40, 52), 22)
+    probs.append((heat_desc(P, u.shape, rate=0, k=3, T=12, alpha=0.12), {0: u}, None, ("heat12", u)))
+    for shape, rate, ro in (((96, 40, 48), 16, 0), ((64, 44, 36), 0, 1)):
+        m = synthetic.wave_model(shape)
+        z = np.zeros(shape, np.float32)
+        w = synthetic.ricker(steps)
+        probs.append((wave_desc(P, shape, rate=rate, k=2, T=32, ro=ro), {0: z, 1: z, 2: m},
+                      (synthetic.centre(shape)[::-1], w), ("wave", z, m, w, shape)))
+    b = _batch(P, [(d, f, s) for d, f, s, _ in probs])
+    try:
+        b.step(steps)
+        b.synchronize(300.0)
+        got = []
+        for bp in b.problems:
+            out = bp.decompress(P.OOCS_FIELD_U)
+            bp.synchronize(120.0)
+            got.append(out.numpy().copy())
+    finally:
+        b.close()
+    for g, (d, _, _, ref_in) in zip(got, probs):
+        if ref_in[0].startswith("heat"):
+            alpha = 0.12 if ref_in[0] == "heat12" else 0.1
+            ref = orc.heat_run(ref_in[1], synthetic.heat_star_coef(alpha), steps)
+            scheme = "heat"
+        else:
+            _, z, m, w, shape = ref_in
+            ref, _ = orc.wave_run(z, z, m, synthetic.wave_star_coef(), steps, src=synthetic.centre(shape), w=w)
+            scheme = "wave"
+        if int(d.rate_bits):
+            assert_compressed(g, ref, int(d.rate_bits), f"{scheme} rate {int(d.rate_bits)}")
+        else:
+            assert_uncompressed(g, ref, scheme, f"{scheme} uncompressed")
