@@ -265,8 +265,10 @@ oocs_status oocs_decompress(oocs_ctx *ctx, int32_t field, float *dst);
 oocs_status oocs_compress_device(oocs_ctx *ctx, int32_t field, const float *src, int64_t z0, int64_t nplanes);
 oocs_status oocs_decompress_device(oocs_ctx *ctx, int32_t field, float *dst, int64_t z0, int64_t nplanes);
 
-/* Page-locked host memory of exactly `bytes` (cudaHostAlloc, portable) for
- * host stores; free with oocs_host_free.  OOCS_ERR_HOST_ALLOC if it fails.  */
+/* Page-locked host memory of exactly `bytes` for host stores, zero-filled:
+ * anonymous pages with transparent-huge-page advice, registered with
+ * cudaHostRegister (portable).  Free with oocs_host_free, which rejects any
+ * other pointer (OOCS_ERR_INVALID_ARG).  OOCS_ERR_HOST_ALLOC if it fails.   */
 oocs_status oocs_host_alloc(uint64_t bytes, void **ptr);
 oocs_status oocs_host_free(void *ptr);
 

@@ -5,8 +5,9 @@ arithmetic of its own: all work runs in liboocs.so's CUDA kernels.  There is no
 CPU fallback: if the library is missing, ``lib()`` raises.
 
 PyTorch is used only as plumbing by the ``OutOfCoreStencil`` helper: device
-workspace (``torch.empty(..., device='cuda')``), page-locked host stores
-(``pin_memory=True``) and the three CUDA streams the pipeline runs on.
+workspace (``torch.empty(..., device='cuda')``), tensor views of the page-locked
+host stores that oocs_host_alloc returns, and the three CUDA streams the
+pipeline runs on.
 """
 from __future__ import annotations
 
@@ -22,7 +23,7 @@ OOCS_OK = 0
 STATUS_NAMES = {0: "OOCS_OK", 1: "OOCS_ERR_INVALID_ARG", 2: "OOCS_ERR_BUDGET",
                 3: "OOCS_ERR_HOST_ALLOC", 4: "OOCS_ERR_CUDA", 5: "OOCS_ERR_TIMEOUT",
                 6: "OOCS_ERR_STATE", 7: "OOCS_ERR_UNSUPPORTED", 8: "OOCS_ERR_NONFINITE"}
-OOCS_ERR_TIMEOUT, OOCS_ERR_NONFINITE = 5, 8
+OOCS_ERR_INVALID_ARG, OOCS_ERR_TIMEOUT, OOCS_ERR_NONFINITE = 1, 5, 8
 OOCS_DEVERR_WAIT_TIMEOUT, OOCS_DEVERR_NONFINITE = 1, 2
 OOCS_HEAT, OOCS_WAVE, OOCS_WAVE_ADJOINT = 0, 1, 2
 OOCS_CODEC_TRANSFORM, OOCS_CODEC_QUANT = 0, 1
@@ -489,9 +490,12 @@ class HostBuffer:
         self.ptr, self.nbytes = p.value, int(nbytes)
 
     def tensor(self):
+        """A uint8 tensor over the buffer; the tensor (and its views) keep the
+        buffer alive until close() is called explicitly."""
         import torch
-        arr = np.ctypeslib.as_array((ctypes.c_uint8 * self.nbytes).from_address(self.ptr))
-        return torch.from_numpy(arr)
+        carr = (ctypes.c_uint8 * self.nbytes).from_address(self.ptr)
+        carr._owner = self
+        return torch.from_numpy(np.ctypeslib.as_array(carr))
 
     def close(self):
         if self.ptr:
@@ -503,6 +507,12 @@ class HostBuffer:
             self.close()
         except Exception:
             pass
+
+
+def pinned_bytes(nbytes: int):
+    """A zero-filled uint8 tensor of nbytes in page-locked host memory from
+    oocs_host_alloc, freed when the tensor and all of its views are gone."""
+    return HostBuffer(int(nbytes)).tensor()
 
 
 def oocs_encode_device(field_ptr, nx, ny, nz, rate, blocks_ptr, stream=0, codec=0):
@@ -519,7 +529,8 @@ class OutOfCoreStencil:
     """A context plus the memory it needs, allocated through PyTorch.
 
     Device workspace: one ``torch.uint8`` CUDA tensor of plan.workspace_bytes.
-    Host stores: one pinned ``torch.uint8`` tensor per streamed field.
+    Host stores: one ``torch.uint8`` tensor per streamed field over page-locked
+    host memory from oocs_host_alloc (pinned_bytes).
     Streams: three ``torch.cuda.Stream`` objects.
     """
 
@@ -545,7 +556,7 @@ class OutOfCoreStencil:
             if stores is not None:
                 st = stores[f][:self.plan.host_store_bytes]
             else:
-                st = torch.zeros(self.plan.host_store_bytes, dtype=torch.uint8, pin_memory=True)
+                st = pinned_bytes(self.plan.host_store_bytes)
             oocs_bind_field(self.ctx, f, st.data_ptr(), st.numel())
             self.stores.append(st)
         self._keep = []
@@ -555,7 +566,8 @@ class OutOfCoreStencil:
         return (self.desc.nz, self.desc.ny, self.desc.nx)
 
     def pinned_field(self):
-        return self.torch.empty(self.shape, dtype=self.torch.float32, pin_memory=True)
+        n = int(np.prod(self.shape))
+        return pinned_bytes(4 * n).view(self.torch.float32).reshape(self.shape)
 
     def set_source(self, x, y, z, w):
         oocs_set_source(self.ctx, x, y, z, w)
@@ -593,7 +605,12 @@ class OutOfCoreStencil:
 
     def snapshot_stores(self):
         """Pinned host copies of the current stores (call after synchronize)."""
-        return [s.clone().pin_memory() for s in self.stores]
+        out = []
+        for s in self.stores:
+            c = pinned_bytes(s.numel())
+            c.copy_(s)
+            out.append(c)
+        return out
 
     def restore_stores(self, snap, t: int = 0):
         """Put the stores back to a snapshot and the time index to t (after synchronize)."""
@@ -640,7 +657,7 @@ class BatchProblem(OutOfCoreStencil):
         nfields = BOUND_FIELDS[desc.scheme]
         self.stores = []
         for f in range(nfields):
-            st = torch.zeros(self.plan.host_store_bytes, dtype=torch.uint8, pin_memory=True)
+            st = pinned_bytes(self.plan.host_store_bytes)
             oocs_bind_field(self.ctx, f, st.data_ptr(), st.numel())
             self.stores.append(st)
         self._keep = []
