@@ -93,8 +93,8 @@ def class_key(desc, budget: int, tol: float) -> str:
 
 
 class _Probe:
-    """FP32 fields of one grid and host stores, page-locked once (the library's
-    host allocation) and reused by every candidate of the grid: the problem's
+    """FP32 fields of one grid and host stores, pinned once and reused by
+    every candidate of the grid: the problem's
     own initial fields when given (`data`: field id -> array), else seeded
     stand-ins of the same kind."""
 
@@ -106,7 +106,7 @@ class _Probe:
         self.shape = shape
         self.fields = {}
         for f in range(nf):
-            t = O.pinned_bytes(4 * int(np.prod(shape))).view(torch.float32).reshape(shape)
+            t = torch.empty(shape, dtype=torch.float32, pin_memory=True)
             a = t.numpy()
             if data is not None and f in data:
                 a[...] = np.asarray(data[f], dtype=np.float32).reshape(shape)
@@ -118,7 +118,7 @@ class _Probe:
                 a[...] = 1e-3 * rng.random(shape, dtype=np.float32)
             self.fields[f] = t
         raw = 4 * int(desc.nx) * int(desc.ny) * int(desc.nz)  # the largest store (rate 0)
-        self.stores = [O.pinned_bytes(raw) for _ in range(nf)]
+        self.stores = [torch.empty(raw, dtype=torch.uint8, pin_memory=True) for _ in range(nf)]
 
 
 def time_candidate(desc, steps: int, probe: _Probe | None = None, reps: int = 3) -> float:

@@ -5,9 +5,9 @@ arithmetic of its own: all work runs in liboocs.so's CUDA kernels.  There is no
 CPU fallback: if the library is missing, ``lib()`` raises.
 
 PyTorch is used only as plumbing by the ``OutOfCoreStencil`` helper: device
-workspace (``torch.empty(..., device='cuda')``), tensor views of the page-locked
-host stores that oocs_host_alloc returns, and the three CUDA streams the
-pipeline runs on.
+workspace (``torch.empty(..., device='cuda')``), page-locked host stores
+(``pin_memory=True``, or views of oocs_host_alloc memory for large stores) and
+the three CUDA streams the pipeline runs on.
 """
 from __future__ import annotations
 
@@ -511,7 +511,9 @@ class HostBuffer:
 
 def pinned_bytes(nbytes: int):
     """A zero-filled uint8 tensor of nbytes in page-locked host memory from
-    oocs_host_alloc, freed when the tensor and all of its views are gone."""
+    oocs_host_alloc, freed when the tensor and all of its views are gone.
+    Each call maps and registers new memory (milliseconds per gigabyte), so it
+    suits long-lived buffers such as large host stores."""
     return HostBuffer(int(nbytes)).tensor()
 
 
@@ -529,8 +531,10 @@ class OutOfCoreStencil:
     """A context plus the memory it needs, allocated through PyTorch.
 
     Device workspace: one ``torch.uint8`` CUDA tensor of plan.workspace_bytes.
-    Host stores: one ``torch.uint8`` tensor per streamed field over page-locked
-    host memory from oocs_host_alloc (pinned_bytes).
+    Host stores: one pinned ``torch.uint8`` tensor per streamed field (PyTorch's
+    caching host allocator), or the caller's (``stores=``): for stores of tens
+    of gigabytes, tensors over oocs_host_alloc memory (``pinned_bytes``,
+    ``HostBuffer``), which keeps its copy speed under sustained traffic.
     Streams: three ``torch.cuda.Stream`` objects.
     """
 
@@ -556,7 +560,7 @@ class OutOfCoreStencil:
             if stores is not None:
                 st = stores[f][:self.plan.host_store_bytes]
             else:
-                st = pinned_bytes(self.plan.host_store_bytes)
+                st = torch.zeros(self.plan.host_store_bytes, dtype=torch.uint8, pin_memory=True)
             oocs_bind_field(self.ctx, f, st.data_ptr(), st.numel())
             self.stores.append(st)
         self._keep = []
@@ -566,8 +570,7 @@ class OutOfCoreStencil:
         return (self.desc.nz, self.desc.ny, self.desc.nx)
 
     def pinned_field(self):
-        n = int(np.prod(self.shape))
-        return pinned_bytes(4 * n).view(self.torch.float32).reshape(self.shape)
+        return self.torch.empty(self.shape, dtype=self.torch.float32, pin_memory=True)
 
     def set_source(self, x, y, z, w):
         oocs_set_source(self.ctx, x, y, z, w)
@@ -605,12 +608,7 @@ class OutOfCoreStencil:
 
     def snapshot_stores(self):
         """Pinned host copies of the current stores (call after synchronize)."""
-        out = []
-        for s in self.stores:
-            c = pinned_bytes(s.numel())
-            c.copy_(s)
-            out.append(c)
-        return out
+        return [s.clone().pin_memory() for s in self.stores]
 
     def restore_stores(self, snap, t: int = 0):
         """Put the stores back to a snapshot and the time index to t (after synchronize)."""
@@ -657,7 +655,7 @@ class BatchProblem(OutOfCoreStencil):
         nfields = BOUND_FIELDS[desc.scheme]
         self.stores = []
         for f in range(nfields):
-            st = pinned_bytes(self.plan.host_store_bytes)
+            st = torch.zeros(self.plan.host_store_bytes, dtype=torch.uint8, pin_memory=True)
             oocs_bind_field(self.ctx, f, st.data_ptr(), st.numel())
             self.stores.append(st)
         self._keep = []
