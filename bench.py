@@ -6,8 +6,8 @@ core): 7-point heat (Jacobi) stencil, FP32, 2560 x 2560 x 5120 grid (one field
 of 134 GB), seeded U[0,1) field, alpha = 0.1, 20 time steps in 5 sweeps of
 temporal depth k = 4 over 42 z-slabs, a 16 GiB device budget, the fixed-rate
 codec at 16 bits/value, one working buffer (Sec. 5).  The field's compressed
-store (67 GB) is pinned host memory: the first half of the 134 GB raw FP32
-array that the e2e leg reads and writes in place.
+store (67 GB) is page-locked host memory from oocs_host_alloc; the e2e leg
+works in place in a 134 GB raw FP32 array (the store in its first half).
 
 One bench step = one oocs_step(20) from the seeded initial state (the store is
 refilled before each, untimed: planes drawn on the GPU and compressed by
@@ -302,7 +302,7 @@ def base_line(args, world, nz):
                        "time_steps_per_step": OOC_STEPS, "temporal_depth": OOC_K, "rate_bits": OOC_RATE,
                        "working_buffers": 1, "device_budget_bytes": OOC_BUDGET,
                        "field_bytes_fp32": OOC_SHAPE[2] * OOC_SHAPE[1] * nz * 4,
-                       "host_store": "pinned host memory, in place in the raw FP32 array",
+                       "host_store": "page-locked host memory (oocs_host_alloc); e2e: in place in the raw FP32 array",
                        "l2": "inputs larger than L2 (the field is 134 GB; one slab window 3.5 GB)",
                        "parallelism": f"replicas{world}"}}
 
@@ -419,11 +419,13 @@ def run_ours(args):
     n_all = nx * ny * nz
     raw_bytes = n_all * 4
 
-    # the raw FP32 array; the rate-16 store lives in its first half (in place)
-    t0 = time.time()
-    host = P.HostBuffer(raw_bytes)
-    t_pin = time.time() - t0
+    # the rate-16 store (67 GB) alone in page-locked host memory for the
+    # timed calls; the raw FP32 array (134 GB, the store in place in its first
+    # half) is allocated later, for e2e and the uncompressed run
     desc16 = ooc_desc(P, OOC_RATE, nz)
+    t0 = time.time()
+    host = P.HostBuffer(P.oocs_query(desc16).host_store_bytes)
+    t_pin = time.time() - t0
     st = P.OutOfCoreStencil(desc16, stores=[host.tensor()])
     plan = st.plan
     t_fill = fill_store(P, torch, st, shape)
@@ -535,6 +537,13 @@ def run_ours(args):
 
     # ---- e2e: the raw FP32 host array in, the result back in it; the store
     # is the array's first half (in place), so the host needs one array
+    st.close()
+    host.close()
+    del st, host
+    t0 = time.time()
+    host = P.HostBuffer(raw_bytes)
+    t_pin_raw = time.time() - t0
+    st = P.OutOfCoreStencil(desc16, stores=[host.tensor()])
     raw = host.tensor().view(torch.float32).reshape(shape)
     fill_raw(torch, raw, shape, dev)
     e2e_ms = []
@@ -601,7 +610,8 @@ def run_ours(args):
                  "plan": {"slabs": plan.num_slabs, "slab_planes": plan.slab_planes,
                           "halo_planes": plan.halo_planes, "window_planes": plan.window_planes,
                           "workspace_bytes": plan.workspace_bytes, "host_store_bytes": plan.host_store_bytes},
-                 "host": {"pin_seconds": t_pin, "fill_seconds": t_fill},
+                 "host": {"pin_seconds_store": t_pin, "pin_seconds_raw": t_pin_raw, "fill_seconds": t_fill,
+                          "allocation": "oocs_host_alloc (huge-page anonymous memory, cudaHostRegister)"},
                  "codec_kernels": codec, "uncompressed": uncompressed})
 
     # ---- FP64 oracle on the dependency cubes: the CPU baseline and the
