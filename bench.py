@@ -514,6 +514,9 @@ def run_ours(args):
                       "d2h_bytes_per_step": d["d2h_bytes"] / args.steps, "link": link,
                       "link_after_timed_calls": link_after,
                       "kernel_chain_ms_per_step": chain_ms,
+                      "t_codec_ms": kernels["load"]["device_ms"] + kernels["store"]["device_ms"],
+                      "t_codec_note": "the codec's integer-instruction bound: live decode + encode time of the "
+                                      "profiled call (no peak: its cost is instructions, not bytes)",
                       "copies_in_profiled_call": copies,
                       "measured_binding": max((chain_ms, "kernel chain"), (copies["h2d"]["device_ms"], "h2d copies"),
                                               (copies["d2h"]["device_ms"], "d2h copies"))[1]}
