@@ -19,7 +19,9 @@
  *  - The caller owns all memory: the device workspace, the host stores and
  *    any raw host arrays.  The library allocates only CUDA events and small
  *    host metadata, and frees only what it allocated.
- *  - Every call returns an oocs_status and never aborts, throws or traps.
+ *  - Every call returns an oocs_status and never aborts, throws or traps (a
+ *    host allocation that fails inside the library returns
+ *    OOCS_ERR_HOST_ALLOC).
  *    OOCS_ERR_CUDA, OOCS_ERR_TIMEOUT and OOCS_ERR_NONFINITE are sticky on a
  *    context until oocs_destroy; the text of the last error is in
  *    oocs_last_error().

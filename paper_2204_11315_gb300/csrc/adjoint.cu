@@ -211,7 +211,7 @@ extern "C" {
 
 oocs_status oocs_adjoint_step(const oocs_desc *desc, const float *lam, float *lam_prev, const float *mu,
                               float *mu_out, const float *m, const float *res, int64_t zr, void *stream)
-{
+try {
     oocs_status s = wave_desc_ok(desc);
     if (s != OOCS_OK)
         return s;
@@ -232,11 +232,13 @@ oocs_status oocs_adjoint_step(const oocs_desc *desc, const float *lam, float *la
     L.res = res;
     L.zr = res ? zr : -1;
     return step_launched(launch_star_step(L, static_cast<cudaStream_t>(stream)), "adjoint step");
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_gradient_accumulate(const oocs_desc *desc, float *grad_m, const float *lam, const float *u,
                                      float w, const int64_t *src_xyz, void *stream)
-{
+try {
     oocs_status s = wave_desc_ok(desc);
     if (s != OOCS_OK)
         return s;
@@ -256,32 +258,40 @@ oocs_status oocs_gradient_accumulate(const oocs_desc *desc, float *grad_m, const
         L.w = w;
     }
     return step_launched(launch_star_step(L, static_cast<cudaStream_t>(stream)), "gradient accumulation");
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_receiver_residual(const float *u_plane, const float *d_plane, int64_t n, float *res,
                                    double *misfit, void *stream)
-{
+try {
     if (!u_plane || !d_plane || !res || n <= 0)
         return bad("u_plane, d_plane, res and n > 0 are required");
     k_residual<<<grid1d(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(u_plane, d_plane, res, n, misfit);
     return launched("receiver residual");
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_model_from_velocity(const float *v, float *m, int64_t n, float dt_over_dx, void *stream)
-{
+try {
     if (!v || !m || n <= 0)
         return bad("v, m and n > 0 are required");
     k_model<<<grid1d(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(v, m, n, dt_over_dx);
     return launched("model from velocity");
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_velocity_gradient(const float *grad_m, const float *v, float *grad_v, int64_t n,
                                    float dt_over_dx, void *stream)
-{
+try {
     if (!grad_m || !v || !grad_v || n <= 0)
         return bad("grad_m, v, grad_v and n > 0 are required");
     k_velocity_grad<<<grid1d(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(grad_m, v, grad_v, n, dt_over_dx);
     return launched("velocity gradient");
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 int64_t oocs_misfit_workspace_bytes(const oocs_desc *desc, int32_t nsteps, int32_t checkpoint_every,
@@ -296,7 +306,7 @@ oocs_status oocs_misfit_forward(const oocs_desc *desc, const float *m, const int
                                 int32_t nw, int64_t zr, const float *d_obs, int32_t nsteps,
                                 int32_t checkpoint_every, int32_t rate_bits, void *workspace,
                                 int64_t workspace_bytes, float *res, double *misfit, void *stream)
-{
+try {
     oocs_status s = driver_args(desc, src_xyz, zr, nsteps, checkpoint_every, rate_bits, workspace,
                                 workspace_bytes);
     if (s != OOCS_OK)
@@ -332,13 +342,15 @@ oocs_status oocs_misfit_forward(const oocs_desc *desc, const float *m, const int
         e = cudaGetLastError();
     }
     return step_launched(e, "misfit forward");
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_misfit_backward(const oocs_desc *desc, const float *m, const int64_t *src_xyz, const float *w,
                                  int32_t nw, int64_t zr, const float *res, int32_t nsteps,
                                  int32_t checkpoint_every, int32_t rate_bits, void *workspace,
                                  int64_t workspace_bytes, float *grad_m, void *stream)
-{
+try {
     oocs_status s = driver_args(desc, src_xyz, zr, nsteps, checkpoint_every, rate_bits, workspace,
                                 workspace_bytes);
     if (s != OOCS_OK)
@@ -399,6 +411,8 @@ oocs_status oocs_misfit_backward(const oocs_desc *desc, const float *m, const in
         }
     }
     return step_launched(e, "misfit backward");
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 }  // extern "C"

@@ -1234,6 +1234,15 @@ oocs_status enqueue_adjoint_slab(oocs_ctx *c, int s, int64_t k, const char *fwd,
 
 // ============================================================== C ABI ======
 
+oocs_status oocs::exception_status(oocs_ctx *ctx)
+{
+    try {
+        fail(ctx, OOCS_ERR_HOST_ALLOC, "a host allocation inside the library failed");
+    } catch (...) {
+    }
+    return OOCS_ERR_HOST_ALLOC;
+}
+
 // oocs_host_alloc's mappings and their sizes (for munmap)
 static std::mutex g_host_mu;
 static std::map<void *, uint64_t> g_host_maps;
@@ -1257,17 +1266,19 @@ extern "C" {
 const char *oocs_version(void) { return kVersion; }
 
 oocs_status oocs_query(const oocs_desc *desc, oocs_plan *plan)
-{
+try {
     std::string err;
     oocs_status s = plan_impl(desc, plan, err);
     if (s != OOCS_OK)
         g_last_error = err;
     return s;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_create(const oocs_desc *desc, void *workspace, uint64_t workspace_bytes,
                         void *const streams[3], oocs_ctx **out)
-{
+try {
     if (!out)
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -1336,10 +1347,12 @@ oocs_status oocs_create(const oocs_desc *desc, void *workspace, uint64_t workspa
     }
     *out = c;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_bind_field(oocs_ctx *ctx, int32_t field, void *host_store, uint64_t bytes)
-{
+try {
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
@@ -1354,10 +1367,12 @@ oocs_status oocs_bind_field(oocs_ctx *ctx, int32_t field, void *host_store, uint
     if (field == OOCS_FIELD_M)
         ctx->ro_dirty = true;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_set_source(oocs_ctx *ctx, int64_t x, int64_t y, int64_t z, const float *w, int32_t nw)
-{
+try {
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
@@ -1376,10 +1391,12 @@ oocs_status oocs_set_source(oocs_ctx *ctx, int64_t x, int64_t y, int64_t z, cons
     if (nd > 0 && !ctx->trace && ctx->L.src_off)
         CU(ctx, cudaMemcpyAsync(ctx->w_dev(), ctx->w.data(), (size_t)nd * 4, cudaMemcpyHostToDevice, ctx->st[0]));
     return OOCS_OK;
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_set_receiver(oocs_ctx *ctx, int64_t zr, float *planes, int64_t nplanes)
-{
+try {
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
@@ -1391,10 +1408,12 @@ oocs_status oocs_set_receiver(oocs_ctx *ctx, int64_t zr, float *planes, int64_t 
     ctx->rec_z = zr;
     ctx->rec_n = nplanes;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_selftest_stuck_wait(oocs_ctx *ctx)
-{
+try {
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
@@ -1403,10 +1422,12 @@ oocs_status oocs_selftest_stuck_wait(oocs_ctx *ctx)
         return s;
     CU(ctx, launch_stuck_wait(ctx->st[0]));
     return OOCS_OK;
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_set_state_record(oocs_ctx *ctx, void *const *stores, int64_t t0, int64_t n)
-{
+try {
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
@@ -1417,6 +1438,8 @@ oocs_status oocs_set_state_record(oocs_ctx *ctx, void *const *stores, int64_t t0
                      n > 0 ? reinterpret_cast<char *const *>(stores) + n : nullptr);
     ctx->srec_t0 = t0;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(ctx);
 }
 
 static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, float *dst, bool enc)
@@ -1506,13 +1529,17 @@ static oocs_status codec_field(oocs_ctx *ctx, int32_t field, const float *src, f
 }
 
 oocs_status oocs_compress(oocs_ctx *ctx, int32_t field, const float *src)
-{
+try {
     return codec_field(ctx, field, src, nullptr, true);
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_decompress(oocs_ctx *ctx, int32_t field, float *dst)
-{
+try {
     return codec_field(ctx, field, nullptr, dst, false);
+} catch (...) {
+    return exception_status(ctx);
 }
 
 // Planes [z0, z0 + nplanes) of `field` between a device array holding them
@@ -1584,17 +1611,21 @@ static oocs_status codec_range_device(oocs_ctx *ctx, int32_t field, const float 
 }
 
 oocs_status oocs_compress_device(oocs_ctx *ctx, int32_t field, const float *src, int64_t z0, int64_t nplanes)
-{
+try {
     return codec_range_device(ctx, field, src, nullptr, z0, nplanes, true);
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_decompress_device(oocs_ctx *ctx, int32_t field, float *dst, int64_t z0, int64_t nplanes)
-{
+try {
     return codec_range_device(ctx, field, nullptr, dst, z0, nplanes, false);
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_host_alloc(uint64_t bytes, void **ptr)
-{
+try {
     if (!ptr || bytes == 0)
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "bytes > 0 and an output pointer are required");
     *ptr = nullptr;
@@ -1624,16 +1655,23 @@ oocs_status oocs_host_alloc(uint64_t bytes, void **ptr)
         const long pg = std::max<long>(sysconf(_SC_PAGESIZE), 4096);
         const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
         const uint64_t per = (bytes + nt - 1) / nt;
+        auto touch = [p, pg](uint64_t a, uint64_t b) {
+            volatile char *c = static_cast<volatile char *>(p);
+            for (uint64_t o = a; o < b; o += (uint64_t)pg)
+                c[o] = 0;
+        };
         std::vector<std::thread> th;
-        for (unsigned i = 0; i < nt; ++i) {
-            const uint64_t a = std::min<uint64_t>(bytes, (uint64_t)i * per);
-            const uint64_t b = std::min<uint64_t>(bytes, a + per);
-            th.emplace_back([p, a, b, pg]() {
-                volatile char *c = static_cast<volatile char *>(p);
-                for (uint64_t o = a; o < b; o += (uint64_t)pg)
-                    c[o] = 0;
-            });
+        uint64_t done = 0;  // [0, done) is handed to threads; the rest is touched here
+        try {
+            for (unsigned i = 0; i < nt; ++i) {
+                const uint64_t a = std::min<uint64_t>(bytes, (uint64_t)i * per);
+                const uint64_t b = std::min<uint64_t>(bytes, a + per);
+                th.emplace_back(touch, a, b);
+                done = b;
+            }
+        } catch (...) {  // no thread could be started: touch the rest on this one
         }
+        touch(done, bytes);
         for (auto &t : th)
             t.join();
     }
@@ -1650,10 +1688,12 @@ oocs_status oocs_host_alloc(uint64_t bytes, void **ptr)
     }
     *ptr = p;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_host_free(void *ptr)
-{
+try {
     if (!ptr)
         return OOCS_OK;
     uint64_t bytes = 0;
@@ -1669,10 +1709,12 @@ oocs_status oocs_host_free(void *ptr)
         cudaGetLastError();
     munmap(ptr, bytes);
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_set_time(oocs_ctx *ctx, int64_t t)
-{
+try {
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
@@ -1680,10 +1722,12 @@ oocs_status oocs_set_time(oocs_ctx *ctx, int64_t t)
         return fail(ctx, OOCS_ERR_INVALID_ARG, "time index must be >= 0");
     ctx->stats.steps_done = (uint64_t)t;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
-{
+try {
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
@@ -1781,10 +1825,12 @@ oocs_status oocs_step(oocs_ctx *ctx, int32_t nsteps)
         ctx->batch->g = ctx->g;
     ctx->timing_pending = !ctx->trace;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns)
-{
+try {
     if (!ctx)
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "ctx is NULL");
     if (ctx->sticky != OOCS_OK)
@@ -1833,11 +1879,13 @@ oocs_status oocs_synchronize(oocs_ctx *ctx, uint64_t timeout_ns)
     }
     collect_profile(ctx);
     return OOCS_OK;
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_get_timeline(const oocs_ctx *ctx, oocs_timeline_entry *entries, int64_t capacity,
                               int64_t *count)
-{
+try {
     if (!ctx || !count || capacity < 0 || (capacity > 0 && !entries))
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "ctx and count are required, entries when capacity > 0");
     const int64_t n = (int64_t)ctx->timeline.size();
@@ -1845,19 +1893,23 @@ oocs_status oocs_get_timeline(const oocs_ctx *ctx, oocs_timeline_entry *entries,
         entries[i] = ctx->timeline[i];
     *count = n;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_set_fault_injection(oocs_ctx *ctx, int64_t nth_call)
-{
+try {
     if (!ctx || nth_call < 0)
         return fail(ctx, OOCS_ERR_INVALID_ARG, "ctx is NULL or nth_call < 0");
     ctx->inject_at = nth_call;
     ctx->inject_seen = 0;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_device_errors(uint32_t *flags, int32_t clear)
-{
+try {
     if (!flags)
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "flags is NULL");
     cudaError_t e = cudaDeviceSynchronize();
@@ -1868,18 +1920,22 @@ oocs_status oocs_device_errors(uint32_t *flags, int32_t clear)
         return fail(nullptr, OOCS_ERR_CUDA, std::string("oocs_device_errors: ") + cudaGetErrorString(e));
     *flags = code;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_get_stats(const oocs_ctx *ctx, oocs_stats *out)
-{
+try {
     if (!ctx || !out)
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "ctx or out is NULL");
     *out = ctx->stats;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_set_profiling(oocs_ctx *ctx, int32_t classes)
-{
+try {
     oocs_status s = check_ready(ctx);
     if (s != OOCS_OK)
         return s;
@@ -1887,11 +1943,13 @@ oocs_status oocs_set_profiling(oocs_ctx *ctx, int32_t classes)
         return fail(ctx, OOCS_ERR_INVALID_ARG, "profiling mask must be in [0, 31]");
     ctx->prof = classes;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(ctx);
 }
 
 oocs_status oocs_trace_schedule(const oocs_desc *desc, const int32_t *nsteps, int32_t ncalls,
                                 oocs_trace_op *ops, int64_t capacity, int64_t *count)
-{
+try {
     if (!count || (ncalls > 0 && !nsteps) || ncalls < 0 || capacity < 0 || (capacity > 0 && !ops))
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "bad trace arguments");
     *count = 0;
@@ -1938,6 +1996,8 @@ oocs_status oocs_trace_schedule(const oocs_desc *desc, const int32_t *nsteps, in
     for (size_t i = 0; i < trace.size(); ++i)
         ops[i] = trace[i];
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 const char *oocs_last_error(const oocs_ctx *ctx)
@@ -1975,13 +2035,15 @@ static void destroy_ctx(oocs_ctx *ctx)
 }
 
 oocs_status oocs_destroy(oocs_ctx *ctx)
-{
+try {
     if (!ctx)
         return OOCS_OK;
     if (ctx->batch)
         return fail(ctx, OOCS_ERR_STATE, "this context belongs to a batch (oocs_batch_destroy)");
     destroy_ctx(ctx);
     return OOCS_OK;
+} catch (...) {
+    return exception_status(ctx);
 }
 
 // ------------------------------------------------------- device-level API --
@@ -1989,7 +2051,7 @@ oocs_status oocs_destroy(oocs_ctx *ctx)
 oocs_status oocs_incore_run(const oocs_desc *desc, float *u, float *u_prev, const float *m,
                             float *scratch, int32_t nsteps, int64_t t0, const int64_t *src_xyz,
                             const float *w, int32_t nw, void *stream)
-{
+try {
     std::string err;
     oocs_status s = validate_desc(desc, err);
     if (s != OOCS_OK)
@@ -2054,6 +2116,8 @@ oocs_status oocs_incore_run(const oocs_desc *desc, float *u, float *u_prev, cons
     if (e != cudaSuccess)
         return fail(nullptr, OOCS_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 static oocs_status codec_args(int64_t nx, int64_t ny, int64_t nz, int32_t rate, int32_t codec, const void *a,
@@ -2072,7 +2136,7 @@ static oocs_status codec_args(int64_t nx, int64_t ny, int64_t nz, int32_t rate, 
 
 oocs_status oocs_encode_device(const float *field, int64_t nx, int64_t ny, int64_t nz, int32_t rate,
                                int32_t codec, void *blocks, void *stream)
-{
+try {
     oocs_status s = codec_args(nx, ny, nz, rate, codec, field, blocks);
     if (s != OOCS_OK)
         return s;
@@ -2081,11 +2145,13 @@ oocs_status oocs_encode_device(const float *field, int64_t nx, int64_t ny, int64
     if (e != cudaSuccess)
         return fail(nullptr, OOCS_ERR_CUDA, std::string("encode: ") + cudaGetErrorString(e));
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_decode_device(const void *blocks, int64_t nx, int64_t ny, int64_t nz, int32_t rate,
                                int32_t codec, float *field, void *stream)
-{
+try {
     oocs_status s = codec_args(nx, ny, nz, rate, codec, blocks, field);
     if (s != OOCS_OK)
         return s;
@@ -2094,6 +2160,8 @@ oocs_status oocs_decode_device(const void *blocks, int64_t nx, int64_t ny, int64
     if (e != cudaSuccess)
         return fail(nullptr, OOCS_ERR_CUDA, std::string("decode: ") + cudaGetErrorString(e));
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 }  // extern "C"
@@ -2374,7 +2442,7 @@ oocs_stats stats_diff(const oocs_stats &after, const oocs_stats &before)
 extern "C" {
 
 oocs_status oocs_batch_query(const oocs_desc *descs, int32_t n, uint64_t *workspace_bytes)
-{
+try {
     if (!workspace_bytes)
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "workspace_bytes is NULL");
     std::vector<oocs_desc> d;
@@ -2387,11 +2455,13 @@ oocs_status oocs_batch_query(const oocs_desc *descs, int32_t n, uint64_t *worksp
     std::vector<uint64_t> ro_off, ro_bytes, src_off;
     *workspace_bytes = batch_layout(d, v, ro_off, ro_bytes, src_off).total;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_batch_create(const oocs_desc *descs, int32_t n, void *workspace, uint64_t workspace_bytes,
                               void *const streams[3], oocs_batch **out)
-{
+try {
     if (!out)
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -2442,18 +2512,22 @@ oocs_status oocs_batch_create(const oocs_desc *descs, int32_t n, void *workspace
     }
     *out = b;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_batch_context(oocs_batch *b, int32_t i, oocs_ctx **ctx)
-{
+try {
     if (!b || !ctx || i < 0 || i >= (int32_t)b->ctx.size())
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "bad batch, index or output pointer");
     *ctx = b->ctx[i];
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_batch_step(oocs_batch *b, int32_t nsteps)
-{
+try {
     oocs_status s = batch_ready(b);
     if (s != OOCS_OK)
         return s;
@@ -2466,10 +2540,12 @@ oocs_status oocs_batch_step(oocs_batch *b, int32_t nsteps)
     SCHED(join_streams(b->ctx[0]));
     SCHED(batch_uploads(b));
     return batch_enqueue(b, nsteps, false);
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_batch_capture(oocs_batch *b, int32_t nsteps)
-{
+try {
     oocs_status s = batch_ready(b);
     if (s != OOCS_OK)
         return s;
@@ -2545,10 +2621,12 @@ oocs_status oocs_batch_capture(oocs_batch *b, int32_t nsteps)
     }
     b->graph_steps = nsteps;
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_batch_launch(oocs_batch *b)
-{
+try {
     oocs_status s = batch_ready(b);
     if (s != OOCS_OK)
         return s;
@@ -2570,10 +2648,12 @@ oocs_status oocs_batch_launch(oocs_batch *b)
     for (size_t i = 0; i < b->ctx.size(); ++i)
         add_stats(b->ctx[i]->stats, b->graph_delta[i], +1);
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_batch_synchronize(oocs_batch *b, uint64_t timeout_ns)
-{
+try {
     if (!b)
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "batch is NULL");
     for (oocs_ctx *c : b->ctx) {
@@ -2582,17 +2662,21 @@ oocs_status oocs_batch_synchronize(oocs_batch *b, uint64_t timeout_ns)
             return fail(nullptr, s, c->err);
     }
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_batch_destroy(oocs_batch *b)
-{
+try {
     batch_free(b);
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 oocs_status oocs_batch_trace_schedule(const oocs_desc *descs, int32_t n, const int32_t *nsteps, int32_t ncalls,
                                       oocs_trace_op *ops, int64_t capacity, int64_t *count)
-{
+try {
     if (!count || (ncalls > 0 && !nsteps) || ncalls < 0 || capacity < 0 || (capacity > 0 && !ops))
         return fail(nullptr, OOCS_ERR_INVALID_ARG, "bad trace arguments");
     *count = 0;
@@ -2626,6 +2710,8 @@ oocs_status oocs_batch_trace_schedule(const oocs_desc *descs, int32_t n, const i
     for (size_t i = 0; i < trace.size(); ++i)
         ops[i] = trace[i];
     return OOCS_OK;
+} catch (...) {
+    return exception_status(nullptr);
 }
 
 }  // extern "C"

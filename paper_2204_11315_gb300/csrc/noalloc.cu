@@ -111,7 +111,7 @@ extern "C" oocs_status oocs_incore_run_noalloc(const oocs_desc *desc, float *u, 
                                                const float *m, int32_t nsteps, int64_t t0,
                                                const int64_t *src_xyz, const float *w, int32_t nw,
                                                void *stream)
-{
+try {
     if (!desc) {
         oocs::set_last_error("desc is NULL");
         return OOCS_ERR_INVALID_ARG;
@@ -132,4 +132,6 @@ extern "C" oocs_status oocs_incore_run_noalloc(const oocs_desc *desc, float *u, 
     if (s != OOCS_OK)
         return s;
     return oocs_incore_run(desc, u, u_prev, m, scratch, nsteps, t0, src_xyz, w, nw, stream);
+} catch (...) {
+    return oocs::exception_status(nullptr);
 }
