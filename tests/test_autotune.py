@@ -31,7 +31,7 @@ def A(monkeypatch):
         def __init__(self, desc, seed=0, data=None):
             self.data = data
 
-    errors = {8: 3e-3, 12: 2e-4, 16: 1e-5}
+    errors = {8: 3e-3, 12: 2e-4, 16: 1e-5, 20: 6e-7, 24: 4e-8}
 
     def fake_errors(desc, steps, probe, rates=A.RATES):
         A.err_calls.append((int(desc.nz), steps, probe.data))
@@ -61,6 +61,8 @@ def test_rate_follows_the_measured_error(A):
     assert A.rate_for(e, 2e-3) == 12        # 2e-4 <= 1e-3 < 3e-3
     assert A.rate_for(e, 0.05) == 8
     assert A.rate_for(e, 1e-6) == 0         # nothing close enough: uncompressed
+    assert A.rate_for({**e, 20: 6e-7, 24: 4e-8}, 2e-6) == 20  # the higher rates when 16 misses
+    assert A.rate_for({**e, 20: 6e-7, 24: 4e-8}, 1e-6) == 24
     assert A.rate_for({8: 0.0, 16: 0.0}, 1e-9) == 8
 
 
@@ -70,7 +72,7 @@ def test_rate_error_is_measured_on_the_problem_data(P, A):
     out, rep = A.tune(descs, 1e-4, 8 << 30, data=data, err_steps=50)
     assert [c[2] for c in A.err_calls] == data and all(c[1] == 50 for c in A.err_calls)
     assert [r["rate"] for r in rep["problems"]] == [16, 16]
-    assert rep["problems"][0]["errors"] == {"8": 3e-3, "12": 2e-4, "16": 1e-5}
+    assert rep["problems"][0]["errors"] == {"8": 3e-3, "12": 2e-4, "16": 1e-5, "20": 6e-7, "24": 4e-8}
 
 
 def test_candidate_plans_respect_region_sharing(P, A):
