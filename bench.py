@@ -95,6 +95,9 @@ def parse():
                     help="nz of the headline grid (default: 5120, fewer if host memory is short)")
     ap.add_argument("--step-fusion", type=int, default=0, choices=[0, 1],
                     help="oocs_desc.step_fusion of the headline grid (1: pairs of heat steps in one kernel)")
+    ap.add_argument("--codec-fusion", type=int, default=0, choices=[0, 1],
+                    help="oocs_desc.codec_fusion of the headline grid (1: the last step of a visit encodes "
+                         "its layers in its epilogue)")
     ap.add_argument("--profile-run", choices=["ooc", "sweep", "kernels", "adjoint"], default=None,
                     help="run only the region to capture under ncu --profile-from-start off: "
                          "'ooc' = one oocs_step(20) of the headline workload; 'sweep' = one "
@@ -1225,6 +1228,7 @@ def run_profile(args):
         shape = (nz, OOC_SHAPE[1], OOC_SHAPE[2])
         desc = ooc_desc(P, OOC_RATE, nz)
         desc.step_fusion = args.step_fusion
+        desc.codec_fusion = args.codec_fusion
         plan = P.oocs_query(desc)
         host = P.HostBuffer(plan.host_store_bytes)
         st = P.OutOfCoreStencil(desc, stores=[host.tensor()])

@@ -129,6 +129,15 @@ typedef struct {
                                   * default); 1 = 64 x 8 (two consumer warps: twice the
                                   * tiles, for planes too small to fill the GPU).  Results
                                   * are bit-identical; the autotuner searches it.            */
+    int32_t codec_fusion;        /* HEAT with radius 1 and the transform codec at rate > 0:
+                                  * 0 = the last step of a slab visit writes the interior to
+                                  * the working buffer and a separate kernel encodes it (the
+                                  * default); 1 = the last step encodes each 4-plane layer
+                                  * of its results in its epilogue straight into the output
+                                  * slot (Sec. 4.2: compression on the way out of the
+                                  * kernel), so the interior never goes back to HBM as FP32.
+                                  * Byte-identical stores either way; measured slower on
+                                  * GB300.  Requires step_fusion = 0.  Ignored otherwise.    */
 } oocs_desc;
 
 /* Resolved plan (Sec. 3.1 chunking and temporal blocking; Sec. 6.2 memory model). */

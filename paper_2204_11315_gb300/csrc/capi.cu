@@ -206,6 +206,14 @@ oocs_status validate_desc(const oocs_desc *d, std::string &err)
         err = "codec must be OOCS_CODEC_TRANSFORM (0) or OOCS_CODEC_QUANT (1)";
         return OOCS_ERR_INVALID_ARG;
     }
+    if (d->codec_fusion != 0 && d->codec_fusion != 1) {
+        err = "codec_fusion must be 0 or 1";
+        return OOCS_ERR_INVALID_ARG;
+    }
+    if (d->codec_fusion == 1 && d->step_fusion == 1) {
+        err = "codec_fusion and step_fusion cannot both be 1";
+        return OOCS_ERR_INVALID_ARG;
+    }
     if (d->step_tile != 0 && d->step_tile != 1) {
         err = "step_tile must be 0 or 1";
         return OOCS_ERR_INVALID_ARG;
@@ -875,6 +883,12 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     uint64_t step_units = 0;
     // heat: pairs of steps in one fused launch (the middle step on chip)
     const bool fuse = d.scheme == OOCS_HEAT && d.radius == 1 && d.step_fusion == 1;
+    // heat: the last step encodes the interior into the out slot itself,
+    // which must then be free before the steps (copied back by visit g-3)
+    const bool enc_fused = d.codec_fusion == 1 && d.scheme == OOCS_HEAT && d.radius == 1 && d.rate_bits > 0 &&
+                           d.codec == OOCS_CODEC_TRANSFORM && !fuse;
+    if (enc_fused && roles && g >= 3)
+        SCHED(sched_wait(c, sk, kEvOut + q));
     uint64_t launches = 0;
     for (int j = 1; j <= k_eff; ++j) {
         if (fuse && j + 1 <= k_eff) {
@@ -926,7 +940,16 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             Ls.src_z = c->src[2];
             Ls.w = c->w[tstep];
         }
-        if (c->trace)
+        Ls.enc_out = nullptr;
+        if (enc_fused && j == k_eff) {
+            Ls.enc_out = c->out_slot(q, 0);
+            Ls.enc_rate = d.rate_bits;
+            Ls.enc_layer0 = z0 / 4;
+        }
+        if (c->trace && Ls.enc_out)  // the step that writes the out slot
+            trace_push(c, OOCS_OP_STEP, sk, -1, (int64_t)g,
+                       {acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true), acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, true)});
+        else if (c->trace)
             trace_push(c, OOCS_OP_STEP, sk, -1, (int64_t)g, {acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
         else
             CU(c, launch_star_step(Ls, st_k));
@@ -947,11 +970,16 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     }
     // 7. interior [z0, z1) -> out slot(s): u^(t+k) and, for the wave, u^(t+k-1);
     //    the slot was copied back by visit g-3 (by role: on another stream)
-    if (roles && g >= 3)
+    if (roles && g >= 3 && !enc_fused)
         SCHED(sched_wait(c, sk, kEvOut + q));
     if (c->trace) {
-        trace_push(c, OOCS_OP_STORE, sk, -1, (int64_t)g,
-                   {acc(OOCS_RES_WORK, wb, z0 / 4, z1 / 4, false), acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, true)});
+        if (!enc_fused)
+            trace_push(c, OOCS_OP_STORE, sk, -1, (int64_t)g,
+                       {acc(OOCS_RES_WORK, wb, z0 / 4, z1 / 4, false),
+                        acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, true)});
+    } else if (enc_fused) {
+        // encoded by the last step: counted as stored, with no launch of its own
+        c->stats.store.units += (uint64_t)(z1 - z0) * plane_f;
     } else if (d.rate_bits > 0) {
         // one encode launch for both output fields
         CodecSegments sg;

@@ -81,6 +81,11 @@ struct StepCfg {
     {
         return 128 + (size_t)NSU * kUStage * 4 + (size_t)NCF * NSC * kCStage * 4 + 2 * (NSU + NSC) * 8;
     }
+    // fused encode: a 4-plane layer of the tile's results and the compressed
+    // words of its (kTX / 4) x (TY / 4) blocks (rate up to 32)
+    static constexpr int kEncBlocks = (kTX / 4) * (TY / 4);
+    static constexpr int kEncStride = 2 * 32 + 1;
+    static constexpr size_t enc_bytes() { return (size_t)4 * TY * kTX * 4 + (size_t)kEncBlocks * kEncStride * 4; }
 };
 
 struct StepArgs {
@@ -100,6 +105,9 @@ struct StepArgs {
     const float *w_dev;  // device-side amplitude (see StepLaunch)
     const int64_t *t_dev;
     int64_t t_rel, nw;
+    uint32_t *enc_out;   // fused encode (see StepLaunch): the out slot's blocks
+    int enc_rate;
+    int enc_layer0;      // global layer of enc_out's first layer
 };
 
 // Whether the step adds a source amplitude, and which (resolved once per
@@ -187,12 +195,13 @@ struct SegCursor {
 //
 // kAdjoint and kGradient (the wave misfit's adjoint, see kernels.h) use the
 // same pipeline with three and two centre fields.
-template <int R, int SCHEME, int CW>
+template <int R, int SCHEME, int CW, bool ENC = false>
 __global__ void __launch_bounds__(32 * (CW + 1), CW == kConsumerWarps ? 2 : 3)
     k_star_step(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
                 const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_c2,
                 const StepArgs a)
 {
+    static_assert(!ENC || (R == 1 && SCHEME == kHeat), "the fused encode is built for the heat step");
     constexpr int NCF = centre_fields<SCHEME>();
     using C = StepCfg<R, NCF, CW>;
     constexpr int Q = C::Q;
@@ -204,8 +213,14 @@ __global__ void __launch_bounds__(32 * (CW + 1), CW == kConsumerWarps ? 2 : 3)
     uint64_t *uempty = ufull + C::NSU;
     uint64_t *cfull = uempty + C::NSU;
     uint64_t *cempty = cfull + C::NSC;
+    // fused encode: the layer of results and the blocks' compressed words
+    [[maybe_unused]] float *lay = reinterpret_cast<float *>(cempty + C::NSC);
+    [[maybe_unused]] uint32_t *rows = reinterpret_cast<uint32_t *>(lay + 4 * C::TY * kTX);
+    __shared__ uint32_t dbl[ENC ? 256 : 1];
 
     const int tx = threadIdx.x, wid = threadIdx.y;
+    if constexpr (ENC)
+        fill_doubling_table(dbl, 32 * wid + tx, 32 * (CW + 1));
 
     if (wid == 0 && tx == 0) {
         for (int i = 0; i < C::NSU; ++i) {
@@ -334,15 +349,68 @@ __global__ void __launch_bounds__(32 * (CW + 1), CW == kConsumerWarps ? 2 : 3)
         const bool src_in_warp =
             a.src_x >= x0 && a.src_x < x0 + kTX && a.src_y >= wy0 && a.src_y < wy0 + kRPT;
 
-        for (int z = zs; good && z < ze; ++z) {
+        // Fused encode, after the fourth plane of each layer (segments are
+        // whole layers): the consumer warps meet, the threads of the tile's
+        // blocks each encode one 4x4x4 block from the layer in shared memory,
+        // the warps meet again and copy the words out, a block row of the tile
+        // being one contiguous run of the out slot.  Every consumer warp
+        // passes both barriers of every layer, also after a wait has run out.
+        [[maybe_unused]] auto enc_layer_end = [&](int z) {
+            if (((z - zs) & 3) != 3)
+                return;
+            constexpr int NBX = kTX / 4, NBY = C::TY / 4;
+            const int t = 32 * wid + tx;
+            const int nw = 2 * a.enc_rate;
+            named_bar_sync(1, 32 * CW);
+            if (good && t < NBX * NBY) {
+                const int bx = t % NBX, by = t / NBX;
+                if (x0 + 4 * bx < a.nx && y0 + 4 * by < a.ny) {
+                    float v[64];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float4 f =
+                                *reinterpret_cast<const float4 *>(lay + (k * C::TY + 4 * by + j) * kTX + 4 * bx);
+                            v[16 * k + 4 * j + 0] = f.x;
+                            v[16 * k + 4 * j + 1] = f.y;
+                            v[16 * k + 4 * j + 2] = f.z;
+                            v[16 * k + 4 * j + 3] = f.w;
+                        }
+                    uint32_t *row = rows + t * C::kEncStride;
+                    if (!encode_block(v, a.enc_rate, dbl, [&](int i, uint32_t w) { row[i] = w; }))
+                        atomicOr(&g_device_error, kErrNonFinite);
+                }
+            }
+            named_bar_sync(1, 32 * CW);
+            if (good) {
+                const int64_t BX = a.nx / 4, BY = a.ny / 4;
+                const int64_t layer = (a.gz0 + z - 3) / 4 - a.enc_layer0;
+                const int nbv = min(NBX, (a.nx - x0) / 4);
+                for (int by = 0; by < NBY && y0 + 4 * by < a.ny; ++by) {
+                    uint32_t *dst = a.enc_out + ((layer * BY + (y0 / 4 + by)) * BX + x0 / 4) * nw;
+                    const uint32_t *src = rows + by * NBX * C::kEncStride;
+                    for (int w = t; w < nbv * nw; w += 32 * CW)
+                        dst[w] = src[(w / nw) * C::kEncStride + w % nw];
+                }
+            }
+        };
+
+        for (int z = zs; (ENC || good) && z < ze; ++z) {
             const int pn = z + R;
-            good = mbar_wait(&ufull[u_stage(pn)], u_phase(pn));
+            if (good)
+                good = mbar_wait(&ufull[u_stage(pn)], u_phase(pn));
             const uint32_t cc = ccn + (uint32_t)(z - zs);
             const int cst = (int)(cc % C::NSC);
             if (NCF > 0 && good)
                 good = mbar_wait(&cfull[cst], (cc / C::NSC) & 1);
-            if (!good)
+            if (!good) {
+                if constexpr (ENC) {
+                    enc_layer_end(z);
+                    continue;
+                }
                 break;
+            }
             const float *Pn = us + u_stage(pn) * C::kUStage;
             const float *P = us + u_stage(z) * C::kUStage;
             const int gz = a.gz0 + z;
@@ -468,6 +536,11 @@ __global__ void __launch_bounds__(32 * (CW + 1), CW == kConsumerWarps ? 2 : 3)
                             }
                         }
                     }
+                    if constexpr (ENC) {
+                        *reinterpret_cast<float2 *>(lay + (((z - zs) & 3) * C::TY + kRPT * wid + r) * kTX +
+                                                    kVX * tx) = make_float2(res[0], res[1]);
+                        continue;
+                    }
                     const int64_t o = (int64_t)z * a.plane + (int64_t)y * a.nx + x;
                     *reinterpret_cast<float2 *>(a.out + o) = make_float2(res[0], res[1]);
                     if constexpr (SCHEME == kAdjoint)
@@ -486,6 +559,8 @@ __global__ void __launch_bounds__(32 * (CW + 1), CW == kConsumerWarps ? 2 : 3)
                 if (NCF > 0)
                     mbar_arrive(&cempty[cst]);
             }
+            if constexpr (ENC)
+                enc_layer_end(z);
         }
         if (!good)
             break;
@@ -818,7 +893,7 @@ static cudaError_t make_plane_map(CUtensorMap *m, const float *base, int64_t nx,
 // that device (cudaFuncSetAttribute acts on the current device only) and how
 // many of its CTAs fit on an SM.
 constexpr int kMaxDevices = 64;
-constexpr int kStepInstances = 16;  // (radius, scheme, tile) instances of k_star_step
+constexpr int kStepInstances = 17;  // (radius, scheme, tile) instances of k_star_step + the fused encode
 
 struct DevInfo {
     int sms = 0;
@@ -849,16 +924,16 @@ static int device_sms()
     return info.sms;
 }
 
-template <int R, int SCHEME, int CW>
-constexpr int step_instance() { return (R == 4 ? 4 : 0) + SCHEME + (CW == kConsumerWarps ? 0 : 8); }
+template <int R, int SCHEME, int CW, bool ENC = false>
+constexpr int step_instance() { return ENC ? 16 : (R == 4 ? 4 : 0) + SCHEME + (CW == kConsumerWarps ? 0 : 8); }
 
 // Applies the step kernel's shared-memory opt-in on the current device (once
 // per device) and returns its CTAs per SM and the device's SM count.
-template <int R, int SCHEME, int CW>
+template <int R, int SCHEME, int CW, bool ENC = false>
 static cudaError_t step_residency(int &resident, int &sms)
 {
     using C = StepCfg<R, centre_fields<SCHEME>(), CW>;
-    static_assert(step_instance<R, SCHEME, CW>() < kStepInstances, "instance table too small");
+    static_assert(step_instance<R, SCHEME, CW, ENC>() < kStepInstances, "instance table too small");
     int dev = 0;
     cudaError_t e = current_device(dev);
     if (e != cudaSuccess)
@@ -870,10 +945,10 @@ static cudaError_t step_residency(int &resident, int &sms)
         if (e != cudaSuccess)
             return e;
     }
-    int &res = info.resident[step_instance<R, SCHEME, CW>()];
+    int &res = info.resident[step_instance<R, SCHEME, CW, ENC>()];
     if (res == 0) {
-        const size_t smem = C::smem_bytes();
-        auto kern = k_star_step<R, SCHEME, CW>;
+        const size_t smem = C::smem_bytes() + (ENC ? C::enc_bytes() : 0);
+        auto kern = k_star_step<R, SCHEME, CW, ENC>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
@@ -927,15 +1002,44 @@ static dim3 step_grid(int64_t nx, int64_t ny, int slots, StepArgs &a, int min_pl
     return dim3((unsigned)std::min<int64_t>(slots, (total + 15) / 16), 1, 1);
 }
 
-template <int R, int SCHEME, int CW = kConsumerWarps>
+// Launch geometry of the fused-encode step: always chunked, every chunk a
+// whole number of 4-plane layers (at least three), the chunk count chosen for
+// the fullest last wave of CTAs.
+static dim3 enc_grid(int64_t nx, int64_t ny, int slots, StepArgs &a, int ty)
+{
+    const int tiles_x = (int)((nx + kTX - 1) / kTX);
+    const int tiles_y = (int)((ny + ty - 1) / ty);
+    const int tiles = tiles_x * tiles_y;
+    const int layers = (a.z_hi - a.z_lo) / 4;
+    a.tiles_y = tiles_y;
+    a.ntiles = tiles;
+    int best = 1;
+    double best_eff = 0.0;
+    for (int nc = 1; nc <= std::max(1, layers / 3) && nc <= 64; ++nc) {
+        const int lc = (layers + nc - 1) / nc;
+        const int real = (layers + lc - 1) / lc;
+        const long total = (long)tiles * real;
+        const long waves = (total + slots - 1) / slots;
+        const double eff = (double)total / (double)(waves * slots);
+        if (eff > best_eff + 0.02) {
+            best_eff = eff;
+            best = nc;
+        }
+    }
+    const int lc = (layers + best - 1) / best;
+    a.zchunk = 4 * lc;
+    return dim3(tiles_x, tiles_y, (layers + lc - 1) / lc);
+}
+
+template <int R, int SCHEME, int CW = kConsumerWarps, bool ENC = false>
 static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s)
 {
     using C = StepCfg<R, centre_fields<SCHEME>(), CW>;
-    const size_t smem = C::smem_bytes();
-    auto kern = k_star_step<R, SCHEME, CW>;
+    const size_t smem = C::smem_bytes() + (ENC ? C::enc_bytes() : 0);
+    auto kern = k_star_step<R, SCHEME, CW, ENC>;
     int resident = 0, sms = 0;
     {
-        cudaError_t e = step_residency<R, SCHEME, CW>(resident, sms);
+        cudaError_t e = step_residency<R, SCHEME, CW, ENC>(resident, sms);
         if (e != cudaSuccess)
             return e;
     }
@@ -951,7 +1055,8 @@ static cudaError_t launch_step_t(const StepLaunch &L, StepArgs a, cudaStream_t s
     if (e != cudaSuccess)
         return e;
 
-    const dim3 grid = step_grid(L.nx, L.ny, sms * resident, a, 12, C::TY);
+    const dim3 grid = ENC ? enc_grid(L.nx, L.ny, sms * resident, a, C::TY)
+                          : step_grid(L.nx, L.ny, sms * resident, a, 12, C::TY);
     dim3 block(32, CW + 1, 1);
     return launch_pdl(kern, grid, block, smem, s, mc, mp, mm, m2, a);
 }
@@ -1038,8 +1143,17 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
     a.t_dev = L.t_dev;
     a.t_rel = L.t_rel;
     a.nw = L.nw;
+    a.enc_out = static_cast<uint32_t *>(L.enc_out);
+    a.enc_rate = L.enc_rate;
+    a.enc_layer0 = (int)L.enc_layer0;
     if (L.tile != 0 && L.tile != 1)
         return cudaErrorInvalidValue;
+    if (L.enc_out) {  // the fused encode: heat, radius 1, whole layers, transform codec
+        if (L.scheme != kHeat || L.radius != 1 || L.tile != 0 || L.enc_rate < 1 || L.enc_rate > 32 ||
+            (L.gz0 + L.z_lo) % 4 != 0 || (L.z_hi - L.z_lo) % 4 != 0 || L.nx % 4 != 0 || L.ny % 4 != 0)
+            return cudaErrorInvalidValue;
+        return launch_step_t<1, kHeat, kConsumerWarps, true>(L, a, s);
+    }
     const bool t8 = L.tile == 1;  // 64 x 8 tiles
     if (L.radius == 1 && L.scheme == kHeat)
         return t8 ? launch_step_t<1, kHeat, 2>(L, a, s) : launch_step_t<1, kHeat>(L, a, s);

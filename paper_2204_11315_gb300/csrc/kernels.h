@@ -45,6 +45,13 @@ struct StepLaunch {
     int64_t t_rel;
     int64_t nw;
     int tile;  // 0: 64 x 16 tiles (4 consumer warps); 1: 64 x 8 tiles (2)
+    // heat with radius 1 only: when enc_out is set, the step encodes its
+    // planes [z_lo, z_hi) (whole 4-plane layers) with the transform codec at
+    // enc_rate straight into the blocks at enc_out, whose first layer is
+    // global layer enc_layer0, instead of writing them to `out`
+    void *enc_out;
+    int enc_rate;
+    int64_t enc_layer0;
 };
 
 cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s);

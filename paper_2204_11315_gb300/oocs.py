@@ -47,7 +47,8 @@ class oocs_desc(ctypes.Structure):
                 ("device_budget", ctypes.c_uint64), ("rate_bits", ctypes.c_int32),
                 ("temporal_depth", ctypes.c_int32), ("slab_planes", ctypes.c_int32),
                 ("working_buffers", ctypes.c_int32), ("readonly_resident", ctypes.c_int32),
-                ("codec", ctypes.c_int32), ("step_fusion", ctypes.c_int32), ("step_tile", ctypes.c_int32)]
+                ("codec", ctypes.c_int32), ("step_fusion", ctypes.c_int32), ("step_tile", ctypes.c_int32),
+                ("codec_fusion", ctypes.c_int32)]
 
 
 class oocs_plan(ctypes.Structure):
@@ -206,7 +207,7 @@ def _check(status: int, ctx=None):
 
 def make_desc(nx, ny, nz, scheme, coef, device_budget, rate_bits=0, temporal_depth=0,
               slab_planes=0, working_buffers=OOCS_SWB, radius=None, readonly_resident=0,
-              codec=0, step_fusion=0, step_tile=0) -> oocs_desc:
+              codec=0, step_fusion=0, step_tile=0, codec_fusion=0) -> oocs_desc:
     coef = [float(c) for c in coef]
     d = oocs_desc()
     d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
@@ -223,6 +224,7 @@ def make_desc(nx, ny, nz, scheme, coef, device_budget, rate_bits=0, temporal_dep
     d.codec = int(codec)
     d.step_fusion = int(step_fusion)
     d.step_tile = int(step_tile)
+    d.codec_fusion = int(codec_fusion)
     return d
 
 

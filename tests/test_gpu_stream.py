@@ -280,3 +280,51 @@ def test_heat_fused_step_pairs_bitexact(P, shape, T, k, rate):
     if rate == 0:
         inc = incore(P, heat_desc(P, shape, rate=0, k=k, T=T), u0, 2 * k + 1)
         assert np.array_equal(ref[0].view(np.uint32), inc.view(np.uint32))
+
+
+@pytest.mark.parametrize("shape,T,k,rate,wb", [((64, 200, 264), 24, 4, 16, 1), ((96, 72, 136), 32, 3, 8, 1),
+                                               ((40, 36, 52), 64, 1, 16, 1), ((128, 128, 128), 32, 4, 32, 1),
+                                               ((64, 52, 68), 16, 2, 12, 3)])
+def test_heat_fused_encode_bitexact(P, shape, T, k, rate, wb):
+    """The last step of each visit encoding its layers in its epilogue
+    (codec_fusion) writes the same store bytes, and decodes to the same field,
+    bit for bit, as the separate encode kernel: tiles ragged in x and y, one
+    or several layers per chunk, depths 1 to 4, rates 8 to 32, several slabs,
+    one or three working buffers; one kernel fewer per visit."""
+    u0 = synthetic.uniform_field(shape, 23)
+    ref = None
+    for fusion in (0, 1):
+        nz, ny, nx = shape
+        desc = P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), 8 << 30, rate_bits=rate,
+                           temporal_depth=k, slab_planes=T, working_buffers=wb, codec_fusion=fusion)
+        got, _, stores, stats, plan = streamed(P, desc, u0, 2 * k + 1)
+        if ref is None:
+            ref = (got, stores, stats)
+        else:
+            assert np.array_equal(stores[0], ref[1][0])
+            assert np.array_equal(got.view(np.uint32), ref[0].view(np.uint32))
+            assert stats["store"]["units"] == ref[2]["store"]["units"]
+            visits = stats["slabs_done"]
+            assert stats["kernel_launches"] == ref[2]["kernel_launches"] - visits
+
+
+def test_fused_encode_flags_nonfinite_results(P):
+    """A field whose step produces an infinity (the neighbour sum of a point
+    inside a cube of 3e38 values overflows FP32) is reported by the fused
+    epilogue like the separate encoder: OOCS_ERR_NONFINITE at oocs_synchronize."""
+    shape = (32, 32, 32)
+    u0 = synthetic.uniform_field(shape, 3)
+    u0[15:18, 15:18, 15:18] = 3.0e38
+    nz, ny, nx = shape
+    desc = P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), 8 << 30, rate_bits=16,
+                       temporal_depth=2, slab_planes=16, codec_fusion=1)
+    st = P.OutOfCoreStencil(desc)
+    try:
+        st.compress(P.OOCS_FIELD_U, u0)
+        st.synchronize(60.0)
+        st.step(2)
+        with pytest.raises(P.OOCSError) as e:
+            st.synchronize(60.0)
+        assert e.value.status == P.OOCS_ERR_NONFINITE
+    finally:
+        st.close()

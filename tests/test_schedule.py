@@ -363,3 +363,18 @@ def test_streams_by_role_with_one_working_buffer(P):
     assert "race" in check(cut)
     classic = P.oocs_trace_schedule(_desc(P, "wave", (128, 72, 40), 16, 4, 32, 3), [12])
     assert {o["stream"] for o in classic if o["op"] == "H2D"} == {0, 1, 2}
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] == "heat" and c[2] > 0])
+def test_schedule_with_fused_encode_is_race_free(P, case):
+    """codec_fusion: the last step of a visit writes the out slot itself, so
+    the slot's copy-back by visit g-3 must be ordered before the steps; the
+    traced schedule (the last step writing the slot, no separate encode)
+    stays race-free."""
+    scheme, shape, rate, k, T, wb, calls = case
+    desc = _desc(P, scheme, shape, rate, k, T, wb)
+    desc.codec_fusion = 1
+    trace = P.oocs_trace_schedule(desc, calls)
+    assert check(trace, swb=(wb == 1)) is None
+    assert not any(o["op"] == "STORE" for o in trace)
+    assert any(o["op"] == "STEP" and any(a[0] == "OUT_SLOT" for a in o["access"]) for o in trace)
