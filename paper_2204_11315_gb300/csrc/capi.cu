@@ -807,7 +807,15 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     const int64_t pz0 = (int64_t)(s - 1) * v.T;
     const int64_t pn0 = (s <= 1) ? 0 : pz0 + v.h;
     const int64_t plane_f = d.nx * d.ny;
-    if (c->trace) {
+    // heat with codec_fusion: step 1 decodes the window itself (shared memory
+    // only), so there is no decode launch and the staging slots are released
+    // after step 1
+    const bool dec_fused = d.codec_fusion == 1 && d.scheme == OOCS_HEAT && d.radius == 1 && d.rate_bits > 0 &&
+                           d.codec == OOCS_CODEC_TRANSFORM && d.step_fusion == 0;
+    if (dec_fused) {
+        // decoded by step 1 (below): counted as loaded, with no launch of its own
+        c->stats.load.units += (uint64_t)v.fin_stream * (w1 - w0) * plane_f;
+    } else if (c->trace) {
         if (s > 0)
             trace_push(c, OOCS_OP_LOAD, sk, -1, (int64_t)g,
                        {acc(OOCS_RES_IN_SLOT, qp, w0 / 4, n0 / 4, false),
@@ -856,7 +864,8 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
                 return r;
         }
     }
-    SCHED(sched_record(c, sk, kEvDecoded + q));
+    if (!dec_fused)
+        SCHED(sched_record(c, sk, kEvDecoded + q));
 
     // 6. k_eff steps over the shrinking trapezoid
     int cur = 0, oth = 1;
@@ -885,8 +894,9 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
     const bool fuse = d.scheme == OOCS_HEAT && d.radius == 1 && d.step_fusion == 1;
     // heat: the last step encodes the interior into the out slot itself,
     // which must then be free before the steps (copied back by visit g-3)
+    // (a single step that also decodes leaves the encode to its own kernel)
     const bool enc_fused = d.codec_fusion == 1 && d.scheme == OOCS_HEAT && d.radius == 1 && d.rate_bits > 0 &&
-                           d.codec == OOCS_CODEC_TRANSFORM && !fuse;
+                           d.codec == OOCS_CODEC_TRANSFORM && !fuse && !(dec_fused && k_eff == 1);
     if (enc_fused && roles && g >= 3)
         SCHED(sched_wait(c, sk, kEvOut + q));
     uint64_t launches = 0;
@@ -946,13 +956,32 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             Ls.enc_rate = d.rate_bits;
             Ls.enc_layer0 = z0 / 4;
         }
-        if (c->trace && Ls.enc_out)  // the step that writes the out slot
+        const bool dec_here = dec_fused && j == 1;
+        if (c->trace && dec_here) {  // the step that reads the staging slots
+            if (s > 0)
+                trace_push(c, OOCS_OP_STEP, sk, -1, (int64_t)g,
+                           {acc(OOCS_RES_IN_SLOT, qp, w0 / 4, n0 / 4, false),
+                            acc(OOCS_RES_IN_SLOT, q, n0 / 4, n1 / 4, false),
+                            acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
+            else
+                trace_push(c, OOCS_OP_STEP, sk, -1, (int64_t)g,
+                           {acc(OOCS_RES_IN_SLOT, q, n0 / 4, n1 / 4, false),
+                            acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
+        } else if (c->trace && Ls.enc_out) {  // the step that writes the out slot
             trace_push(c, OOCS_OP_STEP, sk, -1, (int64_t)g,
                        {acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true), acc(OOCS_RES_OUT_SLOT, q, z0 / 4, z1 / 4, true)});
-        else if (c->trace)
+        } else if (c->trace) {
             trace_push(c, OOCS_OP_STEP, sk, -1, (int64_t)g, {acc(OOCS_RES_WORK, wb, w0 / 4, w1 / 4, true)});
-        else
+        } else if (dec_here) {
+            const bool borrow = s > 0 && n0 > w0;
+            const char *blk0 = borrow ? c->in_slot(qp, 0) + (w0 / 4 - pn0 / 4) * v.layer_bytes : nullptr;
+            CU(c, launch_decode_heat_step(Ls, blk0, borrow ? (n0 - w0) / 4 : 0, c->in_slot(q, 0), (n1 - n0) / 4,
+                                          d.rate_bits, st_k));
+        } else {
             CU(c, launch_star_step(Ls, st_k));
+        }
+        if (dec_here)
+            SCHED(sched_record(c, sk, kEvDecoded + q));
         c->stats.kernel_launches++;
         ++launches;
         step_units += (uint64_t)(hi - lo) * d.nx * d.ny;

@@ -1116,6 +1116,192 @@ cudaError_t launch_heat_step2(const StepLaunch &L, cudaStream_t s)
     return launch_pdl(k_heat_step2, grid, dim3(32, kConsumerWarps + 1, 1), kH2Smem, s, m, a);
 }
 
+// Decode fused into the first heat step of a visit (radius 1, transform
+// codec; the opt-in oocs_desc.codec_fusion): the window's codec blocks are
+// decoded into shared memory, a 4-plane layer at a time, and step 1 reads
+// them there, so the decoded window is never written to HBM.  A CTA of four
+// warps owns a 64 x 16 tile and a z chunk of step 1's planes; it keeps two
+// decoded layers of the tile plus a one-block halo (72 x 24 points: 18 x 6
+// blocks, the halo blocks decoded again by the neighbouring tiles) and
+// decodes the next layer when the plane after the current one needs it.
+// Thread (tx, w) updates the 2 x 4 points x0 + 2 tx + {0, 1}, y0 + 4 w +
+// {0..3} with the operations of k_star_step<1, kHeat> in the same order
+// (shell and out-of-grid points keep their input), so the result equals the
+// separate decode and step bit for bit.
+constexpr int kDSW = kTX + 8;      // 72: decoded columns, x0 - 4 .. x0 + 67
+constexpr int kDSH = kTY + 8;      // 24: decoded rows, y0 - 4 .. y0 + 19
+constexpr int kDSBX = kDSW / 4;    // 18 blocks across
+constexpr int kDSBY = kDSH / 4;    // 6 blocks down
+constexpr int kDSLayer = 4 * kDSH * kDSW;  // floats per decoded layer
+constexpr size_t kDSSmem = (size_t)2 * kDSLayer * 4;
+
+struct DecStepArgs {
+    float *out;                 // step 1 result, window buffer
+    const uint32_t *blk[2];     // codec blocks of window layers [0, nl0) and [nl0, nl0 + nl1)
+    int nl0, nl1;
+    int nx, ny, nz;
+    int gz0, wp;                // global plane of window plane 0; window planes
+    int z_lo, z_hi, zchunk;
+    int rate;
+    StarCoef c;
+};
+
+__global__ void __launch_bounds__(32 * kConsumerWarps, 3) k_decode_heat_step(const DecStepArgs a)
+{
+    extern __shared__ float dsm[];
+    pdl_launch_dependents();
+    pdl_wait_prior_grid();
+    const int tx = threadIdx.x, wid = threadIdx.y, t = 32 * wid + tx;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int zs = a.z_lo + blockIdx.z * a.zchunk, ze = min(zs + a.zchunk, a.z_hi);
+    const int BX = a.nx / 4, BY = a.ny / 4, nw = 2 * a.rate;
+    int held[2] = {-1, -1};  // window layer in each slot (the same in every thread)
+
+    // window layer L into slot (L & 1): block (bxi, byi) of the tile's 18 x 6
+    // by thread bxi + 18 byi; blocks outside the grid or window are zero
+    auto load_layer = [&](int L) {
+        float *dst = dsm + (L & 1) * kDSLayer;
+        __syncthreads();  // the slot's previous layer is no longer read
+        if (t < kDSBX * kDSBY) {
+            const int bxi = t % kDSBX, byi = t / kDSBX;
+            const int gbx = x0 / 4 - 1 + bxi, gby = y0 / 4 - 1 + byi;
+            float v[64];
+            if (L >= 0 && L < a.nl0 + a.nl1 && gbx >= 0 && gbx < BX && gby >= 0 && gby < BY) {
+                const int seg = L < a.nl0 ? 0 : 1;
+                const int ls = seg ? L - a.nl0 : L;
+                const uint32_t *src = a.blk[seg] + (((int64_t)ls * BY + gby) * BX + gbx) * nw;
+                decode_block(a.rate, [&](int i) -> uint32_t { return i < nw ? __ldg(src + i) : 0u; }, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 64; ++i)
+                    v[i] = 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    *reinterpret_cast<float4 *>(dst + (k * kDSH + 4 * byi + j) * kDSW + 4 * bxi) =
+                        make_float4(v[16 * k + 4 * j], v[16 * k + 4 * j + 1], v[16 * k + 4 * j + 2],
+                                    v[16 * k + 4 * j + 3]);
+        }
+        held[L & 1] = L;
+        __syncthreads();
+    };
+    // value of window plane z at tile-relative row ry, column cx (both offset by 4)
+    auto at = [&](int z, int ry, int cx) -> float {
+        if (z < 0 || z >= a.wp)
+            return 0.0f;
+        const int L = z >> 2;
+        return dsm[(L & 1) * kDSLayer + ((z & 3) * kDSH + ry) * kDSW + cx];
+    };
+
+    const int x = x0 + kVX * tx;
+    const bool x_ok = x < a.nx;
+    for (int z = zs; z < ze; ++z) {
+        // planes z - 1 .. z + 1 resident (at most two layers)
+        const int la = (z - 1) >> 2, lb = (z + 1) >> 2;
+        if (z - 1 >= 0 && held[la & 1] != la)
+            load_layer(la);
+        if (z + 1 < a.wp && held[lb & 1] != lb)
+            load_layer(lb);
+        if (held[(z >> 2) & 1] != (z >> 2))
+            load_layer(z >> 2);
+        const int gz = a.gz0 + z;
+        const bool z_interior = gz >= 1 && gz < a.nz - 1;
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r) {
+            const int y = y0 + kRPT * wid + r;
+            if (!x_ok || y >= a.ny)
+                continue;
+            const int ry = 4 + kRPT * wid + r;
+            float res[kVX];
+#pragma unroll
+            for (int c = 0; c < kVX; ++c) {
+                const int cx = 4 + kVX * tx + c;
+                const float u = at(z, ry, cx);
+                res[c] = u;
+                const bool in_x = (x + c) >= 1 && (x + c) < a.nx - 1;
+                const bool in_y = y >= 1 && y < a.ny - 1;
+                if (z_interior && in_y && in_x) {
+                    float s[2];
+                    s[0] = 0.0f;
+                    s[1] = nbr_sum(at(z, ry, cx - 1), at(z, ry, cx + 1), at(z, ry - 1, cx), at(z, ry + 1, cx),
+                                   at(z - 1, ry, cx), at(z + 1, ry, cx));
+                    res[c] = star_L<1>(a.c, u, s);
+                }
+            }
+            const int64_t o = (int64_t)z * a.nx * a.ny + (int64_t)y * a.nx + x;
+            *reinterpret_cast<float2 *>(a.out + o) = make_float2(res[0], res[1]);
+        }
+    }
+}
+
+cudaError_t launch_decode_heat_step(const StepLaunch &L, const void *blk0, int64_t nl0, const void *blk1,
+                                    int64_t nl1, int rate, cudaStream_t s)
+{
+    if (L.z_hi <= L.z_lo)
+        return cudaSuccess;
+    if (L.scheme != kHeat || L.radius != 1 || rate < 1 || rate > 32 || L.nx % 4 != 0 || L.ny % 4 != 0 ||
+        L.gz0 % 4 != 0 || L.wp != 4 * (nl0 + nl1) || (nl0 > 0 && !blk0) || (nl1 > 0 && !blk1))
+        return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t e = current_device(dev);
+    if (e != cudaSuccess)
+        return e;
+    int resident = 0, sms = 0;
+    {
+        static int res_dev[kMaxDevices] = {};
+        std::lock_guard<std::mutex> lock(g_dev_mu);
+        DevInfo &info = g_dev[dev];
+        if (info.sms == 0 && (e = cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        if (res_dev[dev] == 0) {
+            e = cudaFuncSetAttribute(k_decode_heat_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDSSmem);
+            if (e != cudaSuccess)
+                return e;
+            int n = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_decode_heat_step, 32 * kConsumerWarps, kDSSmem);
+            if (e != cudaSuccess)
+                return e;
+            if (n < 1)
+                return cudaErrorInvalidConfiguration;
+            res_dev[dev] = n;
+        }
+        resident = res_dev[dev];
+        sms = info.sms;
+    }
+    DecStepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.out = L.out;
+    a.blk[0] = static_cast<const uint32_t *>(blk0);
+    a.blk[1] = static_cast<const uint32_t *>(blk1);
+    a.nl0 = (int)nl0;
+    a.nl1 = (int)nl1;
+    a.nx = (int)L.nx;
+    a.ny = (int)L.ny;
+    a.nz = (int)L.nz;
+    a.gz0 = (int)L.gz0;
+    a.wp = (int)L.wp;
+    a.z_lo = (int)L.z_lo;
+    a.z_hi = (int)L.z_hi;
+    a.rate = rate;
+    for (int i = 0; i < 5; ++i)
+        a.c.c[i] = L.coef[i];
+    // z chunks for the fullest last wave, at least 16 planes each (a chunk
+    // decodes its planes' layers plus up to two more)
+    StepArgs g;
+    memset(&g, 0, sizeof(g));
+    g.z_lo = a.z_lo;
+    g.z_hi = a.z_hi;
+    const dim3 grid0 = step_grid(L.nx, L.ny, sms * resident, g, 16);
+    const int nplanes = a.z_hi - a.z_lo;
+    a.zchunk = g.zchunk > 0 ? g.zchunk : nplanes;
+    const dim3 grid((unsigned)g.ntiles / (unsigned)g.tiles_y, (unsigned)g.tiles_y,
+                    (unsigned)((nplanes + a.zchunk - 1) / a.zchunk));
+    (void)grid0;
+    return launch_pdl(k_decode_heat_step, grid, dim3(32, kConsumerWarps, 1), kDSSmem, s, a);
+}
+
 cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s)
 {
     if (L.z_hi <= L.z_lo)

@@ -62,6 +62,15 @@ cudaError_t launch_star_step(const StepLaunch &L, cudaStream_t s);
 // launch_star_step calls.
 cudaError_t launch_heat_step2(const StepLaunch &L, cudaStream_t s);
 
+// Decode fused into the first heat step of a visit (radius 1, transform codec
+// at `rate`): L describes step 1 (its planes [z_lo, z_hi) written to L.out);
+// window layers [0, nl0) are decoded from the codec blocks at blk0 and
+// [nl0, nl0 + nl1) from those at blk1 (wp = 4 (nl0 + nl1)), into shared
+// memory only.  Bit-identical to a decode into the window and one
+// launch_star_step.
+cudaError_t launch_decode_heat_step(const StepLaunch &L, const void *blk0, int64_t nl0, const void *blk1,
+                                    int64_t nl1, int rate, cudaStream_t s);
+
 // out = a * b elementwise (FP32, one rounding each); n a multiple of 4.
 cudaError_t launch_product(float *out, const float *a, const float *b, int64_t n, cudaStream_t s);
 

@@ -285,12 +285,14 @@ def test_heat_fused_step_pairs_bitexact(P, shape, T, k, rate):
 @pytest.mark.parametrize("shape,T,k,rate,wb", [((64, 200, 264), 24, 4, 16, 1), ((96, 72, 136), 32, 3, 8, 1),
                                                ((40, 36, 52), 64, 1, 16, 1), ((128, 128, 128), 32, 4, 32, 1),
                                                ((64, 52, 68), 16, 2, 12, 3)])
-def test_heat_fused_encode_bitexact(P, shape, T, k, rate, wb):
-    """The last step of each visit encoding its layers in its epilogue
-    (codec_fusion) writes the same store bytes, and decodes to the same field,
-    bit for bit, as the separate encode kernel: tiles ragged in x and y, one
-    or several layers per chunk, depths 1 to 4, rates 8 to 32, several slabs,
-    one or three working buffers; one kernel fewer per visit."""
+def test_heat_fused_codec_bitexact(P, shape, T, k, rate, wb):
+    """The codec fused into the steps (codec_fusion: step 1 decodes the window
+    in shared memory, the last step encodes its layers in its epilogue)
+    writes the same store bytes, and decodes to the same field, bit for bit,
+    as the separate decode and encode kernels: tiles ragged in x and y, one
+    or several layers per chunk, depths 1 to 4 (a visit of one step keeps its
+    encode kernel), rates 8 to 32, several slabs, one or three working
+    buffers."""
     u0 = synthetic.uniform_field(shape, 23)
     ref = None
     for fusion in (0, 1):
@@ -304,8 +306,10 @@ def test_heat_fused_encode_bitexact(P, shape, T, k, rate, wb):
             assert np.array_equal(stores[0], ref[1][0])
             assert np.array_equal(got.view(np.uint32), ref[0].view(np.uint32))
             assert stats["store"]["units"] == ref[2]["store"]["units"]
+            assert stats["load"]["units"] == ref[2]["load"]["units"]
             visits = stats["slabs_done"]
-            assert stats["kernel_launches"] == ref[2]["kernel_launches"] - visits
+            one_step = plan.num_slabs * (3 if k == 1 else 1)  # 2k + 1 steps: visits of a single step
+            assert stats["kernel_launches"] == ref[2]["kernel_launches"] - (2 * visits - one_step)
 
 
 def test_fused_encode_flags_nonfinite_results(P):

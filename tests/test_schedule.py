@@ -366,15 +366,20 @@ def test_streams_by_role_with_one_working_buffer(P):
 
 
 @pytest.mark.parametrize("case", [c for c in CASES if c[0] == "heat" and c[2] > 0])
-def test_schedule_with_fused_encode_is_race_free(P, case):
-    """codec_fusion: the last step of a visit writes the out slot itself, so
-    the slot's copy-back by visit g-3 must be ordered before the steps; the
-    traced schedule (the last step writing the slot, no separate encode)
-    stays race-free."""
+def test_schedule_with_fused_codec_is_race_free(P, case):
+    """codec_fusion: step 1 of a visit reads the staging slots itself (the
+    slots are released after it) and the last step writes the out slot
+    itself (the slot's copy-back by visit g-3 is ordered before the steps);
+    the traced schedule stays race-free, with no decode launch and, where a
+    visit has two or more steps, no encode launch."""
     scheme, shape, rate, k, T, wb, calls = case
     desc = _desc(P, scheme, shape, rate, k, T, wb)
     desc.codec_fusion = 1
     trace = P.oocs_trace_schedule(desc, calls)
     assert check(trace, swb=(wb == 1)) is None
-    assert not any(o["op"] == "STORE" for o in trace)
-    assert any(o["op"] == "STEP" and any(a[0] == "OUT_SLOT" for a in o["access"]) for o in trace)
+    assert not any(o["op"] == "LOAD" for o in trace)
+    assert any(o["op"] == "STEP" and any(a[0] == "IN_SLOT" for a in o["access"]) for o in trace)
+    if k > 1:
+        assert any(o["op"] == "STEP" and any(a[0] == "OUT_SLOT" for a in o["access"]) for o in trace)
+        if all(c % k == 0 for c in calls):
+            assert not any(o["op"] == "STORE" for o in trace)
