@@ -130,14 +130,16 @@ typedef struct {
                                   * tiles, for planes too small to fill the GPU).  Results
                                   * are bit-identical; the autotuner searches it.            */
     int32_t codec_fusion;        /* HEAT with radius 1 and the transform codec at rate > 0:
-                                  * 0 = the last step of a slab visit writes the interior to
-                                  * the working buffer and a separate kernel encodes it (the
-                                  * default); 1 = the last step encodes each 4-plane layer
-                                  * of its results in its epilogue straight into the output
-                                  * slot (Sec. 4.2: compression on the way out of the
-                                  * kernel), so the interior never goes back to HBM as FP32.
-                                  * Byte-identical stores either way; measured slower on
-                                  * GB300.  Requires step_fusion = 0.  Ignored otherwise.    */
+                                  * 0 = separate decode and encode kernels around the steps
+                                  * of a slab visit (the default); 1 = the codec in the steps
+                                  * (Sec. 4.2: decompression on the way into the kernel,
+                                  * compression on the way out): step 1 decodes the window's
+                                  * blocks into shared memory and the last step encodes each
+                                  * 4-plane layer of its results in its epilogue straight
+                                  * into the output slot (a visit of one step keeps its
+                                  * encode kernel), so the window never goes through HBM as
+                                  * FP32.  Byte-identical stores either way; measured slower
+                                  * on GB300.  Requires step_fusion = 0.  Ignored otherwise. */
 } oocs_desc;
 
 /* Resolved plan (Sec. 3.1 chunking and temporal blocking; Sec. 6.2 memory model). */
