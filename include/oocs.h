@@ -47,7 +47,7 @@ typedef enum {
     OOCS_ERR_CUDA = 4,         /* a CUDA call failed (sticky)                             */
     OOCS_ERR_TIMEOUT = 5,      /* oocs_synchronize ran out of time (sticky)               */
     OOCS_ERR_STATE = 6,        /* call not valid in the context's current state           */
-    OOCS_ERR_UNSUPPORTED = 7,  /* valid request this build does not implement             */
+    OOCS_ERR_UNSUPPORTED = 7,  /* valid request the library does not implement            */
     OOCS_ERR_NONFINITE = 8     /* the codec was handed an Inf or NaN (sticky); see below  */
 } oocs_status;
 

@@ -7,9 +7,9 @@ NCCL send/recv), advances its window [z0 - h, z1 + h) by k steps and keeps
 [z0, z1): the temporal blocking of Sec. 3.1 applied across ranks.  The
 gathered result must equal the unpartitioned oracle run bit for bit (FP64,
 same operations per point).  Heat over three ranks (a middle rank with two
-neighbours), wave (two levels and the read-only model) over two.  Every box
-of this build has one GPU, so the library itself runs replicas only; this
-pins the exchange that a multi-GPU sweep would need.
+neighbours), wave (two levels and the read-only model) over two.  The
+library itself runs one sweep per GPU (replicas); this pins the exchange
+that a sweep sharded over GPUs would need.
 """
 import os
 import socket
