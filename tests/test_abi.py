@@ -110,7 +110,9 @@ def test_auto_slab_thickness_from_budget(P):
 
 @pytest.mark.parametrize("field,value", [("nx", 130), ("nz", 0), ("scheme", 5), ("radius", 2),
                                          ("rate_bits", 33), ("slab_planes", 6),
-                                         ("working_buffers", 2), ("temporal_depth", -1)])
+                                         ("working_buffers", 2), ("temporal_depth", -1),
+                                         ("step_tile", 2), ("step_fusion", 3), ("codec_fusion", 2),
+                                         ("codec", 2)])
 def test_invalid_descriptions(P, field, value):
     d = _c1(P)
     setattr(d, field, value)
@@ -155,3 +157,18 @@ def test_stats_binding_layout(P):
     assert d["h2d_bytes"] == 0 and d["last_step_ms"] == 0.0
     e = P.oocs.oocs_timeline_entry()
     assert [f for f, _ in e._fields_] == ["cls", "stream", "visit", "start_ms", "end_ms"]
+
+
+def test_codec_fusion_excludes_step_pairs(P):
+    """The codec fused into the steps and the fused step pairs are exclusive;
+    each alone is a valid plan with the same workspace as the unfused one."""
+    d = _c1(P)
+    base = P.oocs_query(d).workspace_bytes
+    d.codec_fusion = 1
+    assert P.oocs_query(d).workspace_bytes == base
+    d.step_fusion = 1
+    with pytest.raises(P.OOCSError) as e:
+        P.oocs_query(d)
+    assert e.value.status == 1 and "codec_fusion" in str(e.value)
+    d.codec_fusion = 0
+    assert P.oocs_query(d).workspace_bytes == base
