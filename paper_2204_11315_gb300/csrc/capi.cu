@@ -951,10 +951,12 @@ oocs_status enqueue_slab(oocs_ctx *c, int s, int k_eff, int64_t t)
             Ls.w = c->w[tstep];
         }
         Ls.enc_out = nullptr;
-        if (enc_fused && j == k_eff) {
+        Ls.tile = d.step_tile;
+        if (enc_fused && j == k_eff) {  // (the fused encode is built for the 64 x 16 tile)
             Ls.enc_out = c->out_slot(q, 0);
             Ls.enc_rate = d.rate_bits;
             Ls.enc_layer0 = z0 / 4;
+            Ls.tile = 0;
         }
         const bool dec_here = dec_fused && j == 1;
         if (c->trace && dec_here) {  // the step that reads the staging slots

@@ -282,10 +282,13 @@ def test_heat_fused_step_pairs_bitexact(P, shape, T, k, rate):
         assert np.array_equal(ref[0].view(np.uint32), inc.view(np.uint32))
 
 
-@pytest.mark.parametrize("shape,T,k,rate,wb", [((64, 200, 264), 24, 4, 16, 1), ((96, 72, 136), 32, 3, 8, 1),
-                                               ((40, 36, 52), 64, 1, 16, 1), ((128, 128, 128), 32, 4, 32, 1),
-                                               ((64, 52, 68), 16, 2, 12, 3)])
-def test_heat_fused_codec_bitexact(P, shape, T, k, rate, wb):
+@pytest.mark.parametrize("shape,T,k,rate,wb,tile", [((64, 200, 264), 24, 4, 16, 1, 0),
+                                                    ((96, 72, 136), 32, 3, 8, 1, 0),
+                                                    ((40, 36, 52), 64, 1, 16, 1, 0),
+                                                    ((128, 128, 128), 32, 4, 32, 1, 0),
+                                                    ((64, 52, 68), 16, 2, 12, 3, 0),
+                                                    ((64, 52, 68), 16, 3, 16, 1, 1)])
+def test_heat_fused_codec_bitexact(P, shape, T, k, rate, wb, tile):
     """The codec fused into the steps (codec_fusion: step 1 decodes the window
     in shared memory, the last step encodes its layers in its epilogue)
     writes the same store bytes, and decodes to the same field, bit for bit,
@@ -298,7 +301,8 @@ def test_heat_fused_codec_bitexact(P, shape, T, k, rate, wb):
     for fusion in (0, 1):
         nz, ny, nx = shape
         desc = P.make_desc(nx, ny, nz, P.OOCS_HEAT, synthetic.heat_star_coef(0.1), 8 << 30, rate_bits=rate,
-                           temporal_depth=k, slab_planes=T, working_buffers=wb, codec_fusion=fusion)
+                           temporal_depth=k, slab_planes=T, working_buffers=wb, codec_fusion=fusion,
+                           step_tile=tile)
         got, _, stores, stats, plan = streamed(P, desc, u0, 2 * k + 1)
         if ref is None:
             ref = (got, stores, stats)
